@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of SDC-resilient block-wise SZ compression + decompression on GB300.
+
+One step = compress one field and decompress it again (the whole hot path: range and input
+checksums, prediction/quantization with the ABFT checks, Huffman code, encoding, decoding
+with verification). Default workload: a 512^3 float32 field (8 sinusoids + noise + 1%
+lognormal spikes, seeded), value-range relative bound 1e-3, 6^3 blocks, ABFT on.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank runs an independent replica on its
+own GPU (the blocks are independent; no collective on the data path) and the timing is the
+maximum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress/decompress GB/s at rel eb 1e-3 (% HBM roofline), ABFT overhead %, p99 latency"
+WORKLOADS = {
+    "512cube": dict(shape=(512, 512, 512), block=6, spikes=0.01, seed=2010),
+    "64cube": dict(shape=(64, 64, 64), block=6, spikes=0.0, seed=1),
+}
+REL_EB = 1e-3
+
+# DRAM traffic per launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by the kernel source file's hash at capture time; a changed kernel reports null.
+NCU_TRAFFIC = {}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash(name):
+    p = os.path.join(ROOT, "paper_2010_03144_gb300", "csrc", name)
+    try:
+        return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        if self.uuid:
+            mine = [r for r in rows if self.uuid in r[0]]
+            rows = mine or rows
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[3 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _reduce_max(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def algorithmic_bytes(N, s, nb, n_unpred, n_reg, stream_bytes, abft):
+    """Bytes each kernel must move (inputs read once, outputs written once)."""
+    meta_in = 16 + 16 + 8 + 1 if abft else 16 + 8 + 1
+    return {
+        "prep": N * s + nb * (meta_in),
+        "predict": N * s + 2 * N + n_unpred * s + nb * (meta_in + (25 if abft else 1)) + n_reg * 4 * s,
+        "codebook": 65536 * (8 + 4),
+        "encode": 2 * N + n_unpred * s + nb * ((25 if abft else 1) + 1) + n_reg * 4 * s + stream_bytes,
+        "decode": stream_bytes + N * s,
+    }
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2010_03144_gb300 as sz
+    from paper_2010_03144_gb300 import build as libbuild
+    import synth
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(device)
+    if rank == 0 or world > 1:
+        libbuild.build()
+    _barrier(world)
+    sz.lib()
+
+    wl = WORKLOADS[args.workload]
+    shape, block = wl["shape"], wl["block"]
+    x = synth.sinusoid_field(shape, wl["seed"] + rank, spikes=wl["spikes"])
+    N, s_dt = x.size, 4
+    d = torch.from_numpy(x).to(device)
+    p_on = sz.make_params(shape, np.float32, REL_EB, block=block, abft=True)
+    p_off = sz.make_params(shape, np.float32, REL_EB, block=block, abft=False)
+    ws_on = sz.Workspace(p_on, device)
+    ws_off = sz.Workspace(p_off, device)
+    out = torch.empty(shape, dtype=torch.float32, device=device)
+    dws = torch.empty(sz.decompress_workspace_size(), dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step(ws, p, stage_acc=None):
+        nbytes, ms = sz.compress_traced(d, p, ws)
+        dms = sz.decompress_traced(ws.out, out, dws)
+        if stage_acc is not None:
+            for k, v in zip(("reset", "prep", "predict", "codebook", "encode"), ms):
+                stage_acc[k] = stage_acc.get(k, 0.0) + v
+            stage_acc["decode"] = stage_acc.get("decode", 0.0) + dms
+        return nbytes
+
+    # reports of one run for counts and the compression ratio
+    s_t, rep = sz.compress(d, REL_EB, block=block, workspace=ws_on)
+    stream_bytes = int(rep["compressed_bytes"])
+    rc, y, st, rep_d = sz.decompress(s_t, out=out, ws=dws)
+    assert rc == 0
+    assert float((y - d).abs().max()) <= rep["eb_abs"]
+
+    def timed(ws, p, steps, warmup, stage_acc=None):
+        for _ in range(warmup):
+            step(ws, p)
+        torch.cuda.synchronize()
+        _barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(ws, p, stage_acc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(device).uuid)
+    except Exception:
+        pass
+    clk = ClockSampler(uuid)
+    clk.start()
+    stages = {}
+    ms_on = timed(ws_on, p_on, args.steps, args.warmup, stages)
+    clocks = clk.stop()
+    ms_off = timed(ws_off, p_off, args.steps, args.warmup)
+    ms_on_max = _reduce_max(ms_on, world, device)
+    ms_off_max = _reduce_max(ms_off, world, device)
+    per_step = ms_on_max / args.steps
+    gb = N * s_dt / 1e9
+    value = world * gb * args.steps / (ms_on_max / 1e3)
+
+    # per-kernel averages over the timed region, roofline of the dominant kernel
+    avg = {k: v / args.steps for k, v in stages.items()}
+    comp_ms = sum(avg[k] for k in ("reset", "prep", "predict", "codebook", "encode"))
+    dec_ms = avg["decode"]
+    alg = algorithmic_bytes(N, s_dt, rep["blocks"], rep["unpredictable_points"], rep["regression_blocks"],
+                            stream_bytes, True)
+    dom = max(("prep", "predict", "encode", "decode", "codebook"), key=lambda k: avg[k])
+    peak, peak_kind = _peaks()
+    achieved = alg[dom] / (avg[dom] / 1e3) / 1e9
+    src = {"prep": "k_prep.cu", "predict": "k_predict.cu", "encode": "k_encode.cu", "decode": "k_decode.cu",
+           "codebook": "k_codebook.cu"}[dom]
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash(src) else None
+    kernels = {k: {"ms": round(avg[k], 4), "GB/s": round(alg[k] / (avg[k] / 1e3) / 1e9, 1) if avg[k] > 0 else None,
+                   "frac": round(alg[k] / (avg[k] / 1e3) / 1e9 / peak, 3) if avg[k] > 0 else None}
+               for k in ("prep", "predict", "codebook", "encode", "decode")}
+
+    # end to end through the public API with host buffers: H2D field, compress, D2H stream,
+    # H2D stream, decompress, D2H field
+    h_field = torch.from_numpy(x).pin_memory()
+    h_stream = torch.empty(ws_on.cap, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(shape, dtype=torch.float32).pin_memory()
+    d_in = torch.empty_like(d)
+    d_s = torch.empty(ws_on.cap, dtype=torch.uint8, device=device)
+
+    def e2e_step():
+        d_in.copy_(h_field, non_blocking=True)
+        s_out, r = sz.compress(d_in, REL_EB, block=block, workspace=ws_on)
+        n = int(r["compressed_bytes"])
+        h_stream[:n].copy_(s_out, non_blocking=True)
+        d_s[:n].copy_(h_stream[:n], non_blocking=True)
+        sz.decompress(d_s[:n], out=out, ws=dws, report=False)
+        h_out.copy_(out, non_blocking=True)
+        return n
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        n_s = e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = _reduce_max(e0.elapsed_time(e1), world, device)
+    e2e_value = world * gb * args.steps / (e2e_ms / 1e3)
+
+    result = None
+    if rank == 0:
+        cpu = cpu_baseline(args) if world == 1 and not args.no_cpu else None
+        result = {
+            "metric": METRIC,
+            "value": round(value, 2),
+            "unit": "GB/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(per_step, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload} float32 {shape} sinusoids+noise+{wl['spikes']:.0%} spikes, "
+                                   f"rel eb {REL_EB}, block {block}^3, ABFT on; one step = compress + decompress",
+                       "field_bytes": N * s_dt, "compressed_bytes": stream_bytes,
+                       "compression_ratio": round(N * s_dt / stream_bytes, 3),
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"{world} independent replicas"},
+            "compress_gbs": round(gb / (comp_ms / 1e3), 2),
+            "decompress_gbs": round(gb / (dec_ms / 1e3), 2),
+            "abft_overhead_pct": round(100.0 * (ms_on_max - ms_off_max) / ms_off_max, 2),
+            "abft_off_value": round(world * gb * args.steps / (ms_off_max / 1e3), 2),
+            "p99_latency_ms": None,
+            "kernels": kernels,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "algorithmic_bytes": alg[dom]},
+            "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": N * s_dt + n_s,
+                    "d2h_bytes_per_step": n_s + N * s_dt},
+            "gpu_launches": 5 * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result
+
+
+def _oracle_sample(args):
+    import synth
+    wl = WORKLOADS[args.workload]
+    shape = wl["shape"]
+    # a slab of the same field recipe: the first quarter along the slowest axis
+    slab = (max(1, shape[0] // 4),) + tuple(shape[1:])
+    x = synth.sinusoid_field(slab, wl["seed"], spikes=wl["spikes"])
+    return x, slab
+
+
+def cpu_baseline(args):
+    """The oracle as it stands (single-threaded C++), one compress + decompress of a slab."""
+    import oracle
+    x, slab = _oracle_sample(args)
+    oracle.lib()
+    t0 = time.perf_counter()
+    s, rep = oracle.compress(x, REL_EB, block=WORKLOADS[args.workload]["block"])
+    rc, y, st, _ = oracle.decompress(s)
+    dt = time.perf_counter() - t0
+    return {"value": round(x.nbytes / 1e9 / dt, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one compress+decompress of a {slab} slab of the same recipe ({x.nbytes / 1e6:.0f} MB), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on a bounded slab per step, on rank 0."""
+    world, rank, local = _dist()
+    if rank != 0:
+        return None
+    import oracle
+    x, slab = _oracle_sample(args)
+    oracle.lib()
+    block = WORKLOADS[args.workload]["block"]
+    for _ in range(args.warmup):
+        oracle.compress(x[:8], REL_EB, block=block)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s, rep = oracle.compress(x, REL_EB, block=block)
+        oracle.decompress(s)
+    dt = time.perf_counter() - t0
+    value = x.nbytes * args.steps / 1e9 / dt
+    res = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{args.workload} recipe, slab {slab} per step, rel eb {REL_EB}, block {block}^3, "
+                                  f"ABFT on; one step = compress + decompress"},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{slab} slab per step"},
+           "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="512cube")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * sdcsz — SDC-resilient, error-bounded lossy compression of float32/float64 fields on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The library implements the independent-block SZ compressor with algorithm-based fault
+ * tolerance of "SDC Resilient Error-bounded Lossy Compressor" (Li, Di, Zhao, Liang, Chen,
+ * Cappello, arXiv 2010.03144): per-block Lorenzo or linear-regression prediction (Sec. 3.1),
+ * linear-scaling quantization with an unpredictable-value fallback, one Huffman code for the
+ * whole field with every block encoded on its own (Sec. 5.1), and the checks of Algorithm 1
+ * (input checksums sum_in/isum_in, duplicated prediction and reconstruction, code checksums
+ * sum_q/isum_q, reconstructed-data checksum sum_dc) and Algorithm 2 (block verification and
+ * re-execution) fused into the GPU passes. The lossless Zstd stage of the paper is not part of
+ * this library.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are CUDA device pointers; h_* and plain struct pointers are host
+ *    pointers. The caller owns every buffer; the library allocates no device memory.
+ *  - `stream` is a cudaStream_t (passed as void* so this header needs no CUDA headers); all
+ *    device work is enqueued on it. NULL means the legacy default stream.
+ *  - Fields are dense, C order (last dimension fastest), dims[0] the slowest.
+ *  - Return value 0 = success; a negative SDCSZ_E* code otherwise. Soft errors that were
+ *    detected and corrected still return 0 and are counted in the report.
+ *  - A call returns after enqueueing its work unless it has a host output to fill
+ *    (`out_bytes`, `report`); then it synchronizes `stream` before returning. Errors found on
+ *    the device (invalid error bound, capacity, corrupt stream, spin timeout) are returned only
+ *    by calls that synchronize; the stream header and the per-block status record them too.
+ *  - Calls on different streams must use different workspaces and outputs.
+ */
+#ifndef SDCSZ_H
+#define SDCSZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SDCSZ_VERSION 1
+
+/* Error codes. */
+#define SDCSZ_OK 0
+#define SDCSZ_EINVAL (-1)    /* bad argument: dims, block, bins, eb <= 0 / non-finite, ... */
+#define SDCSZ_ECAPACITY (-2) /* output or workspace buffer too small */
+#define SDCSZ_EFORMAT (-3)   /* not a valid sdcsz stream (magic, version, sizes, code table) */
+#define SDCSZ_ESDC (-4)      /* >= 1 block failed verification twice (Alg. 2: "SDC in
+                                compression"); the block status array names those blocks,
+                                every other block is decompressed normally */
+#define SDCSZ_ETIMEOUT (-5)  /* a bounded device wait gave up (never expected) */
+#define SDCSZ_ECUDA (-6)     /* a CUDA runtime call failed */
+
+typedef enum { SDCSZ_F32 = 0, SDCSZ_F64 = 1 } sdcsz_dtype;
+typedef enum { SDCSZ_EB_ABS = 0, SDCSZ_EB_REL = 1 } sdcsz_eb_mode;
+typedef enum { SDCSZ_PRED_AUTO = 0, SDCSZ_PRED_LORENZO = 1, SDCSZ_PRED_REGRESSION = 2 } sdcsz_predictor;
+
+/*
+ * The compression problem as the paper states it (Alg. 1 input: original data ori[] and
+ * error bound e).
+ *  ndim        1, 2 or 3.
+ *  dtype       sdcsz_dtype.
+ *  dims        dims[0..ndim-1], slowest first; each <= 2^40, product <= 2^40. A zero extent
+ *              gives an empty field.
+ *  block       block edge per dimension (Sec. 5.1 independent blocks), 0 = default
+ *              (3D 6, 2D 12, 1D 128). Limits: 3D 2..16, 2D 2..64, 1D 2..4096, and at most
+ *              4096 points per block. Edge blocks are cut to the field.
+ *  eb_mode/eb  absolute bound, or value-range relative: eb_abs = eb * (max - min) over the
+ *              finite values, rounded to dtype (falls back to eb when the range is 0).
+ *  quant_bins  number of quantization bins, even, 2..65536; 0 = 65536.
+ *  abft        1 = fault-tolerant mode (the paper's ftrsz), 0 = independent blocks without
+ *              checks (rsz).
+ *  predictor   sdcsz_predictor; AUTO selects per block by estimated error (Alg. 1 l. 6-8).
+ */
+typedef struct {
+  uint32_t ndim;
+  uint32_t dtype;
+  uint64_t dims[3];
+  uint32_t block[3];
+  uint32_t eb_mode;
+  double eb;
+  uint32_t quant_bins;
+  uint32_t abft;
+  uint32_t predictor;
+  uint32_t reserved; /* must be 0 */
+} sdcsz_params;
+
+/* Counters of one call (Alg. 2 lines 17 and 19 report to the user). */
+typedef struct {
+  uint64_t blocks;
+  uint64_t regression_blocks;
+  uint64_t unpredictable_points;
+  uint64_t compressed_bytes;
+  uint64_t input_corrected;         /* input words repaired with sum_in/isum_in (Alg. 1 l. 11) */
+  uint64_t codes_corrected;         /* codes repaired with sum_q/isum_q (Alg. 1 l. 35) */
+  uint64_t dup_mismatch_corrected;  /* duplicated prediction/reconstruction disagreed (l. 18, 25) */
+  uint64_t decomp_reexec_corrected; /* blocks fixed by re-execution (Alg. 2 l. 14-17) */
+  uint64_t uncorrectable_blocks;    /* detected, not correctable (outside the single-error model) */
+  uint64_t bound_violations;        /* verify with an original: points with |x - x'| > eb */
+  double eb_abs;                    /* the absolute bound used */
+  double max_abs_err;               /* verify with an original: max |x - x'| over finite points */
+} sdcsz_report;
+
+/* Block status values written by decompress/verify. */
+#define SDCSZ_BLOCK_OK 0
+#define SDCSZ_BLOCK_CORRECTED 1     /* checksum mismatch fixed by re-execution (Alg. 2 l. 17) */
+#define SDCSZ_BLOCK_SDC 2           /* checksum mismatch twice (Alg. 2 l. 19) */
+#define SDCSZ_BLOCK_BAD 3           /* undecodable block data */
+
+/* Upper bound on the stream size for `p` (every point unpredictable with a 24-bit code). */
+int sdcsz_compress_bound(const sdcsz_params* p, size_t* max_bytes);
+
+/* Device workspace bytes needed by sdcsz_compress for `p` (codes, per-block checksums,
+ * histogram, codebook, scan state). 256-byte aligned base required. */
+int sdcsz_workspace_size(const sdcsz_params* p, size_t* bytes);
+
+/* Device workspace bytes needed by sdcsz_decompress and sdcsz_verify (any stream). */
+size_t sdcsz_decompress_workspace_size(void);
+
+/*
+ * Compress one field (Alg. 1 without the Zstd stage).
+ *  d_field     device pointer to the field (dtype, dims from p). Read only.
+ *  d_out       device buffer of out_cap bytes for the stream (size it with
+ *              sdcsz_compress_bound; a smaller buffer returns SDCSZ_ECAPACITY if it overflows).
+ *  out_bytes   host, nullable: receives the stream size (synchronizes).
+ *  d_ws        device workspace of ws_bytes >= sdcsz_workspace_size(p), 256-byte aligned.
+ *  report      host, nullable: receives the counters (synchronizes).
+ * The stream is self-describing: its header carries dims, dtype, block, bins, abft and eb.
+ */
+int sdcsz_compress(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap, size_t* out_bytes,
+                   void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream);
+
+/*
+ * Decompress a stream (Alg. 2): Huffman decoding and Lorenzo/regression reconstruction of
+ * every block, then (abft streams) each block's checksum is compared with sum_dc and a
+ * mismatching block is decompressed once more from its compressed bytes.
+ *  d_stream/nbytes  device pointer to the stream and its length.
+ *  d_field     device buffer of field_bytes >= points * sizeof(dtype).
+ *  d_block_status   device, nullable: one SDCSZ_BLOCK_* byte per block.
+ * Returns SDCSZ_ESDC when a block failed twice (when it synchronizes).
+ */
+int sdcsz_decompress(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes,
+                     uint8_t* d_block_status, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream);
+
+/*
+ * Verify a stream without writing a field: the decompression and checksum checks of Alg. 2.
+ * With d_original (device, nullable) also checks every point against the bound
+ * (|x - x'| <= eb_abs; non-finite points must match bit for bit) and reports max |x - x'|.
+ */
+int sdcsz_verify(const void* d_stream, size_t nbytes, const void* d_original, uint8_t* d_block_status,
+                 void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream);
+
+/*
+ * Profiling variants: the same work as sdcsz_compress / sdcsz_decompress, with CUDA events
+ * recorded on `stream` between the stages; the call synchronizes and writes the elapsed
+ * milliseconds of each stage to stage_ms (host). Compression has 5 stages: buffer reset,
+ * K1 preparation (range, sum_in/isum_in, regression, estimates), K2 prediction/quantization,
+ * K3 Huffman code, K4 encoding. Decompression has 1 stage: K5.
+ */
+int sdcsz_compress_traced(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap, size_t* out_bytes,
+                          void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream, float* stage_ms);
+int sdcsz_decompress_traced(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes,
+                            uint8_t* d_block_status, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,
+                            float* stage_ms);
+
+/* Parse a stream header held in HOST memory (the first 128 bytes suffice for dims and
+ * dtype; total_bytes is the full stream length). */
+int sdcsz_read_header(const void* h_stream, size_t nbytes, sdcsz_params* out, uint64_t* total_bytes);
+
+/* Static string for an error code. */
+const char* sdcsz_strerror(int code);
+
+/*
+ * Soft-error simulation for tests (the paper's evaluation mode A, Sec. 6.1.2, and the
+ * transient errors of Sec. 6.4.3-6.4.4). One record flips one bit:
+ *  SDCSZ_SITE_INPUT  index = global 32-bit word of the field (float64 = 2 words, low
+ *                    first); flipped in the caller's field buffer after the input checksums
+ *                    are taken. The flip stays in d_field after the call.
+ *  SDCSZ_SITE_CODE   block, index = point in the block; the stored quantization code,
+ *                    after its checksums are taken, before encoding.
+ *  SDCSZ_SITE_COEF   block, index = coefficient; after predictor selection, before use.
+ *  SDCSZ_SITE_PRED   block, index = point; the first evaluation of the prediction.
+ *  SDCSZ_SITE_RECON  block, index = point; the first evaluation of the reconstruction.
+ *  SDCSZ_SITE_DECOMP block, index = point; the reconstructed value in the first decompression.
+ * d_flips is a device array of n records sorted by (block, site, index).
+ */
+#define SDCSZ_SITE_INPUT 1
+#define SDCSZ_SITE_CODE 2
+#define SDCSZ_SITE_COEF 3
+#define SDCSZ_SITE_PRED 4
+#define SDCSZ_SITE_RECON 5
+#define SDCSZ_SITE_DECOMP 6
+typedef struct {
+  uint32_t site;
+  uint32_t bit;
+  uint64_t block;
+  uint64_t index;
+} sdcsz_flip;
+
+int sdcsz_debug_compress_flips(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap,
+                               size_t* out_bytes, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,
+                               const sdcsz_flip* d_flips, size_t n_flips);
+int sdcsz_debug_decompress_flips(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes,
+                                 uint8_t* d_block_status, void* d_ws, size_t ws_bytes, sdcsz_report* report,
+                                 void* stream, const sdcsz_flip* d_flips, size_t n_flips);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDCSZ_H */

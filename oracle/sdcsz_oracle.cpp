@@ -272,13 +272,11 @@ bool regression_coefficients(const T* v, const uint32_t e[3], int ndim, float co
   return true;
 }
 
-// Predictor selection by estimated error (Alg. 1 lines 6-8), in fp32 over all points.
-// E_lor adds the expected effect of using reconstructed instead of original neighbours:
-// kappa*eb per point, kappa = E|sum of n uniform(-eb,eb)| / eb for the n = 1, 3, 7 Lorenzo
-// terms of 1D/2D/3D (normal approximation for 2D/3D).
+// Selection estimates (Alg. 1 lines 6-7), in fp32 over all points of the block (the sample):
+// E_reg = sum |x - f_reg|, E_lor = sum |x - Lorenzo(original values)|.
 template <typename T>
-bool choose_regression(const T* v, const uint32_t e[3], int ndim, const float coef[4], float ebf) {
-  static const float kappa[4] = {0.0f, 0.5f, 0.80f, 1.22f};
+void selection_estimates(const T* v, const uint32_t e[3], int ndim, const float coef[4], float* Ereg_out,
+                         float* Elor_out) {
   const uint64_t P = (uint64_t)e[0] * e[1] * e[2];
   std::vector<float> xr(P);
   for (uint64_t k = 0; k < P; ++k) xr[k] = (float)v[k];
@@ -293,6 +291,16 @@ bool choose_regression(const T* v, const uint32_t e[3], int ndim, const float co
         float L = lorenzo<float>(xr.data(), e, ndim, i, j, l);
         Elor = Elor + std::fabs(xr[k] - L);
       }
+  *Ereg_out = Ereg;
+  *Elor_out = Elor;
+}
+
+// Alg. 1 line 8: the predictor with the smaller estimated error. E_lor gets the expected
+// effect of predicting from reconstructed instead of original neighbours: kappa*eb per point,
+// kappa = E|sum of n uniform(-eb,eb)| / eb for the n = 1, 3, 7 Lorenzo terms of 1D/2D/3D
+// (normal approximation for 2D/3D).
+bool select_regression(float Ereg, float Elor, uint64_t P, int ndim, float ebf) {
+  static const float kappa[4] = {0.0f, 0.5f, 0.80f, 1.22f};
   float noise = kappa[ndim] * ebf;
   float total = Elor + (float)P * noise;
   return Ereg < total;
@@ -327,23 +335,55 @@ const orc_flip* find_flip(const Ctx& c, uint32_t site, uint64_t block, uint64_t 
   return nullptr;
 }
 
-// Alg. 1 for one block: verify the input (line 11), regression (line 2), selection
-// (lines 6-8), then the prediction loop (lines 17-31) with duplicated prediction and
-// reconstruction (lines 18, 25) and the block checksums (lines 24, 29).
+// Prediction preparation for one block (Alg. 1 line 2, lines 6-7): regression coefficients
+// and the two error estimates, from the block's values as they are in the first pass.
+struct Prep {
+  float coef[4] = {0, 0, 0, 0};
+  bool finite = false;
+  float Ereg = 0.0f, Elor = 0.0f;
+};
+
+template <typename T>
+void load_block(const Geom& g, const T* field, uint64_t b, std::vector<T>* v, uint32_t ext[3]) {
+  uint64_t org[3];
+  block_box(g, b, org, ext);
+  v->resize((uint64_t)ext[0] * ext[1] * ext[2]);
+  uint64_t k = 0;
+  for (uint32_t i = 0; i < ext[0]; ++i)
+    for (uint32_t j = 0; j < ext[1]; ++j)
+      for (uint32_t l = 0; l < ext[2]; ++l) (*v)[k++] = field[global_index(g, org, i, j, l)];
+}
+
+template <typename T>
+Prep prepare_block(const Ctx& c, const T* field, uint64_t b) {
+  std::vector<T> v;
+  uint32_t e[3];
+  load_block<T>(c.g, field, b, &v, e);
+  Prep pr;
+  pr.finite = regression_coefficients<T>(v.data(), e, c.g.ndim, pr.coef);
+  if (pr.finite && c.predictor_mode == 0) selection_estimates<T>(v.data(), e, c.g.ndim, pr.coef, &pr.Ereg, &pr.Elor);
+  return pr;
+}
+
+bool indicator_of(const Ctx& c, const Prep& pr, uint64_t P, float ebf) {
+  if (!pr.finite) return false;
+  if (c.predictor_mode == 2) return true;
+  if (c.predictor_mode == 1) return false;
+  return select_regression(pr.Ereg, pr.Elor, P, c.g.ndim, ebf);
+}
+
+// Alg. 1 lines 10-31 for one block: verify the input (line 11), pick f() from the indicator
+// (lines 12-16), then the prediction loop with duplicated prediction and reconstruction
+// (lines 18, 25) and the block checksums (lines 24, 29).
 template <typename T>
 void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint64_t sum_in, uint64_t isum_in,
-                    BlockResult<T>* out) {
+                    const Prep& pr, BlockResult<T>* out) {
   const Geom& g = c.g;
-  uint64_t org[3];
-  block_box(g, b, org, out->ext);
+  std::vector<T>& v = out->vin;
+  load_block<T>(g, field, b, &v, out->ext);
   const uint32_t* e = out->ext;
   const uint64_t P = (uint64_t)e[0] * e[1] * e[2];
-  std::vector<T>& v = out->vin;
-  v.resize(P);
   uint64_t k = 0;
-  for (uint32_t i = 0; i < e[0]; ++i)
-    for (uint32_t j = 0; j < e[1]; ++j)
-      for (uint32_t l = 0; l < e[2]; ++l) v[k++] = field[global_index(g, org, i, j, l)];
 
   // Alg. 1 line 11: memory-error detection and correction with sum_in / isum_in.
   if (c.abft) {
@@ -355,16 +395,9 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
       for (uint64_t p = 0; p < P; ++p) v[p] = Bits<T>::from_words(&w[p * W]);
   }
 
-  // Alg. 1 line 2 and lines 6-8.
-  float cf[4] = {0, 0, 0, 0};
-  bool finite = regression_coefficients<T>(v.data(), e, g.ndim, cf);
-  bool use_reg = false;
-  if (finite) {
-    if (c.predictor_mode == 2) use_reg = true;
-    else if (c.predictor_mode == 0) use_reg = choose_regression<T>(v.data(), e, g.ndim, cf, (float)eb);
-  }
+  const bool use_reg = indicator_of(c, pr, P, (float)eb);
   out->regression = use_reg;
-  for (int a = 0; a < 4; ++a) out->coef[a] = (T)cf[a];
+  for (int a = 0; a < 4; ++a) out->coef[a] = (T)pr.coef[a];
   for (int a = 0; a <= g.ndim; ++a) {
     const orc_flip* f = find_flip(c, SITE_COEF, b, (uint64_t)a);
     if (f) out->coef[a] = Bits<T>::flip(out->coef[a], f->bit);
@@ -582,6 +615,22 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   c.flips = flips;
   c.nflips = nflips;
 
+  // Alg. 1 lines 1-5 (with the estimates of lines 6-7): per block input checksums,
+  // regression coefficients and selection estimates; the value range for the bound.
+  std::vector<uint64_t> sum_in(g.nb, 0), isum_in(g.nb, 0);
+  std::vector<Prep> prep(g.nb);
+  for (uint64_t b = 0; b < g.nb; ++b) {
+    prep[b] = prepare_block<T>(c, field_in, b);
+    if (c.abft) {
+      std::vector<T> v;
+      uint32_t e[3];
+      load_block<T>(g, field_in, b, &v, e);
+      const int W = Bits<T>::kWords;
+      std::vector<uint32_t> w(v.size() * W);
+      for (uint64_t p = 0; p < v.size(); ++p) Bits<T>::words(v[p], &w[p * W]);
+      checksum_words(w.data(), w.size(), &sum_in[b], &isum_in[b]);
+    }
+  }
   // Error bound: absolute, or value-range relative over the finite values (Fig. 2 caption).
   double ebd = p->eb;
   if (p->eb_mode == 1) {
@@ -600,26 +649,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   if (!(eb > (T)0) || !std::isfinite(eb) || !std::isnormal(eb)) return EINVAL_;
   const T inv2 = (T)(1.0 / (2.0 * (double)eb));
 
-  // Alg. 1 lines 1-5: input checksums for every block.
-  std::vector<uint64_t> sum_in(g.nb, 0), isum_in(g.nb, 0);
   std::vector<T> field(field_in, field_in + g.N);  // working copy that soft errors may strike
-  if (c.abft) {
-    const int W = Bits<T>::kWords;
-    for (uint64_t b = 0; b < g.nb; ++b) {
-      uint64_t org[3];
-      uint32_t e[3];
-      block_box(g, b, org, e);
-      std::vector<uint32_t> w;
-      for (uint32_t i = 0; i < e[0]; ++i)
-        for (uint32_t j = 0; j < e[1]; ++j)
-          for (uint32_t l = 0; l < e[2]; ++l) {
-            uint32_t ww[2];
-            Bits<T>::words(field[global_index(g, org, i, j, l)], ww);
-            for (int m = 0; m < W; ++m) w.push_back(ww[m]);
-          }
-      checksum_words(w.data(), w.size(), &sum_in[b], &isum_in[b]);
-    }
-  }
   // memory errors in the input strike here, after its checksums (Sec. 6.1.2, mode A)
   for (int n = 0; n < nflips; ++n)
     if (flips[n].site == SITE_INPUT) {
@@ -640,7 +670,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   r.blocks = g.nb;
   r.eb_abs = (double)eb;
   for (uint64_t b = 0; b < g.nb; ++b) {
-    compress_block<T>(c, field.data(), b, eb, inv2, sum_in[b], isum_in[b], &blk[b]);
+    compress_block<T>(c, field.data(), b, eb, inv2, sum_in[b], isum_in[b], prep[b], &blk[b]);
     for (uint16_t q : blk[b].code) hist[q]++;
     if (blk[b].input_status == 1) r.input_corrected++;
     if (blk[b].input_status == 2) r.uncorrectable_blocks++;
@@ -1040,7 +1070,8 @@ int orc_compress_block(const void* field, const orc_params* p, double eb_abs, ui
     BlockResult<T> r;
     Ctx c2 = c;
     c2.abft = false;  // no stored input checksums to verify against
-    compress_block<T>(c2, (const T*)f, b, eb, inv2, sum_in, isum_in, &r);
+    Prep pr = prepare_block<T>(c2, (const T*)f, b);
+    compress_block<T>(c2, (const T*)f, b, eb, inv2, sum_in, isum_in, pr, &r);
     std::memcpy(codes, r.code.data(), 2 * r.code.size());
     std::memcpy(coef, r.coef, sizeof(T) * 4);
     *is_reg = r.regression ? 1 : 0;

@@ -1,0 +1,327 @@
+"""Python binding of libsdcsz: SDC-resilient error-bounded lossy compression on GB300.
+
+Thin ctypes marshalling over the C ABI of ``include/sdcsz.h`` (same function names without
+the ``sdcsz_`` prefix). PyTorch provides device memory and the current CUDA stream; every
+step of compression and decompression runs in the library's CUDA kernels. There is no CPU
+fallback: if ``libsdcsz.so`` is missing or CUDA is unavailable the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsdcsz.so")
+
+OK, EINVAL, ECAPACITY, EFORMAT, ESDC, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
+SITES = {"input": 1, "code": 2, "coef": 3, "pred": 4, "recon": 5, "decomp": 6}
+PREDICTORS = {"auto": 0, "lorenzo": 1, "regression": 2}
+BLOCK_OK, BLOCK_CORRECTED, BLOCK_SDC, BLOCK_BAD = 0, 1, 2, 3
+
+# Symbols the header declares (checked by tests against the shared object's exports).
+EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_workspace_size", "sdcsz_compress",
+           "sdcsz_decompress", "sdcsz_verify", "sdcsz_read_header", "sdcsz_strerror",
+           "sdcsz_debug_compress_flips", "sdcsz_debug_decompress_flips", "sdcsz_compress_traced",
+           "sdcsz_decompress_traced")
+
+
+class SdcszError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_uint32),
+        ("dtype", ctypes.c_uint32),
+        ("dims", ctypes.c_uint64 * 3),
+        ("block", ctypes.c_uint32 * 3),
+        ("eb_mode", ctypes.c_uint32),
+        ("eb", ctypes.c_double),
+        ("quant_bins", ctypes.c_uint32),
+        ("abft", ctypes.c_uint32),
+        ("predictor", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [
+        ("blocks", ctypes.c_uint64),
+        ("regression_blocks", ctypes.c_uint64),
+        ("unpredictable_points", ctypes.c_uint64),
+        ("compressed_bytes", ctypes.c_uint64),
+        ("input_corrected", ctypes.c_uint64),
+        ("codes_corrected", ctypes.c_uint64),
+        ("dup_mismatch_corrected", ctypes.c_uint64),
+        ("decomp_reexec_corrected", ctypes.c_uint64),
+        ("uncorrectable_blocks", ctypes.c_uint64),
+        ("bound_violations", ctypes.c_uint64),
+        ("eb_abs", ctypes.c_double),
+        ("max_abs_err", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Flip(ctypes.Structure):
+    _fields_ = [("site", ctypes.c_uint32), ("bit", ctypes.c_uint32), ("block", ctypes.c_uint64),
+                ("index", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsdcsz.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        P, R = ctypes.POINTER(Params), ctypes.POINTER(Report)
+        L.sdcsz_compress_bound.argtypes = [P, ctypes.POINTER(sz)]
+        L.sdcsz_workspace_size.argtypes = [P, ctypes.POINTER(sz)]
+        L.sdcsz_decompress_workspace_size.argtypes = []
+        L.sdcsz_decompress_workspace_size.restype = sz
+        L.sdcsz_compress.argtypes = [vp, P, vp, sz, ctypes.POINTER(sz), vp, sz, R, vp]
+        L.sdcsz_debug_compress_flips.argtypes = [vp, P, vp, sz, ctypes.POINTER(sz), vp, sz, R, vp, vp, sz]
+        L.sdcsz_decompress.argtypes = [vp, sz, vp, sz, vp, vp, sz, R, vp]
+        L.sdcsz_debug_decompress_flips.argtypes = [vp, sz, vp, sz, vp, vp, sz, R, vp, vp, sz]
+        L.sdcsz_verify.argtypes = [vp, sz, vp, vp, vp, sz, R, vp]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.sdcsz_compress_traced.argtypes = [vp, P, vp, sz, ctypes.POINTER(sz), vp, sz, R, vp, fp]
+        L.sdcsz_decompress_traced.argtypes = [vp, sz, vp, sz, vp, vp, sz, R, vp, fp]
+        L.sdcsz_compress_traced.restype = i32
+        L.sdcsz_decompress_traced.restype = i32
+        L.sdcsz_read_header.argtypes = [vp, sz, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.sdcsz_strerror.argtypes = [i32]
+        L.sdcsz_strerror.restype = ctypes.c_char_p
+        for f in (L.sdcsz_compress_bound, L.sdcsz_workspace_size, L.sdcsz_compress, L.sdcsz_debug_compress_flips,
+                  L.sdcsz_decompress, L.sdcsz_debug_decompress_flips, L.sdcsz_verify, L.sdcsz_read_header):
+            f.restype = i32
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().sdcsz_strerror(int(code)).decode()
+
+
+def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto") -> Params:
+    import torch
+    ndim = len(shape)
+    p = Params()
+    p.ndim = ndim
+    if dtype in (torch.float32, np.float32, "float32"):
+        p.dtype = 0
+    elif dtype in (torch.float64, np.float64, "float64"):
+        p.dtype = 1
+    else:
+        raise ValueError(f"unsupported dtype {dtype}")
+    for a in range(ndim):
+        p.dims[a] = int(shape[a])
+    if block is not None:
+        if isinstance(block, int):
+            block = (block,) * ndim
+        for a in range(ndim):
+            p.block[a] = int(block[a])
+    p.eb_mode = 1 if eb_mode == "rel" else 0
+    p.eb = float(eb)
+    p.quant_bins = int(bins)
+    p.abft = 1 if abft else 0
+    p.predictor = PREDICTORS[predictor]
+    return p
+
+
+def compress_bound(p: Params) -> int:
+    out = ctypes.c_size_t()
+    rc = lib().sdcsz_compress_bound(ctypes.byref(p), ctypes.byref(out))
+    if rc:
+        raise SdcszError(rc, "compress_bound")
+    return out.value
+
+
+def workspace_size(p: Params) -> int:
+    out = ctypes.c_size_t()
+    rc = lib().sdcsz_workspace_size(ctypes.byref(p), ctypes.byref(out))
+    if rc:
+        raise SdcszError(rc, "workspace_size")
+    return out.value
+
+
+def decompress_workspace_size() -> int:
+    return int(lib().sdcsz_decompress_workspace_size())
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def flips_tensor(flips, device):
+    """Device array of flip records sorted by (block, site, index)."""
+    import torch
+    recs = []
+    for site, block, index, bit in flips:
+        recs.append((SITES[site] if isinstance(site, str) else int(site), int(bit), int(block), int(index)))
+    recs.sort(key=lambda r: (r[2], r[0], r[3]))
+    arr = np.zeros(len(recs), dtype=np.dtype([("site", "<u4"), ("bit", "<u4"), ("block", "<u8"), ("index", "<u8")]))
+    for n, r in enumerate(recs):
+        arr[n] = r
+    return torch.from_numpy(arr.view(np.uint8).copy()).to(device)
+
+
+class Workspace:
+    """Reusable device buffers for repeated calls with one parameter set."""
+
+    def __init__(self, p: Params, device):
+        import torch
+        self.p = p
+        self.cap = compress_bound(p)
+        self.out = torch.empty(self.cap, dtype=torch.uint8, device=device)
+        self.ws = torch.empty(workspace_size(p), dtype=torch.uint8, device=device)
+
+
+def compress(field, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto", flips=None,
+             workspace: Workspace | None = None, stream=None, sync=True):
+    """Compress a CUDA tensor (float32/float64, 1-3 dims, contiguous). Returns
+    (stream bytes as a uint8 CUDA tensor view, report dict or None)."""
+    import torch
+    if not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous CUDA tensor")
+    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor)
+    w = workspace if workspace is not None else Workspace(p, field.device)
+    rep = Report()
+    nbytes = ctypes.c_size_t()
+    h = _stream_handle(stream)
+    if flips:
+        ft = flips_tensor(flips, field.device)
+        rc = lib().sdcsz_debug_compress_flips(ctypes.c_void_p(field.data_ptr()), ctypes.byref(p),
+                                              ctypes.c_void_p(w.out.data_ptr()), w.cap, ctypes.byref(nbytes),
+                                              ctypes.c_void_p(w.ws.data_ptr()), w.ws.numel(), ctypes.byref(rep), h,
+                                              ctypes.c_void_p(ft.data_ptr()), len(flips))
+    elif sync:
+        rc = lib().sdcsz_compress(ctypes.c_void_p(field.data_ptr()), ctypes.byref(p), ctypes.c_void_p(w.out.data_ptr()),
+                                  w.cap, ctypes.byref(nbytes), ctypes.c_void_p(w.ws.data_ptr()), w.ws.numel(),
+                                  ctypes.byref(rep), h)
+    else:
+        rc = lib().sdcsz_compress(ctypes.c_void_p(field.data_ptr()), ctypes.byref(p), ctypes.c_void_p(w.out.data_ptr()),
+                                  w.cap, None, ctypes.c_void_p(w.ws.data_ptr()), w.ws.numel(), None, h)
+        if rc:
+            raise SdcszError(rc, "compress")
+        return w.out, None
+    if rc:
+        raise SdcszError(rc, "compress")
+    return w.out[: nbytes.value], rep.as_dict()
+
+
+def read_header(stream_bytes):
+    """Parse a stream header from host bytes (numpy uint8 or bytes)."""
+    b = np.ascontiguousarray(np.frombuffer(bytes(stream_bytes), dtype=np.uint8) if isinstance(stream_bytes, (bytes, bytearray))
+                             else stream_bytes, dtype=np.uint8)
+    p = Params()
+    total = ctypes.c_uint64()
+    rc = lib().sdcsz_read_header(b.ctypes.data_as(ctypes.c_void_p), b.size, ctypes.byref(p), ctypes.byref(total))
+    if rc:
+        raise SdcszError(rc, "read_header")
+    shape = tuple(int(p.dims[a]) for a in range(p.ndim))
+    block = tuple(int(p.block[a]) for a in range(p.ndim))
+    return {"shape": shape, "dtype": "float32" if p.dtype == 0 else "float64", "block": block,
+            "total": int(total.value), "abft": bool(p.abft), "bins": int(p.quant_bins)}
+
+
+def _geometry(stream):
+    import torch
+    hb = stream[:128].cpu().numpy()
+    h = read_header_partial(hb, stream.numel())
+    nb = 1
+    for n, b in zip(h["shape"], h["block"]):
+        nb *= (n + b - 1) // b
+    dt = torch.float32 if h["dtype"] == "float32" else torch.float64
+    return h, nb, dt
+
+
+def read_header_partial(header_bytes: np.ndarray, nbytes: int):
+    """Header parse when only the first 128 bytes are on the host."""
+    b = np.ascontiguousarray(header_bytes, dtype=np.uint8)
+    p = Params()
+    total = ctypes.c_uint64()
+    buf = np.zeros(max(128, b.size), dtype=np.uint8)
+    buf[: b.size] = b
+    rc = lib().sdcsz_read_header(buf.ctypes.data_as(ctypes.c_void_p), int(nbytes), ctypes.byref(p),
+                                 ctypes.byref(total))
+    if rc:
+        raise SdcszError(rc, "read_header")
+    return {"shape": tuple(int(p.dims[a]) for a in range(p.ndim)), "dtype": "float32" if p.dtype == 0 else "float64",
+            "block": tuple(int(p.block[a]) for a in range(p.ndim)), "total": int(total.value)}
+
+
+def decompress(stream, out=None, status=None, flips=None, ws=None, cuda_stream=None, report=True):
+    """Decompress a uint8 CUDA tensor holding a stream. Returns (rc, field, block status, report dict).
+    rc is 0 or ESDC (blocks that failed twice are named in the status); other errors raise."""
+    import torch
+    h, nb, dt = _geometry(stream)
+    field = out if out is not None else torch.empty(h["shape"], dtype=dt, device=stream.device)
+    st = status if status is not None else torch.empty(max(nb, 1), dtype=torch.uint8, device=stream.device)
+    w = ws if ws is not None else torch.empty(decompress_workspace_size(), dtype=torch.uint8, device=stream.device)
+    rep = Report()
+    hs = _stream_handle(cuda_stream)
+    args = [ctypes.c_void_p(stream.data_ptr()), stream.numel(), ctypes.c_void_p(field.data_ptr()),
+            field.numel() * field.element_size(), ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+            w.numel(), ctypes.byref(rep) if report else None, hs]
+    if flips:
+        ft = flips_tensor(flips, stream.device)
+        rc = lib().sdcsz_debug_decompress_flips(*args, ctypes.c_void_p(ft.data_ptr()), len(flips))
+    else:
+        rc = lib().sdcsz_decompress(*args)
+    if rc not in (OK, ESDC):
+        raise SdcszError(rc, "decompress")
+    return rc, field, st[:nb], (rep.as_dict() if report else None)
+
+
+def verify(stream, original=None, status=None, ws=None, cuda_stream=None):
+    """Alg. 2 checks without writing a field; with ``original`` also the bound on every point.
+    Returns (rc, block status, report dict)."""
+    import torch
+    h, nb, dt = _geometry(stream)
+    st = status if status is not None else torch.empty(max(nb, 1), dtype=torch.uint8, device=stream.device)
+    w = ws if ws is not None else torch.empty(decompress_workspace_size(), dtype=torch.uint8, device=stream.device)
+    rep = Report()
+    orig = ctypes.c_void_p(original.data_ptr()) if original is not None else None
+    rc = lib().sdcsz_verify(ctypes.c_void_p(stream.data_ptr()), stream.numel(), orig, ctypes.c_void_p(st.data_ptr()),
+                            ctypes.c_void_p(w.data_ptr()), w.numel(), ctypes.byref(rep), _stream_handle(cuda_stream))
+    if rc not in (OK, ESDC):
+        raise SdcszError(rc, "verify")
+    return rc, st[:nb], rep.as_dict()
+
+
+def compress_traced(field, p: Params, workspace: Workspace, stream=None):
+    """Compress with per-stage CUDA-event timing. Returns (nbytes, stage milliseconds[5])."""
+    ms = (ctypes.c_float * 5)()
+    nbytes = ctypes.c_size_t()
+    rc = lib().sdcsz_compress_traced(ctypes.c_void_p(field.data_ptr()), ctypes.byref(p),
+                                     ctypes.c_void_p(workspace.out.data_ptr()), workspace.cap, ctypes.byref(nbytes),
+                                     ctypes.c_void_p(workspace.ws.data_ptr()), workspace.ws.numel(), None,
+                                     _stream_handle(stream), ms)
+    if rc:
+        raise SdcszError(rc, "compress_traced")
+    return nbytes.value, list(ms)
+
+
+def decompress_traced(stream_t, out, ws, stream=None):
+    """Decompress with CUDA-event timing of the decode kernel. Returns milliseconds."""
+    ms = (ctypes.c_float * 1)()
+    rc = lib().sdcsz_decompress_traced(ctypes.c_void_p(stream_t.data_ptr()), stream_t.numel(),
+                                       ctypes.c_void_p(out.data_ptr()), out.numel() * out.element_size(), None,
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), None, _stream_handle(stream), ms)
+    if rc not in (OK,):
+        raise SdcszError(rc, "decompress_traced")
+    return ms[0]

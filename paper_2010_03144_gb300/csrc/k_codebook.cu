@@ -1,0 +1,273 @@
+// K3: Huffman code for the whole bin array (Alg. 1 line 33), the stream header and the
+// section layout. One CTA of 1024 threads.
+//
+//   1. compact the live symbols into keys (count << 16 | symbol) and sort them ascending:
+//      leaves in increasing (count, symbol) order;
+//   2. two-queue Huffman merge (one thread): the next node is the lighter of the next leaf
+//      and the oldest unmerged internal node, a leaf winning ties. This is Huffman's
+//      algorithm with ties broken by creation order (leaves first, in sorted order);
+//   3. leaf depths, then lengths longer than 24 bits are reduced by the JPEG adjustment
+//      (ITU-T T.81 Annex K.3) and handed out longest-first to the leaves in sorted order;
+//   4. canonical codes: symbols sorted by (length, symbol) get consecutive codes per length.
+#include "sdcsz_internal.cuh"
+
+namespace sdcsz {
+
+namespace {
+
+// Block-wide exclusive scan of one value per thread (1024 threads).
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= (uint32_t)o) inc += n;
+  }
+  if (lane == 31) s_warp[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t t = (lane < (blockDim.x >> 5)) ? s_warp[lane] : 0;
+    uint32_t ti = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t n = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= (uint32_t)o) ti += n;
+    }
+    s_warp[lane] = ti - t;  // exclusive prefix of warp totals
+    if (lane == 31) s_warp[32] = ti;
+  }
+  __syncthreads();
+  const uint32_t r = s_warp[wid] + inc - v;
+  *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
+// Ascending bitonic sort of n_pad (power of two) 64-bit keys, shared or global memory.
+__device__ void bitonic_sort(unsigned long long* a, uint32_t n_pad) {
+  for (uint32_t size = 2; size <= n_pad; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t t = threadIdx.x; t < n_pad / 2; t += blockDim.x) {
+        const uint32_t i = 2 * t - (t & (stride - 1));
+        const uint32_t j = i + stride;
+        const bool up = (i & size) == 0;
+        const unsigned long long x = a[i], y = a[j];
+        if ((x > y) == up) {
+          a[i] = y;
+          a[j] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ void put_u8(uint8_t* o, uint64_t off, uint8_t v) { o[off] = v; }
+__device__ __forceinline__ void put_u16(uint8_t* o, uint64_t off, uint16_t v) {
+  o[off] = (uint8_t)v; o[off + 1] = (uint8_t)(v >> 8);
+}
+__device__ __forceinline__ void put_u32(uint8_t* o, uint64_t off, uint32_t v) {
+  for (int q = 0; q < 4; ++q) o[off + q] = (uint8_t)(v >> (8 * q));
+}
+__device__ __forceinline__ void put_u64(uint8_t* o, uint64_t off, unsigned long long v) {
+  for (int q = 0; q < 8; ++q) o[off + q] = (uint8_t)(v >> (8 * q));
+}
+
+constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this many
+
+}  // namespace
+
+__global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_warp[40];
+  __shared__ uint32_t s_n;
+  __shared__ uint32_t cnt[64];
+  __shared__ uint32_t s_maxlen;
+  __shared__ uint32_t first_code[kMaxLen + 2], first_index[kMaxLen + 2], cum[kMaxLen + 2];
+  State* st = w.st;
+  if (*(volatile unsigned int*)&st->error) return;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t bins = g.bins;
+
+  // 1. live symbols -> keys (global scratch), codebook cleared
+  uint32_t n = 0;
+  for (uint32_t c = 0; c < bins; c += blockDim.x) {
+    const uint32_t s = c + tid;
+    unsigned long long hc = 0;
+    if (s < bins) {
+      hc = w.hist[s];
+      w.codebook[s] = 0;
+    }
+    uint32_t tot;
+    const uint32_t pos = block_excl_scan(hc ? 1u : 0u, s_warp, &tot);
+    if (hc) w.sort_keys[n + pos] = (hc << 16) | s;
+    n += tot;
+  }
+  uint32_t n_pad = 1;
+  while (n_pad < n) n_pad <<= 1;
+  unsigned long long* keys = (n_pad <= kSmemSort) ? reinterpret_cast<unsigned long long*>(smem) : w.sort_keys;
+  __syncthreads();
+  for (uint32_t t = tid; t < n_pad; t += blockDim.x) keys[t] = (t < n) ? w.sort_keys[t] : ~0ull;
+  __syncthreads();
+  if (n > 1) bitonic_sort(keys, n_pad);
+  for (uint32_t t = tid; t < 64; t += blockDim.x) cnt[t] = 0;
+  if (tid == 0) s_maxlen = 0;
+  __syncthreads();
+
+  // 2-3. Huffman merge and leaf depths (one thread), length counts
+  uint8_t* depth = nullptr;
+  if (n >= 2) {
+    // node arrays: internal weights [n-1], parents [2n-1], depths [2n-1]
+    const bool small = n <= 4096;
+    unsigned long long* iw = small ? reinterpret_cast<unsigned long long*>(smem + kSmemSort * 8) : w.node_w;
+    uint32_t* parent = small ? reinterpret_cast<uint32_t*>(smem + kSmemSort * 8 + 4096 * 8) : w.node_parent;
+    depth = small ? (smem + kSmemSort * 8 + 4096 * 8 + 8192 * 4)
+                  : reinterpret_cast<uint8_t*>(w.node_parent + 2 * 65536);
+    if (tid == 0) {
+      uint32_t lp = 0, ip = 0;
+      for (uint32_t ni = 0; ni + 1 < n; ++ni) {
+        unsigned long long wsum = 0;
+        for (int pick = 0; pick < 2; ++pick) {
+          const bool leaf = lp < n && (ip >= ni || (keys[lp] >> 16) <= iw[ip]);
+          if (leaf) {
+            wsum += keys[lp] >> 16;
+            parent[lp] = n + ni;
+            ++lp;
+          } else {
+            wsum += iw[ip];
+            parent[n + ip] = n + ni;
+            ++ip;
+          }
+        }
+        iw[ni] = wsum;
+      }
+      const uint32_t root = 2 * n - 2;
+      depth[root] = 0;
+      for (int64_t v = (int64_t)root - 1; v >= 0; --v) {
+        uint32_t d = depth[parent[v]] + 1u;
+        depth[v] = (uint8_t)(d > 63 ? 63 : d);
+      }
+    }
+    __syncthreads();
+    for (uint32_t p = tid; p < n; p += blockDim.x) {
+      atomicAdd(&cnt[depth[p]], 1u);
+      atomicMax(&s_maxlen, (uint32_t)depth[p]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // JPEG Annex K.3: move pairs of the deepest codes up until none is longer than 24 bits
+      for (uint32_t l = s_maxlen; l > (uint32_t)kMaxLen; --l) {
+        while (cnt[l] > 0) {
+          uint32_t j = l - 2;
+          while (cnt[j] == 0) --j;
+          cnt[l] -= 2;
+          cnt[l - 1] += 1;
+          cnt[j + 1] += 2;
+          cnt[j] -= 1;
+        }
+      }
+      // cum[l] = number of leaves with length > l (longest first)
+      uint32_t acc = 0;
+      for (int l = kMaxLen; l >= 0; --l) {
+        cum[l] = acc;
+        acc += cnt[l];
+      }
+      cum[kMaxLen + 1] = 0;
+    }
+  } else if (n == 1) {
+    if (tid == 0) {
+      cnt[1] = 1;
+      cum[1] = 0;
+      cum[0] = 1;
+      for (int l = 2; l <= kMaxLen + 1; ++l) cum[l] = 0;
+    }
+  }
+  __syncthreads();
+
+  // lengths by leaf rank, then re-sort by (length, symbol) for the canonical order
+  for (uint32_t p = tid; p < n; p += blockDim.x) {
+    uint32_t len = 1;
+    for (uint32_t l = 1; l <= (uint32_t)kMaxLen; ++l)
+      if (cnt[l] && p >= cum[l] && p < cum[l] + cnt[l]) len = l;
+    const unsigned long long sym = keys[p] & 0xffffull;
+    w.sort_keys[p] = ((unsigned long long)len << 16) | sym;  // stage in global: keys may alias
+  }
+  __syncthreads();
+  for (uint32_t t = tid; t < n_pad; t += blockDim.x) keys[t] = (t < n) ? w.sort_keys[t] : ~0ull;
+  __syncthreads();
+  if (n > 1) bitonic_sort(keys, n_pad);
+  if (tid == 0) {
+    uint32_t code = 0, idx = 0;
+    for (uint32_t l = 1; l <= (uint32_t)kMaxLen; ++l) {
+      code = (code + (l >= 2 ? cnt[l - 1] : 0u)) << 1;
+      first_code[l] = code;
+      first_index[l] = idx;
+      idx += cnt[l];
+    }
+    s_n = n;
+  }
+  __syncthreads();
+
+  // the stream layout now that every section size is known
+  const Layout L = make_layout(g, n, st->n_reg, st->n_unpred);
+  if (L.payload > cap) {
+    if (tid == 0) atomicOr(&st->error, ERR_CAPACITY);
+    return;
+  }
+  for (uint32_t r = tid; r < n; r += blockDim.x) {
+    const uint32_t len = (uint32_t)(keys[r] >> 16);
+    const uint32_t sym = (uint32_t)(keys[r] & 0xffffu);
+    const uint32_t code = first_code[len] + (r - first_index[len]);
+    w.codebook[sym] = (code << 5) | len;
+    put_u16(out, L.table + 4 * (kMaxLen + 1) + 2 * (uint64_t)r, (uint16_t)sym);
+  }
+  if (tid <= (uint32_t)kMaxLen) put_u32(out, L.table + 4 * tid, tid == 0 ? 0u : cnt[tid]);
+  if (tid == 0) {
+    st->n_live = n;
+    st->L = L;
+    st->payload_bytes = 0;
+    st->total_bytes = L.payload;
+    // header (128 bytes, little-endian)
+    for (int q = 0; q < kHeaderBytes; ++q) out[q] = 0;
+    out[0] = 'S'; out[1] = 'D'; out[2] = 'S'; out[3] = 'Z';
+    put_u16(out, 4, 1);
+    put_u8(out, 6, (uint8_t)g.dtype);
+    put_u8(out, 7, (uint8_t)g.ndim);
+    const int off = 3 - g.ndim;
+    for (int a = 0; a < g.ndim; ++a) {
+      put_u64(out, 8 + 8 * a, g.d[off + a]);
+      put_u32(out, 32 + 4 * a, g.B[off + a]);
+    }
+    put_u32(out, 44, g.bins);
+    put_u8(out, 48, (uint8_t)g.abft);
+    put_u8(out, 49, (uint8_t)g.predictor);
+    put_u8(out, 50, (uint8_t)g.eb_mode);
+    put_u32(out, 52, n);
+    put_u64(out, 56, (unsigned long long)__double_as_longlong(st->eb));
+    put_u64(out, 64, (unsigned long long)__double_as_longlong(g.e));
+    put_u64(out, 72, g.nb);
+    put_u64(out, 80, st->n_reg);
+    put_u64(out, 88, st->n_unpred);
+    put_u64(out, 96, 0);
+    put_u64(out, 104, L.payload);
+    put_u32(out, 112, st->uncorrectable ? 1u : 0u);
+    // zero the alignment gaps between sections
+    const uint64_t s = g.dtype ? 8 : 4;
+    const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
+    const uint64_t ends[8] = {L.table + 4 * (kMaxLen + 1) + 2 * (uint64_t)n, L.groups + 24 * ngroups,
+                              L.sizes + 2 * g.nb, L.ucounts + 2 * g.nb, L.bitmap + 4 * ((g.nb + 31) / 32),
+                              L.sumdc + (g.abft ? 8 * g.nb : 0), L.coef + s * (uint64_t)(g.ndim + 1) * st->n_reg,
+                              L.unpred + s * st->n_unpred};
+    const uint64_t starts[8] = {L.groups, L.sizes, L.ucounts, L.bitmap, L.sumdc, L.coef, L.unpred, L.payload};
+    for (int q = 0; q < 8; ++q)
+      for (uint64_t o = ends[q]; o < starts[q]; ++o) out[o] = 0;
+    // the last bitmap word may be partial: it is written whole by the encoder
+  }
+}
+
+void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
+  const size_t smem = kSmemSort * 8 + 4096 * 8 + 8192 * 4 + 8192;
+  cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_codebook<<<1, 1024, smem, L.stream>>>(g, w, out, cap);
+}
+
+}  // namespace sdcsz

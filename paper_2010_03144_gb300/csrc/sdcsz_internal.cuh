@@ -1,0 +1,404 @@
+// Internal definitions shared by the sdcsz CUDA kernels and the host entry points.
+//
+// Execution model (one GB300, sm_103a): every kernel maps one independent block (Sec. 5.1 of
+// the paper) to one thread, and a warp to 32 consecutive blocks in row-major block order.
+// Within a block the Lorenzo predictor depends on already reconstructed neighbours, so each
+// thread walks its block point by point in the sequential order of the definition; the
+// warp's lanes run 32 such walks side by side. Neighbour values live in a per-thread slice of
+// shared memory laid out slot-major ([slot][thread]) so a warp's accesses are conflict free.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sdcsz.h"
+
+namespace sdcsz {
+
+constexpr int kMaxLen = 24;           // longest Huffman code in bits
+constexpr int kGroup = 256;           // blocks per random-access group of the stream
+constexpr int kHeaderBytes = 128;
+constexpr int kLutBits = 12;          // first-level decode table covers codes of <= 12 bits
+constexpr int kHistWindow = 4096;     // bins privatised in shared memory around the centre
+constexpr uint32_t kSpinLimit = 1u << 20;  // bounded waits: iterations before giving up
+
+// error flags accumulated in State::error
+enum : uint32_t { ERR_EB = 1u, ERR_CAPACITY = 2u, ERR_TIMEOUT = 4u, ERR_FORMAT = 8u, ERR_FIELD = 16u };
+
+// Geometry and parameters, padded to 3D with leading unit dimensions; passed by value.
+struct Geo {
+  int ndim, dtype;
+  uint64_t d[3];
+  uint32_t B[3];
+  uint64_t nbd[3];
+  uint64_t nb, N;
+  uint32_t P;  // points in a full block
+  uint32_t bins, R;
+  int abft, predictor, eb_mode;
+  double e;
+};
+
+// Byte offsets of the stream sections (16-byte aligned).
+struct Layout {
+  uint64_t table, groups, sizes, ucounts, bitmap, sumdc, coef, unpred, payload;
+};
+
+// Device-side state of one call; lives at the start of the workspace.
+struct State {
+  unsigned long long min_key, max_key;
+  unsigned int k1_done;
+  unsigned int error;
+  double eb;  // absolute bound, the dtype value widened to double
+  unsigned long long n_reg, n_unpred;
+  unsigned long long input_corrected, codes_corrected, dup_fixed, uncorrectable, reexec_corrected, bound_viol;
+  unsigned long long max_err_bits;  // double bits of max |x - x'| (non-negative: ordered as u64)
+  unsigned int ticket, n_live;
+  unsigned long long payload_bytes, total_bytes;
+  Layout L;
+  unsigned long long pad[4];
+};
+
+// Decoupled look-back record of one group (encode kernel).
+struct LookBack {
+  unsigned long long agg;      // flag << 62 | reg << 43 | unpred << 22 | bytes
+  unsigned long long incl[3];  // inclusive prefix: payload bytes, unpredictables, regression blocks
+  unsigned int incl_flag;
+  unsigned int pad[7];
+};
+
+// Pointers into a compress workspace.
+struct Ws {
+  State* st;
+  unsigned long long *sum_in, *isum_in, *sum_q, *isum_q, *sum_dc;
+  float4* coef;        // fp32 regression coefficients per block
+  float2* est;         // (E_reg, E_lor) per block
+  uint8_t* pflag;      // bit0: coefficients finite
+  uint8_t* flags;      // bit0: regression block, bit1: input uncorrectable
+  void* coefT;         // dtype coefficients used by regression blocks (4 per block)
+  unsigned long long* hist;
+  uint32_t* codebook;  // code << 5 | length per symbol
+  LookBack* lb;
+  unsigned long long* sort_keys;  // codebook construction scratch
+  unsigned long long* node_w;
+  uint32_t* node_parent;
+  uint16_t* codes;     // quantization codes, warp-interleaved: ((b/32)*P + k)*32 + b%32
+  void* ustage;        // unpredictable values, same interleaving as codes
+};
+
+__host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
+
+__host__ __device__ inline Layout make_layout(const Geo& g, uint64_t n_live, uint64_t n_reg, uint64_t n_unpred) {
+  const uint64_t s = g.dtype ? 8 : 4;
+  const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
+  Layout L;
+  L.table = kHeaderBytes;
+  L.groups = align16(L.table + 4 * (kMaxLen + 1) + 2 * n_live);
+  L.sizes = align16(L.groups + 24 * ngroups);
+  L.ucounts = align16(L.sizes + 2 * g.nb);
+  L.bitmap = align16(L.ucounts + 2 * g.nb);
+  L.sumdc = align16(L.bitmap + 4 * ((g.nb + 31) / 32));
+  L.coef = align16(L.sumdc + (g.abft ? 8 * g.nb : 0));
+  L.unpred = align16(L.coef + s * (uint64_t)(g.ndim + 1) * n_reg);
+  L.payload = align16(L.unpred + s * n_unpred);
+  return L;
+}
+
+__host__ __device__ inline uint64_t code_index(uint64_t b, uint32_t P, uint32_t k) {
+  return ((b >> 5) * (uint64_t)P + k) * 32 + (b & 31);
+}
+
+// Block b's origin and extents (edge blocks are cut to the field).
+struct Box {
+  uint64_t org[3];
+  uint32_t e[3];
+  uint32_t P;
+};
+
+__device__ __forceinline__ Box block_box(const Geo& g, uint64_t b) {
+  Box x;
+  uint64_t c2 = b % g.nbd[2];
+  uint64_t t = b / g.nbd[2];
+  uint64_t c1 = t % g.nbd[1];
+  uint64_t c0 = t / g.nbd[1];
+  x.org[0] = c0 * g.B[0];
+  x.org[1] = c1 * g.B[1];
+  x.org[2] = c2 * g.B[2];
+  x.e[0] = (uint32_t)min((uint64_t)g.B[0], g.d[0] - x.org[0]);
+  x.e[1] = (uint32_t)min((uint64_t)g.B[1], g.d[1] - x.org[1]);
+  x.e[2] = (uint32_t)min((uint64_t)g.B[2], g.d[2] - x.org[2]);
+  x.P = x.e[0] * x.e[1] * x.e[2];
+  return x;
+}
+
+__device__ __forceinline__ uint64_t row_base(const Geo& g, const Box& x, uint32_t i, uint32_t j) {
+  return ((x.org[0] + i) * g.d[1] + (x.org[1] + j)) * g.d[2] + x.org[2];
+}
+
+// ---------------------------------------------------------------- typed arithmetic
+// Every value-producing operation is an explicitly rounded IEEE operation (no contraction).
+// The *_v variants are volatile inline PTX: the duplicated evaluation of Alg. 1 lines 18 and
+// 25 cannot be merged with the primary one by the compiler.
+template <typename T> struct FT;
+
+template <> struct FT<float> {
+  static constexpr int W = 1;
+  __device__ static __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ static __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  __device__ static __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  __device__ static __forceinline__ float add_v(float a, float b) {
+    float r; asm volatile("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r;
+  }
+  __device__ static __forceinline__ float sub_v(float a, float b) {
+    float r; asm volatile("sub.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r;
+  }
+  __device__ static __forceinline__ float mul_v(float a, float b) {
+    float r; asm volatile("mul.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b)); return r;
+  }
+  __device__ static __forceinline__ float fromi(int v) { return __int2float_rn(v); }
+  __device__ static __forceinline__ int trunc_i(float v) { return __float2int_rz(v); }
+  __device__ static __forceinline__ float absv(float v) { return fabsf(v); }
+  __device__ static __forceinline__ bool same(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+  __device__ static __forceinline__ float flip(float v, uint32_t bit) { return __uint_as_float(__float_as_uint(v) ^ (1u << (bit & 31))); }
+  __device__ static __forceinline__ uint32_t lo(float v) { return __float_as_uint(v); }
+  __device__ static __forceinline__ uint32_t hi(float) { return 0u; }
+  __device__ static __forceinline__ float from_words(uint32_t lo, uint32_t) { return __uint_as_float(lo); }
+  __device__ static __forceinline__ bool finite(float v) { return isfinite(v); }
+  __device__ static __forceinline__ float tofloat(float v) { return v; }
+  __device__ static __forceinline__ float fromfloat(float v) { return v; }
+  // monotone unsigned key: a < b  <=>  key(a) < key(b) (for non-NaN)
+  __device__ static __forceinline__ unsigned long long key(float v) {
+    uint32_t u = __float_as_uint(v);
+    return (unsigned long long)((u & 0x80000000u) ? ~u : (u | 0x80000000u));
+  }
+  __device__ static __forceinline__ float unkey(unsigned long long k) {
+    uint32_t u = (uint32_t)k;
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+  }
+  __device__ static __forceinline__ bool is_normal_pos(float v) { return v >= 1.17549435e-38f && v <= 3.40282347e38f; }
+};
+
+template <> struct FT<double> {
+  static constexpr int W = 2;
+  __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  __device__ static __forceinline__ double add_v(double a, double b) {
+    double r; asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b)); return r;
+  }
+  __device__ static __forceinline__ double sub_v(double a, double b) {
+    double r; asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b)); return r;
+  }
+  __device__ static __forceinline__ double mul_v(double a, double b) {
+    double r; asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b)); return r;
+  }
+  __device__ static __forceinline__ double fromi(int v) { return __int2double_rn(v); }
+  __device__ static __forceinline__ int trunc_i(double v) { return __double2int_rz(v); }
+  __device__ static __forceinline__ double absv(double v) { return fabs(v); }
+  __device__ static __forceinline__ bool same(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+  __device__ static __forceinline__ double flip(double v, uint32_t bit) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (1ll << (bit & 63)));
+  }
+  __device__ static __forceinline__ uint32_t lo(double v) { return (uint32_t)(unsigned long long)__double_as_longlong(v); }
+  __device__ static __forceinline__ uint32_t hi(double v) { return (uint32_t)((unsigned long long)__double_as_longlong(v) >> 32); }
+  __device__ static __forceinline__ double from_words(uint32_t lo, uint32_t hi) {
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+  }
+  __device__ static __forceinline__ bool finite(double v) { return isfinite(v); }
+  __device__ static __forceinline__ float tofloat(double v) { return __double2float_rn(v); }
+  __device__ static __forceinline__ double fromfloat(float v) { return (double)v; }
+  __device__ static __forceinline__ unsigned long long key(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+  }
+  __device__ static __forceinline__ double unkey(unsigned long long k) {
+    return __longlong_as_double((long long)((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
+  }
+  __device__ static __forceinline__ bool is_normal_pos(double v) { return v >= 2.2250738585072014e-308 && v <= 1.7976931348623157e308; }
+};
+
+// Checksum words of one value at point k: sum += words, isum += (word index + 1) * word
+// (Sec. 3.2 and 5.4; float64 = two 32-bit words, low word first).
+template <typename T>
+__device__ __forceinline__ void add_words(T v, uint32_t k, unsigned long long& sum, unsigned long long& isum) {
+  const uint32_t w0 = FT<T>::lo(v);
+  if (FT<T>::W == 1) {
+    sum += w0;
+    isum += (unsigned long long)(k + 1) * w0;
+  } else {
+    const uint32_t w1 = FT<T>::hi(v);
+    sum += (unsigned long long)w0 + w1;
+    isum += (unsigned long long)(2 * k + 1) * w0 + (unsigned long long)(2 * k + 2) * w1;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void add_sum(T v, unsigned long long& sum) {
+  if (FT<T>::W == 1) sum += FT<T>::lo(v);
+  else sum += (unsigned long long)FT<T>::lo(v) + FT<T>::hi(v);
+}
+
+// Sec. 3.2: given the stored (sum0, isum0) and the recomputed (sum1, isum1), locate a single
+// changed word: its 1-based index is (isum1 - isum0) / (sum1 - sum0). Returns the 0-based
+// word index and the repaired word, or -1 when no single-word explanation exists.
+__device__ __forceinline__ long long locate_word(unsigned long long sum0, unsigned long long isum0,
+                                                 unsigned long long sum1, unsigned long long isum1,
+                                                 unsigned long long nwords, uint32_t cur_word_unknown,
+                                                 long long* delta_out) {
+  long long ds = (long long)(sum1 - sum0);
+  long long dis = (long long)(isum1 - isum0);
+  (void)cur_word_unknown;
+  if (ds == 0) return -1;
+  if (dis % ds != 0) return -1;
+  long long pos = dis / ds;
+  if (pos < 1 || (unsigned long long)pos > nwords) return -1;
+  *delta_out = ds;
+  return pos - 1;
+}
+
+// ---------------------------------------------------------------- predictors
+// Lorenzo predictor over reconstructed neighbours with zero outside the block, walked in the
+// block's sequential (row-major) order. The previous plane (3D) / row (2D) sits in this
+// thread's shared-memory slots; the previous point's neighbours stay in registers.
+//   3D: pred = ((((((a + b) + c) - ab) - ac) - bc) + abc) with a = d[i-1,j,l],
+//       b = d[i,j-1,l], c = d[i,j,l-1], ab = d[i-1,j-1,l], ac = d[i-1,j,l-1],
+//       bc = d[i,j-1,l-1], abc = d[i-1,j-1,l-1].
+//   2D: pred = (d[j-1,l] + d[j,l-1]) - d[j-1,l-1].   1D: pred = d[l-1].
+template <typename V, int NDIM>
+struct Walker {
+  V* base;        // this thread's slot 0
+  uint32_t stride;
+  uint32_t B2;    // slots per plane row
+  uint32_t sr;    // first slot of the saved row (3D)
+  V a, b, ab;     // neighbours loaded for the current point
+  V ap, bp, abp, cp;  // the same at l-1, and the previous reconstructed value
+
+  __device__ __forceinline__ V& slot(uint32_t s) { return base[(size_t)s * stride]; }
+  __device__ __forceinline__ void row_start() { ap = bp = abp = cp = V(0); }
+
+  template <class Op>
+  __device__ __forceinline__ V combine() const {
+    if (NDIM == 3) {
+      V s = Op::add(a, b);
+      s = Op::add(s, cp);
+      s = Op::sub(s, ab);
+      s = Op::sub(s, ap);
+      s = Op::sub(s, bp);
+      return Op::add(s, abp);
+    } else if (NDIM == 2) {
+      V s = Op::add(a, cp);
+      return Op::sub(s, ap);
+    } else {
+      return cp;
+    }
+  }
+  __device__ __forceinline__ void load(uint32_t i, uint32_t j, uint32_t l) {
+    if (NDIM == 3) {
+      a = (i > 0) ? slot(j * B2 + l) : V(0);
+      b = (j > 0) ? slot((j - 1) * B2 + l) : V(0);
+      ab = (i > 0 && j > 0) ? slot(sr + l) : V(0);
+    } else if (NDIM == 2) {
+      a = (j > 0) ? slot(l) : V(0);
+    }
+  }
+  __device__ __forceinline__ void commit(uint32_t j, uint32_t l, V x) {
+    if (NDIM == 3) {
+      slot(sr + l) = a;
+      slot(j * B2 + l) = x;
+      ap = a;
+      bp = b;
+      abp = ab;
+    } else if (NDIM == 2) {
+      slot(l) = x;
+      ap = a;
+    }
+    cp = x;
+  }
+};
+
+template <typename T> struct OpRN {
+  __device__ static __forceinline__ T add(T a, T b) { return FT<T>::add(a, b); }
+  __device__ static __forceinline__ T sub(T a, T b) { return FT<T>::sub(a, b); }
+  __device__ static __forceinline__ T mul(T a, T b) { return FT<T>::mul(a, b); }
+};
+template <typename T> struct OpV {
+  __device__ static __forceinline__ T add(T a, T b) { return FT<T>::add_v(a, b); }
+  __device__ static __forceinline__ T sub(T a, T b) { return FT<T>::sub_v(a, b); }
+  __device__ static __forceinline__ T mul(T a, T b) { return FT<T>::mul_v(a, b); }
+};
+
+// Per-thread shared-memory slots the Lorenzo walk needs for a block shape.
+__host__ __device__ inline uint32_t walker_slots(int ndim, const uint32_t B[3]) {
+  if (ndim == 3) return B[1] * B[2] + B[2];
+  if (ndim == 2) return B[2];
+  return 0;
+}
+
+// Regression predictor ((b0*c0 + b1*c1) + b2*c2) + b_n over the block's own coordinates.
+template <typename V, int NDIM, class Op>
+__device__ __forceinline__ V regress(const V* c, uint32_t i, uint32_t j, uint32_t l) {
+  if (NDIM == 3) {
+    V acc = Op::mul(c[0], (V)i);
+    acc = Op::add(acc, Op::mul(c[1], (V)j));
+    acc = Op::add(acc, Op::mul(c[2], (V)l));
+    return Op::add(acc, c[3]);
+  } else if (NDIM == 2) {
+    V acc = Op::mul(c[0], (V)j);
+    acc = Op::add(acc, Op::mul(c[1], (V)l));
+    return Op::add(acc, c[2]);
+  } else {
+    V acc = Op::mul(c[0], (V)l);
+    return Op::add(acc, c[1]);
+  }
+}
+
+// Look up the first soft-error record of `site` for block b in a list sorted by block.
+__device__ __forceinline__ bool find_flip(const sdcsz_flip* f, uint32_t n, uint32_t site, uint64_t b,
+                                          uint64_t* index, uint32_t* bit) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (f[mid].block < b) lo = mid + 1;
+    else hi = mid;
+  }
+  for (uint32_t t = lo; t < n && f[t].block == b; ++t)
+    if (f[t].site == site) {
+      *index = f[t].index;
+      *bit = f[t].bit;
+      return true;
+    }
+  return false;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- host-side launchers
+struct Launch {
+  cudaStream_t stream;
+  int sms;
+};
+
+void launch_prep(const void* field, const Geo& g, const Ws& w, const Launch& L);
+void launch_predict(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+                    const Launch& L);
+void launch_flip_input(void* field, const Geo& g, const sdcsz_flip* flips, uint32_t nflips, const Ws& w,
+                       const Launch& L);
+void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips, const Launch& L);
+void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
+void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
+
+// Parsed stream header (host side) for the decoder.
+struct Hdr {
+  Geo g;
+  Layout L;
+  uint32_t n_live;
+  uint64_t n_reg, n_unpred, payload_bytes, total;
+  double eb;
+};
+void launch_decode(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
+                   const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                   const Launch& L);
+
+}  // namespace sdcsz
