@@ -326,7 +326,7 @@ int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t f
   int rc = parse_header(hb, nbytes, &h, nullptr);
   if (rc) return rc;
   const uint64_t need = h.g.N * (h.g.dtype ? 8 : 4);
-  if (write && (!d_field || field_bytes < need)) return d_field ? SDCSZ_ECAPACITY : SDCSZ_EINVAL;
+  if (write && need && (!d_field || field_bytes < need)) return d_field ? SDCSZ_ECAPACITY : SDCSZ_EINVAL;
   State* st = static_cast<State*>(d_ws);
   if (cudaMemsetAsync(st, 0, sizeof(State), s) != cudaSuccess) return SDCSZ_ECUDA;
   Launch L;

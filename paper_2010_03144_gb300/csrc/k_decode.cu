@@ -352,7 +352,7 @@ static void run_decode(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* fi
   while (threads > 64 && per * threads > 192 * 1024) threads >>= 1;
   const size_t smem = (4u << kLutBits) + per * threads;
   auto kern = k_decode<T, NDIM>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
   if (occ < 1) occ = 1;

@@ -273,7 +273,7 @@ static void run_predict(const void* field, const Geo& g, const Ws& w, const sdcs
   while (threads > 32 && (size_t)per * threads > 160 * 1024) threads >>= 1;
   const size_t smem = (size_t)per * threads;
   auto kern = k_predict<T, NDIM, ABFT>;
-  if (smem > 32 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
   if (occ < 1) occ = 1;
@@ -327,7 +327,9 @@ __global__ void k_flip_codes(Geo g, Ws w, const sdcsz_flip* flips, uint32_t n) {
     const Box x = block_box(g, flips[t].block);
     if (flips[t].index >= x.P) continue;
     uint16_t* c = w.codes + code_index(flips[t].block, g.P, (uint32_t)flips[t].index);
-    *c = (uint16_t)(*c ^ (1u << (flips[t].bit & 15)));
+    const uintptr_t a = reinterpret_cast<uintptr_t>(c);
+    const uint32_t shift = (a & 2) ? 16u : 0u;
+    atomicXor(reinterpret_cast<unsigned int*>(a & ~uintptr_t(3)), (1u << (flips[t].bit & 15)) << shift);
   }
 }
 

@@ -168,8 +168,7 @@ static void run_prep(const void* field, const Geo& g, const Ws& w, const Launch&
   const uint32_t threads = 128;
   const uint64_t grid = g.nb ? (g.nb + threads - 1) / threads : 1;
   const size_t smem = (g.predictor == 0) ? (size_t)walker_slots(g.ndim, g.B) * threads * sizeof(float) : 0;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_prep<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_prep<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_prep<T, NDIM><<<(unsigned)grid, threads, smem, L.stream>>>(static_cast<const T*>(field), g, w);
 }
 
