@@ -26,7 +26,8 @@
 //   * the input is verified/corrected before regression and sampling (the paper verifies
 //     before prediction only; verifying earlier keeps the output identical to a clean run);
 //   * regression: closed-form least squares on the block grid in fp32, sequential sums;
-//   * selection: all block points are the sample; E_lor adds kappa*eb per point;
+//   * selection: the sample is a set of whole rows (one diagonal row per plane in 3D, every
+//     fourth row in 2D); E_lor adds kappa*eb per sample point;
 //   * duplication recomputes once more on a mismatch and keeps the third result;
 //   * the histogram is taken as the codes are produced (before the bin-array window that
 //     the code checksums protect);
@@ -238,7 +239,10 @@ T regress(const T* coef, int ndim, const uint32_t coord3[3]) {
 
 // Closed-form least-squares fit on the regular block grid, in fp32 (Alg. 1 line 2).
 // Slopes decouple on a full grid: b_a = sum x*(c_a - ctr_a) / sum (c_a - ctr_a)^2, and the
-// intercept makes the fit pass through the mean. Sums run in increasing local order.
+// intercept makes the fit pass through the mean. Sums are taken per row along the fastest
+// axis first (r0 = sum x, rl = sum x*(l - ctr_l), in increasing l), then the row sums are
+// added into the block sums in increasing row order (S0 += r0, S_l += rl, S_a += r0*(c_a -
+// ctr_a) for the slower axes, whose coordinate is constant along a row).
 template <typename T>
 bool regression_coefficients(const T* v, const uint32_t e[3], int ndim, float coef[4]) {
   const int off = 3 - ndim;
@@ -251,17 +255,20 @@ bool regression_coefficients(const T* v, const uint32_t e[3], int ndim, float co
   }
   float S0 = 0.0f, S[3] = {0.0f, 0.0f, 0.0f};
   uint64_t k = 0;
+  const int fast = ndim - 1;  // index of the fastest axis among the active ones
   for (uint32_t i = 0; i < e[0]; ++i)
-    for (uint32_t j = 0; j < e[1]; ++j)
+    for (uint32_t j = 0; j < e[1]; ++j) {
+      float r0 = 0.0f, rl = 0.0f;
       for (uint32_t l = 0; l < e[2]; ++l, ++k) {
         float xr = (float)v[k];
-        uint32_t c3[3] = {i, j, l};
-        S0 = S0 + xr;
-        for (int a = 0; a < ndim; ++a) {
-          float t = (float)c3[off + a] - ctr[a];
-          S[a] = S[a] + xr * t;
-        }
+        r0 = r0 + xr;
+        rl = rl + xr * ((float)l - ctr[fast]);
       }
+      uint32_t c3[3] = {i, j, 0};
+      S0 = S0 + r0;
+      S[fast] = S[fast] + rl;
+      for (int a = 0; a < fast; ++a) S[a] = S[a] + r0 * ((float)c3[off + a] - ctr[a]);
+    }
   for (int a = 0; a < ndim; ++a) coef[a] = (e[off + a] > 1) ? S[a] / D[a] : 0.0f;
   float mean = S0 / (float)P;
   float acc = coef[0] * ctr[0];
@@ -272,7 +279,24 @@ bool regression_coefficients(const T* v, const uint32_t e[3], int ndim, float co
   return true;
 }
 
-// Selection estimates (Alg. 1 lines 6-7), in fp32 over all points of the block (the sample):
+// The sample of Alg. 1 line 7: whole rows along the fastest axis. 3D: one row per plane, the
+// "diagonal" rows (i, i mod e1); 2D: every fourth row starting with row 1 (rows 1, 5, 9, ...);
+// 1D: the whole block.
+bool sample_row(int ndim, uint32_t i, uint32_t j, const uint32_t e[3]) {
+  if (ndim == 3) return j == i % e[1];
+  if (ndim == 2) return (j & 3u) == 1u;
+  return true;
+}
+
+uint64_t sample_points(int ndim, const uint32_t e[3]) {
+  uint64_t n = 0;
+  for (uint32_t i = 0; i < e[0]; ++i)
+    for (uint32_t j = 0; j < e[1]; ++j)
+      if (sample_row(ndim, i, j, e)) n += e[2];
+  return n;
+}
+
+// Selection estimates (Alg. 1 lines 6-7), in fp32 over the sample points in local order:
 // E_reg = sum |x - f_reg|, E_lor = sum |x - Lorenzo(original values)|.
 template <typename T>
 void selection_estimates(const T* v, const uint32_t e[3], int ndim, const float coef[4], float* Ereg_out,
@@ -285,6 +309,7 @@ void selection_estimates(const T* v, const uint32_t e[3], int ndim, const float 
   for (uint32_t i = 0; i < e[0]; ++i)
     for (uint32_t j = 0; j < e[1]; ++j)
       for (uint32_t l = 0; l < e[2]; ++l, ++k) {
+        if (!sample_row(ndim, i, j, e)) continue;
         uint32_t c3[3] = {i, j, l};
         float f = regress<float>(coef, ndim, c3);
         Ereg = Ereg + std::fabs(xr[k] - f);
@@ -299,10 +324,10 @@ void selection_estimates(const T* v, const uint32_t e[3], int ndim, const float 
 // effect of predicting from reconstructed instead of original neighbours: kappa*eb per point,
 // kappa = E|sum of n uniform(-eb,eb)| / eb for the n = 1, 3, 7 Lorenzo terms of 1D/2D/3D
 // (normal approximation for 2D/3D).
-bool select_regression(float Ereg, float Elor, uint64_t P, int ndim, float ebf) {
+bool select_regression(float Ereg, float Elor, uint64_t S, int ndim, float ebf) {
   static const float kappa[4] = {0.0f, 0.5f, 0.80f, 1.22f};
   float noise = kappa[ndim] * ebf;
-  float total = Elor + (float)P * noise;
+  float total = Elor + (float)S * noise;
   return Ereg < total;
 }
 
@@ -365,11 +390,11 @@ Prep prepare_block(const Ctx& c, const T* field, uint64_t b) {
   return pr;
 }
 
-bool indicator_of(const Ctx& c, const Prep& pr, uint64_t P, float ebf) {
+bool indicator_of(const Ctx& c, const Prep& pr, const uint32_t e[3], float ebf) {
   if (!pr.finite) return false;
   if (c.predictor_mode == 2) return true;
   if (c.predictor_mode == 1) return false;
-  return select_regression(pr.Ereg, pr.Elor, P, c.g.ndim, ebf);
+  return select_regression(pr.Ereg, pr.Elor, sample_points(c.g.ndim, e), c.g.ndim, ebf);
 }
 
 // Alg. 1 lines 10-31 for one block: verify the input (line 11), pick f() from the indicator
@@ -395,7 +420,7 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
       for (uint64_t p = 0; p < P; ++p) v[p] = Bits<T>::from_words(&w[p * W]);
   }
 
-  const bool use_reg = indicator_of(c, pr, P, (float)eb);
+  const bool use_reg = indicator_of(c, pr, e, (float)eb);
   out->regression = use_reg;
   for (int a = 0; a < 4; ++a) out->coef[a] = (T)pr.coef[a];
   for (int a = 0; a <= g.ndim; ++a) {

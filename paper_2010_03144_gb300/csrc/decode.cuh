@@ -1,0 +1,837 @@
+// K5: fault-tolerant decompression (Alg. 2 of the paper, without the Zstd stage).
+//
+// Persistent CTAs, each taking whole random-access groups of 256 blocks; one thread per
+// block. A CTA builds a 12-bit first-level decode table for the canonical Huffman code in
+// shared memory (longer codes resolve through the canonical first-code table), scans the
+// group's block table for per-block offsets and checks the group table against it. Each
+// thread then decodes its block and reconstructs it with the Lorenzo or regression predictor
+// (lines 2-9). For fault-tolerant streams the block's checksum is compared with sum_dc
+// (lines 11-13); on a mismatch the block is decompressed once more from its compressed bytes
+// (line 14) and reported corrected (line 17) or as an SDC (line 19).
+// As in compression, full blocks of the common shapes take a fast kernel with compile-time
+// edges and edge blocks a generic kernel.
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+
+#include "sdcsz_internal.cuh"
+
+namespace sdcsz {
+namespace kdec {
+namespace {
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+struct Canon {
+  uint32_t fc[kMaxLen + 2];  // first code of each length
+  uint32_t fi[kMaxLen + 2];  // canonical index of that first code
+  uint32_t nc[kMaxLen + 2];  // codes of each length
+};
+
+__device__ __forceinline__ unsigned long long ld_u64(const uint8_t* p) {
+  return *reinterpret_cast<const unsigned long long*>(p);
+}
+
+__device__ __forceinline__ void mad_wide(unsigned long long& acc, uint32_t a, uint32_t b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+template <typename T>
+__device__ __forceinline__ void sum_words(T v, unsigned long long& sum) {
+  mad_wide(sum, FT<T>::lo(v), 1u);
+  if (FT<T>::W == 2) mad_wide(sum, FT<T>::hi(v), 1u);
+}
+
+// Long codes (> 12 bits) through the canonical tables; returns the symbol or -1.
+__device__ __noinline__ int slow_symbol(unsigned long long buf, const Canon& cn, const uint16_t* syms,
+                                        uint32_t n_live, uint32_t* len_out) {
+  for (uint32_t l = kLutBits + 1; l <= (uint32_t)kMaxLen; ++l) {
+    const uint32_t c = (uint32_t)(buf >> (64 - l));
+    if (c - cn.fc[l] < cn.nc[l]) {
+      const uint32_t r = cn.fi[l] + (c - cn.fc[l]);
+      if (r >= n_live) return -1;
+      *len_out = l;
+      return syms[r];
+    }
+  }
+  return -1;
+}
+
+// MSB-first bit reader fed by aligned 32-bit words; never reads at or past `lim`.
+struct BitReader {
+  const uint8_t* wp;   // next aligned word
+  const uint8_t* lim;  // end of the stream
+  unsigned long long buf;
+  int nb;
+  uint32_t used;
+  __device__ __forceinline__ uint32_t word() {
+    uint32_t w;
+    if (wp + 4 <= lim) {
+      w = __byte_perm(__ldg(reinterpret_cast<const uint32_t*>(wp)), 0, 0x0123);
+    } else {
+      w = 0;
+      for (int q = 0; q < 4; ++q) w |= (wp + q < lim ? (uint32_t)wp[q] : 0u) << (24 - 8 * q);
+    }
+    wp += 4;
+    return w;
+  }
+  __device__ __forceinline__ void init(const uint8_t* p, const uint8_t* end) {
+    lim = end;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    wp = reinterpret_cast<const uint8_t*>(a & ~uintptr_t(3));
+    const int skip = (int)(a & 3) * 8;
+    buf = (unsigned long long)word() << 32;
+    buf |= word();
+    buf <<= skip;
+    nb = 64 - skip;
+    used = 0;
+  }
+  // next symbol, or -1 for an invalid code
+  __device__ __forceinline__ int next(const uint32_t* lut, const Canon& cn, const uint16_t* syms, uint32_t n_live) {
+    if (nb <= 32) {
+      buf |= (unsigned long long)word() << (32 - nb);
+      nb += 32;
+    }
+    const uint32_t e = lut[buf >> (64 - kLutBits)];
+    uint32_t len = e & 0xffu;
+    int sym;
+    if (len) {
+      sym = (int)(e >> 8);
+    } else {
+      sym = slow_symbol(buf, cn, syms, n_live, &len);
+      if (sym < 0) return -1;
+    }
+    buf <<= len;
+    nb -= (int)len;
+    used += len;
+    return sym;
+  }
+};
+
+// Unchecked variant for payloads that end at least 8 bytes before the stream's last whole
+// word: the refill is predicated instead of branched (lanes refill at different symbols).
+struct FastReader {
+  const uint32_t* wp;
+  unsigned long long buf;
+  int nb;
+  uint32_t used;
+  __device__ __forceinline__ void init(const uint8_t* p) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    wp = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+    const int skip = (int)(a & 3) * 8;
+    buf = ((unsigned long long)__byte_perm(__ldg(wp), 0, 0x0123) << 32) | __byte_perm(__ldg(wp + 1), 0, 0x0123);
+    wp += 2;
+    buf <<= skip;
+    nb = 64 - skip;
+    used = 0;
+  }
+  __device__ __forceinline__ int next(const uint32_t* lut, const Canon& cn, const uint16_t* syms, uint32_t n_live) {
+    const bool need = nb <= 32;
+    const uint32_t w = __byte_perm(__ldg(wp), 0, 0x0123);
+    buf |= need ? ((unsigned long long)w << (32 - nb)) : 0ull;
+    wp += need ? 1 : 0;
+    nb += need ? 32 : 0;
+    const uint32_t e = lut[buf >> (64 - kLutBits)];
+    uint32_t len = e & 0xffu;
+    int sym = (int)(e >> 8);
+    if (!len) {
+      sym = slow_symbol(buf, cn, syms, n_live, &len);
+      if (sym < 0) return -1;
+    }
+    buf <<= len;
+    nb -= (int)len;
+    used += len;
+    return sym;
+  }
+};
+
+struct BlockIn {
+  uint64_t b, pay_off, un_off;
+  uint32_t size, ucnt;
+  int64_t reg_idx;
+};
+
+struct Tables {
+  const uint32_t* lut;
+  const Canon* cn;
+  const uint16_t* syms;
+  uint32_t n_live;
+};
+
+// ---------------------------------------------------------------- generic path
+template <typename T, int NDIM>
+__device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const uint8_t* lim, const Hdr& h,
+                                            const BlockIn& bi, const Tables& tb, Walker<T, NDIM>& wk,
+                                            T* __restrict__ field, const T* __restrict__ orig, uint32_t kinj,
+                                            uint32_t bitinj, unsigned long long* sum_out, unsigned long long* viol,
+                                            double* maxerr) {
+  const Geo& g = h.g;
+  const Box x = block_box(g, bi.b);
+  const T eb = (T)h.eb;
+  T cT[4] = {T(0), T(0), T(0), T(0)};
+  const bool reg = bi.reg_idx >= 0;
+  if (reg) {
+    const T* c = reinterpret_cast<const T*>(s + h.L.coef) + (uint64_t)(NDIM + 1) * bi.reg_idx;
+    for (int a = 0; a <= NDIM; ++a) cT[a] = c[a];
+  }
+  const T* un = reinterpret_cast<const T*>(s + h.L.unpred) + bi.un_off;
+  BitReader br;
+  br.init(s + h.L.payload + bi.pay_off, lim);
+  bool ok = true;
+  uint32_t used_u = 0, k = 0;
+  unsigned long long sum = 0, nv = 0;
+  double me = 0.0;
+  for (uint32_t i = 0; i < x.e[0]; ++i) {
+    for (uint32_t j = 0; j < x.e[1]; ++j) {
+      const uint64_t rb = row_base(g, x, i, j);
+      wk.row_start();
+      for (uint32_t l = 0; l < x.e[2]; ++l, ++k) {
+        const int q = ok ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : -1;
+        T xr = T(0);
+        if (!reg) wk.load(i, j, l);
+        if (q < 0 || (uint32_t)q >= g.bins) {
+          ok = false;
+        } else if (q == 0) {
+          if (used_u < bi.ucnt) xr = un[used_u];
+          else ok = false;
+          ++used_u;
+        } else {
+          const T pred = reg ? regress<T, NDIM, OpRN<T>>(cT, i, j, l) : wk.template combine<OpRN<T>>();
+          xr = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - (int)g.R)), eb));
+        }
+        if (k == kinj) xr = FT<T>::flip(xr, bitinj);
+        if (!reg) wk.commit(j, l, xr);
+        if (field) field[rb + l] = xr;
+        if (orig) {
+          const T xo = orig[rb + l];
+          bool bad;
+          if (FT<T>::finite(xo)) {
+            const T d = FT<T>::absv(FT<T>::sub(xo, xr));
+            bad = !(d <= eb);
+            if (!bad) me = fmax(me, (double)d);
+          } else {
+            bad = !FT<T>::same(xo, xr);
+          }
+          nv += bad;
+        }
+        sum_words<T>(xr, sum);
+      }
+    }
+  }
+  if (used_u != bi.ucnt || br.used > bi.size * 8u) ok = false;
+  *sum_out = sum;
+  *viol = nv;
+  *maxerr = me;
+  return ok;
+}
+
+// ---------------------------------------------------------------- fast path (full blocks)
+template <typename T, int NDIM, int B0, int B1, int B2, bool REG, bool HOOK>
+__device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const uint8_t* lim, const Hdr& h,
+                                            const BlockIn& bi, const Tables& tb, T* plane, T* __restrict__ blk_out,
+                                            const T* __restrict__ blk_orig, uint64_t si, uint64_t sj, bool vec2,
+                                            uint32_t kinj, uint32_t bitinj, unsigned long long* sum_out,
+                                            unsigned long long* viol, double* maxerr) {
+  const Geo& g = h.g;
+  const T eb = (T)h.eb;
+  const int R = (int)g.R;
+  T cT[4] = {T(0), T(0), T(0), T(0)};
+  if (REG) {
+    const T* c = reinterpret_cast<const T*>(s + h.L.coef) + (uint64_t)(NDIM + 1) * bi.reg_idx;
+#pragma unroll
+    for (int a = 0; a <= NDIM; ++a) cT[a] = c[a];
+  }
+  const T* un = reinterpret_cast<const T*>(s + h.L.unpred) + bi.un_off;
+  FastReader br;
+  br.init(s + h.L.payload + bi.pay_off);
+  (void)lim;
+  bool ok = true;
+  uint32_t used_u = 0;
+  unsigned long long sum = 0, nv = 0;
+  double me = 0.0;
+  if (!REG && NDIM == 3) {
+#pragma unroll
+    for (int q = 0; q < B1 * B2; ++q) plane[q * 256] = T(0);
+  }
+  T brow[B2], arow[B2];
+#pragma unroll 1
+  for (int i = 0; i < B0; ++i) {
+#pragma unroll
+    for (int l = 0; l < B2; ++l) {
+      brow[l] = T(0);
+      arow[l] = T(0);
+    }
+#pragma unroll 1
+    for (int j = 0; j < B1; ++j) {
+      T ra = T(0);
+      if (REG) {
+        if (NDIM == 3) ra = FT<T>::add(FT<T>::mul(cT[0], (T)i), FT<T>::mul(cT[1], (T)j));
+        else ra = FT<T>::mul(cT[0], (T)j);
+      }
+      T* prow = plane + j * B2 * 256;
+      T out[B2];
+      T c = T(0), ac = T(0), bc = T(0), abc = T(0);
+      const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
+#pragma unroll
+      for (int l = 0; l < B2; ++l) {
+        const int q = br.next(tb.lut, *tb.cn, tb.syms, tb.n_live);
+        T a = T(0), bb = T(0), ab = T(0);
+        if (!REG) {
+          if (NDIM == 3) {
+            a = prow[l * 256];
+            bb = brow[l];
+            ab = arow[l];
+          } else {
+            a = brow[l];
+          }
+        }
+        T pred;
+        if (REG) {
+          const int lc = NDIM == 3 ? 2 : 1;
+          pred = FT<T>::add(FT<T>::add(ra, FT<T>::mul(cT[lc], (T)l)), cT[lc + 1]);
+        } else if (NDIM == 3) {
+          T sacc = FT<T>::add(a, bb);
+          sacc = FT<T>::add(sacc, c);
+          sacc = FT<T>::sub(sacc, ab);
+          sacc = FT<T>::sub(sacc, ac);
+          sacc = FT<T>::sub(sacc, bc);
+          pred = FT<T>::add(sacc, abc);
+        } else {
+          pred = FT<T>::sub(FT<T>::add(a, c), ac);
+        }
+        const T xv = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
+        const bool isu = q == 0, has_u = used_u < bi.ucnt;
+        T uval = T(0);
+        if (isu && has_u) uval = un[used_u];
+        const bool okq = q > 0 && (uint32_t)q < g.bins;
+        T xr = okq ? xv : uval;
+        ok = ok && (okq || (isu && has_u));
+        used_u += isu ? 1u : 0u;
+        if (HOOK && k0 + l == kinj) xr = FT<T>::flip(xr, bitinj);
+        if (!REG) {
+          if (NDIM == 3) {
+            prow[l * 256] = xr;
+            arow[l] = a;
+            ac = a;
+            bc = bb;
+            abc = ab;
+          } else {
+            ac = a;
+          }
+          brow[l] = xr;
+          c = xr;
+        }
+        out[l] = xr;
+        sum_words<T>(xr, sum);
+      }
+      const uint64_t ro = (uint64_t)i * si + (uint64_t)j * sj;
+      if (blk_out) {
+        if ((B2 % 2) == 0 && vec2) {
+          typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type V2;
+          V2* p = reinterpret_cast<V2*>(blk_out + ro);
+#pragma unroll
+          for (int l = 0; l < B2 / 2; ++l) {
+            V2 t;
+            t.x = out[2 * l];
+            t.y = out[2 * l + 1];
+            p[l] = t;
+          }
+        } else {
+#pragma unroll
+          for (int l = 0; l < B2; ++l) blk_out[ro + l] = out[l];
+        }
+      }
+      if (blk_orig) {
+#pragma unroll
+        for (int l = 0; l < B2; ++l) {
+          const T xo = blk_orig[ro + l];
+          bool bad;
+          if (FT<T>::finite(xo)) {
+            const T d = FT<T>::absv(FT<T>::sub(xo, out[l]));
+            bad = !(d <= eb);
+            if (!bad) me = fmax(me, (double)d);
+          } else {
+            bad = !FT<T>::same(xo, out[l]);
+          }
+          nv += bad;
+        }
+      }
+    }
+  }
+  if (used_u != bi.ucnt || br.used > bi.size * 8u) ok = false;
+  *sum_out = sum;
+  *viol = nv;
+  *maxerr = me;
+  return ok;
+}
+
+// ---------------------------------------------------------------- CTA set-up and group scan
+struct Smem {
+  Canon cn;
+  uint32_t sz[kGroup], uc[kGroup], rg[kGroup];
+  unsigned long long off[kGroup][3];
+  unsigned long long wt[8][3];
+  int bad;
+};
+
+// Canonical tables (validated) and the first-level decode table; false for a bad code table.
+__device__ bool cta_tables(const uint8_t* s, const Hdr& h, Smem& sm, uint32_t* lut, const uint16_t* syms,
+                           State* st) {
+  if (threadIdx.x == 0) {
+    const uint32_t* blc = reinterpret_cast<const uint32_t*>(s + h.L.table);
+    unsigned long long kraft = 0, total = 0;
+    uint32_t code = 0, idx = 0;
+    int bad = blc[0] != 0;
+    for (uint32_t l = 1; l <= (uint32_t)kMaxLen; ++l) {
+      const uint32_t c = blc[l];
+      code = (code + (l >= 2 ? sm.cn.nc[l - 1] : 0u)) << 1;
+      sm.cn.fc[l] = code;
+      sm.cn.fi[l] = idx;
+      sm.cn.nc[l] = c;
+      idx += c;
+      kraft += (unsigned long long)c << (kMaxLen - l);
+      total += c;
+    }
+    if (total != h.n_live || kraft > (1ull << kMaxLen)) bad = 1;
+    sm.bad = bad;
+    if (bad) atomicOr(&st->error, ERR_FORMAT);
+  }
+  __syncthreads();
+  if (sm.bad) return false;
+  for (uint32_t e = threadIdx.x; e < (1u << kLutBits); e += blockDim.x) {
+    uint32_t v = 0;
+    for (uint32_t l = 1; l <= (uint32_t)kLutBits; ++l) {
+      const uint32_t c = e >> (kLutBits - l);
+      if (c - sm.cn.fc[l] < sm.cn.nc[l]) {
+        const uint32_t r = sm.cn.fi[l] + (c - sm.cn.fc[l]);
+        const uint32_t sym = r < h.n_live ? syms[r] : 0u;
+        v = (sym << 8) | l;
+        break;
+      }
+    }
+    lut[e] = v;
+  }
+  return true;
+}
+
+// Offsets of the group's blocks; false (and a format error) when the stored group bases
+// disagree with the block table.
+__device__ bool group_scan(const uint8_t* s, const Hdr& h, uint64_t gid, uint64_t ngroups, Smem& sm, State* st) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const Geo& g = h.g;
+  const uint64_t b0 = gid * kGroup;
+  const uint32_t nblk = (uint32_t)min((uint64_t)kGroup, g.nb - b0);
+  __syncthreads();
+  for (uint32_t t = tid; t < kGroup; t += blockDim.x) {
+    const uint64_t b = b0 + t;
+    const bool in = t < nblk;
+    sm.sz[t] = in ? *reinterpret_cast<const uint16_t*>(s + h.L.sizes + 2 * b) : 0u;
+    sm.uc[t] = in ? *reinterpret_cast<const uint16_t*>(s + h.L.ucounts + 2 * b) : 0u;
+    sm.rg[t] = in ? ((*reinterpret_cast<const uint32_t*>(s + h.L.bitmap + 4 * (b / 32)) >> (b % 32)) & 1u) : 0u;
+  }
+  __syncthreads();
+  const uint32_t R = kGroup / blockDim.x;
+  unsigned long long loc[3] = {0, 0, 0};
+  for (uint32_t r = 0; r < R; ++r) {
+    const uint32_t e = tid * R + r;
+    loc[0] += sm.sz[e];
+    loc[1] += sm.uc[e];
+    loc[2] += sm.rg[e];
+  }
+  unsigned long long inc[3] = {loc[0], loc[1], loc[2]};
+  for (int o = 1; o < 32; o <<= 1)
+    for (int q = 0; q < 3; ++q) {
+      const unsigned long long n = __shfl_up_sync(0xffffffffu, inc[q], o);
+      if (lane >= (uint32_t)o) inc[q] += n;
+    }
+  if (lane == 31)
+    for (int q = 0; q < 3; ++q) sm.wt[wid][q] = inc[q];
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long run[3] = {0, 0, 0};
+    for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2)
+      for (int q = 0; q < 3; ++q) {
+        const unsigned long long t = sm.wt[w2][q];
+        sm.wt[w2][q] = run[q];
+        run[q] += t;
+      }
+    const uint8_t* gp = s + h.L.groups + 24 * gid;
+    unsigned long long base[3] = {ld_u64(gp), ld_u64(gp + 8), ld_u64(gp + 16)}, next[3];
+    if (gid + 1 < ngroups) {
+      next[0] = ld_u64(gp + 24);
+      next[1] = ld_u64(gp + 32);
+      next[2] = ld_u64(gp + 40);
+    } else {
+      next[0] = h.payload_bytes;
+      next[1] = h.n_unpred;
+      next[2] = h.n_reg;
+    }
+    int bad = 0;
+    for (int q = 0; q < 3; ++q) bad |= (base[q] + run[q] != next[q]) || (gid == 0 && base[q] != 0);
+    sm.bad = bad;
+    if (bad) atomicOr(&st->error, ERR_FORMAT);
+    for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2)
+      for (int q = 0; q < 3; ++q) sm.wt[w2][q] += base[q];
+  }
+  __syncthreads();
+  unsigned long long run[3];
+  for (int q = 0; q < 3; ++q) run[q] = sm.wt[wid][q] + inc[q] - loc[q];
+  for (uint32_t r = 0; r < R; ++r) {
+    const uint32_t e = tid * R + r;
+    sm.off[e][0] = run[0];
+    sm.off[e][1] = run[1];
+    sm.off[e][2] = run[2];
+    run[0] += sm.sz[e];
+    run[1] += sm.uc[e];
+    run[2] += sm.rg[e];
+  }
+  __syncthreads();
+  return !sm.bad;
+}
+
+struct Acc {
+  unsigned long long fix = 0, bad = 0, viol = 0;
+  double maxerr = 0.0;
+  __device__ __forceinline__ void commit(State* st) {
+    fix = warp_sum(fix);
+    bad = warp_sum(bad);
+    viol = warp_sum(viol);
+    for (int o = 16; o > 0; o >>= 1) maxerr = fmax(maxerr, __shfl_xor_sync(0xffffffffu, maxerr, o));
+    if ((threadIdx.x & 31) == 0) {
+      if (fix) atomicAdd(&st->reexec_corrected, fix);
+      if (bad) atomicAdd(&st->uncorrectable, bad);
+      if (viol) atomicAdd(&st->bound_viol, viol);
+      if (maxerr > 0.0) atomicMax(&st->max_err_bits, (unsigned long long)__double_as_longlong(maxerr));
+    }
+  }
+};
+
+__device__ __forceinline__ bool is_full(const Geo& g, uint64_t b) {
+  const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
+  const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+  return (c0 + 1) * g.B[0] <= g.d[0] && (c1 + 1) * g.B[1] <= g.d[1] && (c2 + 1) * g.B[2] <= g.d[2];
+}
+
+// Alg. 2 lines 11-22 around one decode: verify against sum_dc, re-execute once.
+template <class F>
+__device__ __forceinline__ uint8_t verify_block(const uint8_t* s, const Hdr& h, uint64_t b, F run, Acc& acc) {
+  unsigned long long sum = 0, nv = 0;
+  double me = 0.0;
+  bool ok = run(true, &sum, &nv, &me);
+  uint8_t stv = SDCSZ_BLOCK_OK;
+  if (h.g.abft) {
+    const unsigned long long ref = ld_u64(s + h.L.sumdc + 8 * b);
+    if (!ok || sum != ref) {
+      ok = run(false, &sum, &nv, &me);  // line 14: decompress this block again
+      if (ok && sum == ref) {
+        stv = SDCSZ_BLOCK_CORRECTED;
+        ++acc.fix;
+      } else {
+        stv = ok ? SDCSZ_BLOCK_SDC : SDCSZ_BLOCK_BAD;
+        ++acc.bad;
+      }
+    }
+  } else if (!ok) {
+    stv = SDCSZ_BLOCK_BAD;
+    ++acc.bad;
+  }
+  acc.viol += nv;
+  acc.maxerr = fmax(acc.maxerr, me);
+  return stv;
+}
+
+__device__ __forceinline__ void find_inj(const sdcsz_flip* flips, uint32_t nflips, uint64_t b, uint32_t* k,
+                                         uint32_t* bit) {
+  *k = kNone;
+  *bit = 0;
+  uint64_t idx;
+  if (nflips && find_flip(flips, nflips, SDCSZ_SITE_DECOMP, b, &idx, bit)) *k = (uint32_t)min(idx, (uint64_t)kNone - 1);
+}
+
+// Generic kernel: edge blocks (or all blocks when `all`).
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
+                                                uint8_t* status, const T* orig, State* st,
+                                                const sdcsz_flip* __restrict__ flips, uint32_t nflips, int all) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Smem sm;
+  uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
+  const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
+  if (!cta_tables(s, h, sm, lut, syms, st)) return;
+  const Tables tb = {lut, &sm.cn, syms, h.n_live};
+  const uint8_t* lim = s + nbytes;
+  Walker<T, NDIM> wk;
+  wk.base = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
+  wk.stride = blockDim.x;
+  wk.B2 = h.g.B[2];
+  wk.sr = h.g.B[1] * h.g.B[2];
+  const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
+  Acc acc;
+  for (uint64_t gid = blockIdx.x; gid < ngroups; gid += gridDim.x) {
+    const uint64_t b0 = gid * kGroup;
+    const uint32_t nblk = (uint32_t)min((uint64_t)kGroup, h.g.nb - b0);
+    if (!all) {
+      // skip groups without edge blocks
+      int any = 0;
+      for (uint32_t t = threadIdx.x; t < nblk; t += blockDim.x) any |= !is_full(h.g, b0 + t);
+      if (!__syncthreads_or(any)) continue;
+    }
+    if (!group_scan(s, h, gid, ngroups, sm, st)) {
+      if (status)
+        for (uint32_t t = threadIdx.x; t < nblk; t += blockDim.x) status[b0 + t] = SDCSZ_BLOCK_BAD;
+      continue;
+    }
+    for (uint32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
+      const uint64_t b = b0 + t;
+      if (!all && is_full(h.g, b)) continue;
+      BlockIn bi;
+      bi.b = b;
+      bi.pay_off = sm.off[t][0];
+      bi.un_off = sm.off[t][1];
+      bi.reg_idx = sm.rg[t] ? (int64_t)sm.off[t][2] : -1;
+      bi.size = sm.sz[t];
+      bi.ucnt = sm.uc[t];
+      uint32_t kinj, bitinj;
+      find_inj(flips, nflips, b, &kinj, &bitinj);
+      const uint8_t stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv,
+                                                     double* me) {
+        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, field, orig, first ? kinj : kNone, bitinj, sum, nv, me);
+      }, acc);
+      if (status) status[b] = stv;
+    }
+  }
+  acc.commit(st);
+}
+
+// Edge blocks after the fast kernel: one thread per edge block, enumerated compactly; offsets
+// from the stored group base plus the block table of the group up to the block.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_decode_edges(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
+                                                      uint8_t* status, const T* orig, State* st,
+                                                      const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                      uint64_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Smem sm;
+  uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
+  const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
+  if (!cta_tables(s, h, sm, lut, syms, st)) return;
+  const Tables tb = {lut, &sm.cn, syms, h.n_live};
+  const uint8_t* lim = s + nbytes;
+  Walker<T, NDIM> wk;
+  wk.base = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
+  wk.stride = blockDim.x;
+  wk.B2 = h.g.B[2];
+  wk.sr = h.g.B[1] * h.g.B[2];
+  Acc acc;
+  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) {
+    const Geo& g = h.g;
+    const uint64_t b = edge_block(g, e);
+    const uint64_t gid = b / kGroup;
+    const uint8_t* gp = s + h.L.groups + 24 * gid;
+    unsigned long long pay = ld_u64(gp), un = ld_u64(gp + 8), rg = ld_u64(gp + 16);
+    for (uint64_t q = gid * kGroup; q < b; ++q) {
+      pay += *reinterpret_cast<const uint16_t*>(s + h.L.sizes + 2 * q);
+      un += *reinterpret_cast<const uint16_t*>(s + h.L.ucounts + 2 * q);
+      rg += (*reinterpret_cast<const uint32_t*>(s + h.L.bitmap + 4 * (q / 32)) >> (q % 32)) & 1u;
+    }
+    BlockIn bi;
+    bi.b = b;
+    bi.pay_off = pay;
+    bi.un_off = un;
+    bi.size = *reinterpret_cast<const uint16_t*>(s + h.L.sizes + 2 * b);
+    bi.ucnt = *reinterpret_cast<const uint16_t*>(s + h.L.ucounts + 2 * b);
+    const bool reg = (*reinterpret_cast<const uint32_t*>(s + h.L.bitmap + 4 * (b / 32)) >> (b % 32)) & 1u;
+    bi.reg_idx = reg ? (int64_t)rg : -1;
+    uint8_t stv;
+    if (pay + bi.size > h.payload_bytes || un + bi.ucnt > h.n_unpred || (reg && rg >= h.n_reg)) {
+      atomicOr(&st->error, ERR_FORMAT);
+      stv = SDCSZ_BLOCK_BAD;
+      ++acc.bad;
+    } else {
+      uint32_t kinj, bitinj;
+      find_inj(flips, nflips, b, &kinj, &bitinj);
+      stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv, double* me) {
+        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, field, orig, first ? kinj : kNone, bitinj, sum, nv, me);
+      }, acc);
+    }
+    if (status) status[b] = stv;
+  }
+  acc.commit(st);
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2, bool HOOK>
+__device__ __forceinline__ bool fast_dispatch(bool reg, const uint8_t* s, const uint8_t* lim, const Hdr& h,
+                                              const BlockIn& bi, const Tables& tb, T* plane, T* out, const T* org,
+                                              uint64_t si, uint64_t sj, bool vec2, uint32_t kinj, uint32_t bitinj,
+                                              unsigned long long* sum, unsigned long long* nv, double* me) {
+  if (reg)
+    return decode_fast<T, NDIM, B0, B1, B2, true, HOOK>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj, bitinj,
+                                                        sum, nv, me);
+  return decode_fast<T, NDIM, B0, B1, B2, false, HOOK>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj, bitinj,
+                                                       sum, nv, me);
+}
+
+// Fast kernel: full blocks of a compile-time shape.
+template <typename T, int NDIM, int B0, int B1, int B2>
+__global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
+                                                     uint8_t* status, const T* orig, State* st,
+                                                     const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                     int vec2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Smem sm;
+  uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
+  const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
+  if (!cta_tables(s, h, sm, lut, syms, st)) return;
+  const Tables tb = {lut, &sm.cn, syms, h.n_live};
+  const uint8_t* lim = s + nbytes;
+  T* plane = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
+  Walker<T, NDIM> wk;  // for the few blocks that take the generic decoder
+  wk.base = plane;
+  wk.stride = blockDim.x;
+  wk.B2 = B2;
+  wk.sr = B1 * B2;
+  const Geo& g = h.g;
+  const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
+  const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
+  Acc acc;
+  for (uint64_t gid = blockIdx.x; gid < ngroups; gid += gridDim.x) {
+    const uint64_t b0 = gid * kGroup;
+    const uint32_t nblk = (uint32_t)min((uint64_t)kGroup, g.nb - b0);
+    if (!group_scan(s, h, gid, ngroups, sm, st)) {
+      if (status)
+        for (uint32_t t = threadIdx.x; t < nblk; t += blockDim.x) status[b0 + t] = SDCSZ_BLOCK_BAD;
+      continue;
+    }
+    for (uint32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
+      const uint64_t b = b0 + t;
+      const uint64_t c2 = b % g.nbd[2], tq = b / g.nbd[2];
+      const uint64_t c1 = tq % g.nbd[1], c0 = tq / g.nbd[1];
+      if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) continue;
+      const uint64_t bo = (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
+      T* out = field ? field + bo : nullptr;
+      const T* org = orig ? orig + bo : nullptr;
+      BlockIn bi;
+      bi.b = b;
+      bi.pay_off = sm.off[t][0];
+      bi.un_off = sm.off[t][1];
+      const bool reg = sm.rg[t] != 0;
+      bi.reg_idx = reg ? (int64_t)sm.off[t][2] : -1;
+      bi.size = sm.sz[t];
+      bi.ucnt = sm.uc[t];
+      uint32_t kinj, bitinj;
+      find_inj(flips, nflips, b, &kinj, &bitinj);
+      // The unchecked reader consumes at most 24 bits per point whatever the data, reads at
+      // most 12 bytes ahead of what it consumed and starts up to 3 bytes early; blocks whose
+      // worst case could reach the end of the stream take the bounds-checked reader.
+      const bool safe = (uint64_t)(lim - (s + h.L.payload)) >= bi.pay_off + 3ull * (B0 * B1 * B2) + 16;
+      const uint8_t stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv,
+                                                     double* me) {
+        if (!safe)
+          return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, field, orig, first ? kinj : kNone, bitinj, sum, nv,
+                                         me);
+        if (first && kinj != kNone)
+          return fast_dispatch<T, NDIM, B0, B1, B2, true>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj,
+                                                          bitinj, sum, nv, me);
+        return fast_dispatch<T, NDIM, B0, B1, B2, false>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kNone,
+                                                         0, sum, nv, me);
+      }, acc);
+      if (status) status[b] = stv;
+    }
+  }
+  acc.commit(st);
+}
+
+// ---------------------------------------------------------------- launch
+template <class K>
+inline unsigned persistent_grid(K kern, uint32_t threads, size_t smem, uint64_t ngroups, const Launch& L) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
+  if (occ < 1) occ = 1;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ngroups, (uint64_t)occ * L.sms));
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2>
+void run_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
+              const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
+  const size_t smem = (4u << kLutBits) + (size_t)walker_slots(NDIM, h.g.B) * 256 * sizeof(T);
+  auto kern = k_decode_fast<T, NDIM, B0, B1, B2>;
+  const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
+  const unsigned grid = persistent_grid(kern, 256, smem, ngroups, L);
+  const uintptr_t al = 2 * sizeof(T);
+  const bool vec2 = (B2 % 2 == 0) && (h.g.d[2] % 2 == 0) && (reinterpret_cast<uintptr_t>(field) % al == 0);
+  kern<<<grid, 256, smem, L.stream>>>(s, nbytes, h, field, status, orig, st, flips, nflips, vec2 ? 1 : 0);
+}
+
+template <typename T>
+bool try_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
+              const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
+  const Geo& g = h.g;
+  // a 3D 16^3 float64 plane would not fit 256 threads' shared memory: generic path
+  if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2]) {
+    switch (g.B[2]) {
+      case 4: run_fast<T, 3, 4, 4, 4>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      case 6: run_fast<T, 3, 6, 6, 6>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      case 8: run_fast<T, 3, 8, 8, 8>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      case 10:
+        if (sizeof(T) == 8) return false;
+        run_fast<T, 3, 10, 10, 10>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
+        return true;
+      case 12:
+        if (sizeof(T) == 8) return false;
+        run_fast<T, 3, 12, 12, 12>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
+        return true;
+      default: return false;
+    }
+  }
+  if (g.ndim == 2 && g.B[1] == g.B[2]) {
+    switch (g.B[2]) {
+      case 8: run_fast<T, 2, 1, 8, 8>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      case 12: run_fast<T, 2, 1, 12, 12>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      case 16: run_fast<T, 2, 1, 16, 16>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
+template <typename T, int NDIM>
+void run_generic(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
+                 const sdcsz_flip* flips, uint32_t nflips, bool all, const Launch& L) {
+  const size_t per = (size_t)walker_slots(h.g.ndim, h.g.B) * sizeof(T);
+  uint32_t threads = 256;
+  while (threads > 64 && per * threads > 192 * 1024) threads >>= 1;
+  const size_t smem = (4u << kLutBits) + per * threads;
+  if (!all) {
+    const uint64_t count = edge_count(h.g);
+    if (!count) return;
+    auto ke = k_decode_edges<T, NDIM>;
+    cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ke<<<(unsigned)((count + threads - 1) / threads), threads, smem, L.stream>>>(s, nbytes, h, field, status, orig,
+                                                                                  st, flips, nflips, count);
+    return;
+  }
+  auto kern = k_decode<T, NDIM>;
+  const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
+  const unsigned grid = persistent_grid(kern, threads, smem, ngroups, L);
+  kern<<<grid, threads, smem, L.stream>>>(s, nbytes, h, field, status, orig, st, flips, nflips, all ? 1 : 0);
+}
+
+template <typename T>
+void launch_decode_t(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field_v, uint8_t* status,
+                     const void* orig_v, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                     const Launch& L) {
+  if (h.g.nb == 0) return;
+  T* field = write ? static_cast<T*>(field_v) : nullptr;
+  const T* orig = static_cast<const T*>(orig_v);
+  const bool fast = try_fast<T>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
+  if (h.g.ndim == 3) run_generic<T, 3>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, L);
+  else if (h.g.ndim == 2) run_generic<T, 2>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, L);
+  else run_generic<T, 1>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, L);
+}
+
+}  // namespace
+}  // namespace kdec
+}  // namespace sdcsz

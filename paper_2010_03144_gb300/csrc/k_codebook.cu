@@ -79,7 +79,6 @@ constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this
 __global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_warp[40];
-  __shared__ uint32_t s_n;
   __shared__ uint32_t cnt[64];
   __shared__ uint32_t s_maxlen;
   __shared__ uint32_t first_code[kMaxLen + 2], first_index[kMaxLen + 2], cum[kMaxLen + 2];
@@ -88,19 +87,20 @@ __global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restr
   const uint32_t tid = threadIdx.x;
   const uint32_t bins = g.bins;
 
-  // 1. live symbols -> keys (global scratch), codebook cleared
-  uint32_t n = 0;
-  for (uint32_t c = 0; c < bins; c += blockDim.x) {
-    const uint32_t s = c + tid;
-    unsigned long long hc = 0;
-    if (s < bins) {
-      hc = w.hist[s];
-      w.codebook[s] = 0;
-    }
-    uint32_t tot;
-    const uint32_t pos = block_excl_scan(hc ? 1u : 0u, s_warp, &tot);
-    if (hc) w.sort_keys[n + pos] = (hc << 16) | s;
-    n += tot;
+  // 1. live symbols -> keys (global scratch), codebook cleared. Thread t owns the bins
+  //    t, t + blockDim, ... (coalesced); the keys are sorted next, so their order here is free.
+  uint32_t mine = 0;
+#pragma unroll 4
+  for (uint32_t s = tid; s < bins; s += blockDim.x) {
+    mine += __ldg(&w.hist[s]) ? 1u : 0u;
+    w.codebook[s] = 0;
+  }
+  uint32_t n;
+  uint32_t pos = block_excl_scan(mine, s_warp, &n);
+#pragma unroll 4
+  for (uint32_t s = tid; s < bins; s += blockDim.x) {
+    const unsigned long long hc = __ldg(&w.hist[s]);
+    if (hc) w.sort_keys[pos++] = (hc << 16) | s;
   }
   uint32_t n_pad = 1;
   while (n_pad < n) n_pad <<= 1;
@@ -203,7 +203,6 @@ __global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restr
       first_index[l] = idx;
       idx += cnt[l];
     }
-    s_n = n;
   }
   __syncthreads();
 

@@ -1,0 +1,12 @@
+// K5 kernels instantiated for double fields (see decode.cuh).
+#include "decode.cuh"
+
+namespace sdcsz {
+
+void launch_decode_f64(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
+                      const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                      const Launch& L) {
+  kdec::launch_decode_t<double>(s, nbytes, h, field, status, original, st, write, flips, nflips, L);
+}
+
+}  // namespace sdcsz

@@ -1,0 +1,72 @@
+// Dispatch of K2 by dtype, and the soft-error injectors used by the test entry points.
+#include "sdcsz_internal.cuh"
+
+namespace sdcsz {
+
+void launch_predict_f32(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+                        const Launch& L);
+void launch_predict_f64(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+                        const Launch& L);
+
+void launch_predict(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+                    const Launch& L) {
+  if (g.dtype == 0) launch_predict_f32(field, g, w, flips, nflips, L);
+  else launch_predict_f64(field, g, w, flips, nflips, L);
+}
+
+// Soft-error simulation: flip bits of the caller's input after K1 took its checksums.
+template <typename T>
+__global__ void k_flip_input(T* field, Geo g, const sdcsz_flip* flips, uint32_t n) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    if (flips[t].site != SDCSZ_SITE_INPUT) continue;
+    const uint64_t word = flips[t].index, pt = word / FT<T>::W;
+    if (pt >= g.N) continue;
+    uint32_t* wp = reinterpret_cast<uint32_t*>(field + pt) + (word % FT<T>::W);
+    atomicXor(wp, 1u << (flips[t].bit & 31));
+  }
+}
+
+void launch_flip_input(void* field, const Geo& g, const sdcsz_flip* flips, uint32_t nflips, const Ws& w,
+                       const Launch& L) {
+  (void)w;
+  const unsigned grid = (nflips + 255) / 256;
+  if (!grid) return;
+  if (g.dtype == 0) k_flip_input<float><<<grid, 256, 0, L.stream>>>(static_cast<float*>(field), g, flips, nflips);
+  else k_flip_input<double><<<grid, 256, 0, L.stream>>>(static_cast<double*>(field), g, flips, nflips);
+}
+
+// Soft-error simulation: flip bits of stored codes after their checksums were taken.
+__global__ void k_flip_codes(Geo g, Ws w, const sdcsz_flip* flips, uint32_t n) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    if (flips[t].site != SDCSZ_SITE_CODE || flips[t].block >= g.nb) continue;
+    const Box x = block_box(g, flips[t].block);
+    if (flips[t].index >= x.P) continue;
+    uint16_t* c = w.codes + code_index(flips[t].block, g.P, (uint32_t)flips[t].index);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(c);
+    const uint32_t shift = (a & 2) ? 16u : 0u;
+    atomicXor(reinterpret_cast<unsigned int*>(a & ~uintptr_t(3)), (1u << (flips[t].bit & 15)) << shift);
+  }
+}
+
+void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
+  const unsigned grid = (nflips + 255) / 256;
+  if (!grid) return;
+  k_flip_codes<<<grid, 256, 0, L.stream>>>(g, w, flips, nflips);
+}
+
+
+void launch_decode_f32(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
+                       const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                       const Launch& L);
+void launch_decode_f64(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
+                       const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                       const Launch& L);
+
+void launch_decode(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
+                   const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                   const Launch& L) {
+  if (h.g.dtype == 0) launch_decode_f32(s, nbytes, h, field, status, original, st, write, flips, nflips, L);
+  else launch_decode_f64(s, nbytes, h, field, status, original, st, write, flips, nflips, L);
+}
+
+}  // namespace sdcsz

@@ -3,26 +3,151 @@
 // One thread per block, a warp per 32 consecutive blocks. A single pass over the block
 // computes, from the input as it is when compression starts:
 //   * sum_in / isum_in over the block's 32-bit words (Alg. 1 lines 3-4; Sec. 3.2, 5.4),
-//   * the regression sums and the closed-form least-squares coefficients (line 2),
+//   * the regression sums (per row first, then per block) and the closed-form least-squares
+//     coefficients (line 2),
 //   * the Lorenzo estimate E_lor on the original values (lines 6-7),
 //   * the value range for the value-range relative bound;
-// a second pass over the same block (L1/L2 resident) adds the regression estimate E_reg.
-// The last CTA to finish turns the global range into the absolute bound eb.
+// the regression estimate E_reg, which needs the coefficients, is taken by K2 just before it
+// predicts the block (its re-read of the block then hits the cache).
+// Full blocks of the common shapes take a fast path with compile-time edges; edge blocks and
+// other shapes take the generic path. A one-thread kernel then turns the range into eb.
+#include <algorithm>
+#include <type_traits>
+
 #include "sdcsz_internal.cuh"
 
 namespace sdcsz {
 
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void mad_wide(unsigned long long& acc, uint32_t a, uint32_t b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+template <typename T>
+__device__ __forceinline__ void cks(T v, uint32_t k, unsigned long long& sum, unsigned long long& isum) {
+  const uint32_t w0 = FT<T>::lo(v);
+  if (FT<T>::W == 1) {
+    mad_wide<T>(sum, w0, 1u);
+    mad_wide<T>(isum, w0, k + 1);
+  } else {
+    const uint32_t w1 = FT<T>::hi(v);
+    mad_wide<T>(sum, w0, 1u);
+    mad_wide<T>(sum, w1, 1u);
+    mad_wide<T>(isum, w0, 2 * k + 1);
+    mad_wide<T>(isum, w1, 2 * k + 2);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void minmax(T v, T& mn, T& mx) {
+  if (FT<T>::finite(v)) {
+    mn = v < mn ? v : mn;
+    mx = v > mx ? v : mx;
+  }
+}
+
+__device__ __forceinline__ float denom(uint32_t P, uint32_t ed) {
+  return __double2float_rn(__ddiv_rn(__dmul_rn((double)P, __dsub_rn(__dmul_rn((double)ed, (double)ed), 1.0)), 12.0));
+}
+
+// Coefficients from the block sums (slopes of the active axes, then the intercept).
+template <int NDIM>
+__device__ __forceinline__ bool coefficients(uint32_t P, const uint32_t e[3], float S0, float Si, float Sj, float Sl,
+                                             float c0, float c1, float c2, float cf[4]) {
+  const float mean = __fdiv_rn(S0, (float)P);
+  if (NDIM == 3) {
+    cf[0] = e[0] > 1 ? __fdiv_rn(Si, denom(P, e[0])) : 0.0f;
+    cf[1] = e[1] > 1 ? __fdiv_rn(Sj, denom(P, e[1])) : 0.0f;
+    cf[2] = e[2] > 1 ? __fdiv_rn(Sl, denom(P, e[2])) : 0.0f;
+    float acc = __fmul_rn(cf[0], c0);
+    acc = __fadd_rn(acc, __fmul_rn(cf[1], c1));
+    acc = __fadd_rn(acc, __fmul_rn(cf[2], c2));
+    cf[3] = __fsub_rn(mean, acc);
+  } else if (NDIM == 2) {
+    cf[0] = e[1] > 1 ? __fdiv_rn(Sj, denom(P, e[1])) : 0.0f;
+    cf[1] = e[2] > 1 ? __fdiv_rn(Sl, denom(P, e[2])) : 0.0f;
+    float acc = __fmul_rn(cf[0], c1);
+    acc = __fadd_rn(acc, __fmul_rn(cf[1], c2));
+    cf[2] = __fsub_rn(mean, acc);
+    cf[3] = 0.0f;
+  } else {
+    cf[0] = e[2] > 1 ? __fdiv_rn(Sl, denom(P, e[2])) : 0.0f;
+    cf[1] = __fsub_rn(mean, __fmul_rn(cf[0], c2));
+    cf[2] = cf[3] = 0.0f;
+  }
+  bool finite = true;
+  for (int a = 0; a <= NDIM; ++a) finite = finite && isfinite(cf[a]);
+  return finite;
+}
+
+// Range reduction to the grid-wide minimum/maximum keys.
+template <typename T>
+__device__ __forceinline__ void reduce_range(T mn, T mx, State* st) {
+  __shared__ unsigned long long s_min[32], s_max[32];
+  unsigned long long kmin_inv = (mn <= mx) ? ~FT<T>::key(mn) : 0ull;
+  unsigned long long kmax = (mn <= mx) ? FT<T>::key(mx) : 0ull;
+  for (int o = 16; o > 0; o >>= 1) {
+    kmin_inv = max(kmin_inv, __shfl_xor_sync(0xffffffffu, kmin_inv, o));
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_min[threadIdx.x >> 5] = kmin_inv;
+    s_max[threadIdx.x >> 5] = kmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, m = 0;
+    for (uint32_t q = 0; q < (blockDim.x + 31) / 32; ++q) {
+      a = max(a, s_min[q]);
+      m = max(m, s_max[q]);
+    }
+    if (m) {
+      atomicMax(&st->min_key, a);
+      atomicMax(&st->max_key, m);
+    }
+  }
+}
+
+template <typename T, int B2>
+__device__ __forceinline__ void load_row(const T* __restrict__ row, bool vec2, T (&x)[B2]) {
+  if ((B2 % 2) == 0 && vec2) {
+    typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type V2;
+    const V2* p = reinterpret_cast<const V2*>(row);
+#pragma unroll
+    for (int l = 0; l < B2 / 2; ++l) {
+      const V2 t = __ldg(p + l);
+      x[2 * l] = t.x;
+      x[2 * l + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < B2; ++l) x[l] = __ldg(row + l);
+  }
+}
+
+__device__ __forceinline__ bool full_block(const Geo& g, uint64_t b, uint64_t c[3]) {
+  c[2] = b % g.nbd[2];
+  const uint64_t t = b / g.nbd[2];
+  c[1] = t % g.nbd[1];
+  c[0] = t / g.nbd[1];
+  return (c[0] + 1) * g.B[0] <= g.d[0] && (c[1] + 1) * g.B[1] <= g.d[1] && (c[2] + 1) * g.B[2] <= g.d[2];
+}
+
+}  // namespace
+
+// Generic path: edge blocks (or every block when `all`), runtime extents.
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(128) k_prep(const T* __restrict__ field, Geo g, Ws w) {
+__global__ void __launch_bounds__(128) k_prep(const T* __restrict__ field, Geo g, Ws w, int all, uint64_t count) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long s_min[4], s_max[4];
   State* st = w.st;
   const uint32_t tid = threadIdx.x;
-  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + tid;
+  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + tid;
   const bool rel = g.eb_mode == 1;
-  unsigned long long kmin_inv = 0ull, kmax = 0ull;  // 0 = no finite value seen
-
-  if (b < g.nb) {
+  T mn = T(1.0 / 0.0), mx = T(-1.0 / 0.0);
+  if (e < count) {
+    const uint64_t b = all ? e : edge_block(g, e);
     const Box x = block_box(g, b);
     const bool est = g.predictor == 0;
     Walker<float, NDIM> wk;
@@ -30,7 +155,6 @@ __global__ void __launch_bounds__(128) k_prep(const T* __restrict__ field, Geo g
     wk.stride = blockDim.x;
     wk.B2 = g.B[2];
     wk.sr = g.B[1] * g.B[2];
-    // centre of each active axis (half-integers, exact in fp32)
     const float c0 = 0.5f * (float)(x.e[0] - 1), c1 = 0.5f * (float)(x.e[1] - 1), c2 = 0.5f * (float)(x.e[2] - 1);
     float S0 = 0.0f, Si = 0.0f, Sj = 0.0f, Sl = 0.0f, Elor = 0.0f;
     unsigned long long sum = 0, isum = 0;
@@ -40,148 +164,235 @@ __global__ void __launch_bounds__(128) k_prep(const T* __restrict__ field, Geo g
       for (uint32_t j = 0; j < x.e[1]; ++j) {
         const float tj = __fsub_rn((float)j, c1);
         const T* row = field + row_base(g, x, i, j);
+        const bool samp = sample_row(NDIM, i, j, x.e[1]);
         wk.row_start();
+        float r0 = 0.0f, rl = 0.0f;
         for (uint32_t l = 0; l < x.e[2]; ++l, ++k) {
           const T v = __ldg(row + l);
-          if (rel && FT<T>::finite(v)) {
-            const unsigned long long key = FT<T>::key(v);
-            kmin_inv = max(kmin_inv, ~key);
-            kmax = max(kmax, key);
-          }
-          if (g.abft) add_words<T>(v, k, sum, isum);
+          if (rel) minmax<T>(v, mn, mx);
+          if (g.abft) cks<T>(v, k, sum, isum);
           const float xr = FT<T>::tofloat(v);
-          const float tl = __fsub_rn((float)l, c2);
-          S0 = __fadd_rn(S0, xr);
-          if (NDIM == 3) {
-            Si = __fadd_rn(Si, __fmul_rn(xr, ti));
-            Sj = __fadd_rn(Sj, __fmul_rn(xr, tj));
-            Sl = __fadd_rn(Sl, __fmul_rn(xr, tl));
-          } else if (NDIM == 2) {
-            Sj = __fadd_rn(Sj, __fmul_rn(xr, tj));
-            Sl = __fadd_rn(Sl, __fmul_rn(xr, tl));
-          } else {
-            Sl = __fadd_rn(Sl, __fmul_rn(xr, tl));
-          }
+          r0 = __fadd_rn(r0, xr);
+          rl = __fadd_rn(rl, __fmul_rn(xr, __fsub_rn((float)l, c2)));
           if (est) {
             wk.load(i, j, l);
-            const float L = wk.template combine<OpRN<float>>();
-            Elor = __fadd_rn(Elor, fabsf(__fsub_rn(xr, L)));
+            if (samp) {
+              const float L = wk.template combine<OpRN<float>>();
+              Elor = __fadd_rn(Elor, fabsf(__fsub_rn(xr, L)));
+            }
             wk.commit(j, l, xr);
           }
         }
+        S0 = __fadd_rn(S0, r0);
+        Sl = __fadd_rn(Sl, rl);
+        if (NDIM == 3) {
+          Si = __fadd_rn(Si, __fmul_rn(r0, ti));
+          Sj = __fadd_rn(Sj, __fmul_rn(r0, tj));
+        } else if (NDIM == 2) {
+          Sj = __fadd_rn(Sj, __fmul_rn(r0, tj));
+        }
       }
     }
-    // closed-form least squares on the block grid: slope = sum x*(c - ctr) / sum (c - ctr)^2
-    const float Pf = (float)x.P;
-    auto denom = [&](uint32_t ed) -> float {
-      return __double2float_rn(__ddiv_rn(__dmul_rn((double)x.P, __dsub_rn(__dmul_rn((double)ed, (double)ed), 1.0)), 12.0));
-    };
-    float cf[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const float mean = __fdiv_rn(S0, Pf);
-    if (NDIM == 3) {
-      cf[0] = x.e[0] > 1 ? __fdiv_rn(Si, denom(x.e[0])) : 0.0f;
-      cf[1] = x.e[1] > 1 ? __fdiv_rn(Sj, denom(x.e[1])) : 0.0f;
-      cf[2] = x.e[2] > 1 ? __fdiv_rn(Sl, denom(x.e[2])) : 0.0f;
-      float acc = __fmul_rn(cf[0], c0);
-      acc = __fadd_rn(acc, __fmul_rn(cf[1], c1));
-      acc = __fadd_rn(acc, __fmul_rn(cf[2], c2));
-      cf[3] = __fsub_rn(mean, acc);
-    } else if (NDIM == 2) {
-      cf[0] = x.e[1] > 1 ? __fdiv_rn(Sj, denom(x.e[1])) : 0.0f;
-      cf[1] = x.e[2] > 1 ? __fdiv_rn(Sl, denom(x.e[2])) : 0.0f;
-      float acc = __fmul_rn(cf[0], c1);
-      acc = __fadd_rn(acc, __fmul_rn(cf[1], c2));
-      cf[2] = __fsub_rn(mean, acc);
-    } else {
-      cf[0] = x.e[2] > 1 ? __fdiv_rn(Sl, denom(x.e[2])) : 0.0f;
-      cf[1] = __fsub_rn(mean, __fmul_rn(cf[0], c2));
-    }
-    bool finite = true;
-    for (int a = 0; a <= NDIM; ++a) finite = finite && isfinite(cf[a]);
-    float Ereg = 0.0f;
-    if (est && finite) {
-      for (uint32_t i = 0; i < x.e[0]; ++i)
-        for (uint32_t j = 0; j < x.e[1]; ++j) {
-          const T* row = field + row_base(g, x, i, j);
-          for (uint32_t l = 0; l < x.e[2]; ++l) {
-            const float xr = FT<T>::tofloat(__ldg(row + l));
-            const float f = regress<float, NDIM, OpRN<float>>(cf, i, j, l);
-            Ereg = __fadd_rn(Ereg, fabsf(__fsub_rn(xr, f)));
-          }
-        }
-    }
+    float cf[4];
+    const bool finite = coefficients<NDIM>(x.P, x.e, S0, Si, Sj, Sl, c0, c1, c2, cf);
     if (g.abft) {
       w.sum_in[b] = sum;
       w.isum_in[b] = isum;
     }
     w.coef[b] = make_float4(cf[0], cf[1], cf[2], cf[3]);
-    w.est[b] = make_float2(Ereg, Elor);
+    w.est[b] = make_float2(0.0f, Elor);
     w.pflag[b] = finite ? 1 : 0;
   }
+  if (rel) reduce_range<T>(mn, mx, st);
+}
 
-  // value range: warp, CTA, then grid (atomics on monotone keys)
-  if (rel) {
-    for (int o = 16; o > 0; o >>= 1) {
-      kmin_inv = max(kmin_inv, __shfl_xor_sync(0xffffffffu, kmin_inv, o));
-      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+// Fast path: full blocks of a compile-time shape B0 x B1 x B2 (leading 1 for 2D).
+template <typename T, int NDIM, int B0, int B1, int B2>
+__global__ void __launch_bounds__(128) k_prep_fast(const T* __restrict__ field, Geo g, Ws w, int vec2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  State* st = w.st;
+  const uint32_t tid = threadIdx.x;
+  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + tid;
+  const bool rel = g.eb_mode == 1;
+  const bool est = g.predictor == 0;
+  T mn = T(1.0 / 0.0), mx = T(-1.0 / 0.0);
+  uint64_t c[3];
+  if (b < g.nb && full_block(g, b, c)) {
+    constexpr uint32_t P = B0 * B1 * B2;
+    const T* blk = field + (c[0] * B0 * g.d[1] + c[1] * B1) * g.d[2] + c[2] * B2;
+    const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
+    const float c0 = 0.5f * (float)(B0 - 1), c1 = 0.5f * (float)(B1 - 1), c2 = 0.5f * (float)(B2 - 1);
+    float S0 = 0.0f, Si = 0.0f, Sj = 0.0f, Sl = 0.0f, Elor = 0.0f;
+    unsigned long long sum = 0, isum = 0;
+    // E_lor neighbours of the sample rows: the previous row of this plane (brow) and, in 3D,
+    // rows (s, s-1) of the previous plane (pa, pb), saved while that plane was walked (na, nb).
+    float brow[B2], pa[B2], pb[B2], na[B2], nb[B2];
+#pragma unroll
+    for (int l = 0; l < B2; ++l) pa[l] = pb[l] = na[l] = nb[l] = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < B0; ++i) {
+      const float ti = __fsub_rn((float)i, c0);
+      const int s_cur = i % B1, s_next = (i + 1) % B1;
+#pragma unroll 1
+      for (int j = 0; j < B1; ++j) {
+        const float tj = __fsub_rn((float)j, c1);
+        T x[B2];
+        load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)j * sj, vec2, x);
+        const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
+        float r0 = 0.0f, rl = 0.0f;
+#pragma unroll
+        for (int l = 0; l < B2; ++l) {
+          const T v = x[l];
+          if (rel) minmax<T>(v, mn, mx);
+          if (g.abft) cks<T>(v, k0 + l, sum, isum);
+          const float xr = FT<T>::tofloat(v);
+          r0 = __fadd_rn(r0, xr);
+          rl = __fadd_rn(rl, __fmul_rn(xr, (float)l - c2));
+        }
+        if (est) {
+          const bool samp = NDIM == 3 ? (j == s_cur) : ((j & 3) == 1);
+          if (samp) {
+            const bool hj = j > 0;
+            float cp = 0.0f, ac = 0.0f, bc = 0.0f, abc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < B2; ++l) {
+              const float xr = FT<T>::tofloat(x[l]);
+              const float bb = hj ? brow[l] : 0.0f;
+              float L;
+              if (NDIM == 3) {
+                const float a = pa[l], ab = hj ? pb[l] : 0.0f;
+                float t = __fadd_rn(a, bb);
+                t = __fadd_rn(t, cp);
+                t = __fsub_rn(t, ab);
+                t = __fsub_rn(t, ac);
+                t = __fsub_rn(t, bc);
+                L = __fadd_rn(t, abc);
+                ac = a;
+                abc = ab;
+              } else {
+                L = __fsub_rn(__fadd_rn(bb, cp), bc);
+              }
+              bc = bb;
+              cp = xr;
+              Elor = __fadd_rn(Elor, fabsf(__fsub_rn(xr, L)));
+            }
+          }
+          if (NDIM == 3) {
+#pragma unroll
+            for (int l = 0; l < B2; ++l) {
+              const float xr = FT<T>::tofloat(x[l]);
+              if (j == s_next) na[l] = xr;
+              if (j + 1 == s_next) nb[l] = xr;
+            }
+          }
+#pragma unroll
+          for (int l = 0; l < B2; ++l) brow[l] = FT<T>::tofloat(x[l]);
+        }
+        S0 = __fadd_rn(S0, r0);
+        Sl = __fadd_rn(Sl, rl);
+        if (NDIM == 3) {
+          Si = __fadd_rn(Si, __fmul_rn(r0, ti));
+          Sj = __fadd_rn(Sj, __fmul_rn(r0, tj));
+        } else {
+          Sj = __fadd_rn(Sj, __fmul_rn(r0, tj));
+        }
+      }
+      if (NDIM == 3) {
+#pragma unroll
+        for (int l = 0; l < B2; ++l) {
+          pa[l] = na[l];
+          pb[l] = nb[l];
+        }
+      }
     }
-    if ((tid & 31) == 0) {
-      s_min[tid >> 5] = kmin_inv;
-      s_max[tid >> 5] = kmax;
+    const uint32_t e[3] = {B0, B1, B2};
+    float cf[4];
+    const bool finite = coefficients<NDIM>(P, e, S0, Si, Sj, Sl, c0, c1, c2, cf);
+    if (g.abft) {
+      w.sum_in[b] = sum;
+      w.isum_in[b] = isum;
+    }
+    w.coef[b] = make_float4(cf[0], cf[1], cf[2], cf[3]);
+    w.est[b] = make_float2(0.0f, Elor);
+    w.pflag[b] = finite ? 1 : 0;
+  }
+  if (rel) reduce_range<T>(mn, mx, st);
+}
+
+// The absolute bound: value-range relative (rel * (max - min) over finite values, rounded
+// to the dtype; the user's value when the range is empty or zero) or absolute.
+template <typename T>
+__global__ void k_bound(Geo g, State* st) {
+  double ebd = g.e;
+  const unsigned long long mi = st->min_key, ma = st->max_key;
+  if (g.eb_mode == 1 && ma != 0ull) {
+    const T mn = FT<T>::unkey(~mi), mx = FT<T>::unkey(ma);
+    if (mx > mn) ebd = __dmul_rn(g.e, __dsub_rn((double)mx, (double)mn));
+  }
+  T eb;
+  if (sizeof(T) == 4) eb = (T)__double2float_rn(ebd);
+  else eb = (T)ebd;
+  if (!FT<T>::is_normal_pos(eb)) atomicOr(&st->error, ERR_EB);
+  st->eb = (double)eb;
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2>
+static void run_fast(const void* field, const Geo& g, const Ws& w, const Launch& L) {
+  const size_t smem = 0;
+  auto kern = k_prep_fast<T, NDIM, B0, B1, B2>;
+  const bool vec2 = (B2 % 2 == 0) && (g.d[2] % 2 == 0) && (reinterpret_cast<uintptr_t>(field) % (2 * sizeof(T)) == 0);
+  kern<<<(unsigned)((g.nb + 127) / 128), 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, vec2 ? 1 : 0);
+}
+
+template <typename T>
+static bool try_fast(const void* field, const Geo& g, const Ws& w, const Launch& L) {
+  if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2]) {
+    switch (g.B[2]) {
+      case 4: run_fast<T, 3, 4, 4, 4>(field, g, w, L); return true;
+      case 6: run_fast<T, 3, 6, 6, 6>(field, g, w, L); return true;
+      case 8: run_fast<T, 3, 8, 8, 8>(field, g, w, L); return true;
+      case 10: run_fast<T, 3, 10, 10, 10>(field, g, w, L); return true;
+      case 12: run_fast<T, 3, 12, 12, 12>(field, g, w, L); return true;
+      case 16: run_fast<T, 3, 16, 16, 16>(field, g, w, L); return true;
+      default: return false;
     }
   }
-  __syncthreads();
-  if (tid == 0) {
-    if (rel) {
-      unsigned long long a = 0, m = 0;
-      for (uint32_t q = 0; q < (blockDim.x + 31) / 32; ++q) {
-        a = max(a, s_min[q]);
-        m = max(m, s_max[q]);
-      }
-      if (m) {
-        atomicMax(&st->min_key, a);
-        atomicMax(&st->max_key, m);
-      }
-    }
-    __threadfence();
-    const unsigned int done = atomicAdd(&st->k1_done, 1u);
-    if (done == gridDim.x - 1) {
-      // last CTA: the absolute bound (value-range relative, or the user's absolute bound)
-      __threadfence();
-      double ebd = g.e;
-      const unsigned long long mi = atomicAdd(&st->min_key, 0ull), ma = atomicAdd(&st->max_key, 0ull);
-      if (rel && ma != 0ull) {
-        const T mn = FT<T>::unkey(~mi), mx = FT<T>::unkey(ma);
-        if (mx > mn) ebd = __dmul_rn(g.e, __dsub_rn((double)mx, (double)mn));
-      }
-      T eb;
-      if (sizeof(T) == 4) eb = (T)__double2float_rn(ebd);
-      else eb = (T)ebd;
-      if (!FT<T>::is_normal_pos(eb)) atomicOr(&st->error, ERR_EB);
-      st->eb = (double)eb;
+  if (g.ndim == 2 && g.B[1] == g.B[2]) {
+    switch (g.B[2]) {
+      case 8: run_fast<T, 2, 1, 8, 8>(field, g, w, L); return true;
+      case 12: run_fast<T, 2, 1, 12, 12>(field, g, w, L); return true;
+      case 16: run_fast<T, 2, 1, 16, 16>(field, g, w, L); return true;
+      default: return false;
     }
   }
+  return false;
 }
 
 template <typename T, int NDIM>
-static void run_prep(const void* field, const Geo& g, const Ws& w, const Launch& L) {
+static void run_generic(const void* field, const Geo& g, const Ws& w, bool all, const Launch& L) {
   const uint32_t threads = 128;
-  const uint64_t grid = g.nb ? (g.nb + threads - 1) / threads : 1;
+  const uint64_t count = all ? g.nb : edge_count(g);
+  if (!count) return;
   const size_t smem = (g.predictor == 0) ? (size_t)walker_slots(g.ndim, g.B) * threads * sizeof(float) : 0;
   cudaFuncSetAttribute(k_prep<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_prep<T, NDIM><<<(unsigned)grid, threads, smem, L.stream>>>(static_cast<const T*>(field), g, w);
+  k_prep<T, NDIM><<<(unsigned)((count + threads - 1) / threads), threads, smem, L.stream>>>(
+      static_cast<const T*>(field), g, w, all ? 1 : 0, count);
+}
+
+template <typename T>
+static void launch_prep_t(const void* field, const Geo& g, const Ws& w, const Launch& L) {
+  const bool fast = g.nb && try_fast<T>(field, g, w, L);
+  if (g.nb) {
+    if (g.ndim == 3) run_generic<T, 3>(field, g, w, !fast, L);
+    else if (g.ndim == 2) run_generic<T, 2>(field, g, w, !fast, L);
+    else run_generic<T, 1>(field, g, w, !fast, L);
+  }
+  k_bound<T><<<1, 1, 0, L.stream>>>(g, w.st);
 }
 
 void launch_prep(const void* field, const Geo& g, const Ws& w, const Launch& L) {
-  if (g.dtype == 0) {
-    if (g.ndim == 3) run_prep<float, 3>(field, g, w, L);
-    else if (g.ndim == 2) run_prep<float, 2>(field, g, w, L);
-    else run_prep<float, 1>(field, g, w, L);
-  } else {
-    if (g.ndim == 3) run_prep<double, 3>(field, g, w, L);
-    else if (g.ndim == 2) run_prep<double, 2>(field, g, w, L);
-    else run_prep<double, 1>(field, g, w, L);
-  }
+  if (g.dtype == 0) launch_prep_t<float>(field, g, w, L);
+  else launch_prep_t<double>(field, g, w, L);
 }
 
 }  // namespace sdcsz

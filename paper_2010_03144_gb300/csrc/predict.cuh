@@ -1,0 +1,749 @@
+// K2: prediction, quantization and block checksums (Alg. 1 lines 8 and 10-32 of the paper).
+//
+// One thread per block, a warp per 32 consecutive blocks, persistent CTAs. Per block:
+//   * predictor choice from the K1 estimates (line 8),
+//   * one pass over the block in its sequential order: prediction evaluated twice
+//     (f_dup, line 18), linear-scaling quantization (lines 19-21), reconstruction evaluated
+//     twice (dec_dup, line 25), the machine-epsilon double check (lines 26-28), the code,
+//     sum_q/isum_q (line 24) and sum_dc (line 29), and the input words' checksums;
+//   * the input check of line 11 is done speculatively: the words used by the pass are
+//     summed on the fly and compared with sum_in/isum_in at the end; a mismatch (a memory
+//     error since K1) is located, repaired, and the block is run again with the repaired
+//     value, so the output equals that of an error-free run.
+// Two kernels: a fast path for full blocks of the common shapes (compile-time block edges,
+// the fastest-axis row unrolled in registers, the Lorenzo neighbours of the previous row in
+// registers and of the previous plane in one in-place shared-memory plane per thread), and a
+// generic path for edge blocks and other shapes. Codes and unpredictable values go to
+// warp-interleaved staging arrays (coalesced stores); the code histogram is privatised in
+// shared memory around the central bin.
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+
+#include "sdcsz_internal.cuh"
+
+namespace sdcsz {
+namespace kpred {
+namespace {
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+struct PassRes {
+  unsigned long long sw, isw;  // checksums of the input words used
+  unsigned long long isq, sdc; // isum_q, sum_dc
+  uint32_t sq, nun, dup;       // sum_q (< 2^28), unpredictables, duplicate mismatches
+};
+
+struct Hist {
+  uint32_t* s;            // shared window
+  unsigned long long* g;  // global histogram
+  uint32_t lo, hi;
+  __device__ __forceinline__ void add(uint32_t code, uint32_t cnt) const {
+    if (code - lo < hi - lo) atomicAdd(&s[code - lo], cnt);
+    else atomicAdd(&g[code], (unsigned long long)cnt);
+  }
+  __device__ __forceinline__ void sub1(uint32_t code) const {
+    if (code - lo < hi - lo) atomicSub(&s[code - lo], 1u);
+    else atomicAdd(&g[code], ~0ull);
+  }
+};
+
+// Histogram front end: the central bin (prediction within one bin) is counted in a register
+// without branching; every other code costs one shared (or global) atomic.
+struct Run {
+  uint32_t centre, n = 0;
+  __device__ __forceinline__ explicit Run(uint32_t R) : centre(R) {}
+  __device__ __forceinline__ void push(uint32_t c, const Hist& h) {
+    n += (c == centre);
+    if (c != centre) h.add(c, 1u);
+  }
+  __device__ __forceinline__ void flush(const Hist& h) {
+    if (n) h.add(centre, n);
+    n = 0;
+  }
+};
+
+// acc += a * b with one 32x32 -> 64 multiply-add
+__device__ __forceinline__ void mad_wide(unsigned long long& acc, uint32_t a, uint32_t b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+template <typename T>
+__device__ __forceinline__ void cks_words(T v, uint32_t k, unsigned long long& sum, unsigned long long& isum) {
+  const uint32_t w0 = FT<T>::lo(v);
+  if (FT<T>::W == 1) {
+    mad_wide(sum, w0, 1u);
+    mad_wide(isum, w0, k + 1);
+  } else {
+    const uint32_t w1 = FT<T>::hi(v);
+    mad_wide(sum, w0, 1u);
+    mad_wide(sum, w1, 1u);
+    mad_wide(isum, w0, 2 * k + 1);
+    mad_wide(isum, w1, 2 * k + 2);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void sum_words(T v, unsigned long long& sum) {
+  mad_wide(sum, FT<T>::lo(v), 1u);
+  if (FT<T>::W == 2) mad_wide(sum, FT<T>::hi(v), 1u);
+}
+
+// Alg. 1 lines 19-28 for one point with its (already duplicated) prediction: linear-scaling
+// quantization, reconstruction with dec_dup, and the machine-epsilon double check.
+// Returns the code (0 = unpredictable) and the value later points are predicted from.
+template <typename T, bool ABFT, bool HOOK>
+__device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, uint32_t R, bool hit_r, uint32_t bitr,
+                                             T& xr, uint32_t& dup) {
+  const T diff = FT<T>::sub(v, pred);
+  const T t = FT<T>::mul(FT<T>::absv(diff), inv2);
+  const bool inr = t < Rh;
+  const int m = FT<T>::trunc_i(FT<T>::add(t, T(0.5)));
+  const int q = (diff < T(0)) ? -m : m;
+  const T tq = FT<T>::fromi(2 * q);
+  T xd = FT<T>::add(pred, FT<T>::mul(tq, eb));
+  if (ABFT) {
+    if (HOOK && hit_r) xd = FT<T>::flip(xd, bitr);
+    const T x2 = FT<T>::add_v(pred, FT<T>::mul_v(tq, eb));
+    if (inr && !FT<T>::same(xd, x2)) {
+      xd = FT<T>::add_v(pred, FT<T>::mul_v(tq, eb));
+      ++dup;
+    }
+  }
+  const bool ok = inr && (FT<T>::absv(FT<T>::sub(v, xd)) <= eb);
+  xr = ok ? xd : v;
+  return ok ? (uint32_t)(q + (int)R) : 0u;
+}
+
+// f_dup for a prediction computed by `prim` (rounded intrinsics) and `dupf` (volatile PTX).
+template <typename T, bool ABFT, bool HOOK, class F1, class F2>
+__device__ __forceinline__ T dup_pred(F1 prim, F2 dupf, bool hit_p, uint32_t bitp, uint32_t& dup) {
+  T pred = prim();
+  if (ABFT) {
+    if (HOOK && hit_p) pred = FT<T>::flip(pred, bitp);
+    const T p2 = dupf();
+    if (!FT<T>::same(pred, p2)) {
+      pred = dupf();
+      ++dup;
+    }
+  }
+  return pred;
+}
+
+struct Hooks {
+  uint32_t kp, bitp, kr, bitr, kfix;
+};
+
+// ---------------------------------------------------------------- generic path
+template <typename T, int NDIM, bool REG, bool ABFT>
+__device__ __noinline__ PassRes generic_pass(const T* __restrict__ field, const Geo& g, const Box& x, uint64_t b,
+                                             const T* cT, Walker<T, NDIM>& wk, T eb, T inv2, T Rh,
+                                             uint16_t* __restrict__ codes, T* __restrict__ ustage, const Hist& h,
+                                             const Hooks hk, T xfix) {
+  PassRes r = {0, 0, 0, 0, 0, 0, 0};
+  Run run(g.R);
+  uint64_t ci = code_index(b, g.P, 0);
+  uint32_t k = 0;
+  for (uint32_t i = 0; i < x.e[0]; ++i) {
+    for (uint32_t j = 0; j < x.e[1]; ++j) {
+      const T* row = field + row_base(g, x, i, j);
+      if (!REG) wk.row_start();
+      for (uint32_t l = 0; l < x.e[2]; ++l, ++k, ci += 32) {
+        const T v = (k == hk.kfix) ? xfix : __ldg(row + l);
+        if (ABFT) cks_words<T>(v, k, r.sw, r.isw);
+        if (!REG) wk.load(i, j, l);
+        const T pred = dup_pred<T, ABFT, true>(
+            [&] { return REG ? regress<T, NDIM, OpRN<T>>(cT, i, j, l) : wk.template combine<OpRN<T>>(); },
+            [&] { return REG ? regress<T, NDIM, OpV<T>>(cT, i, j, l) : wk.template combine<OpV<T>>(); },
+            k == hk.kp, hk.bitp, r.dup);
+        T xr;
+        const uint32_t code = quantize<T, ABFT, true>(v, pred, eb, inv2, Rh, g.R, k == hk.kr, hk.bitr, xr, r.dup);
+        codes[ci] = (uint16_t)code;
+        if (!code) {
+          ustage[ci] = v;
+          ++r.nun;
+        }
+        if (ABFT) {
+          r.sq += code;
+          mad_wide(r.isq, code, k + 1);
+          sum_words<T>(xr, r.sdc);
+        }
+        run.push(code, h);
+        if (!REG) wk.commit(j, l, xr);
+      }
+    }
+  }
+  run.flush(h);
+  return r;
+}
+
+// ---------------------------------------------------------------- fast path (full blocks)
+template <typename T, int B2>
+__device__ __forceinline__ void load_row(const T* __restrict__ row, bool vec2, T (&x)[B2]) {
+  if ((B2 % 2) == 0 && vec2) {
+    typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type V2;
+    const V2* p = reinterpret_cast<const V2*>(row);
+#pragma unroll
+    for (int l = 0; l < B2 / 2; ++l) {
+      const V2 t = __ldg(p + l);
+      x[2 * l] = t.x;
+      x[2 * l + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < B2; ++l) x[l] = __ldg(row + l);
+  }
+}
+
+// One full block with compile-time edges. `blk` points at the block origin in the field,
+// `plane` at this thread's shared-memory slot 0 (3D Lorenzo only; slot stride kCta).
+template <typename T, int NDIM, int B0, int B1, int B2, int kCta, bool REG, bool ABFT, bool HOOK>
+__device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t si, uint64_t sj, bool vec2,
+                                             const T* cT, T* plane, T eb, T inv2, T Rh, uint32_t R,
+                                             uint16_t* __restrict__ cptr, T* __restrict__ uptr, const Hist& h,
+                                             const Hooks hk, T xfix) {
+  PassRes r = {0, 0, 0, 0, 0, 0, 0};
+  Run run(R);
+  if (!REG && NDIM == 3) {
+#pragma unroll
+    for (int s = 0; s < B1 * B2; ++s) plane[s * kCta] = T(0);
+  }
+  T brow[B2], arow[B2];  // Lorenzo: d[i][j-1][l] and d[i-1][j-1][l] (3D); d[j-1][l] (2D)
+#pragma unroll 1
+  for (int i = 0; i < B0; ++i) {
+#pragma unroll
+    for (int l = 0; l < B2; ++l) {
+      brow[l] = T(0);
+      arow[l] = T(0);
+    }
+    T xn[B2];
+    load_row<T, B2>(blk + (uint64_t)i * si, vec2, xn);
+#pragma unroll 1
+    for (int j = 0; j < B1; ++j) {
+      T x[B2];
+#pragma unroll
+      for (int l = 0; l < B2; ++l) x[l] = xn[l];
+      if (j + 1 < B1) load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)(j + 1) * sj, vec2, xn);  // next row
+      const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
+      uint16_t* crow = cptr + (uint64_t)k0 * 32;
+      T* urow = uptr + (uint64_t)k0 * 32;
+      // regression: (b0*i + b1*j) of this row, twice (primary and duplicate)
+      T ra = T(0), rv = T(0);
+      if (REG) {
+        if (NDIM == 3) {
+          ra = FT<T>::add(FT<T>::mul(cT[0], (T)i), FT<T>::mul(cT[1], (T)j));
+          rv = FT<T>::add_v(FT<T>::mul_v(cT[0], (T)i), FT<T>::mul_v(cT[1], (T)j));
+        } else if (NDIM == 2) {
+          ra = FT<T>::mul(cT[0], (T)j);
+          rv = FT<T>::mul_v(cT[0], (T)j);
+        }
+      }
+      T* prow = plane + (uint64_t)j * B2 * kCta;
+      T c = T(0), ac = T(0), bc = T(0), abc = T(0);
+#pragma unroll
+      for (int l = 0; l < B2; ++l) {
+        const uint32_t k = k0 + l;
+        T v = x[l];
+        if (HOOK && k == hk.kfix) v = xfix;
+        if (ABFT) cks_words<T>(v, k, r.sw, r.isw);
+        T a = T(0), bb = T(0), ab = T(0);
+        if (!REG) {
+          if (NDIM == 3) {
+            a = prow[l * kCta];
+            bb = brow[l];
+            ab = arow[l];
+          } else if (NDIM == 2) {
+            a = brow[l];
+          }
+        }
+        const T L = (T)l;
+        const T pred = dup_pred<T, ABFT, HOOK>(
+            [&] {
+              if (REG) {
+                const int lc = NDIM == 3 ? 2 : (NDIM == 2 ? 1 : 0);
+                if (NDIM == 1) return FT<T>::add(FT<T>::mul(cT[0], L), cT[1]);
+                return FT<T>::add(FT<T>::add(ra, FT<T>::mul(cT[lc], L)), cT[lc + 1]);
+              }
+              if (NDIM == 3) {
+                T s = FT<T>::add(a, bb);
+                s = FT<T>::add(s, c);
+                s = FT<T>::sub(s, ab);
+                s = FT<T>::sub(s, ac);
+                s = FT<T>::sub(s, bc);
+                return FT<T>::add(s, abc);
+              }
+              if (NDIM == 2) return FT<T>::sub(FT<T>::add(a, c), ac);
+              return c;
+            },
+            [&] {
+              if (REG) {
+                const int lc = NDIM == 3 ? 2 : (NDIM == 2 ? 1 : 0);
+                if (NDIM == 1) return FT<T>::add_v(FT<T>::mul_v(cT[0], L), cT[1]);
+                return FT<T>::add_v(FT<T>::add_v(rv, FT<T>::mul_v(cT[lc], L)), cT[lc + 1]);
+              }
+              if (NDIM == 3) {
+                T s = FT<T>::add_v(a, bb);
+                s = FT<T>::add_v(s, c);
+                s = FT<T>::sub_v(s, ab);
+                s = FT<T>::sub_v(s, ac);
+                s = FT<T>::sub_v(s, bc);
+                return FT<T>::add_v(s, abc);
+              }
+              if (NDIM == 2) return FT<T>::sub_v(FT<T>::add_v(a, c), ac);
+              return c;
+            },
+            HOOK && k == hk.kp, hk.bitp, r.dup);
+        T xr;
+        const uint32_t code = quantize<T, ABFT, HOOK>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup);
+        crow[l * 32] = (uint16_t)code;
+        if (!code) {
+          urow[l * 32] = v;
+          ++r.nun;
+        }
+        if (ABFT) {
+          r.sq += code;
+          mad_wide(r.isq, code, k + 1);
+          sum_words<T>(xr, r.sdc);
+        }
+        run.push(code, h);
+        if (!REG) {
+          if (NDIM == 3) {
+            prow[l * kCta] = xr;
+            arow[l] = a;
+            ac = a;
+            bc = bb;
+            abc = ab;
+            brow[l] = xr;
+          } else if (NDIM == 2) {
+            ac = a;
+            brow[l] = xr;
+          }
+          c = xr;
+        }
+      }
+    }
+  }
+  run.flush(h);
+  return r;
+}
+
+// ---------------------------------------------------------------- kernels
+struct Prologue {
+  float noise;
+  bool reg;
+};
+
+// Line 8: regression when its estimated error is the smaller one. E_lor comes from K1; E_reg
+// (which needs the coefficients) is summed here by `ereg()` just before the block is
+// predicted, so its re-read of the block hits the cache.
+template <class F>
+__device__ __forceinline__ bool choose_reg(const Geo& g, const Ws& w, uint64_t b, uint32_t S, float noise, F ereg) {
+  if (!(w.pflag[b] & 1)) return false;
+  if (g.predictor == 2) return true;
+  if (g.predictor == 1) return false;
+  const float Elor = w.est[b].y;
+  const float Ereg = ereg();
+  return Ereg < __fadd_rn(Elor, __fmul_rn((float)S, noise));
+}
+
+// E_reg = sum |x - f(p)| over the sample rows in local order (fp32; any extents).
+// (kfix, xfix): a repaired input value used in place of the stored one.
+template <typename T, int NDIM>
+__device__ __noinline__ float ereg_generic(const T* __restrict__ field, const Geo& g, const Box& x, float4 c4,
+                                           uint32_t kfix, T xfix) {
+  const float cf[4] = {c4.x, c4.y, c4.z, c4.w};
+  float E = 0.0f;
+  uint32_t k = 0;
+  for (uint32_t i = 0; i < x.e[0]; ++i)
+    for (uint32_t j = 0; j < x.e[1]; ++j) {
+      if (!sample_row(NDIM, i, j, x.e[1])) {
+        k += x.e[2];
+        continue;
+      }
+      const T* row = field + row_base(g, x, i, j);
+      for (uint32_t l = 0; l < x.e[2]; ++l, ++k) {
+        const float f = regress<float, NDIM, OpRN<float>>(cf, i, j, l);
+        const T v = k == kfix ? xfix : __ldg(row + l);
+        E = __fadd_rn(E, fabsf(__fsub_rn(FT<T>::tofloat(v), f)));
+      }
+    }
+  return E;
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2, bool HOOK>
+__device__ __forceinline__ float ereg_fast(const T* __restrict__ blk, uint64_t si, uint64_t sj, bool vec2, float4 c4,
+                                           uint32_t kfix, T xfix) {
+  float E = 0.0f;
+  // sample rows: (i, i mod B1) in 3D; rows 1, 5, 9, ... in 2D
+  constexpr int NR = NDIM == 3 ? B0 : (B1 + 2) / 4;
+#pragma unroll 1
+  for (int r = 0; r < NR; ++r) {
+    const int i = NDIM == 3 ? r : 0;
+    const int j = NDIM == 3 ? r % B1 : 4 * r + 1;
+    {
+      T x[B2];
+      load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)j * sj, vec2, x);
+      float ra, cl, cn;
+      if (NDIM == 3) {
+        ra = __fadd_rn(__fmul_rn(c4.x, (float)i), __fmul_rn(c4.y, (float)j));
+        cl = c4.z;
+        cn = c4.w;
+      } else {
+        ra = __fmul_rn(c4.x, (float)j);
+        cl = c4.y;
+        cn = c4.z;
+      }
+#pragma unroll
+      for (int l = 0; l < B2; ++l) {
+        const float f = __fadd_rn(__fadd_rn(ra, __fmul_rn(cl, (float)l)), cn);
+        const T v = (HOOK && (uint32_t)((i * B1 + j) * B2 + l) == kfix) ? xfix : x[l];
+        E = __fadd_rn(E, fabsf(__fsub_rn(FT<T>::tofloat(v), f)));
+      }
+    }
+  }
+  return E;
+}
+
+template <typename T, int NDIM>
+__device__ __forceinline__ void load_coefs(const Ws& w, uint64_t b, const sdcsz_flip* flips, uint32_t nflips, T cT[4],
+                                           Hooks& hk) {
+  const float4 c4 = w.coef[b];
+  cT[0] = FT<T>::fromfloat(c4.x);
+  cT[1] = FT<T>::fromfloat(c4.y);
+  cT[2] = FT<T>::fromfloat(c4.z);
+  cT[3] = FT<T>::fromfloat(c4.w);
+  hk.kp = hk.kr = hk.kfix = kNone;
+  hk.bitp = hk.bitr = 0;
+  if (!nflips) return;
+  uint32_t lo = 0, hi = nflips;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (flips[mid].block < b) lo = mid + 1;
+    else hi = mid;
+  }
+  for (uint32_t t = lo; t < nflips && flips[t].block == b; ++t) {
+    const sdcsz_flip f = flips[t];
+    if (f.site == SDCSZ_SITE_COEF && f.index <= (uint64_t)NDIM) cT[f.index] = FT<T>::flip(cT[f.index], f.bit);
+    if (f.site == SDCSZ_SITE_PRED && hk.kp == kNone) {
+      hk.kp = (uint32_t)min(f.index, (uint64_t)kNone - 1);
+      hk.bitp = f.bit;
+    }
+    if (f.site == SDCSZ_SITE_RECON && hk.kr == kNone) {
+      hk.kr = (uint32_t)min(f.index, (uint64_t)kNone - 1);
+      hk.bitr = f.bit;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void block_epilogue(const Ws& w, uint64_t b, bool reg, int ndim, const T cT[4],
+                                               const PassRes& r, bool abft, uint8_t flag) {
+  if (abft) {
+    w.sum_q[b] = r.sq;
+    w.isum_q[b] = r.isq;
+    w.sum_dc[b] = r.sdc;
+  }
+  w.flags[b] = flag | (reg ? 1 : 0);
+  if (reg) {
+    T* coefT = static_cast<T*>(w.coefT) + 4 * b;
+    for (int a = 0; a <= ndim; ++a) coefT[a] = cT[a];
+  }
+}
+
+struct Counters {
+  unsigned long long unpred = 0, reg = 0, dup = 0, fix = 0, bad = 0;
+  __device__ __forceinline__ void commit(State* st) {
+    unpred = warp_sum(unpred);
+    reg = warp_sum(reg);
+    dup = warp_sum(dup);
+    fix = warp_sum(fix);
+    bad = warp_sum(bad);
+    if ((threadIdx.x & 31) == 0) {
+      if (unpred) atomicAdd(&st->n_unpred, unpred);
+      if (reg) atomicAdd(&st->n_reg, reg);
+      if (dup) atomicAdd(&st->dup_fixed, dup);
+      if (fix) atomicAdd(&st->input_corrected, fix);
+      if (bad) atomicAdd(&st->uncorrectable, bad);
+    }
+  }
+};
+
+template <typename T>
+struct Consts {
+  T eb, inv2, Rh;
+  float noise;
+  __device__ __forceinline__ Consts(double ebd, uint32_t R, int ndim) {
+    eb = (T)ebd;
+    if (sizeof(T) == 4) inv2 = (T)__double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, ebd)));
+    else inv2 = (T)__ddiv_rn(1.0, __dmul_rn(2.0, ebd));
+    Rh = FT<T>::sub(FT<T>::fromi((int)R), T(0.5));
+    const float kappa = ndim == 3 ? 1.22f : (ndim == 2 ? 0.80f : 0.5f);
+    noise = __fmul_rn(kappa, FT<T>::tofloat(eb));
+  }
+};
+
+__device__ __forceinline__ bool block_is_full(const Geo& g, uint64_t b) {
+  const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
+  const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+  return (c0 + 1) * g.B[0] <= g.d[0] && (c1 + 1) * g.B[1] <= g.d[1] && (c2 + 1) * g.B[2] <= g.d[2];
+}
+
+__device__ __forceinline__ void hist_init(uint32_t* hist_s, Hist& h, const Geo& g, const Ws& w) {
+  for (uint32_t q = threadIdx.x; q < kHistWindow; q += blockDim.x) hist_s[q] = 0;
+  h.s = hist_s;
+  h.g = w.hist;
+  h.lo = g.R > kHistWindow / 2 ? g.R - kHistWindow / 2 : 0;
+  h.hi = min(g.bins, h.lo + (uint32_t)kHistWindow);
+}
+
+__device__ __forceinline__ void hist_flush(uint32_t* hist_s, const Hist& h, const Ws& w) {
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < h.hi - h.lo; q += blockDim.x)
+    if (hist_s[q]) atomicAdd(&w.hist[h.lo + q], (unsigned long long)hist_s[q]);
+}
+
+// The input check of Alg. 1 line 11 after a speculative pass: returns the repaired point and
+// value when a single corrupted word explains the checksum difference.
+template <typename T>
+__device__ __forceinline__ bool locate_input(const T* field, const Geo& g, const Box& x, unsigned long long s0,
+                                             unsigned long long i0, const PassRes& r, uint32_t* kf_out, T* xf_out) {
+  long long delta = 0;
+  const long long m = locate_word(s0, i0, r.sw, r.isw, (unsigned long long)x.P * FT<T>::W, 0, &delta);
+  if (m < 0) return false;
+  const uint32_t kf = (uint32_t)(m / FT<T>::W), wi = (uint32_t)(m % FT<T>::W);
+  const uint32_t lf = kf % x.e[2], tq = kf / x.e[2];
+  const uint32_t jf = tq % x.e[1], i_f = tq / x.e[1];
+  const T cur = field[row_base(g, x, i_f, jf) + lf];
+  uint32_t wd[2] = {FT<T>::lo(cur), FT<T>::hi(cur)};
+  const long long nw = (long long)wd[wi] - delta;
+  if (nw < 0 || nw > 0xffffffffll) return false;
+  wd[wi] = (uint32_t)nw;
+  *kf_out = kf;
+  *xf_out = FT<T>::from_words(wd[0], wd[1]);
+  return true;
+}
+
+__device__ __forceinline__ void withdraw(const Ws& w, const Geo& g, uint64_t b, uint32_t P, const Hist& h) {
+  uint64_t ci = code_index(b, g.P, 0);
+  for (uint32_t kk = 0; kk < P; ++kk, ci += 32) h.sub1(w.codes[ci]);
+}
+
+// Generic kernel: edge blocks (or every block when `all`), any shape.
+template <typename T, int NDIM, bool ABFT>
+__global__ void __launch_bounds__(128) k_predict(const T* __restrict__ field, Geo g, Ws w,
+                                                 const sdcsz_flip* __restrict__ flips, uint32_t nflips, int all,
+                                                 uint64_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t hist_s[kHistWindow];
+  State* st = w.st;
+  if (*(volatile unsigned int*)&st->error) return;
+  Hist h;
+  hist_init(hist_s, h, g, w);
+  __syncthreads();
+  const Consts<T> K(st->eb, g.R, NDIM);
+  Walker<T, NDIM> wk;
+  wk.base = reinterpret_cast<T*>(smem) + threadIdx.x;
+  wk.stride = blockDim.x;
+  wk.B2 = g.B[2];
+  wk.sr = g.B[1] * g.B[2];
+  T* ustage = static_cast<T*>(w.ustage);
+  Counters cnt;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x < count; e += step) {
+    if (e >= count) continue;
+    const uint64_t b = all ? e : edge_block(g, e);
+    const Box x = block_box(g, b);
+    const uint32_t S = sample_points(NDIM, x.e);
+    bool reg = choose_reg(g, w, b, S, K.noise,
+                          [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kNone, T(0)); });
+    T cT[4];
+    Hooks hk;
+    load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
+    PassRes r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
+                                                        h, hk, T(0))
+                    : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
+                                                         h, hk, T(0));
+    uint8_t flag = 0;
+    if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
+      uint32_t kf;
+      T xf;
+      if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
+        withdraw(w, g, b, x.P, h);
+        hk.kfix = kf;
+        // the selection estimate and the prediction both see the repaired value
+        reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kf, xf); });
+        r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
+                                                    hk, xf)
+                : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
+                                                     hk, xf);
+        ++cnt.fix;
+      } else {
+        ++cnt.bad;
+        flag = 2;
+      }
+    }
+    block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
+    cnt.unpred += r.nun;
+    cnt.reg += reg;
+    cnt.dup += r.dup;
+  }
+  cnt.commit(st);
+  hist_flush(hist_s, h, w);
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool HOOK>
+__device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_t si, uint64_t sj, bool vec2,
+                                                 const T* cT, T* plane, const Consts<T>& K, uint32_t R, uint16_t* cptr,
+                                                 T* uptr, const Hist& h, const Hooks& hk, T xfix) {
+  if (reg)
+    return fast_pass<T, NDIM, B0, B1, B2, 128, true, ABFT, HOOK>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh, R,
+                                                                 cptr, uptr, h, hk, xfix);
+  return fast_pass<T, NDIM, B0, B1, B2, 128, false, ABFT, HOOK>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh, R,
+                                                                cptr, uptr, h, hk, xfix);
+}
+
+// Fast kernel: full blocks of a compile-time shape (B0 x B1 x B2, leading 1s below 3D).
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+__global__ void __launch_bounds__(128) k_predict_fast(const T* __restrict__ field, Geo g, Ws w,
+                                                      const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                      int vec2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t hist_s[kHistWindow];
+  State* st = w.st;
+  if (*(volatile unsigned int*)&st->error) return;
+  Hist h;
+  hist_init(hist_s, h, g, w);
+  __syncthreads();
+  const Consts<T> K(st->eb, g.R, NDIM);
+  T* plane = reinterpret_cast<T*>(smem) + threadIdx.x;
+  T* ustage = static_cast<T*>(w.ustage);
+  constexpr uint32_t P = B0 * B1 * B2;
+  const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
+  Counters cnt;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b - threadIdx.x < g.nb; b += step) {
+    if (b >= g.nb) continue;
+    const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
+    const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+    if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) continue;
+    const T* blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
+    constexpr uint32_t S = NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2;
+    bool reg = choose_reg(g, w, b, S, K.noise, [&] {
+      return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, w.coef[b], kNone, T(0));
+    });
+    T cT[4];
+    Hooks hk;
+    load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
+    uint16_t* cptr = w.codes + code_index(b, P, 0);
+    T* uptr = ustage + code_index(b, P, 0);
+    const bool hooked = (hk.kp != kNone) || (hk.kr != kNone);
+    PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
+                                                                        cptr, uptr, h, hk, T(0))
+                       : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, false>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
+                                                                         cptr, uptr, h, hk, T(0));
+    uint8_t flag = 0;
+    if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
+      const Box x = block_box(g, b);
+      uint32_t kf;
+      T xf;
+      if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
+        withdraw(w, g, b, P, h);
+        hk.kfix = kf;
+        reg = choose_reg(g, w, b, S, K.noise, [&] {
+          return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, w.coef[b], kf, xf);
+        });
+        r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
+                                                           hk, xf);
+        ++cnt.fix;
+      } else {
+        ++cnt.bad;
+        flag = 2;
+      }
+    }
+    block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
+    cnt.unpred += r.nun;
+    cnt.reg += reg;
+    cnt.dup += r.dup;
+  }
+  cnt.commit(st);
+  hist_flush(hist_s, h, w);
+}
+
+// ---------------------------------------------------------------- launch
+template <class K>
+inline void launch_persistent(K kern, uint32_t threads, size_t smem, uint64_t nb, const Launch& L, dim3* grid_out) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
+  if (occ < 1) occ = 1;
+  const uint64_t need = (nb + threads - 1) / threads;
+  *grid_out = dim3((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)occ * L.sms)));
+}
+
+template <typename T, int NDIM, bool ABFT>
+void run_generic(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips, bool all,
+                 const Launch& L) {
+  const uint32_t per = walker_slots(g.ndim, g.B) * sizeof(T);
+  uint32_t threads = 128;
+  while (threads > 32 && (size_t)per * threads > 160 * 1024) threads >>= 1;
+  const size_t smem = (size_t)per * threads;
+  auto kern = k_predict<T, NDIM, ABFT>;
+  const uint64_t count = all ? g.nb : edge_count(g);
+  if (!count) return;
+  dim3 grid;
+  launch_persistent(kern, threads, smem, count, L, &grid);
+  kern<<<grid, threads, smem, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, all ? 1 : 0, count);
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+void run_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+              const Launch& L) {
+  const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
+  auto kern = k_predict_fast<T, NDIM, B0, B1, B2, ABFT>;
+  dim3 grid;
+  launch_persistent(kern, 128, smem, g.nb, L, &grid);
+  const bool vec2 = (B2 % 2 == 0) && (g.d[2] % 2 == 0) &&
+                    (reinterpret_cast<uintptr_t>(field) % (2 * sizeof(T)) == 0);
+  kern<<<grid, 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, vec2 ? 1 : 0);
+}
+
+// Shapes with a fast path: cubes 4..16 in 3D, squares 8/12/16 in 2D.
+template <typename T, bool ABFT>
+bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+              const Launch& L) {
+  if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2]) {
+    switch (g.B[2]) {
+      case 4: run_fast<T, 3, 4, 4, 4, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 6: run_fast<T, 3, 6, 6, 6, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 8: run_fast<T, 3, 8, 8, 8, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 10: run_fast<T, 3, 10, 10, 10, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 12: run_fast<T, 3, 12, 12, 12, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 16: run_fast<T, 3, 16, 16, 16, ABFT>(field, g, w, flips, nflips, L); return true;
+      default: return false;
+    }
+  }
+  if (g.ndim == 2 && g.B[1] == g.B[2]) {
+    switch (g.B[2]) {
+      case 8: run_fast<T, 2, 1, 8, 8, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 12: run_fast<T, 2, 1, 12, 12, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 16: run_fast<T, 2, 1, 16, 16, ABFT>(field, g, w, flips, nflips, L); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
+template <typename T, bool ABFT>
+void launch_predict_t(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+                      const Launch& L) {
+  const bool fast = try_fast<T, ABFT>(field, g, w, flips, nflips, L);
+  // edge blocks (or everything when no fast path exists for the shape)
+  if (g.ndim == 3) run_generic<T, 3, ABFT>(field, g, w, flips, nflips, !fast, L);
+  else if (g.ndim == 2) run_generic<T, 2, ABFT>(field, g, w, flips, nflips, !fast, L);
+  else run_generic<T, 1, ABFT>(field, g, w, flips, nflips, !fast, L);
+}
+
+}  // namespace
+}  // namespace kpred
+}  // namespace sdcsz

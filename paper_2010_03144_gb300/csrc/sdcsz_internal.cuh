@@ -19,7 +19,7 @@ constexpr int kMaxLen = 24;           // longest Huffman code in bits
 constexpr int kGroup = 256;           // blocks per random-access group of the stream
 constexpr int kHeaderBytes = 128;
 constexpr int kLutBits = 12;          // first-level decode table covers codes of <= 12 bits
-constexpr int kHistWindow = 4096;     // bins privatised in shared memory around the centre
+constexpr int kHistWindow = 2048;     // bins privatised in shared memory around the centre
 constexpr uint32_t kSpinLimit = 1u << 20;  // bounded waits: iterations before giving up
 
 // error flags accumulated in State::error
@@ -128,6 +128,52 @@ __device__ __forceinline__ Box block_box(const Geo& g, uint64_t b) {
   x.e[2] = (uint32_t)min((uint64_t)g.B[2], g.d[2] - x.org[2]);
   x.P = x.e[0] * x.e[1] * x.e[2];
   return x;
+}
+
+// Edge blocks (cut by the field boundary) enumerated compactly, so a warp gets 32 of them:
+// the slab c0 = last (when dims[0] is not a multiple), then c1 = last, then c2 = last.
+__host__ __device__ inline uint64_t edge_count(const Geo& g) {
+  const uint64_t p0 = g.d[0] % g.B[0] != 0, p1 = g.d[1] % g.B[1] != 0, p2 = g.d[2] % g.B[2] != 0;
+  const uint64_t F0 = g.nbd[0] - p0, F1 = g.nbd[1] - p1;
+  return p0 * g.nbd[1] * g.nbd[2] + F0 * p1 * g.nbd[2] + F0 * F1 * p2;
+}
+
+__device__ __forceinline__ uint64_t edge_block(const Geo& g, uint64_t e) {
+  const uint64_t p0 = g.d[0] % g.B[0] != 0, p1 = g.d[1] % g.B[1] != 0;
+  const uint64_t F0 = g.nbd[0] - p0, F1 = g.nbd[1] - p1, F2 = g.nbd[2] - (g.d[2] % g.B[2] != 0);
+  const uint64_t A = p0 * g.nbd[1] * g.nbd[2], Bn = F0 * p1 * g.nbd[2];
+  uint64_t c0, c1, c2;
+  if (e < A) {
+    const uint64_t r = e % (g.nbd[1] * g.nbd[2]);
+    c0 = F0 + e / (g.nbd[1] * g.nbd[2]);
+    c1 = r / g.nbd[2];
+    c2 = r % g.nbd[2];
+  } else if (e < A + Bn) {
+    const uint64_t r = e - A;
+    c0 = r / g.nbd[2];
+    c1 = F1;
+    c2 = r % g.nbd[2];
+  } else {
+    const uint64_t r = e - A - Bn;
+    c0 = r / F1;
+    c1 = r % F1;
+    c2 = F2;
+  }
+  return (c0 * g.nbd[1] + c1) * g.nbd[2] + c2;
+}
+
+// Rows of the predictor-selection sample (whole rows along the fastest axis): one diagonal
+// row per plane in 3D, every fourth row from row 1 in 2D, the whole block in 1D.
+__host__ __device__ inline bool sample_row(int ndim, uint32_t i, uint32_t j, uint32_t e1) {
+  if (ndim == 3) return j == i % e1;
+  if (ndim == 2) return (j & 3u) == 1u;
+  return true;
+}
+
+__host__ __device__ inline uint32_t sample_points(int ndim, const uint32_t e[3]) {
+  if (ndim == 3) return e[0] * e[2];
+  if (ndim == 2) return ((e[1] + 2) / 4) * e[2];
+  return e[2];
 }
 
 __device__ __forceinline__ uint64_t row_base(const Geo& g, const Box& x, uint32_t i, uint32_t j) {
