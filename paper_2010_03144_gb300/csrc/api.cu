@@ -6,6 +6,7 @@
 // from the caller (stream, field, workspace).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "sdcsz_internal.cuh"
 
@@ -29,6 +30,20 @@ int sm_count() {
   }
   return cached[dev];
 }
+
+}  // namespace
+
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+  return streams[dev];
+}
+
+namespace {
 
 // Validate parameters and fill the padded-3D geometry.
 int make_geo(const sdcsz_params* p, Geo* g) {

@@ -27,6 +27,7 @@ struct Canon {
   uint32_t fc[kMaxLen + 2];  // first code of each length
   uint32_t fi[kMaxLen + 2];  // canonical index of that first code
   uint32_t nc[kMaxLen + 2];  // codes of each length
+  uint32_t bins;             // symbols must be below this
 };
 
 __device__ __forceinline__ unsigned long long ld_u64(const uint8_t* p) {
@@ -50,7 +51,7 @@ __device__ __noinline__ int slow_symbol(unsigned long long buf, const Canon& cn,
     const uint32_t c = (uint32_t)(buf >> (64 - l));
     if (c - cn.fc[l] < cn.nc[l]) {
       const uint32_t r = cn.fi[l] + (c - cn.fc[l]);
-      if (r >= n_live) return -1;
+      if (r >= n_live || syms[r] >= cn.bins) return -1;
       *len_out = l;
       return syms[r];
     }
@@ -109,39 +110,43 @@ struct BitReader {
   }
 };
 
-// Unchecked variant for payloads that end at least 8 bytes before the stream's last whole
-// word: the refill is predicated instead of branched (lanes refill at different symbols).
+// Unchecked variant for payloads far enough from the end of the stream (the caller checks
+// the worst case). Two big-endian words w0:w1 hold the next 64 bits from bit `pos` of w0; a
+// symbol is a 12-bit table lookup on a funnel shift, and crossing into the next word is
+// predicated rather than branched (lanes cross at different symbols).
 struct FastReader {
-  const uint32_t* wp;
-  unsigned long long buf;
-  int nb;
-  uint32_t used;
+  const uint32_t* wp;  // next word to prefetch
+  const uint32_t* w_start;
+  uint32_t w0, w1, w2, pos, skip;  // w2: the word after w1, loaded ahead of use
   __device__ __forceinline__ void init(const uint8_t* p) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
     wp = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
-    const int skip = (int)(a & 3) * 8;
-    buf = ((unsigned long long)__byte_perm(__ldg(wp), 0, 0x0123) << 32) | __byte_perm(__ldg(wp + 1), 0, 0x0123);
-    wp += 2;
-    buf <<= skip;
-    nb = 64 - skip;
-    used = 0;
+    w_start = wp;
+    w0 = __byte_perm(__ldg(wp), 0, 0x0123);
+    w1 = __byte_perm(__ldg(wp + 1), 0, 0x0123);
+    w2 = __ldg(wp + 2);
+    wp += 3;
+    skip = pos = (uint32_t)(a & 3) * 8;
   }
+  // bits consumed since init
+  __device__ __forceinline__ uint32_t used() const { return (uint32_t)(wp - w_start - 3) * 32u + pos - skip; }
   __device__ __forceinline__ int next(const uint32_t* lut, const Canon& cn, const uint16_t* syms, uint32_t n_live) {
-    const bool need = nb <= 32;
-    const uint32_t w = __byte_perm(__ldg(wp), 0, 0x0123);
-    buf |= need ? ((unsigned long long)w << (32 - nb)) : 0ull;
-    wp += need ? 1 : 0;
-    nb += need ? 32 : 0;
-    const uint32_t e = lut[buf >> (64 - kLutBits)];
+    const uint32_t peek = __funnelshift_l(w1, w0, pos);
+    const uint32_t e = lut[peek >> (32 - kLutBits)];
     uint32_t len = e & 0xffu;
     int sym = (int)(e >> 8);
     if (!len) {
-      sym = slow_symbol(buf, cn, syms, n_live, &len);
+      sym = slow_symbol((unsigned long long)peek << 32, cn, syms, n_live, &len);
       if (sym < 0) return -1;
     }
-    buf <<= len;
-    nb -= (int)len;
-    used += len;
+    pos += len;
+    if (pos >= 32) {  // only lanes crossing a word boundary touch memory
+      pos -= 32;
+      w0 = w1;
+      w1 = __byte_perm(w2, 0, 0x0123);
+      w2 = __ldg(wp);
+      ++wp;
+    }
     return sym;
   }
 };
@@ -300,14 +305,13 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
         } else {
           pred = FT<T>::sub(FT<T>::add(a, c), ac);
         }
-        const T xv = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
-        const bool isu = q == 0, has_u = used_u < bi.ucnt;
-        T uval = T(0);
-        if (isu && has_u) uval = un[used_u];
-        const bool okq = q > 0 && (uint32_t)q < g.bins;
-        T xr = okq ? xv : uval;
-        ok = ok && (okq || (isu && has_u));
-        used_u += isu ? 1u : 0u;
+        T xr = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
+        if (q <= 0) {  // unpredictable value (code 0) or an undecodable block (rare)
+          xr = T(0);
+          if (q == 0 && used_u < bi.ucnt) xr = un[used_u];
+          else ok = false;
+          ++used_u;
+        }
         if (HOOK && k0 + l == kinj) xr = FT<T>::flip(xr, bitinj);
         if (!REG) {
           if (NDIM == 3) {
@@ -359,7 +363,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       }
     }
   }
-  if (used_u != bi.ucnt || br.used > bi.size * 8u) ok = false;
+  if (used_u != bi.ucnt || br.used() > bi.size * 8u) ok = false;
   *sum_out = sum;
   *viol = nv;
   *maxerr = me;
@@ -394,6 +398,7 @@ __device__ bool cta_tables(const uint8_t* s, const Hdr& h, Smem& sm, uint32_t* l
       total += c;
     }
     if (total != h.n_live || kraft > (1ull << kMaxLen)) bad = 1;
+    sm.cn.bins = h.g.bins;
     sm.bad = bad;
     if (bad) atomicOr(&st->error, ERR_FORMAT);
   }
@@ -405,8 +410,8 @@ __device__ bool cta_tables(const uint8_t* s, const Hdr& h, Smem& sm, uint32_t* l
       const uint32_t c = e >> (kLutBits - l);
       if (c - sm.cn.fc[l] < sm.cn.nc[l]) {
         const uint32_t r = sm.cn.fi[l] + (c - sm.cn.fc[l]);
-        const uint32_t sym = r < h.n_live ? syms[r] : 0u;
-        v = (sym << 8) | l;
+        const uint32_t sym = r < h.n_live ? syms[r] : 0xffffffffu;
+        v = sym < h.g.bins ? ((sym << 8) | l) : 0u;  // an out-of-range symbol decodes as invalid
         break;
       }
     }
@@ -766,6 +771,14 @@ void run_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t
 }
 
 template <typename T>
+bool has_fast(const Geo& g) {
+  if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2])
+    return g.B[2] == 4 || g.B[2] == 6 || g.B[2] == 8 || (sizeof(T) == 4 && (g.B[2] == 10 || g.B[2] == 12));
+  if (g.ndim == 2 && g.B[1] == g.B[2]) return g.B[2] == 8 || g.B[2] == 12 || g.B[2] == 16;
+  return false;
+}
+
+template <typename T>
 bool try_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
               const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
   const Geo& g = h.g;
@@ -826,10 +839,14 @@ void launch_decode_t(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* fiel
   if (h.g.nb == 0) return;
   T* field = write ? static_cast<T*>(field_v) : nullptr;
   const T* orig = static_cast<const T*>(orig_v);
-  const bool fast = try_fast<T>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
-  if (h.g.ndim == 3) run_generic<T, 3>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, L);
-  else if (h.g.ndim == 2) run_generic<T, 2>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, L);
-  else run_generic<T, 1>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, L);
+  Fork fk(L);
+  const bool fast = has_fast<T>(h.g);
+  const Launch Lg = fast ? fk.side_launch(L) : L;
+  if (h.g.ndim == 3) run_generic<T, 3>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, Lg);
+  else if (h.g.ndim == 2) run_generic<T, 2>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, Lg);
+  else run_generic<T, 1>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, Lg);
+  if (fast) try_fast<T>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
+  fk.join();
 }
 
 }  // namespace

@@ -6,7 +6,8 @@
 // and repaired) and sums the code lengths. A CTA scan plus a single-pass decoupled look-back
 // across groups (group ids taken from a ticket in launch order, every wait bounded) gives each
 // block its payload, unpredictable-value and coefficient offsets. Pass 2 re-reads the codes
-// (L2 resident), packs the bits MSB-first and writes the block table entries.
+// (L2 resident) and packs the bits MSB-first into 32-bit words: words wholly inside the
+// block's byte range are stored whole, the partial first and last words byte by byte.
 #include "sdcsz_internal.cuh"
 
 namespace sdcsz {
@@ -14,63 +15,95 @@ namespace sdcsz {
 namespace {
 
 constexpr unsigned long long kFlagAgg = 1ull, kMaskBytes = (1ull << 22) - 1, kMaskUn = (1ull << 21) - 1;
+constexpr uint32_t kCbWindow = 2048;  // codebook entries around the centre kept in shared memory
 
 __device__ __forceinline__ unsigned long long pack_agg(unsigned long long bytes, unsigned long long un,
                                                        unsigned long long rg) {
   return (kFlagAgg << 62) | (rg << 43) | (un << 22) | bytes;
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
-  return *(volatile const unsigned long long*)p;
+__device__ __forceinline__ void mad_wide(unsigned long long& acc, uint32_t a, uint32_t b) {
+  asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+struct Codebook {
+  const uint32_t* s;  // shared window [lo, lo + kCbWindow)
+  const uint32_t* g;
+  uint32_t lo;
+  __device__ __forceinline__ uint32_t operator()(uint32_t c) const {
+    const uint32_t d = c - lo;
+    return d < kCbWindow ? s[d] : __ldg(&g[c]);
+  }
+};
+
+// Store the 32-bit big-endian word `v` at aligned word address `wa` of the stream, keeping
+// only the bytes inside [lo, hi).
+__device__ __forceinline__ void put_word(uint8_t* out, uint64_t wa, uint32_t v, uint64_t lo, uint64_t hi, bool fits) {
+  if (!fits) return;
+  if (wa >= lo && wa + 4 <= hi) {
+    *reinterpret_cast<uint32_t*>(out + wa) = __byte_perm(v, 0, 0x0123);
+  } else {
+    for (int q = 0; q < 4; ++q)
+      if (wa + q >= lo && wa + q < hi) out[wa + q] = (uint8_t)(v >> (24 - 8 * q));
+  }
 }
 
 }  // namespace
 
-template <typename T>
+template <typename T, bool ABFT>
 __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
   __shared__ uint32_t s_gid;
   __shared__ unsigned long long s_wt[8][3];
   __shared__ unsigned long long s_excl[3];
   __shared__ unsigned long long s_tot[3];
+  __shared__ uint32_t cb_s[kCbWindow];
   State* st = w.st;
   if (*(volatile unsigned int*)&st->error) return;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_gid = atomicAdd(&st->ticket, 1u);
+  Codebook cb;
+  cb.lo = g.R > kCbWindow / 2 ? g.R - kCbWindow / 2 : 0;
+  cb.s = cb_s;
+  cb.g = w.codebook;
+  for (uint32_t q = tid; q < kCbWindow; q += blockDim.x) cb_s[q] = cb.lo + q < g.bins ? __ldg(&w.codebook[cb.lo + q]) : 0u;
   __syncthreads();
   const uint64_t gid = s_gid;
   const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
   const uint64_t b = gid * kGroup + tid;
   const bool active = b < g.nb;
   const Layout L = st->L;
+  const uint16_t* __restrict__ codes = w.codes;
 
   // pass 1: verify codes, count bits and unpredictables
-  Box x;
-  x.P = 0;
-  uint32_t bits = 0, nun = 0, kfix = 0xffffffffu, vfix = 0;
+  uint32_t P = 0, bits = 0, nun = 0, kfix = 0xffffffffu, vfix = 0;
   bool reg = false, bad = false;
   if (active) {
-    x = block_box(g, b);
+    P = block_box(g, b).P;
     reg = w.flags[b] & 1;
-    unsigned long long s = 0, is = 0;
-    uint64_t ci = code_index(b, g.P, 0);
-    for (uint32_t k = 0; k < x.P; ++k, ci += 32) {
-      const uint32_t c = w.codes[ci];
-      bits += __ldg(&w.codebook[c]) & 31u;
+    uint32_t s = 0;
+    unsigned long long is = 0;
+    const uint16_t* cp = codes + code_index(b, g.P, 0);
+#pragma unroll 8
+    for (uint32_t k = 0; k < P; ++k) {
+      const uint32_t c = cp[32 * (uint64_t)k];
+      bits += cb(c) & 31u;
       nun += (c == 0);
-      s += c;
-      is += (unsigned long long)(k + 1) * c;
+      if (ABFT) {
+        s += c;
+        mad_wide(is, c, k + 1);
+      }
     }
-    if (g.abft && (s != w.sum_q[b] || is != w.isum_q[b])) {
+    if (ABFT && (s != w.sum_q[b] || is != w.isum_q[b])) {
       long long delta = 0;
-      const long long m = locate_word(w.sum_q[b], w.isum_q[b], s, is, x.P, 0, &delta);
+      const long long m = locate_word(w.sum_q[b], w.isum_q[b], s, is, P, 0, &delta);
       bool fixed = false;
       if (m >= 0) {
-        const uint32_t old = w.codes[code_index(b, g.P, (uint32_t)m)];
+        const uint32_t old = cp[32 * (uint64_t)m];
         const long long nv = (long long)old - delta;
         if (nv >= 0 && nv < (long long)g.bins) {
           kfix = (uint32_t)m;
           vfix = (uint32_t)nv;
-          bits += (__ldg(&w.codebook[vfix]) & 31u) - (__ldg(&w.codebook[old]) & 31u);
+          bits += (cb(vfix) & 31u) - (cb(old) & 31u);
           nun += (vfix == 0) - (old == 0);
           fixed = true;
         }
@@ -94,69 +127,79 @@ __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict
   if (lane == 31)
     for (int q = 0; q < 3; ++q) s_wt[wid][q] = inc[q];
   __syncthreads();
-  if (tid == 0) {
+  if (wid == 0) {
+    // warp totals -> exclusive prefixes (lane 0), then a warp-wide decoupled look-back
     unsigned long long run[3] = {0, 0, 0};
-    for (int q2 = 0; q2 < 8; ++q2)
-      for (int q = 0; q < 3; ++q) {
-        unsigned long long t = s_wt[q2][q];
-        s_wt[q2][q] = run[q];
-        run[q] += t;
-      }
-    for (int q = 0; q < 3; ++q) s_tot[q] = run[q];
-    // decoupled look-back: publish the aggregate, sum predecessors until an inclusive prefix
+    if (lane == 0) {
+      for (int q2 = 0; q2 < 8; ++q2)
+        for (int q = 0; q < 3; ++q) {
+          const unsigned long long t = s_wt[q2][q];
+          s_wt[q2][q] = run[q];
+          run[q] += t;
+        }
+      for (int q = 0; q < 3; ++q) s_tot[q] = run[q];
+    }
+    for (int q = 0; q < 3; ++q) run[q] = __shfl_sync(0xffffffffu, run[q], 0);
     LookBack* me = &w.lb[gid];
     unsigned long long excl[3] = {0, 0, 0};
-    if (gid == 0) {
-      me->incl[0] = run[0];
-      me->incl[1] = run[1];
-      me->incl[2] = run[2];
-      __threadfence();
-      *(volatile unsigned int*)&me->incl_flag = 1u;
-    } else {
+    if (gid > 0 && lane == 0) {
       *(volatile unsigned long long*)&me->agg = pack_agg(run[0], run[1], run[2]);
       __threadfence();
-      int64_t p = (int64_t)gid - 1;
-      while (p >= 0) {
-        const LookBack* pr = &w.lb[p];
-        uint32_t spins = 0;
-        bool done = false;
-        for (;;) {
+    }
+    // lane l looks at predecessor gid-1-l-32r; the nearest one with an inclusive prefix ends it
+    bool finished = gid == 0;
+    for (int64_t base = (int64_t)gid - 1; !finished; base -= 32) {
+      const int64_t p = base - (int64_t)lane;
+      unsigned long long va[3] = {0, 0, 0};
+      bool incl = p < 0, ready = p < 0;
+      uint32_t spins = 0;
+      while (true) {
+        if (!ready) {
+          const LookBack* pr = &w.lb[p];
           if (*(volatile const unsigned int*)&pr->incl_flag) {
             __threadfence();
-            excl[0] += *(volatile const unsigned long long*)&pr->incl[0];
-            excl[1] += *(volatile const unsigned long long*)&pr->incl[1];
-            excl[2] += *(volatile const unsigned long long*)&pr->incl[2];
-            done = true;
-            break;
+            va[0] = *(volatile const unsigned long long*)&pr->incl[0];
+            va[1] = *(volatile const unsigned long long*)&pr->incl[1];
+            va[2] = *(volatile const unsigned long long*)&pr->incl[2];
+            incl = ready = true;
+          } else {
+            const unsigned long long a = *(volatile const unsigned long long*)&pr->agg;
+            if (a >> 62) {
+              va[0] = a & kMaskBytes;
+              va[1] = (a >> 22) & kMaskUn;
+              va[2] = (a >> 43) & 0x7ffffull;
+              ready = true;
+            }
           }
-          const unsigned long long a = ld_volatile(&pr->agg);
-          if (a >> 62) {
-            excl[0] += a & kMaskBytes;
-            excl[1] += (a >> 22) & kMaskUn;
-            excl[2] += (a >> 43) & 0x7ffffull;
-            break;
-          }
-          if (++spins > kSpinLimit) {
-            atomicOr(&st->error, ERR_TIMEOUT);
-            done = true;
-            break;
-          }
-          __nanosleep(64);
         }
-        if (done) break;
-        --p;
+        if (__all_sync(0xffffffffu, ready)) break;
+        if (++spins > kSpinLimit) {
+          if (lane == 0) atomicOr(&st->error, ERR_TIMEOUT);
+          ready = incl = true;  // give up: the stream is then reported as failed
+        }
+        __nanosleep(32);
       }
+      // lanes up to the nearest inclusive prefix contribute
+      const unsigned int im = __ballot_sync(0xffffffffu, incl);
+      const uint32_t stop = im ? (uint32_t)(__ffs(im) - 1) : 31u;
+      for (int q = 0; q < 3; ++q) {
+        unsigned long long c = lane <= stop ? va[q] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        excl[q] += c;
+      }
+      finished = im != 0;
+    }
+    if (lane == 0) {
       me->incl[0] = excl[0] + run[0];
       me->incl[1] = excl[1] + run[1];
       me->incl[2] = excl[2] + run[2];
       __threadfence();
       *(volatile unsigned int*)&me->incl_flag = 1u;
+      for (int q = 0; q < 3; ++q) s_excl[q] = excl[q];
     }
-    for (int q = 0; q < 3; ++q) s_excl[q] = excl[q];
   }
   __syncthreads();
 
-  const uint64_t s_dt = g.dtype ? 8 : 4;
   if (tid == 0) {
     const uint64_t go = L.groups + 24 * gid;
     for (int q = 0; q < 3; ++q) *reinterpret_cast<unsigned long long*>(out + go + 8 * q) = s_excl[q];
@@ -180,54 +223,60 @@ __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict
   const unsigned long long rg_off = s_excl[2] + s_wt[wid][2] + inc[2] - v[2];
   *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * b) = (uint16_t)bytes;
   *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * b) = (uint16_t)nun;
-  if (g.abft) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * b) = w.sum_dc[b];
+  if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * b) = w.sum_dc[b];
   if (reg) {
     const T* cT = static_cast<const T*>(w.coefT) + 4 * b;
     T* dst = reinterpret_cast<T*>(out + L.coef) + (uint64_t)(g.ndim + 1) * rg_off;
     for (int a = 0; a <= g.ndim; ++a) dst[a] = cT[a];
   }
   // pass 2: pack the codes MSB-first; copy the unpredictable values in order
-  const uint64_t pstart = L.payload + pay_off;
-  const bool fits = pstart + bytes <= cap;
+  const uint64_t lo = L.payload + pay_off, hi = lo + bytes;
+  const bool fits = hi <= cap;
   if (!fits) atomicOr(&st->error, ERR_CAPACITY);
-  uint8_t* dst = out + pstart;
+  uint64_t wa = lo & ~uint64_t(3);                  // aligned word being filled
+  unsigned long long acc = 0;
+  uint32_t nacc = 8u * (uint32_t)(lo & 3);          // leading bytes of the first word are not ours
   const T* ust = static_cast<const T*>(w.ustage);
   T* udst = reinterpret_cast<T*>(out + L.unpred);
   unsigned long long uidx = un_off;
   const unsigned long long ulim = st->n_unpred;
-  unsigned long long acc = 0;
-  uint32_t nacc = 0;
-  uint64_t ci = code_index(b, g.P, 0);
-  for (uint32_t k = 0; k < x.P; ++k, ci += 32) {
-    uint32_t c = w.codes[ci];
-    if (k == kfix) c = vfix;
-    const uint32_t cw = __ldg(&w.codebook[c]);
+  const uint16_t* cp = codes + code_index(b, g.P, 0);
+  const T* up = ust + code_index(b, g.P, 0);
+#pragma unroll 4
+  for (uint32_t k = 0; k < P; ++k) {
+    uint32_t c = cp[32 * (uint64_t)k];
+    if (ABFT && k == kfix) c = vfix;
+    const uint32_t cw = cb(c);
     const uint32_t len = cw & 31u;
     acc = (acc << len) | (cw >> 5);
     nacc += len;
-    while (nacc >= 8) {
-      nacc -= 8;
-      if (fits) *dst = (uint8_t)(acc >> nacc);
-      ++dst;
+    if (nacc >= 32) {
+      nacc -= 32;
+      put_word(out, wa, (uint32_t)(acc >> nacc), lo, hi, fits);
+      wa += 4;
     }
     if (c == 0) {
-      if (uidx < ulim) udst[uidx] = ust[ci];
+      if (uidx < ulim) udst[uidx] = up[32 * (uint64_t)k];
       ++uidx;
     }
   }
-  if (nacc && fits) *dst = (uint8_t)(acc << (8 - nacc));
+  if (nacc) put_word(out, wa, (uint32_t)(acc << (32 - nacc)), lo, hi, fits);
   if (bad) {
     // a block whose codes could not be repaired is reported in the header status word
     atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
   }
-  (void)s_dt;
 }
 
 void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
   const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
   if (!ngroups) return;
-  if (g.dtype == 0) k_encode<float><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
-  else k_encode<double><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
+  if (g.dtype == 0) {
+    if (g.abft) k_encode<float, true><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
+    else k_encode<float, false><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
+  } else {
+    if (g.abft) k_encode<double, true><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
+    else k_encode<double, false><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
+  }
 }
 
 }  // namespace sdcsz

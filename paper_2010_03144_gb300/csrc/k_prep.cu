@@ -344,6 +344,14 @@ static void run_fast(const void* field, const Geo& g, const Ws& w, const Launch&
   kern<<<(unsigned)((g.nb + 127) / 128), 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, vec2 ? 1 : 0);
 }
 
+// The full-block shapes with a fast path (cubes 4..16 in 3D, squares 8/12/16 in 2D).
+static bool has_fast(const Geo& g) {
+  if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2])
+    return g.B[2] == 4 || g.B[2] == 6 || g.B[2] == 8 || g.B[2] == 10 || g.B[2] == 12 || g.B[2] == 16;
+  if (g.ndim == 2 && g.B[1] == g.B[2]) return g.B[2] == 8 || g.B[2] == 12 || g.B[2] == 16;
+  return false;
+}
+
 template <typename T>
 static bool try_fast(const void* field, const Geo& g, const Ws& w, const Launch& L) {
   if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2]) {
@@ -381,11 +389,16 @@ static void run_generic(const void* field, const Geo& g, const Ws& w, bool all, 
 
 template <typename T>
 static void launch_prep_t(const void* field, const Geo& g, const Ws& w, const Launch& L) {
-  const bool fast = g.nb && try_fast<T>(field, g, w, L);
   if (g.nb) {
-    if (g.ndim == 3) run_generic<T, 3>(field, g, w, !fast, L);
-    else if (g.ndim == 2) run_generic<T, 2>(field, g, w, !fast, L);
-    else run_generic<T, 1>(field, g, w, !fast, L);
+    // edge blocks on the side stream, concurrently with the full blocks
+    Fork fk(L);
+    const Launch Ls = fk.side_launch(L);
+    const bool fast = has_fast(g);
+    if (g.ndim == 3) run_generic<T, 3>(field, g, w, !fast, fast ? Ls : L);
+    else if (g.ndim == 2) run_generic<T, 2>(field, g, w, !fast, fast ? Ls : L);
+    else run_generic<T, 1>(field, g, w, !fast, fast ? Ls : L);
+    if (fast) try_fast<T>(field, g, w, L);
+    fk.join();
   }
   k_bound<T><<<1, 1, 0, L.stream>>>(g, w.st);
 }

@@ -605,7 +605,7 @@ __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_
 
 // Fast kernel: full blocks of a compile-time shape (B0 x B1 x B2, leading 1s below 3D).
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
-__global__ void __launch_bounds__(128) k_predict_fast(const T* __restrict__ field, Geo g, Ws w,
+__global__ void __launch_bounds__(128, 7) k_predict_fast(const T* __restrict__ field, Geo g, Ws w,
                                                       const sdcsz_flip* __restrict__ flips, uint32_t nflips,
                                                       int vec2) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -709,6 +709,13 @@ void run_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
 }
 
 // Shapes with a fast path: cubes 4..16 in 3D, squares 8/12/16 in 2D.
+inline bool has_fast(const Geo& g) {
+  if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2])
+    return g.B[2] == 4 || g.B[2] == 6 || g.B[2] == 8 || g.B[2] == 10 || g.B[2] == 12 || g.B[2] == 16;
+  if (g.ndim == 2 && g.B[1] == g.B[2]) return g.B[2] == 8 || g.B[2] == 12 || g.B[2] == 16;
+  return false;
+}
+
 template <typename T, bool ABFT>
 bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
               const Launch& L) {
@@ -737,11 +744,16 @@ bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
 template <typename T, bool ABFT>
 void launch_predict_t(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
                       const Launch& L) {
-  const bool fast = try_fast<T, ABFT>(field, g, w, flips, nflips, L);
-  // edge blocks (or everything when no fast path exists for the shape)
-  if (g.ndim == 3) run_generic<T, 3, ABFT>(field, g, w, flips, nflips, !fast, L);
-  else if (g.ndim == 2) run_generic<T, 2, ABFT>(field, g, w, flips, nflips, !fast, L);
-  else run_generic<T, 1, ABFT>(field, g, w, flips, nflips, !fast, L);
+  // edge blocks (or everything when no fast path exists for the shape) on the side stream,
+  // concurrently with the full blocks
+  Fork fk(L);
+  const bool fast = has_fast(g);
+  const Launch Lg = fast ? fk.side_launch(L) : L;
+  if (g.ndim == 3) run_generic<T, 3, ABFT>(field, g, w, flips, nflips, !fast, Lg);
+  else if (g.ndim == 2) run_generic<T, 2, ABFT>(field, g, w, flips, nflips, !fast, Lg);
+  else run_generic<T, 1, ABFT>(field, g, w, flips, nflips, !fast, Lg);
+  if (fast) try_fast<T, ABFT>(field, g, w, flips, nflips, L);
+  fk.join();
 }
 
 }  // namespace

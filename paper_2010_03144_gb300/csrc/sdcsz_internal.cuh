@@ -426,6 +426,43 @@ struct Launch {
   int sms;
 };
 
+// A library-owned stream per device for work that can overlap the caller's stream.
+cudaStream_t side_stream();
+
+// Fork/join: work launched on `side` runs concurrently with the caller's stream between the
+// constructor and join(); join() makes the caller's stream wait for it. Events carry the
+// dependencies, so this also works while the caller's stream is being captured into a graph.
+struct Fork {
+  cudaStream_t main = nullptr, side = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool on = false;
+  explicit Fork(const Launch& L) : main(L.stream) {
+    side = side_stream();
+    if (!side || cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess) return;
+    if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) return;
+    cudaEventRecord(e0, main);
+    cudaStreamWaitEvent(side, e0, 0);
+    on = true;
+  }
+  Launch side_launch(const Launch& L) const {
+    Launch s = L;
+    if (on) s.stream = side;
+    return s;
+  }
+  void join() {
+    if (on) {
+      cudaEventRecord(e1, side);
+      cudaStreamWaitEvent(main, e1, 0);
+      on = false;
+    }
+  }
+  ~Fork() {
+    join();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
 void launch_prep(const void* field, const Geo& g, const Ws& w, const Launch& L);
 void launch_predict(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
                     const Launch& L);
