@@ -107,6 +107,7 @@ WsPlan plan_ws(const Geo& g) {
   const size_t nb = g.nb, s = g.dtype ? 8 : 4;
   const size_t ngroups = (nb + kGroup - 1) / kGroup;
   const size_t slots = ((nb + 31) / 32) * 32 * (size_t)g.P;
+  const size_t pair_slots = ((nb + 31) / 32) * 32 * (size_t)pairs_of(g.P);
   w.state = take(sizeof(State));
   w.sum_in = take(8 * nb);
   w.isum_in = take(8 * nb);
@@ -124,7 +125,7 @@ WsPlan plan_ws(const Geo& g) {
   w.sort_keys = take(8 * 65536);
   w.node_w = take(8 * 65536);
   w.node_parent = take(4 * 2 * 65536 + 2 * 65536);
-  w.codes = take(2 * slots);
+  w.codes = take(4 * pair_slots);
   w.ustage = take(s * slots);
   w.total = o;
   return w;

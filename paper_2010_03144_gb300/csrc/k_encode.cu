@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict
   const uint64_t b = gid * kGroup + tid;
   const bool active = b < g.nb;
   const Layout L = st->L;
-  const uint16_t* __restrict__ codes = w.codes;
+  const uint32_t* __restrict__ codes = reinterpret_cast<const uint32_t*>(w.codes);
 
   // pass 1: verify codes, count bits and unpredictables
   uint32_t P = 0, bits = 0, nun = 0, kfix = 0xffffffffu, vfix = 0;
@@ -82,15 +82,27 @@ __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict
     reg = w.flags[b] & 1;
     uint32_t s = 0;
     unsigned long long is = 0;
-    const uint16_t* cp = codes + code_index(b, g.P, 0);
-#pragma unroll 8
-    for (uint32_t k = 0; k < P; ++k) {
-      const uint32_t c = cp[32 * (uint64_t)k];
-      bits += cb(c) & 31u;
-      nun += (c == 0);
+    const uint32_t* pp = codes + pair_index(b, g.P, 0);
+    const uint32_t P2 = P >> 1;
+#pragma unroll 4
+    for (uint32_t k2 = 0; k2 < P2; ++k2) {
+      const uint32_t wp2 = pp[32 * (uint64_t)k2];
+      const uint32_t c0 = wp2 & 0xffffu, c1 = wp2 >> 16;
+      bits += (cb(c0) & 31u) + (cb(c1) & 31u);
+      nun += (c0 == 0) + (c1 == 0);
       if (ABFT) {
-        s += c;
-        mad_wide(is, c, k + 1);
+        s += c0 + c1;
+        mad_wide(is, c0, 2 * k2 + 1);
+        mad_wide(is, c1, 2 * k2 + 2);
+      }
+    }
+    if (P & 1) {  // odd point count: the last pair holds one code
+      const uint32_t c0 = pp[32 * (uint64_t)P2] & 0xffffu;
+      bits += cb(c0) & 31u;
+      nun += (c0 == 0);
+      if (ABFT) {
+        s += c0;
+        mad_wide(is, c0, P);
       }
     }
     if (ABFT && (s != w.sum_q[b] || is != w.isum_q[b])) {
@@ -98,7 +110,7 @@ __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict
       const long long m = locate_word(w.sum_q[b], w.isum_q[b], s, is, P, 0, &delta);
       bool fixed = false;
       if (m >= 0) {
-        const uint32_t old = cp[32 * (uint64_t)m];
+        const uint32_t old = (pp[32 * (uint64_t)(m >> 1)] >> (16 * (m & 1))) & 0xffffu;
         const long long nv = (long long)old - delta;
         if (nv >= 0 && nv < (long long)g.bins) {
           kfix = (uint32_t)m;
@@ -229,30 +241,43 @@ __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict
     T* dst = reinterpret_cast<T*>(out + L.coef) + (uint64_t)(g.ndim + 1) * rg_off;
     for (int a = 0; a <= g.ndim; ++a) dst[a] = cT[a];
   }
-  // pass 2: pack the codes MSB-first; copy the unpredictable values in order
+  // pass 2: pack the codes MSB-first; copy the unpredictable values in order. Every word
+  // emitted inside the loop is whole and inside the block except the first one when the block
+  // starts mid-word (its leading bytes belong to the previous block); the last, partial word
+  // is written after the loop.
   const uint64_t lo = L.payload + pay_off, hi = lo + bytes;
   const bool fits = hi <= cap;
   if (!fits) atomicOr(&st->error, ERR_CAPACITY);
   uint64_t wa = lo & ~uint64_t(3);                  // aligned word being filled
   unsigned long long acc = 0;
   uint32_t nacc = 8u * (uint32_t)(lo & 3);          // leading bytes of the first word are not ours
+  bool head = (lo & 3) != 0;
   const T* ust = static_cast<const T*>(w.ustage);
   T* udst = reinterpret_cast<T*>(out + L.unpred);
   unsigned long long uidx = un_off;
   const unsigned long long ulim = st->n_unpred;
-  const uint16_t* cp = codes + code_index(b, g.P, 0);
+  const uint32_t* pp = codes + pair_index(b, g.P, 0);
   const T* up = ust + code_index(b, g.P, 0);
+  const uint32_t cw0 = __ldg(&w.codebook[0]);
+  uint32_t wp2 = 0;
 #pragma unroll 4
   for (uint32_t k = 0; k < P; ++k) {
-    uint32_t c = cp[32 * (uint64_t)k];
+    if (!(k & 1)) wp2 = pp[32 * (uint64_t)(k >> 1)];
+    uint32_t c = (k & 1) ? (wp2 >> 16) : (wp2 & 0xffffu);
     if (ABFT && k == kfix) c = vfix;
-    const uint32_t cw = cb(c);
+    const uint32_t cw = c ? cb(c) : cw0;
     const uint32_t len = cw & 31u;
     acc = (acc << len) | (cw >> 5);
     nacc += len;
     if (nacc >= 32) {
       nacc -= 32;
-      put_word(out, wa, (uint32_t)(acc >> nacc), lo, hi, fits);
+      const uint32_t word = (uint32_t)(acc >> nacc);
+      if (head) {
+        put_word(out, wa, word, lo, hi, fits);
+        head = false;
+      } else if (fits) {
+        *reinterpret_cast<uint32_t*>(out + wa) = __byte_perm(word, 0, 0x0123);
+      }
       wa += 4;
     }
     if (c == 0) {

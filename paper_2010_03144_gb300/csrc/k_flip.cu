@@ -41,10 +41,9 @@ __global__ void k_flip_codes(Geo g, Ws w, const sdcsz_flip* flips, uint32_t n) {
     if (flips[t].site != SDCSZ_SITE_CODE || flips[t].block >= g.nb) continue;
     const Box x = block_box(g, flips[t].block);
     if (flips[t].index >= x.P) continue;
-    uint16_t* c = w.codes + code_index(flips[t].block, g.P, (uint32_t)flips[t].index);
-    const uintptr_t a = reinterpret_cast<uintptr_t>(c);
-    const uint32_t shift = (a & 2) ? 16u : 0u;
-    atomicXor(reinterpret_cast<unsigned int*>(a & ~uintptr_t(3)), (1u << (flips[t].bit & 15)) << shift);
+    const uint32_t k = (uint32_t)flips[t].index;
+    unsigned int* pw = reinterpret_cast<unsigned int*>(w.codes) + pair_index(flips[t].block, g.P, k);
+    atomicXor(pw, (1u << (flips[t].bit & 15)) << (16u * (k & 1)));
   }
 }
 

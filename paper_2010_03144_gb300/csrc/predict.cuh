@@ -143,7 +143,7 @@ __device__ __noinline__ PassRes generic_pass(const T* __restrict__ field, const 
                                              const Hooks hk, T xfix) {
   PassRes r = {0, 0, 0, 0, 0, 0, 0};
   Run run(g.R);
-  uint64_t ci = code_index(b, g.P, 0);
+  uint64_t ci = code_index(b, g.P, 0);  // unpredictable staging (one slot per point)
   uint32_t k = 0;
   for (uint32_t i = 0; i < x.e[0]; ++i) {
     for (uint32_t j = 0; j < x.e[1]; ++j) {
@@ -159,7 +159,7 @@ __device__ __noinline__ PassRes generic_pass(const T* __restrict__ field, const 
             k == hk.kp, hk.bitp, r.dup);
         T xr;
         const uint32_t code = quantize<T, ABFT, true>(v, pred, eb, inv2, Rh, g.R, k == hk.kr, hk.bitr, xr, r.dup);
-        codes[ci] = (uint16_t)code;
+        codes[code_pos(b, g.P, k)] = (uint16_t)code;
         if (!code) {
           ustage[ci] = v;
           ++r.nun;
@@ -201,7 +201,7 @@ __device__ __forceinline__ void load_row(const T* __restrict__ row, bool vec2, T
 template <typename T, int NDIM, int B0, int B1, int B2, int kCta, bool REG, bool ABFT, bool HOOK>
 __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t si, uint64_t sj, bool vec2,
                                              const T* cT, T* plane, T eb, T inv2, T Rh, uint32_t R,
-                                             uint16_t* __restrict__ cptr, T* __restrict__ uptr, const Hist& h,
+                                             uint32_t* __restrict__ pptr, T* __restrict__ uptr, const Hist& h,
                                              const Hooks hk, T xfix) {
   PassRes r = {0, 0, 0, 0, 0, 0, 0};
   Run run(R);
@@ -226,8 +226,9 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
       for (int l = 0; l < B2; ++l) x[l] = xn[l];
       if (j + 1 < B1) load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)(j + 1) * sj, vec2, xn);  // next row
       const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
-      uint16_t* crow = cptr + (uint64_t)k0 * 32;
+      uint32_t* prow = pptr + (uint64_t)(k0 >> 1) * 32;  // B2 is even: rows start on a pair
       T* urow = uptr + (uint64_t)k0 * 32;
+      uint32_t lowc = 0;
       // regression: (b0*i + b1*j) of this row, twice (primary and duplicate)
       T ra = T(0), rv = T(0);
       if (REG) {
@@ -239,7 +240,7 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
           rv = FT<T>::mul_v(cT[0], (T)j);
         }
       }
-      T* prow = plane + (uint64_t)j * B2 * kCta;
+      T* plrow = plane + (uint64_t)j * B2 * kCta;
       T c = T(0), ac = T(0), bc = T(0), abc = T(0);
 #pragma unroll
       for (int l = 0; l < B2; ++l) {
@@ -250,7 +251,7 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
         T a = T(0), bb = T(0), ab = T(0);
         if (!REG) {
           if (NDIM == 3) {
-            a = prow[l * kCta];
+            a = plrow[l * kCta];
             bb = brow[l];
             ab = arow[l];
           } else if (NDIM == 2) {
@@ -296,7 +297,8 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
             HOOK && k == hk.kp, hk.bitp, r.dup);
         T xr;
         const uint32_t code = quantize<T, ABFT, HOOK>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup);
-        crow[l * 32] = (uint16_t)code;
+        if (l & 1) prow[(l >> 1) * 32] = lowc | (code << 16);
+        else lowc = code;
         if (!code) {
           urow[l * 32] = v;
           ++r.nun;
@@ -309,7 +311,7 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
         run.push(code, h);
         if (!REG) {
           if (NDIM == 3) {
-            prow[l * kCta] = xr;
+            plrow[l * kCta] = xr;
             arow[l] = a;
             ac = a;
             bc = bb;
@@ -525,8 +527,7 @@ __device__ __forceinline__ bool locate_input(const T* field, const Geo& g, const
 }
 
 __device__ __forceinline__ void withdraw(const Ws& w, const Geo& g, uint64_t b, uint32_t P, const Hist& h) {
-  uint64_t ci = code_index(b, g.P, 0);
-  for (uint32_t kk = 0; kk < P; ++kk, ci += 32) h.sub1(w.codes[ci]);
+  for (uint32_t kk = 0; kk < P; ++kk) h.sub1(w.codes[code_pos(b, g.P, kk)]);
 }
 
 // Generic kernel: edge blocks (or every block when `all`), any shape.
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__(128) k_predict(const T* __restrict__ field, Ge
 
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool HOOK>
 __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_t si, uint64_t sj, bool vec2,
-                                                 const T* cT, T* plane, const Consts<T>& K, uint32_t R, uint16_t* cptr,
+                                                 const T* cT, T* plane, const Consts<T>& K, uint32_t R, uint32_t* cptr,
                                                  T* uptr, const Hist& h, const Hooks& hk, T xfix) {
   if (reg)
     return fast_pass<T, NDIM, B0, B1, B2, 128, true, ABFT, HOOK>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh, R,
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(128, 7) k_predict_fast(const T* __restrict__ f
     T cT[4];
     Hooks hk;
     load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
-    uint16_t* cptr = w.codes + code_index(b, P, 0);
+    uint32_t* cptr = reinterpret_cast<uint32_t*>(w.codes) + pair_index(b, P, 0);
     T* uptr = ustage + code_index(b, P, 0);
     const bool hooked = (hk.kp != kNone) || (hk.kr != kNone);
     PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R,

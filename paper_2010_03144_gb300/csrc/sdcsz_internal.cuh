@@ -81,7 +81,7 @@ struct Ws {
   unsigned long long* sort_keys;  // codebook construction scratch
   unsigned long long* node_w;
   uint32_t* node_parent;
-  uint16_t* codes;     // quantization codes, warp-interleaved: ((b/32)*P + k)*32 + b%32
+  uint16_t* codes;     // quantization codes in warp-interleaved pairs (see pair_index)
   void* ustage;        // unpredictable values, same interleaving as codes
 };
 
@@ -105,6 +105,17 @@ __host__ __device__ inline Layout make_layout(const Geo& g, uint64_t n_live, uin
 
 __host__ __device__ inline uint64_t code_index(uint64_t b, uint32_t P, uint32_t k) {
   return ((b >> 5) * (uint64_t)P + k) * 32 + (b & 31);
+}
+
+// Quantization codes are staged in pairs: the 32-bit word pair_index(b, P, k) holds the codes
+// of points k & ~1 (low half) and k | 1 (high half) of block b, warp-interleaved so that a
+// warp's 32 lanes (32 consecutive blocks) move 128 contiguous bytes per instruction.
+__host__ __device__ inline uint32_t pairs_of(uint32_t P) { return (P + 1) / 2; }
+__host__ __device__ inline uint64_t pair_index(uint64_t b, uint32_t P, uint32_t k) {
+  return ((b >> 5) * (uint64_t)pairs_of(P) + (k >> 1)) * 32 + (b & 31);
+}
+__host__ __device__ inline uint64_t code_pos(uint64_t b, uint32_t P, uint32_t k) {
+  return 2 * pair_index(b, P, k) + (k & 1);
 }
 
 // Block b's origin and extents (edge blocks are cut to the field).
