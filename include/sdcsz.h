@@ -161,6 +161,23 @@ int sdcsz_decompress_traced(const void* d_stream, size_t nbytes, void* d_field, 
                             uint8_t* d_block_status, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,
                             float* stage_ms);
 
+/*
+ * Allocation-free compression. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory when they compress (while capturing a stream
+ * into a CUDA graph, inside callbacks or latency-critical serving loops, or when another
+ * framework owns the device memory pool). It runs the same kernels as sdcsz_compress, with the
+ * workspace in a fixed 64 MiB device array that every GPU loading this library holds until the
+ * process exits; it calls no allocator. Arguments as for sdcsz_compress, without d_ws/ws_bytes.
+ *  - Returns SDCSZ_ECAPACITY when sdcsz_workspace_size(p) exceeds 64 MiB (float32 fields up to
+ *    about ten million points fit).
+ *  - The first call on a device looks up the array's device address; make that first call
+ *    before any stream capture.
+ *  - All calls share the array: calls whose GPU work overlaps (different streams, or
+ *    different host threads) race and corrupt each other's output. Serialize them.
+ */
+int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap,
+                           size_t* out_bytes, sdcsz_report* report, void* stream);
+
 /* Parse a stream header held in HOST memory (the first 128 bytes suffice for dims and
  * dtype; total_bytes is the full stream length). */
 int sdcsz_read_header(const void* h_stream, size_t nbytes, sdcsz_params* out, uint64_t* total_bytes);

@@ -25,7 +25,7 @@ BLOCK_OK, BLOCK_CORRECTED, BLOCK_SDC, BLOCK_BAD = 0, 1, 2, 3
 EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_workspace_size", "sdcsz_compress",
            "sdcsz_decompress", "sdcsz_verify", "sdcsz_read_header", "sdcsz_strerror",
            "sdcsz_debug_compress_flips", "sdcsz_debug_decompress_flips", "sdcsz_compress_traced",
-           "sdcsz_decompress_traced")
+           "sdcsz_decompress_traced", "sdcsz_compress_noalloc")
 
 
 class SdcszError(RuntimeError):
@@ -99,6 +99,8 @@ def lib():
         L.sdcsz_compress_traced.argtypes = [vp, P, vp, sz, ctypes.POINTER(sz), vp, sz, R, vp, fp]
         L.sdcsz_decompress_traced.argtypes = [vp, sz, vp, sz, vp, vp, sz, R, vp, fp]
         L.sdcsz_compress_traced.restype = i32
+        L.sdcsz_compress_noalloc.argtypes = [vp, P, vp, sz, ctypes.POINTER(sz), R, vp]
+        L.sdcsz_compress_noalloc.restype = i32
         L.sdcsz_decompress_traced.restype = i32
         L.sdcsz_read_header.argtypes = [vp, sz, P, ctypes.POINTER(ctypes.c_uint64)]
         L.sdcsz_strerror.argtypes = [i32]
@@ -325,3 +327,18 @@ def decompress_traced(stream_t, out, ws, stream=None):
     if rc not in (OK,):
         raise SdcszError(rc, "decompress_traced")
     return ms[0]
+
+
+def compress_noalloc(field, out, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
+                     stream=None):
+    """Compress into the caller's uint8 CUDA tensor `out` with the library's fixed scratch
+    (no device allocation by the library). Returns (stream bytes view, report dict)."""
+    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor)
+    n = ctypes.c_size_t()
+    rep = Report()
+    rc = lib().sdcsz_compress_noalloc(ctypes.c_void_p(field.data_ptr()), ctypes.byref(p),
+                                      ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(n),
+                                      ctypes.byref(rep), _stream_handle(stream))
+    if rc:
+        raise SdcszError(rc, "compress_noalloc")
+    return out[: n.value], rep.as_dict()

@@ -472,3 +472,50 @@ const char* sdcsz_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free compression
+// Some callers cannot allocate device memory at the moment they compress: code running while
+// a stream is being captured into a CUDA graph (allocation is not a capturable operation),
+// callbacks and latency-critical serving loops that must not enter the allocator, and hosts
+// whose device memory is owned by another framework's pool. For them, sdcsz_compress_noalloc
+// runs the same kernels with the workspace placed in a fixed device array of this library.
+
+namespace sdcsz {
+namespace {
+
+// Workspace of the allocation-free entry point. Every GPU that loads this library holds these
+// 64 MiB until the process exits; all calls share them.
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// In host code `g_static_scratch` only names the symbol; its device address is looked up once
+// per device (with that device current) and cached.
+void* static_scratch_address() {
+  static std::mutex mu;
+  static void* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return nullptr;
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+}  // namespace
+}  // namespace sdcsz
+
+extern "C" int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap,
+                                      size_t* out_bytes, sdcsz_report* report, void* stream) {
+  Geo g;
+  const int rc = make_geo(p, &g);
+  if (rc) return rc;
+  if (plan_ws(g).total > kStaticScratchBytes) return SDCSZ_ECAPACITY;  // field too large for the array
+  void* ws = static_scratch_address();
+  if (!ws) return SDCSZ_ECUDA;
+  // the regions that must start at zero (state, histogram, look-back records) are cleared on
+  // the stream by every call; everything else is written before it is read
+  return compress_impl(d_field, p, d_out, out_cap, out_bytes, ws, kStaticScratchBytes, report, stream, nullptr, 0);
+}

@@ -1,0 +1,60 @@
+"""The allocation-free compression entry point (sdcsz_compress_noalloc).
+
+Callers that cannot allocate device memory while they compress (stream capture, callbacks,
+serving loops, memory owned by another framework) use this entry point; the library then works
+in its fixed 64 MiB device array. Its streams must be identical to those of sdcsz_compress, call
+after call: the array keeps the previous call's contents, so two calls in a row check that
+everything which must start at zero is cleared by each call.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from parity import gpu_sz
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(sz, d, p, out):
+    n = ctypes.c_size_t()
+    rep = sz.Report()
+    rc = sz.lib().sdcsz_compress_noalloc(ctypes.c_void_p(d.data_ptr()), ctypes.byref(p),
+                                         ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(n),
+                                         ctypes.byref(rep), sz._stream_handle(None))
+    return rc, n.value, rep.as_dict()
+
+
+def test_noalloc_matches_compress_on_consecutive_calls():
+    import torch
+    sz = gpu_sz()
+    cases = [((64, 64, 64), np.float32, 6, 1e-3, 1), ((50, 61, 47), np.float32, 6, 1e-4, 2),
+             ((180, 361), np.float64, 12, 1e-5, 3), ((64, 64, 64), np.float32, 6, 1e-3, 4)]
+    for shape, dt, block, eb, seed in cases:
+        x = synth.sinusoid_field(shape, seed, dtype=dt, spikes=0.01)
+        d = torch.from_numpy(x).cuda()
+        ref, rep_ref = sz.compress(d, eb, block=block)
+        p = sz.make_params(shape, dt, eb, block=block)
+        out = torch.zeros(sz.compress_bound(p), dtype=torch.uint8, device="cuda")
+        for call in range(2):  # two calls in a row on the shared array
+            out.fill_(0xA5)
+            rc, n, rep = _noalloc(sz, d, p, out)
+            assert rc == 0, sz.strerror(rc)
+            assert n == ref.numel()
+            assert torch.equal(out[:n], ref), (shape, call)
+            assert rep["eb_abs"] == rep_ref["eb_abs"] and rep["blocks"] == rep_ref["blocks"]
+        rc, y, st, _ = sz.decompress(out[:n])
+        rc2, y2, _, _ = sz.decompress(ref)
+        assert rc == rc2 == 0 and torch.equal(y, y2)
+
+
+def test_noalloc_rejects_fields_beyond_its_array():
+    import torch
+    sz = gpu_sz()
+    tiny = torch.zeros(16, dtype=torch.float32, device="cuda")
+    out = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    p = sz.make_params((1024, 1024, 1024), np.float32, 1e-3)
+    rc, n, rep = _noalloc(sz, tiny, p, out)
+    assert rc == sz.ECAPACITY
