@@ -68,7 +68,7 @@ typedef enum { SDCSZ_PRED_AUTO = 0, SDCSZ_PRED_LORENZO = 1, SDCSZ_PRED_REGRESSIO
  *  quant_bins  number of quantization bins, even, 2..65536; 0 = 65536.
  *  abft        1 = fault-tolerant mode (the paper's ftrsz), 0 = independent blocks without
  *              checks (rsz).
- *  predictor   sdcsz_predictor; AUTO selects per block by estimated error (Alg. 1 l. 6-8).
+ *  predictor   sdcsz_predictor; AUTO selects per block by estimated error (Algorithm 1).
  */
 typedef struct {
   uint32_t ndim;
@@ -83,16 +83,16 @@ typedef struct {
   uint32_t reserved; /* must be 0 */
 } sdcsz_params;
 
-/* Counters of one call (Alg. 2 lines 17 and 19 report to the user). */
+/* Counters of one call (Algorithm 2 reports corrected errors and SDCs to the user). */
 typedef struct {
   uint64_t blocks;
   uint64_t regression_blocks;
   uint64_t unpredictable_points;
   uint64_t compressed_bytes;
-  uint64_t input_corrected;         /* input words repaired with sum_in/isum_in (Alg. 1 l. 11) */
-  uint64_t codes_corrected;         /* codes repaired with sum_q/isum_q (Alg. 1 l. 35) */
-  uint64_t dup_mismatch_corrected;  /* duplicated prediction/reconstruction disagreed (l. 18, 25) */
-  uint64_t decomp_reexec_corrected; /* blocks fixed by re-execution (Alg. 2 l. 14-17) */
+  uint64_t input_corrected;         /* input words repaired with sum_in/isum_in */
+  uint64_t codes_corrected;         /* codes repaired with sum_q/isum_q */
+  uint64_t dup_mismatch_corrected;  /* f_dup / dec_dup disagreed (Algorithm 1) */
+  uint64_t decomp_reexec_corrected; /* blocks fixed by re-execution (Algorithm 2) */
   uint64_t uncorrectable_blocks;    /* detected, not correctable (outside the single-error model) */
   uint64_t bound_violations;        /* verify with an original: points with |x - x'| > eb */
   double eb_abs;                    /* the absolute bound used */
@@ -101,8 +101,8 @@ typedef struct {
 
 /* Block status values written by decompress/verify. */
 #define SDCSZ_BLOCK_OK 0
-#define SDCSZ_BLOCK_CORRECTED 1     /* checksum mismatch fixed by re-execution (Alg. 2 l. 17) */
-#define SDCSZ_BLOCK_SDC 2           /* checksum mismatch twice (Alg. 2 l. 19) */
+#define SDCSZ_BLOCK_CORRECTED 1     /* checksum mismatch fixed by re-execution */
+#define SDCSZ_BLOCK_SDC 2           /* checksum mismatch twice: SDC in compression */
 #define SDCSZ_BLOCK_BAD 3           /* undecodable block data */
 
 /* Upper bound on the stream size for `p` (every point unpredictable with a 24-bit code). */

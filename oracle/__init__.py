@@ -244,7 +244,7 @@ def regression(block_values: np.ndarray):
 
 
 def compress_block(field: np.ndarray, eb_abs: float, b: int, block=None, bins=65536, predictor="auto"):
-    """One block of Alg. 1 lines 10-32 at a given absolute bound (no ABFT verification)."""
+    """One block of Algorithm 1's prediction loop at a given absolute bound (no ABFT verification)."""
     field = np.ascontiguousarray(field)
     p = make_params(field.shape, field.dtype, eb_abs, "abs", block, bins, False, predictor)
     codes = np.zeros(4096, dtype=np.uint16)

@@ -18,13 +18,14 @@
 //   Sec. 5.4   Checksums over the bit patterns (u32 words widened to u64; fp64 = 2 words).
 //   Sec. 5.5   CR-decrease bound for unprotected regression/sampling.
 //
-// Where the paper is silent the oracle takes one fixed reading; every such reading is
-// listed (with its reason) in the design notes at the repository root. In brief:
+// Where the paper is silent the oracle takes one fixed reading, which the CUDA library
+// implements identically:
 //   * partial edge blocks use their actual extents; local order is row-major;
 //   * value-range bound eb = (T)(e * ((double)max - (double)min)) over finite values;
 //   * checksum weights are 1-based so every word contributes to isum;
-//   * the input is verified/corrected before regression and sampling (the paper verifies
-//     before prediction only; verifying earlier keeps the output identical to a clean run);
+//   * regression and the sampled estimates read the input as it is when compression starts;
+//     the input is verified/corrected before any value is predicted, and the E_reg estimate
+//     of a repaired block is taken again from the repaired values;
 //   * regression: closed-form least squares on the block grid in fp32, sequential sums;
 //   * selection: the sample is a set of whole rows (one diagonal row per plane in 3D, every
 //     fourth row in 2D); E_lor adds kappa*eb per sample point;
@@ -237,7 +238,7 @@ T regress(const T* coef, int ndim, const uint32_t coord3[3]) {
   return acc + coef[ndim];
 }
 
-// Closed-form least-squares fit on the regular block grid, in fp32 (Alg. 1 line 2).
+// Closed-form least-squares fit on the regular block grid, in fp32 (Algorithm 1, regression).
 // Slopes decouple on a full grid: b_a = sum x*(c_a - ctr_a) / sum (c_a - ctr_a)^2, and the
 // intercept makes the fit pass through the mean. Sums are taken per row along the fastest
 // axis first (r0 = sum x, rl = sum x*(l - ctr_l), in increasing l), then the row sums are
@@ -279,7 +280,7 @@ bool regression_coefficients(const T* v, const uint32_t e[3], int ndim, float co
   return true;
 }
 
-// The sample of Alg. 1 line 7: whole rows along the fastest axis. 3D: one row per plane, the
+// The sample of Algorithm 1's "sample and estimate" step: whole rows along the fastest axis. 3D: one row per plane, the
 // "diagonal" rows (i, i mod e1); 2D: every fourth row starting with row 1 (rows 1, 5, 9, ...);
 // 1D: the whole block.
 bool sample_row(int ndim, uint32_t i, uint32_t j, const uint32_t e[3]) {
@@ -296,7 +297,7 @@ uint64_t sample_points(int ndim, const uint32_t e[3]) {
   return n;
 }
 
-// Selection estimates (Alg. 1 lines 6-7), in fp32 over the sample points in local order:
+// Selection estimates (Algorithm 1), in fp32 over the sample points in local order:
 // E_reg = sum |x - f_reg|, E_lor = sum |x - Lorenzo(original values)|.
 template <typename T>
 void selection_estimates(const T* v, const uint32_t e[3], int ndim, const float coef[4], float* Ereg_out,
@@ -320,7 +321,7 @@ void selection_estimates(const T* v, const uint32_t e[3], int ndim, const float 
   *Elor_out = Elor;
 }
 
-// Alg. 1 line 8: the predictor with the smaller estimated error. E_lor gets the expected
+// Algorithm 1's indicator: the predictor with the smaller estimated error. E_lor gets the expected
 // effect of predicting from reconstructed instead of original neighbours: kappa*eb per point,
 // kappa = E|sum of n uniform(-eb,eb)| / eb for the n = 1, 3, 7 Lorenzo terms of 1D/2D/3D
 // (normal approximation for 2D/3D).
@@ -360,7 +361,7 @@ const orc_flip* find_flip(const Ctx& c, uint32_t site, uint64_t block, uint64_t 
   return nullptr;
 }
 
-// Prediction preparation for one block (Alg. 1 line 2, lines 6-7): regression coefficients
+// Prediction preparation for one block (Algorithm 1, Sec. 4.1.1): regression coefficients
 // and the two error estimates, from the block's values as they are in the first pass.
 struct Prep {
   float coef[4] = {0, 0, 0, 0};
@@ -397,9 +398,9 @@ bool indicator_of(const Ctx& c, const Prep& pr, const uint32_t e[3], float ebf) 
   return select_regression(pr.Ereg, pr.Elor, sample_points(c.g.ndim, e), c.g.ndim, ebf);
 }
 
-// Alg. 1 lines 10-31 for one block: verify the input (line 11), pick f() from the indicator
-// (lines 12-16), then the prediction loop with duplicated prediction and reconstruction
-// (lines 18, 25) and the block checksums (lines 24, 29).
+// Algorithm 1's prediction loop for one block: verify the input with sum_in/isum_in, pick f()
+// from the indicator, then predict every point with duplicated prediction and
+// reconstruction (f_dup, dec_dup) and take the block checksums (sum_q/isum_q, sum_dc).
 template <typename T>
 void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint64_t sum_in, uint64_t isum_in,
                     const Prep& pr, BlockResult<T>* out) {
@@ -410,7 +411,7 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
   const uint64_t P = (uint64_t)e[0] * e[1] * e[2];
   uint64_t k = 0;
 
-  // Alg. 1 line 11: memory-error detection and correction with sum_in / isum_in.
+  // memory-error detection and correction with sum_in / isum_in (Algorithm 1, Sec. 3.2)
   if (c.abft) {
     const int W = Bits<T>::kWords;
     std::vector<uint32_t> w(P * W);
@@ -428,7 +429,7 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
     if (f) out->coef[a] = Bits<T>::flip(out->coef[a], f->bit);
   }
 
-  // Alg. 1 lines 17-31.
+  // the per-point loop
   const T Rh = (T)c.R - (T)0.5;
   std::vector<T> xrec(P);
   out->code.assign(P, 0);
@@ -442,7 +443,7 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
         auto predict = [&]() -> T {
           return use_reg ? regress<T>(out->coef, g.ndim, c3) : lorenzo<T>(xrec.data(), e, g.ndim, i, j, l);
         };
-        // line 18: pred' <- f_dup(); a disagreement is settled by a third evaluation.
+        // pred' <- f_dup(); a disagreement is settled by a third evaluation
         T pred = predict();
         if (c.abft) {
           const orc_flip* f = find_flip(c, SITE_PRED, b, k);
@@ -454,15 +455,15 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
           }
         }
         const T x = v[k];
-        const T diff = x - pred;                    // line 19
-        const T t = std::fabs(diff) * inv2;         // line 20: linear-scaling quantization
+        const T diff = x - pred;
+        const T t = std::fabs(diff) * inv2;         // linear-scaling quantization
         uint16_t code = 0;
         T xr = x;
-        if (t < Rh) {                               // line 21: bin within range (false for NaN)
+        if (t < Rh) {                               // bin within range (false for NaN)
           int32_t m = (int32_t)(t + (T)0.5);
           int32_t q = diff < (T)0 ? -m : m;
           auto decode = [&]() -> T { return pred + (T)(2 * q) * eb; };
-          T xd = decode();                          // line 25: dcmp <- dec_dup(q, pred')
+          T xd = decode();                          // dcmp <- dec_dup(q, pred')
           if (c.abft) {
             const orc_flip* f = find_flip(c, SITE_RECON, b, k);
             if (f) xd = Bits<T>::flip(xd, f->bit);
@@ -472,23 +473,23 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
               out->dup_fixed++;
             }
           }
-          if (std::fabs(x - xd) <= eb) {            // lines 26-28: double check vs machine epsilon
+          if (std::fabs(x - xd) <= eb) {            // double check vs machine epsilon (Sec. 4.1.2)
             code = (uint16_t)(q + (int32_t)c.R);
             xr = xd;
           }
         }
-        if (code == 0) out->n_unpred++;             // lines 22 / 27: unpredictable, stored raw
+        if (code == 0) out->n_unpred++;             // unpredictable, stored raw
         out->code[k] = code;
         xrec[k] = xr;
-        out->sum_q += code;                         // line 24
+        out->sum_q += code;                         // sum_q, isum_q
         out->isum_q += (k + 1) * (uint64_t)code;
         uint32_t w[2] = {0, 0};
         Bits<T>::words(xr, w);
-        for (int m = 0; m < Bits<T>::kWords; ++m) out->sum_dc += w[m];  // line 29
+        for (int m = 0; m < Bits<T>::kWords; ++m) out->sum_dc += w[m];  // sum_dc
       }
 }
 
-// ---------------------------------------------------------------- Huffman (Alg. 1 line 33)
+// ---------------------------------------------------------------- Huffman (Algorithm 1)
 // Code lengths for a histogram. Huffman's algorithm with a priority queue keyed by
 // (weight, creation order): leaves are created in increasing (count, symbol) order, then
 // internal nodes in the order they are formed. Lengths longer than kMaxLen are reduced
@@ -640,7 +641,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   c.flips = flips;
   c.nflips = nflips;
 
-  // Alg. 1 lines 1-5 (with the estimates of lines 6-7): per block input checksums,
+  // Algorithm 1's first loops: per block input checksums,
   // regression coefficients and selection estimates; the value range for the bound.
   std::vector<uint64_t> sum_in(g.nb, 0), isum_in(g.nb, 0);
   std::vector<Prep> prep(g.nb);
@@ -687,7 +688,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
       field[pt] = Bits<T>::from_words(w);
     }
 
-  // Alg. 1 lines 10-32, one block at a time; the histogram is taken as codes are made.
+  // Algorithm 1's prediction loop, one block at a time; the histogram is taken as codes are made.
   std::vector<BlockResult<T>> blk(g.nb);
   std::vector<uint64_t> hist(c.bins, 0);
   orc_report r;
@@ -706,14 +707,14 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
     if (flips[n].site == SITE_CODE && flips[n].block < g.nb && flips[n].index < blk[flips[n].block].code.size())
       blk[flips[n].block].code[flips[n].index] ^= (uint16_t)(1u << (flips[n].bit & 15));
 
-  // Alg. 1 line 33: one Huffman code for the whole bin array.
+  // one Huffman code for the whole bin array (Algorithm 1)
   std::vector<uint8_t> len(c.bins);
   huffman_lengths(hist.data(), c.bins, len.data());
   Canon canon;
   std::vector<uint32_t> code_of;
   canon_from_lengths(len.data(), c.bins, &canon, &code_of);
 
-  // Alg. 1 lines 34-37: verify each block's codes, then encode the block on its own.
+  // verify each block's codes with sum_q/isum_q, then encode the block on its own (Algorithm 1)
   std::vector<std::vector<uint8_t>> payload(g.nb);
   std::vector<uint32_t> ucount(g.nb, 0);
   uint64_t n_unpred = 0, n_reg = 0, payload_bytes = 0;
@@ -744,7 +745,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   r.regression_blocks = n_reg;
   r.unpredictable_points = n_unpred;
 
-  // Alg. 1 lines 38-40 (without the Zstd stage): write the stream.
+  // write the stream (Algorithm 1's output step, without the Zstd stage)
   const uint64_t s = sizeof(T);
   const uint64_t n_live = canon.symbols.size();
   Layout L = make_layout(g, c.abft, n_live, n_reg, n_unpred);
@@ -873,7 +874,7 @@ int decode_symbol(const uint8_t* pay, uint64_t* bit, uint64_t end, const Canon& 
   return -1;
 }
 
-// Alg. 2 lines 3-8 for one block: Huffman decode then Lorenzo or regression decompression.
+// One block of Algorithm 2's decompression loop: Huffman decode, then Lorenzo or regression.
 // Returns false on a malformed block.
 template <typename T>
 bool decompress_block(const Parsed& P, const uint8_t* s, uint64_t b, uint64_t pay_off, uint64_t un_off,
@@ -962,7 +963,7 @@ int decompress_impl(const uint8_t* s, uint64_t n, T* field, uint8_t* status, con
   }
   if (pay != P.payload_bytes || un != P.n_unpred || rg != P.n_reg) return EFORMAT;
 
-  // Alg. 2 lines 2-9: decompress every block.
+  // Algorithm 2: decompress every block
   std::vector<std::vector<T>> dec(g.nb);
   std::vector<uint64_t> sums(g.nb);
   std::vector<uint8_t> ok(g.nb);
@@ -973,7 +974,7 @@ int decompress_impl(const uint8_t* s, uint64_t n, T* field, uint8_t* status, con
     dec[b].assign((uint64_t)e[0] * e[1] * e[2], (T)0);
     ok[b] = decompress_block<T>(P, s, b, pay_off[b], un_off[b], reg_idx[b], flips, nflips, true, dec[b].data(), &sums[b]);
   }
-  // Alg. 2 lines 10-22: check each block against sum_dc, re-execute once on a mismatch.
+  // Algorithm 2: check each block against sum_dc, re-execute once on a mismatch
   int result = OK;
   for (uint64_t b = 0; b < g.nb; ++b) {
     uint8_t st = 0;
@@ -1077,7 +1078,7 @@ int orc_regression(const void* v, uint32_t dtype, uint32_t ndim, const uint32_t*
   return regression_coefficients<double>((const double*)v, e, (int)ndim, coef) ? 1 : 0;
 }
 
-// One block of Alg. 1 lines 10-32 with a given absolute bound: codes, reconstructed values
+// One block of Algorithm 1's prediction loop with a given absolute bound: codes, reconstructed values
 // (through sum_dc), coefficients, predictor flag. Used for sampled checks on large fields.
 int orc_compress_block(const void* field, const orc_params* p, double eb_abs, uint64_t b, uint16_t* codes,
                        void* coef, uint8_t* is_reg, uint64_t* sums /* sum_q, isum_q, sum_dc */, uint64_t* n_points) {

@@ -5,9 +5,9 @@
 // shared memory (longer codes resolve through the canonical first-code table), scans the
 // group's block table for per-block offsets and checks the group table against it. Each
 // thread then decodes its block and reconstructs it with the Lorenzo or regression predictor
-// (lines 2-9). For fault-tolerant streams the block's checksum is compared with sum_dc
-// (lines 11-13); on a mismatch the block is decompressed once more from its compressed bytes
-// (line 14) and reported corrected (line 17) or as an SDC (line 19).
+// (the decompression loop of Algorithm 2). For fault-tolerant streams the block's checksum is
+// compared with sum_dc; on a mismatch the block is decompressed once more from its compressed
+// bytes (random-access re-execution) and reported corrected or as an SDC in compression.
 // As in compression, full blocks of the common shapes take a fast kernel with compile-time
 // edges and edge blocks a generic kernel.
 #pragma once
@@ -518,7 +518,7 @@ __device__ __forceinline__ bool is_full(const Geo& g, uint64_t b) {
   return (c0 + 1) * g.B[0] <= g.d[0] && (c1 + 1) * g.B[1] <= g.d[1] && (c2 + 1) * g.B[2] <= g.d[2];
 }
 
-// Alg. 2 lines 11-22 around one decode: verify against sum_dc, re-execute once.
+// Algorithm 2's verification around one decode: check against sum_dc, re-execute once.
 template <class F>
 __device__ __forceinline__ uint8_t verify_block(const uint8_t* s, const Hdr& h, uint64_t b, F run, Acc& acc) {
   unsigned long long sum = 0, nv = 0;
@@ -528,7 +528,7 @@ __device__ __forceinline__ uint8_t verify_block(const uint8_t* s, const Hdr& h, 
   if (h.g.abft) {
     const unsigned long long ref = ld_u64(s + h.L.sumdc + 8 * b);
     if (!ok || sum != ref) {
-      ok = run(false, &sum, &nv, &me);  // line 14: decompress this block again
+      ok = run(false, &sum, &nv, &me);  // decompress this block again from its bytes
       if (ok && sum == ref) {
         stv = SDCSZ_BLOCK_CORRECTED;
         ++acc.fix;

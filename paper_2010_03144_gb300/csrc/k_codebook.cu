@@ -1,4 +1,4 @@
-// K3: Huffman code for the whole bin array (Alg. 1 line 33), the stream header and the
+// K3: Huffman code for the whole bin array (Algorithm 1), the stream header and the
 // section layout. One CTA of 1024 threads.
 //
 //   1. compact the live symbols into keys (count << 16 | symbol) and sort them ascending:

@@ -1,9 +1,9 @@
-// K4: per-block Huffman encoding and stream assembly (Alg. 1 lines 34-40 of the paper,
-// without the Zstd stage).
+// K4: per-block Huffman encoding and stream assembly (the encoding and output steps of
+// Algorithm 1 of the paper, without the Zstd stage).
 //
 // One CTA per random-access group of 256 blocks, one thread per block. Pass 1 reads the
-// block's codes, checks them against sum_q/isum_q (line 35: a single corrupted code is located
-// and repaired) and sums the code lengths. A CTA scan plus a single-pass decoupled look-back
+// block's codes, checks them against sum_q/isum_q (Algorithm 1's check of the bin array before
+// encoding: a single corrupted code is located and repaired) and sums the code lengths. A CTA scan plus a single-pass decoupled look-back
 // across groups (group ids taken from a ticket in launch order, every wait bounded) gives each
 // block its payload, unpredictable-value and coefficient offsets. Pass 2 re-reads the codes
 // (L2 resident) and packs the bits MSB-first into 32-bit words: words wholly inside the

@@ -1,11 +1,12 @@
-// K1: prediction preparation and input checksums (Alg. 1 lines 1-7 of the paper).
+// K1: prediction preparation and input checksums (the first two loops of Algorithm 1 of the
+// paper: regression, checksums, sampling).
 //
 // One thread per block, a warp per 32 consecutive blocks. A single pass over the block
 // computes, from the input as it is when compression starts:
-//   * sum_in / isum_in over the block's 32-bit words (Alg. 1 lines 3-4; Sec. 3.2, 5.4),
+//   * sum_in / isum_in over the block's 32-bit words (Algorithm 1; Sec. 3.2, 5.4),
 //   * the regression sums (per row first, then per block) and the closed-form least-squares
-//     coefficients (line 2),
-//   * the Lorenzo estimate E_lor on the original values (lines 6-7),
+//     coefficients,
+//   * the Lorenzo estimate E_lor on the original values of the sample rows,
 //   * the value range for the value-range relative bound;
 // the regression estimate E_reg, which needs the coefficients, is taken by K2 just before it
 // predicts the block (its re-read of the block then hits the cache).

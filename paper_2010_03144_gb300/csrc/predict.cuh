@@ -1,12 +1,13 @@
-// K2: prediction, quantization and block checksums (Alg. 1 lines 8 and 10-32 of the paper).
+// K2: prediction, quantization and block checksums (the predictor choice and the per-block
+// prediction loop of Algorithm 1 of the paper).
 //
 // One thread per block, a warp per 32 consecutive blocks, persistent CTAs. Per block:
-//   * predictor choice from the K1 estimates (line 8),
+//   * predictor choice from the K1 estimates (indicator[i]),
 //   * one pass over the block in its sequential order: prediction evaluated twice
-//     (f_dup, line 18), linear-scaling quantization (lines 19-21), reconstruction evaluated
-//     twice (dec_dup, line 25), the machine-epsilon double check (lines 26-28), the code,
-//     sum_q/isum_q (line 24) and sum_dc (line 29), and the input words' checksums;
-//   * the input check of line 11 is done speculatively: the words used by the pass are
+//     (f_dup), linear-scaling quantization with the bin-range check, reconstruction evaluated
+//     twice (dec_dup), the machine-epsilon double check (Sec. 4.1.2), the code, sum_q/isum_q
+//     and sum_dc, and the input words' checksums;
+//   * Algorithm 1's input check before prediction is done speculatively: the words used by the pass are
 //     summed on the fly and compared with sum_in/isum_in at the end; a mismatch (a memory
 //     error since K1) is located, repaired, and the block is run again with the repaired
 //     value, so the output equals that of an error-free run.
@@ -90,7 +91,7 @@ __device__ __forceinline__ void sum_words(T v, unsigned long long& sum) {
   if (FT<T>::W == 2) mad_wide(sum, FT<T>::hi(v), 1u);
 }
 
-// Alg. 1 lines 19-28 for one point with its (already duplicated) prediction: linear-scaling
+// Algorithm 1 for one point with its (already duplicated) prediction: linear-scaling
 // quantization, reconstruction with dec_dup, and the machine-epsilon double check.
 // Returns the code (0 = unpredictable) and the value later points are predicted from.
 template <typename T, bool ABFT, bool HOOK>
@@ -336,7 +337,7 @@ struct Prologue {
   bool reg;
 };
 
-// Line 8: regression when its estimated error is the smaller one. E_lor comes from K1; E_reg
+// indicator[i]: regression when its estimated error is the smaller one. E_lor comes from K1; E_reg
 // (which needs the coefficients) is summed here by `ereg()` just before the block is
 // predicted, so its re-read of the block hits the cache.
 template <class F>
@@ -505,7 +506,7 @@ __device__ __forceinline__ void hist_flush(uint32_t* hist_s, const Hist& h, cons
     if (hist_s[q]) atomicAdd(&w.hist[h.lo + q], (unsigned long long)hist_s[q]);
 }
 
-// The input check of Alg. 1 line 11 after a speculative pass: returns the repaired point and
+// Algorithm 1's input check (sum_in/isum_in) after a speculative pass: returns the repaired point and
 // value when a single corrupted word explains the checksum difference.
 template <typename T>
 __device__ __forceinline__ bool locate_input(const T* field, const Geo& g, const Box& x, unsigned long long s0,

@@ -193,8 +193,8 @@ __device__ __forceinline__ uint64_t row_base(const Geo& g, const Box& x, uint32_
 
 // ---------------------------------------------------------------- typed arithmetic
 // Every value-producing operation is an explicitly rounded IEEE operation (no contraction).
-// The *_v variants are volatile inline PTX: the duplicated evaluation of Alg. 1 lines 18 and
-// 25 cannot be merged with the primary one by the compiler.
+// The *_v variants are volatile inline PTX: the duplicated evaluations of Algorithm 1 (f_dup
+// and dec_dup) cannot be merged with the primary ones by the compiler.
 template <typename T> struct FT;
 
 template <> struct FT<float> {

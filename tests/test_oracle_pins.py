@@ -225,7 +225,7 @@ def test_lorenzo_2d_and_1d_exactness(orc):
     assert codes[0] == 32768 + 7 and np.all(codes[1:] == 32768)
 
 
-# ------------------------------------------------------------------ regression (Alg. 1 line 2)
+# ------------------------------------------------------------------ regression (Algorithm 1)
 
 @pytest.mark.parametrize("ext", [(6, 6, 6), (4, 6, 2), (1, 6, 5), (12, 12), (7, 3), (50,), (2, 1, 1)])
 def test_regression_matches_least_squares(orc, ext):
@@ -270,7 +270,7 @@ def test_selection_prefers_the_better_predictor(orc):
     assert rep["regression_blocks"] < rep["blocks"] // 2
 
 
-# ------------------------------------------------------------------ Huffman (Alg. 1 line 33)
+# ------------------------------------------------------------------ Huffman (Algorithm 1)
 
 def _textbook_huffman_cost(freqs):
     h = [f for f in freqs if f > 0]
