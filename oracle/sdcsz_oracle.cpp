@@ -23,9 +23,9 @@
 //   * partial edge blocks use their actual extents; local order is row-major;
 //   * value-range bound eb = (T)(e * ((double)max - (double)min)) over finite values;
 //   * checksum weights are 1-based so every word contributes to isum;
-//   * regression and the sampled estimates read the input as it is when compression starts;
-//     the input is verified/corrected before any value is predicted, and the E_reg estimate
-//     of a repaired block is taken again from the repaired values;
+//   * regression and the sampled estimates read the input as it is when compression starts
+//     (simulated input errors land after them); the input is verified/corrected before any
+//     value is predicted, so a repaired block compresses as the error-free one;
 //   * regression: closed-form least squares on the block grid in fp32, sequential sums;
 //   * selection: the sample is a set of whole rows (one diagonal row per plane in 3D, every
 //     fourth row in 2D); E_lor adds kappa*eb per sample point;
