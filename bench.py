@@ -34,6 +34,8 @@ METRIC = "compress/decompress GB/s at rel eb 1e-3 (% HBM roofline), ABFT overhea
 WORKLOADS = {
     "512cube": dict(shape=(512, 512, 512), block=6, spikes=0.01, seed=2010),
     "64cube": dict(shape=(64, 64, 64), block=6, spikes=0.0, seed=1),
+    # profiling size for ncu captures: the same recipe, 226 MB (above L2), a few hundred MB held
+    "384cube": dict(shape=(384, 384, 384), block=6, spikes=0.01, seed=2010),
 }
 REL_EB = 1e-3
 
@@ -51,12 +53,25 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _src_hash(name):
-    p = os.path.join(ROOT, "paper_2010_03144_gb300", "csrc", name)
+# sources that define each stage's kernels (the hash keys the stored ncu traffic)
+KERNEL_SOURCES = {
+    "prep": ("k_prep.cu", "sdcsz_internal.cuh"),
+    "predict": ("predict.cuh", "k_predict_f32.cu", "sdcsz_internal.cuh"),
+    "codebook": ("k_codebook.cu", "sdcsz_internal.cuh"),
+    "encode": ("k_encode.cu", "sdcsz_internal.cuh"),
+    "decode": ("decode.cuh", "k_decode_f32.cu", "sdcsz_internal.cuh"),
+}
+
+
+def _src_hash(stage):
+    h = hashlib.sha1()
     try:
-        return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+        for name in KERNEL_SOURCES[stage]:
+            with open(os.path.join(ROOT, "paper_2010_03144_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
+    return h.hexdigest()[:12]
 
 
 class ClockSampler:
@@ -199,14 +214,16 @@ def run_ours(args):
         _barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = sz.kernel_launches()
         e0.record(stream)
         for _ in range(steps):
             step(ws, p, stage_acc)
         e1.record(stream)
         torch.cuda.synchronize()
+        launches = sz.kernel_launches() - n0
         _barrier(world)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        return e0.elapsed_time(e1), launches
 
     uuid = None
     try:
@@ -216,9 +233,10 @@ def run_ours(args):
     clk = ClockSampler(uuid)
     clk.start()
     stages = {}
-    ms_on = timed(ws_on, p_on, args.steps, args.warmup, stages)
+    ms_on, launches = timed(ws_on, p_on, args.steps, args.warmup, stages)
     clocks = clk.stop()
-    ms_off = timed(ws_off, p_off, args.steps, args.warmup)
+    stages_off = {}
+    ms_off, _ = timed(ws_off, p_off, args.steps, args.warmup, stages_off)
     ms_on_max = _reduce_max(ms_on, world, device)
     ms_off_max = _reduce_max(ms_off, world, device)
     per_step = ms_on_max / args.steps
@@ -234,10 +252,8 @@ def run_ours(args):
     dom = max(("prep", "predict", "encode", "decode", "codebook"), key=lambda k: avg[k])
     peak, peak_kind = _peaks()
     achieved = alg[dom] / (avg[dom] / 1e3) / 1e9
-    src = {"prep": "k_prep.cu", "predict": "k_predict.cu", "encode": "k_encode.cu", "decode": "k_decode.cu",
-           "codebook": "k_codebook.cu"}[dom]
-    tr = NCU_TRAFFIC.get(dom)
-    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash(src) else None
+    tr = NCU_TRAFFIC.get((args.workload, dom))
+    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash(dom) else None
     kernels = {k: {"ms": round(avg[k], 4), "GB/s": round(alg[k] / (avg[k] / 1e3) / 1e9, 1) if avg[k] > 0 else None,
                    "frac": round(alg[k] / (avg[k] / 1e3) / 1e9 / peak, 3) if avg[k] > 0 else None}
                for k in ("prep", "predict", "codebook", "encode", "decode")}
@@ -301,12 +317,13 @@ def run_ours(args):
             "abft_off_value": round(world * gb * args.steps / (ms_off_max / 1e3), 2),
             "p99_latency_ms": None,
             "kernels": kernels,
+            "kernels_abft_off_ms": {k: round(v / args.steps, 4) for k, v in stages_off.items()},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes": alg[dom]},
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": N * s_dt + n_s,
                     "d2h_bytes_per_step": n_s + N * s_dt},
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

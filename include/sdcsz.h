@@ -185,6 +185,10 @@ int sdcsz_read_header(const void* h_stream, size_t nbytes, sdcsz_params* out, ui
 /* Static string for an error code. */
 const char* sdcsz_strerror(int code);
 
+/* Number of CUDA kernels the library has launched in this process so far (all devices, all
+ * entry points). Instrumentation only; the paper has no counterpart. */
+unsigned long long sdcsz_kernel_launches(void);
+
 /*
  * Soft-error simulation for tests (the paper's evaluation mode A, Sec. 6.1.2, and the
  * transient errors of Sec. 6.4.3-6.4.4). One record flips one bit:

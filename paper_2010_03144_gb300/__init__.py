@@ -25,7 +25,7 @@ BLOCK_OK, BLOCK_CORRECTED, BLOCK_SDC, BLOCK_BAD = 0, 1, 2, 3
 EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_workspace_size", "sdcsz_compress",
            "sdcsz_decompress", "sdcsz_verify", "sdcsz_read_header", "sdcsz_strerror",
            "sdcsz_debug_compress_flips", "sdcsz_debug_decompress_flips", "sdcsz_compress_traced",
-           "sdcsz_decompress_traced", "sdcsz_compress_noalloc")
+           "sdcsz_decompress_traced", "sdcsz_compress_noalloc", "sdcsz_kernel_launches")
 
 
 class SdcszError(RuntimeError):
@@ -105,11 +105,18 @@ def lib():
         L.sdcsz_read_header.argtypes = [vp, sz, P, ctypes.POINTER(ctypes.c_uint64)]
         L.sdcsz_strerror.argtypes = [i32]
         L.sdcsz_strerror.restype = ctypes.c_char_p
+        L.sdcsz_kernel_launches.argtypes = []
+        L.sdcsz_kernel_launches.restype = ctypes.c_ulonglong
         for f in (L.sdcsz_compress_bound, L.sdcsz_workspace_size, L.sdcsz_compress, L.sdcsz_debug_compress_flips,
                   L.sdcsz_decompress, L.sdcsz_debug_decompress_flips, L.sdcsz_verify, L.sdcsz_read_header):
             f.restype = i32
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().sdcsz_kernel_launches())
 
 
 def strerror(code: int) -> str:

@@ -6,6 +6,7 @@
 // from the caller (stream, field, workspace).
 #include <algorithm>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "sdcsz_internal.cuh"
@@ -32,6 +33,12 @@ int sm_count() {
 }
 
 }  // namespace
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 cudaStream_t side_stream() {
   static std::mutex mu;
@@ -519,3 +526,5 @@ extern "C" int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p
   // the stream by every call; everything else is written before it is read
   return compress_impl(d_field, p, d_out, out_cap, out_bytes, ws, kStaticScratchBytes, report, stream, nullptr, 0);
 }
+
+extern "C" unsigned long long sdcsz_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

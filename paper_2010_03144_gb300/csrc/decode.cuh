@@ -768,6 +768,7 @@ void run_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t
   const uintptr_t al = 2 * sizeof(T);
   const bool vec2 = (B2 % 2 == 0) && (h.g.d[2] % 2 == 0) && (reinterpret_cast<uintptr_t>(field) % al == 0);
   kern<<<grid, 256, smem, L.stream>>>(s, nbytes, h, field, status, orig, st, flips, nflips, vec2 ? 1 : 0);
+  note_launch();
 }
 
 template <typename T>
@@ -824,12 +825,14 @@ void run_generic(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint
     cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ke<<<(unsigned)((count + threads - 1) / threads), threads, smem, L.stream>>>(s, nbytes, h, field, status, orig,
                                                                                   st, flips, nflips, count);
+    note_launch();
     return;
   }
   auto kern = k_decode<T, NDIM>;
   const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
   const unsigned grid = persistent_grid(kern, threads, smem, ngroups, L);
   kern<<<grid, threads, smem, L.stream>>>(s, nbytes, h, field, status, orig, st, flips, nflips, all ? 1 : 0);
+  note_launch();
 }
 
 template <typename T>

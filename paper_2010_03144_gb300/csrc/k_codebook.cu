@@ -267,6 +267,7 @@ void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, cons
   const size_t smem = kSmemSort * 8 + 4096 * 8 + 8192 * 4 + 8192;
   cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_codebook<<<1, 1024, smem, L.stream>>>(g, w, out, cap);
+  note_launch();
 }
 
 }  // namespace sdcsz

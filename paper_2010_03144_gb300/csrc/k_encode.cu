@@ -301,7 +301,7 @@ void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const 
   } else {
     if (g.abft) k_encode<double, true><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
     else k_encode<double, false><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
-  }
+  }  note_launch();
 }
 
 }  // namespace sdcsz

@@ -33,6 +33,7 @@ void launch_flip_input(void* field, const Geo& g, const sdcsz_flip* flips, uint3
   if (!grid) return;
   if (g.dtype == 0) k_flip_input<float><<<grid, 256, 0, L.stream>>>(static_cast<float*>(field), g, flips, nflips);
   else k_flip_input<double><<<grid, 256, 0, L.stream>>>(static_cast<double*>(field), g, flips, nflips);
+  note_launch();
 }
 
 // Soft-error simulation: flip bits of stored codes after their checksums were taken.
@@ -51,6 +52,7 @@ void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint3
   const unsigned grid = (nflips + 255) / 256;
   if (!grid) return;
   k_flip_codes<<<grid, 256, 0, L.stream>>>(g, w, flips, nflips);
+  note_launch();
 }
 
 

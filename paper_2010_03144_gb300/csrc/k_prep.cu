@@ -343,6 +343,7 @@ static void run_fast(const void* field, const Geo& g, const Ws& w, const Launch&
   auto kern = k_prep_fast<T, NDIM, B0, B1, B2>;
   const bool vec2 = (B2 % 2 == 0) && (g.d[2] % 2 == 0) && (reinterpret_cast<uintptr_t>(field) % (2 * sizeof(T)) == 0);
   kern<<<(unsigned)((g.nb + 127) / 128), 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, vec2 ? 1 : 0);
+  note_launch();
 }
 
 // The full-block shapes with a fast path (cubes 4..16 in 3D, squares 8/12/16 in 2D).
@@ -386,6 +387,7 @@ static void run_generic(const void* field, const Geo& g, const Ws& w, bool all, 
   cudaFuncSetAttribute(k_prep<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_prep<T, NDIM><<<(unsigned)((count + threads - 1) / threads), threads, smem, L.stream>>>(
       static_cast<const T*>(field), g, w, all ? 1 : 0, count);
+  note_launch();
 }
 
 template <typename T>
@@ -402,6 +404,7 @@ static void launch_prep_t(const void* field, const Geo& g, const Ws& w, const La
     fk.join();
   }
   k_bound<T><<<1, 1, 0, L.stream>>>(g, w.st);
+  note_launch();
 }
 
 void launch_prep(const void* field, const Geo& g, const Ws& w, const Launch& L) {

@@ -696,6 +696,7 @@ void run_generic(const void* field, const Geo& g, const Ws& w, const sdcsz_flip*
   dim3 grid;
   launch_persistent(kern, threads, smem, count, L, &grid);
   kern<<<grid, threads, smem, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, all ? 1 : 0, count);
+  note_launch();
 }
 
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
@@ -708,6 +709,7 @@ void run_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
   const bool vec2 = (B2 % 2 == 0) && (g.d[2] % 2 == 0) &&
                     (reinterpret_cast<uintptr_t>(field) % (2 * sizeof(T)) == 0);
   kern<<<grid, 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, vec2 ? 1 : 0);
+  note_launch();
 }
 
 // Shapes with a fast path: cubes 4..16 in 3D, squares 8/12/16 in 2D.

@@ -437,6 +437,9 @@ struct Launch {
   int sms;
 };
 
+// Counts every kernel launch the library issues (read back by sdcsz_kernel_launches).
+void note_launch();
+
 // A library-owned stream per device for work that can overlap the caller's stream.
 cudaStream_t side_stream();
 
