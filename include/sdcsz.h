@@ -185,6 +185,54 @@ int sdcsz_read_header(const void* h_stream, size_t nbytes, sdcsz_params* out, ui
 /* Static string for an error code. */
 const char* sdcsz_strerror(int code);
 
+/*
+ * Batches (no counterpart in the paper, which compresses one field per call). A batch
+ * compresses up to 64 fields of any shapes, dtypes and parameters with one persistent launch
+ * per stage and kernel shape: the fields are rows of a device-side job table and the CTAs of
+ * each launch pull (field, block range) items from a queue counter in the workspace. Each
+ * field's stream is byte-identical to sdcsz_compress of that field with the same parameters.
+ *
+ *   sdcsz_batch_create       validate the items and plan the workspace (host only); the
+ *                            item array is copied.
+ *   sdcsz_batch_workspace_size  bytes of device workspace the batch needs (one buffer,
+ *                            256-byte aligned, owned by the caller, reused by every run).
+ *   sdcsz_batch_bind         bind the workspace, build the job table and copy it to the
+ *                            device (waits for `stream`); drops any captured graph.
+ *   sdcsz_batch_set_fields   point the batch at other field / output buffers (NULL arrays
+ *                            keep the current ones); shapes and parameters stay. Waits for
+ *                            `stream`, so no run may be in flight on another stream.
+ *   sdcsz_batch_compress     enqueue the compression of every field on `stream`; no host
+ *                            synchronisation and no allocation, so it may be captured.
+ *   sdcsz_batch_capture      capture sdcsz_batch_compress into a CUDA graph owned by the
+ *                            batch (`stream` must not be the legacy default stream).
+ *   sdcsz_batch_launch       replay the captured graph on `stream` (or enqueue directly when
+ *                            nothing was captured).
+ *   sdcsz_batch_results      wait for `stream`, then per field the stream size (0 on error)
+ *                            and the report; returns the first field's error, if any.
+ *   sdcsz_batch_destroy      free the host-side plan (not the caller's device memory).
+ * The workspace and outputs belong to one run at a time: runs of one batch on different
+ * streams must not overlap.
+ */
+typedef struct sdcsz_batch_item {
+  const void* d_field;
+  sdcsz_params params;
+  void* d_out;
+  size_t out_cap;
+} sdcsz_batch_item;
+
+typedef struct sdcsz_batch sdcsz_batch;
+
+int sdcsz_batch_create(const sdcsz_batch_item* items, uint32_t n, sdcsz_batch** out);
+int sdcsz_batch_workspace_size(const sdcsz_batch* b, size_t* bytes);
+int sdcsz_batch_bind(sdcsz_batch* b, void* d_ws, size_t ws_bytes, void* stream);
+int sdcsz_batch_set_fields(sdcsz_batch* b, const void* const* d_fields, void* const* d_outs, const size_t* out_caps,
+                           void* stream);
+int sdcsz_batch_compress(sdcsz_batch* b, void* stream);
+int sdcsz_batch_capture(sdcsz_batch* b, void* stream);
+int sdcsz_batch_launch(sdcsz_batch* b, void* stream);
+int sdcsz_batch_results(sdcsz_batch* b, size_t* out_bytes, sdcsz_report* reports, void* stream);
+void sdcsz_batch_destroy(sdcsz_batch* b);
+
 /* Number of CUDA kernels the library has launched in this process so far (all devices, all
  * entry points). Instrumentation only; the paper has no counterpart. */
 unsigned long long sdcsz_kernel_launches(void);

@@ -25,7 +25,9 @@ BLOCK_OK, BLOCK_CORRECTED, BLOCK_SDC, BLOCK_BAD = 0, 1, 2, 3
 EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_workspace_size", "sdcsz_compress",
            "sdcsz_decompress", "sdcsz_verify", "sdcsz_read_header", "sdcsz_strerror",
            "sdcsz_debug_compress_flips", "sdcsz_debug_decompress_flips", "sdcsz_compress_traced",
-           "sdcsz_decompress_traced", "sdcsz_compress_noalloc", "sdcsz_kernel_launches")
+           "sdcsz_decompress_traced", "sdcsz_compress_noalloc", "sdcsz_kernel_launches", "sdcsz_batch_create",
+           "sdcsz_batch_workspace_size", "sdcsz_batch_bind", "sdcsz_batch_set_fields", "sdcsz_batch_compress",
+           "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy")
 
 
 class SdcszError(RuntimeError):
@@ -69,6 +71,15 @@ class Report(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("d_field", ctypes.c_void_p),
+        ("params", Params),
+        ("d_out", ctypes.c_void_p),
+        ("out_cap", ctypes.c_size_t),
+    ]
+
+
 class Flip(ctypes.Structure):
     _fields_ = [("site", ctypes.c_uint32), ("bit", ctypes.c_uint32), ("block", ctypes.c_uint64),
                 ("index", ctypes.c_uint64)]
@@ -107,6 +118,20 @@ def lib():
         L.sdcsz_strerror.restype = ctypes.c_char_p
         L.sdcsz_kernel_launches.argtypes = []
         L.sdcsz_kernel_launches.restype = ctypes.c_ulonglong
+        BI, BP = ctypes.POINTER(BatchItem), ctypes.c_void_p
+        L.sdcsz_batch_create.argtypes = [BI, ctypes.c_uint32, ctypes.POINTER(BP)]
+        L.sdcsz_batch_workspace_size.argtypes = [BP, ctypes.POINTER(sz)]
+        L.sdcsz_batch_bind.argtypes = [BP, vp, sz, vp]
+        L.sdcsz_batch_set_fields.argtypes = [BP, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(sz), vp]
+        L.sdcsz_batch_compress.argtypes = [BP, vp]
+        L.sdcsz_batch_capture.argtypes = [BP, vp]
+        L.sdcsz_batch_launch.argtypes = [BP, vp]
+        L.sdcsz_batch_results.argtypes = [BP, ctypes.POINTER(sz), R, vp]
+        L.sdcsz_batch_destroy.argtypes = [BP]
+        L.sdcsz_batch_destroy.restype = None
+        for f in (L.sdcsz_batch_create, L.sdcsz_batch_workspace_size, L.sdcsz_batch_bind, L.sdcsz_batch_set_fields,
+                  L.sdcsz_batch_compress, L.sdcsz_batch_capture, L.sdcsz_batch_launch, L.sdcsz_batch_results):
+            f.restype = i32
         for f in (L.sdcsz_compress_bound, L.sdcsz_workspace_size, L.sdcsz_compress, L.sdcsz_debug_compress_flips,
                   L.sdcsz_decompress, L.sdcsz_debug_decompress_flips, L.sdcsz_verify, L.sdcsz_read_header):
             f.restype = i32
@@ -349,3 +374,98 @@ def compress_noalloc(field, out, eb, eb_mode="rel", block=None, bins=65536, abft
     if rc:
         raise SdcszError(rc, "compress_noalloc")
     return out[: n.value], rep.as_dict()
+
+
+class Batch:
+    """Many fields compressed together: one persistent launch per stage and kernel shape over
+    a device-side job table (see sdcsz_batch_* in the C header). ``eb``, ``eb_mode``,
+    ``abft`` and ``predictor`` are one value for every field or a list/tuple with one entry
+    per field; ``block`` is None, an int or a tuple for every field, or a list with one entry
+    per field. Each field's stream is byte-identical to ``compress`` of that field."""
+
+    def __init__(self, fields, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto", stream=None):
+        import torch
+        n = len(fields)
+        ebs = list(eb) if isinstance(eb, (list, tuple)) else [eb] * n
+        modes = list(eb_mode) if isinstance(eb_mode, (list, tuple)) else [eb_mode] * n
+        blocks = list(block) if isinstance(block, list) else [block] * n
+        abfts = list(abft) if isinstance(abft, (list, tuple)) else [abft] * n
+        preds = list(predictor) if isinstance(predictor, (list, tuple)) else [predictor] * n
+        self.fields = list(fields)
+        self.params = [make_params(tuple(f.shape), f.dtype, ebs[i], modes[i], blocks[i], bins, abfts[i], preds[i])
+                       for i, f in enumerate(self.fields)]
+        self.caps = [compress_bound(p) for p in self.params]
+        dev = self.fields[0].device
+        self.outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in self.caps]
+        items = (BatchItem * n)()
+        for i, f in enumerate(self.fields):
+            if not f.is_cuda or not f.is_contiguous():
+                raise ValueError("fields must be contiguous CUDA tensors")
+            items[i].d_field = f.data_ptr()
+            items[i].params = self.params[i]
+            items[i].d_out = self.outs[i].data_ptr()
+            items[i].out_cap = self.caps[i]
+        self.h = ctypes.c_void_p()
+        rc = lib().sdcsz_batch_create(items, n, ctypes.byref(self.h))
+        if rc:
+            raise SdcszError(rc, "batch_create")
+        nb = ctypes.c_size_t()
+        lib().sdcsz_batch_workspace_size(self.h, ctypes.byref(nb))
+        self.ws = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+        rc = lib().sdcsz_batch_bind(self.h, ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                    _stream_handle(stream))
+        if rc:
+            raise SdcszError(rc, "batch_bind")
+
+    def set_fields(self, fields, stream=None):
+        """Point the batch at new field tensors of the same shapes and dtypes."""
+        n = len(self.fields)
+        if len(fields) != n:
+            raise ValueError("one tensor per field")
+        for a, b in zip(fields, self.fields):
+            if tuple(a.shape) != tuple(b.shape) or a.dtype != b.dtype or not a.is_contiguous():
+                raise ValueError("set_fields keeps shapes and dtypes")
+        arr = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
+        rc = lib().sdcsz_batch_set_fields(self.h, arr, None, None, _stream_handle(stream))
+        if rc:
+            raise SdcszError(rc, "batch_set_fields")
+        self.fields = list(fields)
+
+    def compress(self, stream=None):
+        """Enqueue the compression of every field (asynchronous)."""
+        rc = lib().sdcsz_batch_compress(self.h, _stream_handle(stream))
+        if rc:
+            raise SdcszError(rc, "batch_compress")
+
+    def capture(self, stream):
+        """Capture the batch compression into a CUDA graph (``stream``: a non-default torch stream)."""
+        rc = lib().sdcsz_batch_capture(self.h, ctypes.c_void_p(stream.cuda_stream))
+        if rc:
+            raise SdcszError(rc, "batch_capture")
+
+    def launch(self, stream=None):
+        """Replay the captured graph (or enqueue directly when nothing was captured)."""
+        rc = lib().sdcsz_batch_launch(self.h, _stream_handle(stream))
+        if rc:
+            raise SdcszError(rc, "batch_launch")
+
+    def results(self, stream=None, check=True):
+        """Wait, then return [(stream bytes view, report dict)] per field."""
+        n = len(self.fields)
+        sizes = (ctypes.c_size_t * n)()
+        reps = (Report * n)()
+        rc = lib().sdcsz_batch_results(self.h, sizes, reps, _stream_handle(stream))
+        if rc and check:
+            raise SdcszError(rc, "batch_results")
+        return [(self.outs[i][: sizes[i]], reps[i].as_dict()) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().sdcsz_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

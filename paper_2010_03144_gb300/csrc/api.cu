@@ -8,6 +8,7 @@
 #include <cstring>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "sdcsz_internal.cuh"
 
@@ -528,3 +529,377 @@ extern "C" int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p
 }
 
 extern "C" unsigned long long sdcsz_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- batches
+// A batch holds the plan of one set of fields: each field's geometry and workspace slice, the
+// device job table, and the launches of each stage (one per kernel shape, each a persistent
+// grid pulling items from its own queue counter). Compression of the whole batch is a fixed
+// sequence of launches on one stream (edge-block launches forked to a batch-owned side
+// stream and joined), with no host synchronisation, so it can be captured into a CUDA graph
+// and replayed; the kernels read fields, outputs and workspaces from the job table, so a
+// replay after sdcsz_batch_set_fields works on new buffers of the same shapes.
+namespace sdcsz {
+namespace {
+
+__global__ void k_batch_reset(const Job* __restrict__ jobs, unsigned long long* heads, uint32_t nheads) {
+  const Job& jb = jobs[blockIdx.x];
+  const uint64_t ngroups = (jb.g.nb + kGroup - 1) / kGroup;
+  const uint64_t nst = sizeof(State) / 8, nh = jb.g.bins, nl = ngroups * (sizeof(LookBack) / 8);
+  unsigned long long* st = reinterpret_cast<unsigned long long*>(jb.w.st);
+  unsigned long long* lb = reinterpret_cast<unsigned long long*>(jb.w.lb);
+  for (uint64_t q = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; q < nst + nh + nl;
+       q += (uint64_t)gridDim.y * blockDim.x) {
+    if (q < nst) st[q] = 0ull;
+    else if (q < nst + nh) jb.w.hist[q - nst] = 0ull;
+    else lb[q - nst - nh] = 0ull;
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0)
+    for (uint32_t q = threadIdx.x; q < nheads; q += blockDim.x) heads[q] = 0ull;
+}
+
+enum BatchKind { BK_PREP_FAST, BK_PREP_GENERIC, BK_PREDICT_FAST, BK_PREDICT_GENERIC, BK_ENCODE };
+
+struct BatchLaunch {
+  BatchKind kind;
+  int dtype, ndim;
+  uint32_t B;
+  bool abft;
+  uint32_t threads;
+  size_t smem;
+  std::vector<uint32_t> jobs;
+  std::vector<uint64_t> items;
+  BatchArgs args;
+};
+
+uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+}  // namespace sdcsz
+
+struct sdcsz_batch {
+  std::vector<sdcsz_batch_item> items;
+  std::vector<sdcsz::Geo> geo;
+  std::vector<sdcsz::WsPlan> plan;
+  std::vector<size_t> ws_off;
+  std::vector<sdcsz::BatchLaunch> launches;
+  size_t heads_off = 0, table_off = 0, total = 0;
+  void* d_ws = nullptr;
+  sdcsz::Job* h_table = nullptr;  // pinned host copy of the job table
+  sdcsz::Job* d_table = nullptr;
+  unsigned long long* d_heads = nullptr;
+  int device = -1;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace sdcsz {
+namespace {
+
+void batch_release(sdcsz_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->h_table) cudaFreeHost(b->h_table);
+  b->exec = nullptr;
+  b->side = nullptr;
+  b->h_table = nullptr;
+  for (auto& e : b->ev) e = nullptr;
+}
+
+// The job table entries that depend on the caller's buffers.
+void batch_fill_jobs(sdcsz_batch* b) {
+  for (size_t j = 0; j < b->items.size(); ++j) {
+    Job& jb = b->h_table[j];
+    const Geo& g = b->geo[j];
+    const size_t s = g.dtype ? 8 : 4;
+    jb.field = b->items[j].d_field;
+    jb.out = static_cast<uint8_t*>(b->items[j].d_out);
+    jb.cap = b->items[j].out_cap;
+    jb.vec2 = (g.B[2] % 2 == 0) && (g.d[2] % 2 == 0) && (reinterpret_cast<uintptr_t>(jb.field) % (2 * s) == 0);
+  }
+}
+
+// Group the jobs into launches (one per stage and kernel shape) and number their items.
+void batch_plan_launches(sdcsz_batch* b) {
+  b->launches.clear();
+  auto add = [&](BatchKind kind, int dtype, int ndim, uint32_t B, bool abft, uint32_t threads, size_t smem,
+                 uint32_t j, uint64_t items) {
+    if (!items) return;
+    for (auto& L : b->launches)
+      if (L.kind == kind && L.dtype == dtype && L.ndim == ndim && L.B == B && L.abft == abft) {
+        L.jobs.push_back(j);
+        L.items.push_back(items);
+        L.threads = std::min(L.threads, threads);
+        L.smem = std::max(L.smem, smem);
+        return;
+      }
+    BatchLaunch L;
+    L.kind = kind;
+    L.dtype = dtype;
+    L.ndim = ndim;
+    L.B = B;
+    L.abft = abft;
+    L.threads = threads;
+    L.smem = smem;
+    L.jobs.push_back(j);
+    L.items.push_back(items);
+    b->launches.push_back(L);
+  };
+  for (uint32_t j = 0; j < (uint32_t)b->geo.size(); ++j) {
+    const Geo& g = b->geo[j];
+    const Job& jb = b->h_table[j];
+    const size_t s = g.dtype ? 8 : 4;
+    const uint32_t slots = walker_slots(g.ndim, g.B);
+    if (jb.fast) {
+      add(BK_PREP_FAST, g.dtype, g.ndim, g.B[2], false, 128, 0, j, ceil_div(g.nb, 128));
+      add(BK_PREDICT_FAST, g.dtype, g.ndim, g.B[2], g.abft != 0, 128, 0, j, ceil_div(g.nb, 128));
+    }
+    add(BK_PREP_GENERIC, g.dtype, g.ndim, 0, false, 128, g.predictor == 0 ? (size_t)slots * 128 * 4 : 0, j,
+        ceil_div(jb.gcount, 128));
+    uint32_t threads = 128;
+    while (threads > 32 && (size_t)slots * s * threads > 160 * 1024) threads >>= 1;
+    add(BK_PREDICT_GENERIC, g.dtype, g.ndim, 0, g.abft != 0, threads, 0, j, 1);  // items set below
+    add(BK_ENCODE, g.dtype, 0, 0, g.abft != 0, 256, 0, j, ceil_div(g.nb, kGroup));
+  }
+  // generic predict: threads are the class minimum, so the items follow it
+  for (auto& L : b->launches) {
+    if (L.kind != BK_PREDICT_GENERIC) continue;
+    size_t per = 0;
+    std::vector<uint32_t> jobs;
+    std::vector<uint64_t> items;
+    for (uint32_t j : L.jobs) {
+      const Geo& g = b->geo[j];
+      const uint64_t n = ceil_div(b->h_table[j].gcount, L.threads);
+      if (!n) continue;
+      per = std::max(per, (size_t)walker_slots(g.ndim, g.B) * (g.dtype ? 8 : 4));
+      jobs.push_back(j);
+      items.push_back(n);
+    }
+    L.jobs = jobs;
+    L.items = items;
+    L.smem = per * L.threads;
+  }
+  b->launches.erase(std::remove_if(b->launches.begin(), b->launches.end(),
+                                   [](const BatchLaunch& L) { return L.jobs.empty(); }),
+                    b->launches.end());
+  for (size_t q = 0; q < b->launches.size(); ++q) {
+    BatchLaunch& L = b->launches[q];
+    std::memset(&L.args, 0, sizeof(L.args));
+    L.args.jobs = b->d_table;
+    L.args.head = b->d_heads + q;
+    L.args.n = (uint32_t)L.jobs.size();
+    uint64_t acc = 0;
+    for (size_t t = 0; t < L.jobs.size(); ++t) {
+      L.args.idx[t] = L.jobs[t];
+      L.args.start[t] = acc;
+      acc += L.items[t];
+    }
+    L.args.start[L.jobs.size()] = acc;
+  }
+}
+
+// Enqueue the whole batch on `s` (no host synchronisation).
+int batch_enqueue(sdcsz_batch* b, cudaStream_t s) {
+  Launch L;
+  L.stream = s;
+  L.sms = sm_count();
+  Launch Ls = L;
+  Ls.stream = b->side;
+  const uint32_t n = (uint32_t)b->items.size();
+  cudaGetLastError();
+  k_batch_reset<<<dim3(n, 16), 256, 0, s>>>(b->d_table, b->d_heads, (uint32_t)kMaxQueues);
+  note_launch();
+  auto stage = [&](BatchKind fast_kind, BatchKind gen_kind, int e) {
+    cudaEventRecord(b->ev[e], s);
+    cudaStreamWaitEvent(b->side, b->ev[e], 0);
+    for (auto& Q : b->launches) {
+      if (Q.kind == gen_kind) {
+        if (gen_kind == BK_PREP_GENERIC) batch_prep_generic(Q.dtype, Q.ndim, Q.args, Q.smem, Ls);
+        else batch_predict_generic(Q.dtype, Q.ndim, Q.abft, Q.args, Q.threads, Q.smem, Ls);
+      }
+    }
+    for (auto& Q : b->launches) {
+      if (Q.kind == fast_kind) {
+        if (fast_kind == BK_PREP_FAST) batch_prep_fast(Q.dtype, Q.ndim, Q.B, Q.args, L);
+        else batch_predict_fast(Q.dtype, Q.ndim, Q.B, Q.abft, Q.args, L);
+      }
+    }
+    cudaEventRecord(b->ev[e + 1], b->side);
+    cudaStreamWaitEvent(s, b->ev[e + 1], 0);
+  };
+  stage(BK_PREP_FAST, BK_PREP_GENERIC, 0);
+  batch_bound(b->d_table, n, L);
+  stage(BK_PREDICT_FAST, BK_PREDICT_GENERIC, 2);
+  batch_codebook(b->d_table, n, L);
+  for (auto& Q : b->launches)
+    if (Q.kind == BK_ENCODE) batch_encode(Q.dtype, Q.abft, Q.args, L);
+  return cudaGetLastError() == cudaSuccess ? SDCSZ_OK : SDCSZ_ECUDA;
+}
+
+}  // namespace
+}  // namespace sdcsz
+
+extern "C" {
+
+int sdcsz_batch_create(const sdcsz_batch_item* items, uint32_t n, sdcsz_batch** out) {
+  using namespace sdcsz;
+  if (!out || !items || n == 0 || n > (uint32_t)kMaxBatch) return SDCSZ_EINVAL;
+  *out = nullptr;
+  sdcsz_batch* b = new sdcsz_batch();
+  b->items.assign(items, items + n);
+  size_t o = 0;
+  b->heads_off = o;
+  o = align256(o + 8 * kMaxQueues);
+  b->table_off = o;
+  o = align256(o + sizeof(Job) * n);
+  for (uint32_t j = 0; j < n; ++j) {
+    Geo g;
+    const int rc = make_geo(&items[j].params, &g);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    b->geo.push_back(g);
+    b->plan.push_back(plan_ws(g));
+    b->ws_off.push_back(o);
+    o = align256(o + b->plan.back().total);
+  }
+  b->total = o;
+  *out = b;
+  return SDCSZ_OK;
+}
+
+int sdcsz_batch_workspace_size(const sdcsz_batch* b, size_t* bytes) {
+  if (!b || !bytes) return SDCSZ_EINVAL;
+  *bytes = b->total;
+  return SDCSZ_OK;
+}
+
+int sdcsz_batch_bind(sdcsz_batch* b, void* d_ws, size_t ws_bytes, void* stream) {
+  using namespace sdcsz;
+  if (!b || !d_ws || ws_bytes < b->total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return SDCSZ_EINVAL;
+  const uint32_t n = (uint32_t)b->items.size();
+  for (uint32_t j = 0; j < n; ++j) {
+    const sdcsz_batch_item& it = b->items[j];
+    if ((!it.d_field && b->geo[j].N) || !it.d_out || it.out_cap < (size_t)kHeaderBytes) return SDCSZ_EINVAL;
+  }
+  batch_release(b);
+  if (cudaGetDevice(&b->device) != cudaSuccess) return SDCSZ_ECUDA;
+  if (cudaMallocHost(&b->h_table, sizeof(Job) * n) != cudaSuccess) return SDCSZ_ECUDA;
+  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) return SDCSZ_ECUDA;
+  for (auto& e : b->ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SDCSZ_ECUDA;
+  uint8_t* base = static_cast<uint8_t*>(d_ws);
+  b->d_ws = d_ws;
+  b->d_heads = reinterpret_cast<unsigned long long*>(base + b->heads_off);
+  b->d_table = reinterpret_cast<Job*>(base + b->table_off);
+  std::memset(b->h_table, 0, sizeof(Job) * n);
+  for (uint32_t j = 0; j < n; ++j) {
+    Job& jb = b->h_table[j];
+    jb.g = b->geo[j];
+    jb.w = bind_ws(base + b->ws_off[j], b->plan[j]);
+    jb.fast = prep_has_fast(jb.g) ? 1 : 0;
+    jb.gcount = jb.fast ? edge_count(jb.g) : jb.g.nb;
+  }
+  batch_fill_jobs(b);
+  batch_plan_launches(b);
+  if (b->launches.size() > (size_t)kMaxQueues) return SDCSZ_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(b->d_table, b->h_table, sizeof(Job) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return SDCSZ_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? SDCSZ_OK : SDCSZ_ECUDA;
+}
+
+int sdcsz_batch_set_fields(sdcsz_batch* b, const void* const* d_fields, void* const* d_outs, const size_t* out_caps,
+                           void* stream) {
+  using namespace sdcsz;
+  if (!b || !b->h_table) return SDCSZ_EINVAL;
+  const uint32_t n = (uint32_t)b->items.size();
+  for (uint32_t j = 0; j < n; ++j) {
+    if (d_fields) {
+      if (!d_fields[j] && b->geo[j].N) return SDCSZ_EINVAL;
+      b->items[j].d_field = d_fields[j];
+    }
+    if (d_outs) {
+      if (!d_outs[j]) return SDCSZ_EINVAL;
+      b->items[j].d_out = d_outs[j];
+    }
+    if (out_caps) {
+      if (out_caps[j] < (size_t)kHeaderBytes) return SDCSZ_EINVAL;
+      b->items[j].out_cap = out_caps[j];
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the pinned table may still be in flight from an earlier update
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SDCSZ_ECUDA;
+  batch_fill_jobs(b);
+  if (cudaMemcpyAsync(b->d_table, b->h_table, sizeof(Job) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return SDCSZ_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? SDCSZ_OK : SDCSZ_ECUDA;
+}
+
+int sdcsz_batch_compress(sdcsz_batch* b, void* stream) {
+  if (!b || !b->h_table) return SDCSZ_EINVAL;
+  return sdcsz::batch_enqueue(b, static_cast<cudaStream_t>(stream));
+}
+
+int sdcsz_batch_capture(sdcsz_batch* b, void* stream) {
+  if (!b || !b->h_table || !stream) return SDCSZ_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SDCSZ_ECUDA;
+  const int rc = sdcsz::batch_enqueue(b, s);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (rc || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc ? rc : SDCSZ_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    b->exec = nullptr;
+    return SDCSZ_ECUDA;
+  }
+  return SDCSZ_OK;
+}
+
+int sdcsz_batch_launch(sdcsz_batch* b, void* stream) {
+  if (!b || !b->h_table) return SDCSZ_EINVAL;
+  if (!b->exec) return sdcsz::batch_enqueue(b, static_cast<cudaStream_t>(stream));
+  return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? SDCSZ_OK : SDCSZ_ECUDA;
+}
+
+int sdcsz_batch_results(sdcsz_batch* b, size_t* out_bytes, sdcsz_report* reports, void* stream) {
+  using namespace sdcsz;
+  if (!b || !b->h_table) return SDCSZ_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint32_t n = (uint32_t)b->items.size();
+  int first = SDCSZ_OK;
+  std::vector<State> h(n);
+  for (uint32_t j = 0; j < n; ++j)
+    if (cudaMemcpyAsync(&h[j], b->h_table[j].w.st, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return SDCSZ_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SDCSZ_ECUDA;
+  for (uint32_t j = 0; j < n; ++j) {
+    const int rc = map_error(h[j].error);
+    if (reports) fill_report(h[j], b->geo[j].nb, &reports[j]);
+    if (out_bytes) out_bytes[j] = rc ? 0 : (size_t)h[j].total_bytes;
+    if (rc && !first) first = rc;
+  }
+  return first;
+}
+
+void sdcsz_batch_destroy(sdcsz_batch* b) {
+  if (!b) return;
+  sdcsz::batch_release(b);
+  delete b;
+}
+
+}  // extern "C"

@@ -76,14 +76,13 @@ constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this
 
 }  // namespace
 
-__global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
+                                         unsigned char* smem) {
   __shared__ uint32_t s_warp[40];
   __shared__ uint32_t cnt[64];
   __shared__ uint32_t s_maxlen;
   __shared__ uint32_t first_code[kMaxLen + 2], first_index[kMaxLen + 2], cum[kMaxLen + 2];
   State* st = w.st;
-  if (*(volatile unsigned int*)&st->error) return;
   const uint32_t tid = threadIdx.x;
   const uint32_t bins = g.bins;
 
@@ -263,8 +262,37 @@ __global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restr
   }
 }
 
+__global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (*(volatile unsigned int*)&w.st->error) return;
+  codebook(g, w, out, cap, smem);
+}
+
+// One CTA per job of a batch.
+__global__ void __launch_bounds__(1024) k_codebook_batch(const Job* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Job s_job;
+  __shared__ int s_skip;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&jobs[blockIdx.x]);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_job);
+  for (uint32_t q = threadIdx.x; q < sizeof(Job) / 8; q += blockDim.x) dst[q] = src[q];
+  __syncthreads();
+  if (threadIdx.x == 0) s_skip = *(volatile unsigned int*)&s_job.w.st->error != 0;
+  __syncthreads();
+  if (s_skip) return;
+  codebook(s_job.g, s_job.w, s_job.out, s_job.cap, smem);
+}
+
+constexpr size_t kCodebookSmem = kSmemSort * 8 + 4096 * 8 + 8192 * 4 + 8192;
+
+void batch_codebook(const Job* jobs, uint32_t n, const Launch& L) {
+  cudaFuncSetAttribute(k_codebook_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCodebookSmem);
+  k_codebook_batch<<<n, 1024, kCodebookSmem, L.stream>>>(jobs);
+  note_launch();
+}
+
 void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
-  const size_t smem = kSmemSort * 8 + 4096 * 8 + 8192 * 4 + 8192;
+  const size_t smem = kCodebookSmem;
   cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_codebook<<<1, 1024, smem, L.stream>>>(g, w, out, cap);
   note_launch();

@@ -8,6 +8,8 @@
 // block its payload, unpredictable-value and coefficient offsets. Pass 2 re-reads the codes
 // (L2 resident) and packs the bits MSB-first into 32-bit words: words wholly inside the
 // block's byte range are stored whole, the partial first and last words byte by byte.
+#include <algorithm>
+
 #include "sdcsz_internal.cuh"
 
 namespace sdcsz {
@@ -50,24 +52,28 @@ __device__ __forceinline__ void put_word(uint8_t* out, uint64_t wa, uint32_t v, 
 
 }  // namespace
 
+__device__ __forceinline__ uint32_t cb_lo(const Geo& g) { return g.R > kCbWindow / 2 ? g.R - kCbWindow / 2 : 0; }
+
+// Shared-memory window of the codebook around the centre bin.
+__device__ __forceinline__ void cb_load(uint32_t* cb_s, const Geo& g, const Ws& w) {
+  const uint32_t lo = cb_lo(g);
+  for (uint32_t q = threadIdx.x; q < kCbWindow; q += blockDim.x)
+    cb_s[q] = lo + q < g.bins ? __ldg(&w.codebook[lo + q]) : 0u;
+}
+
+// One random-access group (256 blocks, one per thread) of the stream.
 template <typename T, bool ABFT>
-__global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
-  __shared__ uint32_t s_gid;
+__device__ __forceinline__ void encode_group(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
+                                             uint64_t gid, const uint32_t* cb_s) {
   __shared__ unsigned long long s_wt[8][3];
   __shared__ unsigned long long s_excl[3];
   __shared__ unsigned long long s_tot[3];
-  __shared__ uint32_t cb_s[kCbWindow];
   State* st = w.st;
-  if (*(volatile unsigned int*)&st->error) return;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) s_gid = atomicAdd(&st->ticket, 1u);
   Codebook cb;
-  cb.lo = g.R > kCbWindow / 2 ? g.R - kCbWindow / 2 : 0;
+  cb.lo = cb_lo(g);
   cb.s = cb_s;
   cb.g = w.codebook;
-  for (uint32_t q = tid; q < kCbWindow; q += blockDim.x) cb_s[q] = cb.lo + q < g.bins ? __ldg(&w.codebook[cb.lo + q]) : 0u;
-  __syncthreads();
-  const uint64_t gid = s_gid;
   const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
   const uint64_t b = gid * kGroup + tid;
   const bool active = b < g.nb;
@@ -289,6 +295,54 @@ __global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict
   if (bad) {
     // a block whose codes could not be repaired is reported in the header status word
     atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
+  }
+}
+
+template <typename T, bool ABFT>
+__global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
+  __shared__ uint32_t s_gid;
+  __shared__ uint32_t cb_s[kCbWindow];
+  State* st = w.st;
+  if (*(volatile unsigned int*)&st->error) return;
+  if (threadIdx.x == 0) s_gid = atomicAdd(&st->ticket, 1u);
+  cb_load(cb_s, g, w);
+  __syncthreads();
+  encode_group<T, ABFT>(g, w, out, cap, s_gid, cb_s);
+}
+
+// Batched: the groups of every job; a job's groups are pulled in increasing order, so each
+// look-back only waits for groups already taken by running CTAs.
+template <typename T, bool ABFT>
+__global__ void __launch_bounds__(256) k_encode_batch(BatchArgs a) {
+  __shared__ uint32_t cb_s[kCbWindow];
+  __shared__ Job s_job;
+  batch_loop(
+      a, s_job,
+      [&] {
+        cb_load(cb_s, s_job.g, s_job.w);
+        __syncthreads();
+      },
+      [&](uint64_t it) { encode_group<T, ABFT>(s_job.g, s_job.w, s_job.out, s_job.cap, it, cb_s); }, NoOp());
+}
+
+template <typename T, bool ABFT>
+static void batch_encode_t(const BatchArgs& a, const Launch& L) {
+  auto kern = k_encode_batch<T, ABFT>;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+  if (occ < 1) occ = 1;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(a.start[a.n], (uint64_t)occ * L.sms));
+  kern<<<grid, 256, 0, L.stream>>>(a);
+  note_launch();
+}
+
+void batch_encode(int dtype, bool abft, const BatchArgs& a, const Launch& L) {
+  if (dtype == 0) {
+    if (abft) batch_encode_t<float, true>(a, L);
+    else batch_encode_t<float, false>(a, L);
+  } else {
+    if (abft) batch_encode_t<double, true>(a, L);
+    else batch_encode_t<double, false>(a, L);
   }
 }
 

@@ -56,6 +56,23 @@ void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint3
 }
 
 
+bool batch_predict_fast_f32(int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L);
+bool batch_predict_fast_f64(int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L);
+void batch_predict_generic_f32(int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
+                               const Launch& L);
+void batch_predict_generic_f64(int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
+                               const Launch& L);
+
+bool batch_predict_fast(int dtype, int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L) {
+  return dtype == 0 ? batch_predict_fast_f32(ndim, B, abft, a, L) : batch_predict_fast_f64(ndim, B, abft, a, L);
+}
+
+void batch_predict_generic(int dtype, int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
+                           const Launch& L) {
+  if (dtype == 0) batch_predict_generic_f32(ndim, abft, a, threads, smem, L);
+  else batch_predict_generic_f64(ndim, abft, a, threads, smem, L);
+}
+
 void launch_decode_f32(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
                        const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
                        const Launch& L);

@@ -9,4 +9,14 @@ void launch_predict_f64(const void* field, const Geo& g, const Ws& w, const sdcs
   else kpred::launch_predict_t<double, false>(field, g, w, flips, nflips, L);
 }
 
+bool batch_predict_fast_f64(int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L) {
+  return abft ? kpred::batch_fast_shape<double, true>(ndim, B, a, L) : kpred::batch_fast_shape<double, false>(ndim, B, a, L);
+}
+
+void batch_predict_generic_f64(int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
+                               const Launch& L) {
+  if (abft) kpred::batch_generic_dim<double, true>(ndim, a, threads, smem, L);
+  else kpred::batch_generic_dim<double, false>(ndim, a, threads, smem, L);
+}
+
 }  // namespace sdcsz

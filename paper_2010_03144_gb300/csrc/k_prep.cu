@@ -140,11 +140,11 @@ __device__ __forceinline__ bool full_block(const Geo& g, uint64_t b, uint64_t c[
 
 // Generic path: edge blocks (or every block when `all`), runtime extents.
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(128) k_prep(const T* __restrict__ field, Geo g, Ws w, int all, uint64_t count) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void prep_generic(const T* __restrict__ field, const Geo& g, const Ws& w, bool all,
+                                             uint64_t count, uint64_t cta, unsigned char* smem) {
   State* st = w.st;
   const uint32_t tid = threadIdx.x;
-  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + tid;
+  const uint64_t e = cta * blockDim.x + tid;
   const bool rel = g.eb_mode == 1;
   T mn = T(1.0 / 0.0), mx = T(-1.0 / 0.0);
   if (e < count) {
@@ -207,13 +207,29 @@ __global__ void __launch_bounds__(128) k_prep(const T* __restrict__ field, Geo g
   if (rel) reduce_range<T>(mn, mx, st);
 }
 
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(128) k_prep(const T* __restrict__ field, Geo g, Ws w, int all, uint64_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  prep_generic<T, NDIM>(field, g, w, all != 0, count, blockIdx.x, smem);
+}
+
+// Batched generic path: the edge blocks (or all blocks) of every job of one dimensionality.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(128) k_prep_batch(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Job s_job;
+  batch_loop(a, s_job, NoOp(), [&](uint64_t it) {
+    prep_generic<T, NDIM>(static_cast<const T*>(s_job.field), s_job.g, s_job.w, !s_job.fast, s_job.gcount, it, smem);
+  }, NoOp());
+}
+
 // Fast path: full blocks of a compile-time shape B0 x B1 x B2 (leading 1 for 2D).
 template <typename T, int NDIM, int B0, int B1, int B2>
-__global__ void __launch_bounds__(128) k_prep_fast(const T* __restrict__ field, Geo g, Ws w, int vec2) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo& g, const Ws& w, int vec2,
+                                          uint64_t cta) {
   State* st = w.st;
   const uint32_t tid = threadIdx.x;
-  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + tid;
+  const uint64_t b = cta * blockDim.x + tid;
   const bool rel = g.eb_mode == 1;
   const bool est = g.predictor == 0;
   T mn = T(1.0 / 0.0), mx = T(-1.0 / 0.0);
@@ -320,10 +336,23 @@ __global__ void __launch_bounds__(128) k_prep_fast(const T* __restrict__ field, 
   if (rel) reduce_range<T>(mn, mx, st);
 }
 
+template <typename T, int NDIM, int B0, int B1, int B2>
+__global__ void __launch_bounds__(128) k_prep_fast(const T* __restrict__ field, Geo g, Ws w, int vec2) {
+  prep_fast<T, NDIM, B0, B1, B2>(field, g, w, vec2, blockIdx.x);
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2>
+__global__ void __launch_bounds__(128) k_prep_fast_batch(BatchArgs a) {
+  __shared__ Job s_job;
+  batch_loop(a, s_job, NoOp(), [&](uint64_t it) {
+    prep_fast<T, NDIM, B0, B1, B2>(static_cast<const T*>(s_job.field), s_job.g, s_job.w, s_job.vec2, it);
+  }, NoOp());
+}
+
 // The absolute bound: value-range relative (rel * (max - min) over finite values, rounded
 // to the dtype; the user's value when the range is empty or zero) or absolute.
 template <typename T>
-__global__ void k_bound(Geo g, State* st) {
+__device__ __forceinline__ void bound_of(const Geo& g, State* st) {
   double ebd = g.e;
   const unsigned long long mi = st->min_key, ma = st->max_key;
   if (g.eb_mode == 1 && ma != 0ull) {
@@ -335,6 +364,18 @@ __global__ void k_bound(Geo g, State* st) {
   else eb = (T)ebd;
   if (!FT<T>::is_normal_pos(eb)) atomicOr(&st->error, ERR_EB);
   st->eb = (double)eb;
+}
+
+template <typename T>
+__global__ void k_bound(Geo g, State* st) { bound_of<T>(g, st); }
+
+// One thread per job of a batch.
+__global__ void k_bound_batch(const Job* jobs, uint32_t n) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const Job& jb = jobs[j];
+  if (jb.g.dtype == 0) bound_of<float>(jb.g, jb.w.st);
+  else bound_of<double>(jb.g, jb.w.st);
 }
 
 template <typename T, int NDIM, int B0, int B1, int B2>
@@ -406,6 +447,79 @@ static void launch_prep_t(const void* field, const Geo& g, const Ws& w, const La
   k_bound<T><<<1, 1, 0, L.stream>>>(g, w.st);
   note_launch();
 }
+
+// ---------------------------------------------------------------- batched launches
+template <class K>
+static unsigned batch_grid(K kern, uint32_t threads, size_t smem, uint64_t items, const Launch& L) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
+  if (occ < 1) occ = 1;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(items, (uint64_t)occ * L.sms));
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2>
+static void batch_fast_t(const BatchArgs& a, const Launch& L) {
+  auto kern = k_prep_fast_batch<T, NDIM, B0, B1, B2>;
+  const unsigned grid = batch_grid(kern, 128, 0, a.start[a.n], L);
+  kern<<<grid, 128, 0, L.stream>>>(a);
+  note_launch();
+}
+
+template <typename T>
+static bool batch_fast_dt(int ndim, uint32_t B, const BatchArgs& a, const Launch& L) {
+  if (ndim == 3) {
+    switch (B) {
+      case 4: batch_fast_t<T, 3, 4, 4, 4>(a, L); return true;
+      case 6: batch_fast_t<T, 3, 6, 6, 6>(a, L); return true;
+      case 8: batch_fast_t<T, 3, 8, 8, 8>(a, L); return true;
+      case 10: batch_fast_t<T, 3, 10, 10, 10>(a, L); return true;
+      case 12: batch_fast_t<T, 3, 12, 12, 12>(a, L); return true;
+      case 16: batch_fast_t<T, 3, 16, 16, 16>(a, L); return true;
+      default: return false;
+    }
+  }
+  if (ndim == 2) {
+    switch (B) {
+      case 8: batch_fast_t<T, 2, 1, 8, 8>(a, L); return true;
+      case 12: batch_fast_t<T, 2, 1, 12, 12>(a, L); return true;
+      case 16: batch_fast_t<T, 2, 1, 16, 16>(a, L); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
+bool batch_prep_fast(int dtype, int ndim, uint32_t B, const BatchArgs& a, const Launch& L) {
+  return dtype == 0 ? batch_fast_dt<float>(ndim, B, a, L) : batch_fast_dt<double>(ndim, B, a, L);
+}
+
+template <typename T, int NDIM>
+static void batch_generic_t(const BatchArgs& a, size_t smem, const Launch& L) {
+  auto kern = k_prep_batch<T, NDIM>;
+  const unsigned grid = batch_grid(kern, 128, smem, a.start[a.n], L);
+  kern<<<grid, 128, smem, L.stream>>>(a);
+  note_launch();
+}
+
+void batch_prep_generic(int dtype, int ndim, const BatchArgs& a, size_t smem, const Launch& L) {
+  if (dtype == 0) {
+    if (ndim == 3) batch_generic_t<float, 3>(a, smem, L);
+    else if (ndim == 2) batch_generic_t<float, 2>(a, smem, L);
+    else batch_generic_t<float, 1>(a, smem, L);
+  } else {
+    if (ndim == 3) batch_generic_t<double, 3>(a, smem, L);
+    else if (ndim == 2) batch_generic_t<double, 2>(a, smem, L);
+    else batch_generic_t<double, 1>(a, smem, L);
+  }
+}
+
+void batch_bound(const Job* jobs, uint32_t n, const Launch& L) {
+  k_bound_batch<<<(n + 63) / 64, 64, 0, L.stream>>>(jobs, n);
+  note_launch();
+}
+
+bool prep_has_fast(const Geo& g) { return has_fast(g); }
 
 void launch_prep(const void* field, const Geo& g, const Ws& w, const Launch& L) {
   if (g.dtype == 0) launch_prep_t<float>(field, g, w, L);

@@ -531,6 +531,57 @@ __device__ __forceinline__ void withdraw(const Ws& w, const Geo& g, uint64_t b, 
   for (uint32_t kk = 0; kk < P; ++kk) h.sub1(w.codes[code_pos(b, g.P, kk)]);
 }
 
+// One block of the generic path (runtime extents).
+template <typename T, int NDIM, bool ABFT>
+__device__ __forceinline__ void predict_generic_block(const T* __restrict__ field, const Geo& g, const Ws& w,
+                                                      const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                      uint64_t b, Walker<T, NDIM>& wk, const Consts<T>& K,
+                                                      const Hist& h, Counters& cnt) {
+  T* ustage = static_cast<T*>(w.ustage);
+  const Box x = block_box(g, b);
+  const uint32_t S = sample_points(NDIM, x.e);
+  bool reg = choose_reg(g, w, b, S, K.noise,
+                        [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kNone, T(0)); });
+  T cT[4];
+  Hooks hk;
+  load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
+  PassRes r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
+                                                      h, hk, T(0))
+                  : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
+                                                       h, hk, T(0));
+  uint8_t flag = 0;
+  if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
+    uint32_t kf;
+    T xf;
+    if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
+      withdraw(w, g, b, x.P, h);
+      hk.kfix = kf;
+      // the selection estimate and the prediction both see the repaired value
+      reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kf, xf); });
+      r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
+                                                  hk, xf)
+              : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
+                                                   hk, xf);
+      ++cnt.fix;
+    } else {
+      ++cnt.bad;
+      flag = 2;
+    }
+  }
+  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
+  cnt.unpred += r.nun;
+  cnt.reg += reg;
+  cnt.dup += r.dup;
+}
+
+template <typename T, int NDIM>
+__device__ __forceinline__ void walker_init(Walker<T, NDIM>& wk, unsigned char* smem, const Geo& g) {
+  wk.base = reinterpret_cast<T*>(smem) + threadIdx.x;
+  wk.stride = blockDim.x;
+  wk.B2 = g.B[2];
+  wk.sr = g.B[1] * g.B[2];
+}
+
 // Generic kernel: edge blocks (or every block when `all`), any shape.
 template <typename T, int NDIM, bool ABFT>
 __global__ void __launch_bounds__(128) k_predict(const T* __restrict__ field, Geo g, Ws w,
@@ -545,53 +596,47 @@ __global__ void __launch_bounds__(128) k_predict(const T* __restrict__ field, Ge
   __syncthreads();
   const Consts<T> K(st->eb, g.R, NDIM);
   Walker<T, NDIM> wk;
-  wk.base = reinterpret_cast<T*>(smem) + threadIdx.x;
-  wk.stride = blockDim.x;
-  wk.B2 = g.B[2];
-  wk.sr = g.B[1] * g.B[2];
-  T* ustage = static_cast<T*>(w.ustage);
+  walker_init(wk, smem, g);
   Counters cnt;
   const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x < count; e += step) {
     if (e >= count) continue;
-    const uint64_t b = all ? e : edge_block(g, e);
-    const Box x = block_box(g, b);
-    const uint32_t S = sample_points(NDIM, x.e);
-    bool reg = choose_reg(g, w, b, S, K.noise,
-                          [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kNone, T(0)); });
-    T cT[4];
-    Hooks hk;
-    load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
-    PassRes r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
-                                                        h, hk, T(0))
-                    : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
-                                                         h, hk, T(0));
-    uint8_t flag = 0;
-    if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
-      uint32_t kf;
-      T xf;
-      if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
-        withdraw(w, g, b, x.P, h);
-        hk.kfix = kf;
-        // the selection estimate and the prediction both see the repaired value
-        reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kf, xf); });
-        r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
-                                                    hk, xf)
-                : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
-                                                     hk, xf);
-        ++cnt.fix;
-      } else {
-        ++cnt.bad;
-        flag = 2;
-      }
-    }
-    block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
-    cnt.unpred += r.nun;
-    cnt.reg += reg;
-    cnt.dup += r.dup;
+    predict_generic_block<T, NDIM, ABFT>(field, g, w, flips, nflips, all ? e : edge_block(g, e), wk, K, h, cnt);
   }
   cnt.commit(st);
   hist_flush(hist_s, h, w);
+}
+
+// Batched generic kernel: the edge blocks (or all blocks) of every job of one dimensionality.
+template <typename T, int NDIM, bool ABFT>
+__global__ void __launch_bounds__(128) k_predict_batch(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t hist_s[kHistWindow];
+  __shared__ Job s_job;
+  Hist h;
+  Counters cnt;
+  batch_loop(
+      a, s_job,
+      [&] {
+        hist_init(hist_s, h, s_job.g, s_job.w);
+        __syncthreads();
+      },
+      [&](uint64_t it) {
+        const uint64_t e = it * blockDim.x + threadIdx.x;
+        if (e < s_job.gcount) {
+          const Geo& g = s_job.g;
+          const Consts<T> K(s_job.w.st->eb, g.R, NDIM);
+          Walker<T, NDIM> wk;
+          walker_init(wk, smem, g);
+          predict_generic_block<T, NDIM, ABFT>(static_cast<const T*>(s_job.field), g, s_job.w, nullptr, 0,
+                                               s_job.fast ? edge_block(g, e) : e, wk, K, h, cnt);
+        }
+      },
+      [&] {
+        cnt.commit(s_job.w.st);
+        cnt = Counters();
+        hist_flush(hist_s, h, s_job.w);
+      });
 }
 
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool HOOK>
@@ -605,7 +650,60 @@ __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_
                                                                 cptr, uptr, h, hk, xfix);
 }
 
-// Fast kernel: full blocks of a compile-time shape (B0 x B1 x B2, leading 1s below 3D).
+// One full block of a compile-time shape (B0 x B1 x B2, leading 1s below 3D); edge blocks
+// are skipped (the generic path takes them).
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+__device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, const Geo& g, const Ws& w,
+                                                   const sdcsz_flip* __restrict__ flips, uint32_t nflips, int vec2,
+                                                   uint64_t b, T* plane, const Consts<T>& K, const Hist& h,
+                                                   Counters& cnt) {
+  T* ustage = static_cast<T*>(w.ustage);
+  constexpr uint32_t P = B0 * B1 * B2;
+  const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
+  const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
+  const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+  if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) return;
+  const T* blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
+  constexpr uint32_t S = NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2;
+  bool reg = choose_reg(g, w, b, S, K.noise, [&] {
+    return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, w.coef[b], kNone, T(0));
+  });
+  T cT[4];
+  Hooks hk;
+  load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
+  uint32_t* cptr = reinterpret_cast<uint32_t*>(w.codes) + pair_index(b, P, 0);
+  T* uptr = ustage + code_index(b, P, 0);
+  const bool hooked = (hk.kp != kNone) || (hk.kr != kNone);
+  PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
+                                                                      cptr, uptr, h, hk, T(0))
+                     : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, false>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
+                                                                       cptr, uptr, h, hk, T(0));
+  uint8_t flag = 0;
+  if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
+    const Box x = block_box(g, b);
+    uint32_t kf;
+    T xf;
+    if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
+      withdraw(w, g, b, P, h);
+      hk.kfix = kf;
+      reg = choose_reg(g, w, b, S, K.noise, [&] {
+        return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, w.coef[b], kf, xf);
+      });
+      r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
+                                                         hk, xf);
+      ++cnt.fix;
+    } else {
+      ++cnt.bad;
+      flag = 2;
+    }
+  }
+  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
+  cnt.unpred += r.nun;
+  cnt.reg += reg;
+  cnt.dup += r.dup;
+}
+
+// Fast kernel: full blocks of a compile-time shape.
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
 __global__ void __launch_bounds__(128, 7) k_predict_fast(const T* __restrict__ field, Geo g, Ws w,
                                                       const sdcsz_flip* __restrict__ flips, uint32_t nflips,
@@ -619,57 +717,44 @@ __global__ void __launch_bounds__(128, 7) k_predict_fast(const T* __restrict__ f
   __syncthreads();
   const Consts<T> K(st->eb, g.R, NDIM);
   T* plane = reinterpret_cast<T*>(smem) + threadIdx.x;
-  T* ustage = static_cast<T*>(w.ustage);
-  constexpr uint32_t P = B0 * B1 * B2;
-  const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
   Counters cnt;
   const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b - threadIdx.x < g.nb; b += step) {
     if (b >= g.nb) continue;
-    const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
-    const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
-    if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) continue;
-    const T* blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
-    constexpr uint32_t S = NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2;
-    bool reg = choose_reg(g, w, b, S, K.noise, [&] {
-      return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, w.coef[b], kNone, T(0));
-    });
-    T cT[4];
-    Hooks hk;
-    load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
-    uint32_t* cptr = reinterpret_cast<uint32_t*>(w.codes) + pair_index(b, P, 0);
-    T* uptr = ustage + code_index(b, P, 0);
-    const bool hooked = (hk.kp != kNone) || (hk.kr != kNone);
-    PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
-                                                                        cptr, uptr, h, hk, T(0))
-                       : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, false>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
-                                                                         cptr, uptr, h, hk, T(0));
-    uint8_t flag = 0;
-    if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
-      const Box x = block_box(g, b);
-      uint32_t kf;
-      T xf;
-      if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
-        withdraw(w, g, b, P, h);
-        hk.kfix = kf;
-        reg = choose_reg(g, w, b, S, K.noise, [&] {
-          return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, w.coef[b], kf, xf);
-        });
-        r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
-                                                           hk, xf);
-        ++cnt.fix;
-      } else {
-        ++cnt.bad;
-        flag = 2;
-      }
-    }
-    block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
-    cnt.unpred += r.nun;
-    cnt.reg += reg;
-    cnt.dup += r.dup;
+    predict_fast_block<T, NDIM, B0, B1, B2, ABFT>(field, g, w, flips, nflips, vec2, b, plane, K, h, cnt);
   }
   cnt.commit(st);
   hist_flush(hist_s, h, w);
+}
+
+// Batched fast kernel: the full blocks of every job with this block shape.
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+__global__ void __launch_bounds__(128, 7) k_predict_fast_batch(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t hist_s[kHistWindow];
+  __shared__ Job s_job;
+  Hist h;
+  Counters cnt;
+  T* plane = reinterpret_cast<T*>(smem) + threadIdx.x;
+  batch_loop(
+      a, s_job,
+      [&] {
+        hist_init(hist_s, h, s_job.g, s_job.w);
+        __syncthreads();
+      },
+      [&](uint64_t it) {
+        const uint64_t b = it * blockDim.x + threadIdx.x;
+        if (b < s_job.g.nb) {
+          const Consts<T> K(s_job.w.st->eb, s_job.g.R, NDIM);
+          predict_fast_block<T, NDIM, B0, B1, B2, ABFT>(static_cast<const T*>(s_job.field), s_job.g, s_job.w,
+                                                        nullptr, 0, s_job.vec2, b, plane, K, h, cnt);
+        }
+      },
+      [&] {
+        cnt.commit(s_job.w.st);
+        cnt = Counters();
+        hist_flush(hist_s, h, s_job.w);
+      });
 }
 
 // ---------------------------------------------------------------- launch
@@ -758,6 +843,57 @@ void launch_predict_t(const void* field, const Geo& g, const Ws& w, const sdcsz_
   else run_generic<T, 1, ABFT>(field, g, w, flips, nflips, !fast, Lg);
   if (fast) try_fast<T, ABFT>(field, g, w, flips, nflips, L);
   fk.join();
+}
+
+// ---------------------------------------------------------------- batched launches
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+void batch_fast(const BatchArgs& a, const Launch& L) {
+  const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
+  auto kern = k_predict_fast_batch<T, NDIM, B0, B1, B2, ABFT>;
+  dim3 grid;
+  launch_persistent(kern, 128, smem, a.start[a.n] * 128, L, &grid);
+  kern<<<grid, 128, smem, L.stream>>>(a);
+  note_launch();
+}
+
+template <typename T, bool ABFT>
+bool batch_fast_shape(int ndim, uint32_t B, const BatchArgs& a, const Launch& L) {
+  if (ndim == 3) {
+    switch (B) {
+      case 4: batch_fast<T, 3, 4, 4, 4, ABFT>(a, L); return true;
+      case 6: batch_fast<T, 3, 6, 6, 6, ABFT>(a, L); return true;
+      case 8: batch_fast<T, 3, 8, 8, 8, ABFT>(a, L); return true;
+      case 10: batch_fast<T, 3, 10, 10, 10, ABFT>(a, L); return true;
+      case 12: batch_fast<T, 3, 12, 12, 12, ABFT>(a, L); return true;
+      case 16: batch_fast<T, 3, 16, 16, 16, ABFT>(a, L); return true;
+      default: return false;
+    }
+  }
+  if (ndim == 2) {
+    switch (B) {
+      case 8: batch_fast<T, 2, 1, 8, 8, ABFT>(a, L); return true;
+      case 12: batch_fast<T, 2, 1, 12, 12, ABFT>(a, L); return true;
+      case 16: batch_fast<T, 2, 1, 16, 16, ABFT>(a, L); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
+template <typename T, int NDIM, bool ABFT>
+void batch_generic(const BatchArgs& a, uint32_t threads, size_t smem, const Launch& L) {
+  auto kern = k_predict_batch<T, NDIM, ABFT>;
+  dim3 grid;
+  launch_persistent(kern, threads, smem, a.start[a.n] * threads, L, &grid);
+  kern<<<grid, threads, smem, L.stream>>>(a);
+  note_launch();
+}
+
+template <typename T, bool ABFT>
+void batch_generic_dim(int ndim, const BatchArgs& a, uint32_t threads, size_t smem, const Launch& L) {
+  if (ndim == 3) batch_generic<T, 3, ABFT>(a, threads, smem, L);
+  else if (ndim == 2) batch_generic<T, 2, ABFT>(a, threads, smem, L);
+  else batch_generic<T, 1, ABFT>(a, threads, smem, L);
 }
 
 }  // namespace

@@ -486,6 +486,95 @@ void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint3
 void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
 void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
 
+// ---------------------------------------------------------------- batches
+// A batch compresses many fields with one launch per stage and kernel shape: every field is
+// a Job in a device-side table, and the CTAs of a persistent launch pull work items (a field
+// and a range of its blocks) from a queue counter in device memory. A field's items are
+// numbered from 0 like the CTAs of a single-field launch, so the same per-item code runs in
+// both cases and a field's output is the same alone and in a batch.
+constexpr int kMaxBatch = 64;    // fields per batch
+constexpr int kMaxQueues = 64;   // queue counters per batch (one per launch)
+
+struct Job {
+  Geo g;
+  Ws w;
+  const void* field;
+  uint8_t* out;
+  uint64_t cap;
+  int vec2;        // the field's rows allow two-value vector loads
+  int fast;        // the block shape has a compile-time fast path
+  uint64_t gcount; // blocks of the generic path: edge blocks, or all blocks without a fast path
+};
+
+// One batched launch: the jobs it serves and the first item of each.
+struct BatchArgs {
+  const Job* jobs;
+  unsigned long long* head;         // this launch's queue counter (zero before the launch)
+  uint32_t n;
+  uint32_t idx[kMaxBatch];          // job table indices
+  uint64_t start[kMaxBatch + 1];    // item prefix sums; start[n] = items in the launch
+};
+
+__device__ __forceinline__ uint32_t find_job(const BatchArgs& a, uint64_t item) {
+  uint32_t lo = 0, hi = a.n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a.start[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The CTA loop of a batched launch: pull an item, make its job current in shared memory
+// (calling leave() for the previous job and enter() for the new one; both run on every
+// thread), skip jobs whose call already failed, and run body(local item index). Every
+// decision is taken once per CTA and broadcast, so the body's barriers stay uniform.
+template <class Enter, class Body, class Leave>
+__device__ __forceinline__ void batch_loop(const BatchArgs& a, Job& s_job, Enter&& enter, Body&& body,
+                                           Leave&& leave) {
+  __shared__ unsigned long long s_item;
+  __shared__ int s_cur, s_skip;
+  if (threadIdx.x == 0) s_cur = -1;
+  const uint64_t total = a.start[a.n];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1ull);
+    __syncthreads();
+    const uint64_t item = s_item;
+    const int cur = s_cur;
+    const int j = item < total ? (int)find_job(a, item) : -1;
+    if (j != cur) {
+      if (cur >= 0) leave();
+      __syncthreads();
+      if (j < 0) break;
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&a.jobs[a.idx[j]]);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_job);
+      for (uint32_t q = threadIdx.x; q < sizeof(Job) / 8; q += blockDim.x) dst[q] = src[q];
+      __syncthreads();
+      if (threadIdx.x == 0) s_cur = j;
+      enter();
+    }
+    if (threadIdx.x == 0) s_skip = *(volatile unsigned int*)&s_job.w.st->error != 0;
+    __syncthreads();
+    if (!s_skip) body(item - a.start[j]);
+  }
+}
+
+struct NoOp {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// Batched launches (one per stage and kernel shape; see BatchArgs).
+bool prep_has_fast(const Geo& g);
+bool batch_prep_fast(int dtype, int ndim, uint32_t B, const BatchArgs& a, const Launch& L);
+void batch_prep_generic(int dtype, int ndim, const BatchArgs& a, size_t smem, const Launch& L);
+void batch_bound(const Job* jobs, uint32_t n, const Launch& L);
+bool batch_predict_fast(int dtype, int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L);
+void batch_predict_generic(int dtype, int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
+                           const Launch& L);
+void batch_codebook(const Job* jobs, uint32_t n, const Launch& L);
+void batch_encode(int dtype, bool abft, const BatchArgs& a, const Launch& L);
+
 // Parsed stream header (host side) for the decoder.
 struct Hdr {
   Geo g;
