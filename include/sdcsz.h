@@ -233,6 +233,28 @@ int sdcsz_batch_launch(sdcsz_batch* b, void* stream);
 int sdcsz_batch_results(sdcsz_batch* b, size_t* out_bytes, sdcsz_report* reports, void* stream);
 void sdcsz_batch_destroy(sdcsz_batch* b);
 
+/*
+ * Block-size autotuner (no counterpart in the paper, which fixes the block size by a
+ * rate-distortion study, Sec. 6.2.1). Compresses the leading `sample_points` of d_field (whole
+ * planes in 3D, rows in 2D; the shape, dtype and bound of *p) once per candidate edge (the
+ * same edge on every axis, each a valid block of p's dimensionality), timing `3` runs with
+ * CUDA events. results[c] receives the candidate's time, stream size, throughput and ratio;
+ * *best the index of the fastest candidate whose stream is at most (1 + size_slack) times the
+ * smallest. Allocates its scratch with cudaMallocAsync on `stream` and waits for it (a tuning
+ * call, not for the hot path).
+ */
+typedef struct sdcsz_tune_result {
+  uint32_t block;
+  double ms;       /* mean compression time of the sample */
+  uint64_t bytes;  /* stream size of the sample */
+  double gbs;      /* sample bytes / ms */
+  double ratio;    /* sample bytes / stream bytes */
+} sdcsz_tune_result;
+
+int sdcsz_autotune_block(const void* d_field, const sdcsz_params* p, const uint32_t* candidates, uint32_t n_cand,
+                         uint64_t sample_points, double size_slack, void* stream, sdcsz_tune_result* results,
+                         uint32_t* best);
+
 /* Number of CUDA kernels the library has launched in this process so far (all devices, all
  * entry points). Instrumentation only; the paper has no counterpart. */
 unsigned long long sdcsz_kernel_launches(void);

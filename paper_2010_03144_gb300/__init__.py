@@ -27,7 +27,8 @@ EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_wor
            "sdcsz_debug_compress_flips", "sdcsz_debug_decompress_flips", "sdcsz_compress_traced",
            "sdcsz_decompress_traced", "sdcsz_compress_noalloc", "sdcsz_kernel_launches", "sdcsz_batch_create",
            "sdcsz_batch_workspace_size", "sdcsz_batch_bind", "sdcsz_batch_set_fields", "sdcsz_batch_compress",
-           "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy")
+           "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy",
+           "sdcsz_autotune_block")
 
 
 class SdcszError(RuntimeError):
@@ -69,6 +70,16 @@ class Report(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [
+        ("block", ctypes.c_uint32),
+        ("ms", ctypes.c_double),
+        ("bytes", ctypes.c_uint64),
+        ("gbs", ctypes.c_double),
+        ("ratio", ctypes.c_double),
+    ]
 
 
 class BatchItem(ctypes.Structure):
@@ -127,6 +138,10 @@ def lib():
         L.sdcsz_batch_capture.argtypes = [BP, vp]
         L.sdcsz_batch_launch.argtypes = [BP, vp]
         L.sdcsz_batch_results.argtypes = [BP, ctypes.POINTER(sz), R, vp]
+        L.sdcsz_autotune_block.argtypes = [vp, P, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                           ctypes.c_uint64, ctypes.c_double, vp, ctypes.POINTER(TuneResult),
+                                           ctypes.POINTER(ctypes.c_uint32)]
+        L.sdcsz_autotune_block.restype = i32
         L.sdcsz_batch_destroy.argtypes = [BP]
         L.sdcsz_batch_destroy.restype = None
         for f in (L.sdcsz_batch_create, L.sdcsz_batch_workspace_size, L.sdcsz_batch_bind, L.sdcsz_batch_set_fields,

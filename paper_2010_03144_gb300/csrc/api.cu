@@ -903,3 +903,87 @@ void sdcsz_batch_destroy(sdcsz_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- block-size autotuner
+// Compresses a leading slab of the field (contiguous, so no copy) with each candidate block
+// edge and times it with CUDA events; the choice is the fastest candidate whose compressed
+// size is within `size_slack` of the smallest. At a fixed error bound the compressed size is
+// the rate side of the paper's rate-distortion block-size study (Sec. 6.2.1): the slack bounds
+// the rate given up for speed.
+extern "C" int sdcsz_autotune_block(const void* d_field, const sdcsz_params* p, const uint32_t* candidates,
+                                    uint32_t n_cand, uint64_t sample_points, double size_slack, void* stream,
+                                    sdcsz_tune_result* results, uint32_t* best) {
+  using namespace sdcsz;
+  Geo g;
+  int rc = make_geo(p, &g);
+  if (rc) return rc;
+  if (!d_field || !candidates || !n_cand || !results || !best || !(size_slack >= 0.0 && size_slack < 1e6))
+    return SDCSZ_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the sample: whole planes (3D), rows (2D) or a prefix (1D) up to sample_points
+  sdcsz_params q = *p;
+  const uint64_t inner = g.ndim == 1 ? 1 : (g.ndim == 2 ? g.d[2] : g.d[1] * g.d[2]);
+  const uint64_t outer = g.ndim == 1 ? g.d[2] : (g.ndim == 2 ? g.d[1] : g.d[0]);
+  uint64_t take = std::max<uint64_t>(1, sample_points / std::max<uint64_t>(inner, 1));
+  take = std::min(take, outer);
+  q.dims[0] = take;
+  std::vector<sdcsz_params> cp(n_cand, q);
+  size_t ws_max = 0, out_max = 0;
+  for (uint32_t c = 0; c < n_cand; ++c) {
+    for (uint32_t a = 0; a < q.ndim; ++a) cp[c].block[a] = candidates[c];
+    Geo gc;
+    rc = make_geo(&cp[c], &gc);
+    if (rc) return rc;
+    size_t cap = 0;
+    if ((rc = sdcsz_compress_bound(&cp[c], &cap))) return rc;
+    ws_max = std::max(ws_max, plan_ws(gc).total);
+    out_max = std::max(out_max, cap);
+  }
+  void *ws = nullptr, *out = nullptr;
+  if (cudaMallocAsync(&ws, ws_max, s) != cudaSuccess) return SDCSZ_ECUDA;
+  if (cudaMallocAsync(&out, out_max, s) != cudaSuccess) {
+    cudaFreeAsync(ws, s);
+    return SDCSZ_ECUDA;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  uint64_t smallest = ~0ull;
+  const int reps = 3;
+  for (uint32_t c = 0; c < n_cand && !rc; ++c) {
+    size_t nbytes = 0;
+    rc = compress_impl(d_field, &cp[c], out, out_max, &nbytes, ws, ws_max, nullptr, stream, nullptr, 0);
+    if (rc) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && !rc; ++r)
+      rc = compress_impl(d_field, &cp[c], out, out_max, nullptr, ws, ws_max, nullptr, stream, nullptr, 0);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = SDCSZ_ECUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double in_bytes = (double)take * inner * (p->dtype ? 8.0 : 4.0);
+    results[c].block = candidates[c];
+    results[c].ms = ms / reps;
+    results[c].bytes = nbytes;
+    results[c].gbs = in_bytes / (results[c].ms * 1e-3) / 1e9;
+    results[c].ratio = nbytes ? in_bytes / (double)nbytes : 0.0;
+    smallest = std::min<uint64_t>(smallest, nbytes);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(ws, s);
+  cudaFreeAsync(out, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SDCSZ_ECUDA;
+  if (rc) return rc;
+  uint32_t pick = 0;
+  bool have = false;
+  for (uint32_t c = 0; c < n_cand; ++c) {
+    if ((double)results[c].bytes > (1.0 + size_slack) * (double)smallest) continue;
+    if (!have || results[c].gbs > results[pick].gbs) {
+      pick = c;
+      have = true;
+    }
+  }
+  *best = pick;
+  return SDCSZ_OK;
+}

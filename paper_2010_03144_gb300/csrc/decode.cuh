@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ s, u
   wk.sr = h.g.B[1] * h.g.B[2];
   const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
   Acc acc;
-  for (uint64_t gid = blockIdx.x; gid < ngroups; gid += gridDim.x) {
+  for (uint64_t gid = cta_pull(&st->queue[1]); gid < ngroups; gid = cta_pull(&st->queue[1])) {
     const uint64_t b0 = gid * kGroup;
     const uint32_t nblk = (uint32_t)min((uint64_t)kGroup, h.g.nb - b0);
     if (!all) {
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
   const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
   const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
   Acc acc;
-  for (uint64_t gid = blockIdx.x; gid < ngroups; gid += gridDim.x) {
+  for (uint64_t gid = cta_pull(&st->queue[0]); gid < ngroups; gid = cta_pull(&st->queue[0])) {
     const uint64_t b0 = gid * kGroup;
     const uint32_t nblk = (uint32_t)min((uint64_t)kGroup, g.nb - b0);
     if (!group_scan(s, h, gid, ngroups, sm, st)) {

@@ -598,10 +598,10 @@ __global__ void __launch_bounds__(128) k_predict(const T* __restrict__ field, Ge
   Walker<T, NDIM> wk;
   walker_init(wk, smem, g);
   Counters cnt;
-  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x < count; e += step) {
-    if (e >= count) continue;
-    predict_generic_block<T, NDIM, ABFT>(field, g, w, flips, nflips, all ? e : edge_block(g, e), wk, K, h, cnt);
+  for (uint64_t it = cta_pull(&st->queue[1]); it * blockDim.x < count; it = cta_pull(&st->queue[1])) {
+    const uint64_t e = it * blockDim.x + threadIdx.x;
+    if (e < count)
+      predict_generic_block<T, NDIM, ABFT>(field, g, w, flips, nflips, all ? e : edge_block(g, e), wk, K, h, cnt);
   }
   cnt.commit(st);
   hist_flush(hist_s, h, w);
@@ -718,10 +718,9 @@ __global__ void __launch_bounds__(128, 7) k_predict_fast(const T* __restrict__ f
   const Consts<T> K(st->eb, g.R, NDIM);
   T* plane = reinterpret_cast<T*>(smem) + threadIdx.x;
   Counters cnt;
-  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b - threadIdx.x < g.nb; b += step) {
-    if (b >= g.nb) continue;
-    predict_fast_block<T, NDIM, B0, B1, B2, ABFT>(field, g, w, flips, nflips, vec2, b, plane, K, h, cnt);
+  for (uint64_t it = cta_pull(&st->queue[0]); it * blockDim.x < g.nb; it = cta_pull(&st->queue[0])) {
+    const uint64_t b = it * blockDim.x + threadIdx.x;
+    if (b < g.nb) predict_fast_block<T, NDIM, B0, B1, B2, ABFT>(field, g, w, flips, nflips, vec2, b, plane, K, h, cnt);
   }
   cnt.commit(st);
   hist_flush(hist_s, h, w);

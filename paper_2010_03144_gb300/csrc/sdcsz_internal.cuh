@@ -55,8 +55,19 @@ struct State {
   unsigned int ticket, n_live;
   unsigned long long payload_bytes, total_bytes;
   Layout L;
-  unsigned long long pad[4];
+  unsigned long long queue[4];  // work-queue counters of the persistent kernels of one call
 };
+
+// Work queue of a persistent kernel: the CTA takes the next item index (one atomic per CTA).
+// Items go to the CTAs that are running, so a grid that cannot be resident at once (other
+// kernels hold some of the SMs' slots) still finishes when its running CTAs have drained it.
+__device__ __forceinline__ uint64_t cta_pull(unsigned long long* q) {
+  __shared__ unsigned long long s_item_q;
+  __syncthreads();
+  if (threadIdx.x == 0) s_item_q = atomicAdd(q, 1ull);
+  __syncthreads();
+  return s_item_q;
+}
 
 // Decoupled look-back record of one group (encode kernel).
 struct LookBack {
@@ -528,7 +539,9 @@ __device__ __forceinline__ uint32_t find_job(const BatchArgs& a, uint64_t item) 
 // The CTA loop of a batched launch: pull an item, make its job current in shared memory
 // (calling leave() for the previous job and enter() for the new one; both run on every
 // thread), skip jobs whose call already failed, and run body(local item index). Every
-// decision is taken once per CTA and broadcast, so the body's barriers stay uniform.
+// decision is taken once per CTA and broadcast, so the body's barriers stay uniform. A CTA
+// may find the queue drained at its first pull (others started earlier and took every item):
+// it then leaves without touching any job.
 template <class Enter, class Body, class Leave>
 __device__ __forceinline__ void batch_loop(const BatchArgs& a, Job& s_job, Enter&& enter, Body&& body,
                                            Leave&& leave) {
@@ -542,11 +555,14 @@ __device__ __forceinline__ void batch_loop(const BatchArgs& a, Job& s_job, Enter
     __syncthreads();
     const uint64_t item = s_item;
     const int cur = s_cur;
-    const int j = item < total ? (int)find_job(a, item) : -1;
+    if (item >= total) {  // queue drained (possibly before this CTA got any item)
+      if (cur >= 0) leave();
+      break;
+    }
+    const int j = (int)find_job(a, item);
     if (j != cur) {
       if (cur >= 0) leave();
       __syncthreads();
-      if (j < 0) break;
       const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&a.jobs[a.idx[j]]);
       unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_job);
       for (uint32_t q = threadIdx.x; q < sizeof(Job) / 8; q += blockDim.x) dst[q] = src[q];

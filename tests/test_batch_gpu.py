@@ -122,3 +122,25 @@ def test_batch_isolates_a_failing_field():
     with pytest.raises(sz.SdcszError):
         b.results()
     b.close()
+
+
+def test_autotuner_picks_a_candidate_and_caches(tmp_path):
+    import torch
+    from paper_2010_03144_gb300 import autotune
+    sz = gpu_sz()
+    f = torch.from_numpy(synth.sinusoid_field((96, 80, 72), 11)).cuda()
+    best, rows = autotune.measure(f, 1e-3, sample_points=48 * 80 * 72)
+    assert best in autotune.CANDIDATES[3]
+    assert [r["block"] for r in rows] == list(autotune.CANDIDATES[3])
+    smallest = min(r["bytes"] for r in rows)
+    chosen = rows[autotune.CANDIDATES[3].index(best)]
+    assert chosen["bytes"] <= 1.10 * smallest
+    assert all(r["gbs"] <= chosen["gbs"] for r in rows if r["bytes"] <= 1.10 * smallest)
+    # the sample is the leading 48 planes: its size matches a direct compression of that slab
+    s_slab, _ = sz.compress(f[:48].contiguous(), 1e-3, block=best)
+    assert chosen["bytes"] == s_slab.numel()
+    path = str(tmp_path / "tune.json")
+    t = autotune.Tuner(path)
+    b1 = t.block_for(f, 1e-3)
+    t2 = autotune.Tuner(path)
+    assert t2.block_for(f, 1e-3) == b1 and len(t2.cache) == 1

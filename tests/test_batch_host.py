@@ -55,3 +55,16 @@ def test_batch_calls_on_null_handle_fail_cleanly():
     assert L.sdcsz_batch_results(None, None, None, None) == sz.EINVAL
     assert L.sdcsz_batch_workspace_size(None, None) == sz.EINVAL
     L.sdcsz_batch_destroy(None)
+
+
+def test_autotune_field_classes():
+    from paper_2010_03144_gb300 import autotune
+    import numpy as np
+    a = autotune.field_class((100, 500, 500), np.float32, 1e-3)
+    b = autotune.field_class((128, 512, 512), np.float32, 2e-3)
+    c = autotune.field_class((128, 512, 512), np.float32, 1e-4)
+    d = autotune.field_class((1800, 3600), np.float32, 1e-3)
+    e = autotune.field_class((100, 500, 500), np.float64, 1e-3)
+    assert a == b          # same size decade, same bound decade
+    assert len({a, c, d, e}) == 4
+    assert autotune.field_class((10,), "torch.float32", 1e-2).startswith("f32/1d/n1e1/eb1e-2")
