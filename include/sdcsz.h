@@ -293,6 +293,70 @@ int sdcsz_debug_decompress_flips(const void* d_stream, size_t nbytes, void* d_fi
                                  uint8_t* d_block_status, void* d_ws, size_t ws_bytes, sdcsz_report* report,
                                  void* stream, const sdcsz_flip* d_flips, size_t n_flips);
 
+/*
+ * Request server (no counterpart in the paper). One scheduler thread and `slots` CUDA
+ * streams on the current device. Requests are admitted in arrival order as soon as a slot is
+ * free and the device memory they need fits in `hbm_budget` (their workspace, plus the
+ * output when d_out is NULL and the server provides it); admitted requests run concurrently,
+ * and a slot goes to the next pending request the moment its work completes (continuous
+ * batching, no batch boundaries). Each request runs the same kernels as the single-call
+ * entry points, so its result is the same alone and in any mix.
+ *   compress:   d_in = field (device), params; result = the stream (d_out, or server memory)
+ *   decompress: d_in/in_bytes = stream (device); result = the field (d_out, or server memory)
+ *   verify:     d_in/in_bytes = stream, d_original optional; result = report only
+ * Caller buffers (d_in, d_out, d_original, d_flips) must stay valid until the request's
+ * completion is polled. Server-provided results stay in device memory (and count against
+ * the budget) until sdcsz_server_release(id). SITE_INPUT flips modify d_in, as with
+ * sdcsz_debug_compress_flips. Completions carry the server-clock times (seconds) of submit,
+ * admission and completion (observed by the scheduler), the status (an SDCSZ_E* code or
+ * SDCSZ_OK; decompress/verify return SDCSZ_ESDC when a block failed twice) and the report.
+ * sdcsz_server_destroy finishes every submitted request, then frees the server's memory.
+ */
+enum { SDCSZ_OP_COMPRESS = 1, SDCSZ_OP_DECOMPRESS = 2, SDCSZ_OP_VERIFY = 3 };
+
+typedef struct sdcsz_server_config {
+  uint64_t hbm_budget; /* bytes of device memory admitted requests may hold */
+  uint32_t slots;      /* requests on the device at once (1..64) */
+  uint32_t reserved;
+} sdcsz_server_config;
+
+typedef struct sdcsz_request {
+  uint32_t op;
+  uint32_t reserved;
+  uint64_t id;               /* returned with the completion */
+  const void* d_in;
+  size_t in_bytes;           /* decompress / verify: stream length */
+  sdcsz_params params;       /* compress */
+  void* d_out;               /* NULL: the server provides the output */
+  size_t out_cap;
+  const void* d_original;    /* verify: optional */
+  const sdcsz_flip* d_flips; /* optional soft-error records (sorted by block) */
+  size_t n_flips;
+} sdcsz_request;
+
+typedef struct sdcsz_completion {
+  uint64_t id;
+  uint32_t op;
+  int status;
+  const void* d_result;
+  size_t result_bytes;
+  sdcsz_report report;
+  double t_submit, t_admit, t_done;
+} sdcsz_completion;
+
+typedef struct sdcsz_server_stats {
+  uint64_t pending, in_flight, admitted, completed, bytes_in_use, peak_bytes;
+} sdcsz_server_stats;
+
+typedef struct sdcsz_server sdcsz_server;
+
+int sdcsz_server_create(const sdcsz_server_config* cfg, sdcsz_server** out);
+int sdcsz_server_submit(sdcsz_server* s, const sdcsz_request* r);
+int sdcsz_server_poll(sdcsz_server* s, sdcsz_completion* out, uint32_t max, uint32_t* n, uint32_t wait_us);
+int sdcsz_server_release(sdcsz_server* s, uint64_t id);
+int sdcsz_server_get_stats(sdcsz_server* s, sdcsz_server_stats* out);
+void sdcsz_server_destroy(sdcsz_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_wor
            "sdcsz_decompress_traced", "sdcsz_compress_noalloc", "sdcsz_kernel_launches", "sdcsz_batch_create",
            "sdcsz_batch_workspace_size", "sdcsz_batch_bind", "sdcsz_batch_set_fields", "sdcsz_batch_compress",
            "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy",
-           "sdcsz_autotune_block")
+           "sdcsz_autotune_block", "sdcsz_server_create", "sdcsz_server_submit", "sdcsz_server_poll",
+           "sdcsz_server_release", "sdcsz_server_get_stats", "sdcsz_server_destroy")
 
 
 class SdcszError(RuntimeError):
@@ -70,6 +71,48 @@ class Report(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+OP_COMPRESS, OP_DECOMPRESS, OP_VERIFY = 1, 2, 3
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("id", ctypes.c_uint64),
+        ("d_in", ctypes.c_void_p),
+        ("in_bytes", ctypes.c_size_t),
+        ("params", Params),
+        ("d_out", ctypes.c_void_p),
+        ("out_cap", ctypes.c_size_t),
+        ("d_original", ctypes.c_void_p),
+        ("d_flips", ctypes.c_void_p),
+        ("n_flips", ctypes.c_size_t),
+    ]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_uint64),
+        ("op", ctypes.c_uint32),
+        ("status", ctypes.c_int),
+        ("d_result", ctypes.c_void_p),
+        ("result_bytes", ctypes.c_size_t),
+        ("report", Report),
+        ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("pending", "in_flight", "admitted", "completed", "bytes_in_use",
+                                               "peak_bytes")]
 
 
 class TuneResult(ctypes.Structure):
@@ -142,6 +185,18 @@ def lib():
                                            ctypes.c_uint64, ctypes.c_double, vp, ctypes.POINTER(TuneResult),
                                            ctypes.POINTER(ctypes.c_uint32)]
         L.sdcsz_autotune_block.restype = i32
+        SP = ctypes.c_void_p
+        L.sdcsz_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(SP)]
+        L.sdcsz_server_submit.argtypes = [SP, ctypes.POINTER(Request)]
+        L.sdcsz_server_poll.argtypes = [SP, ctypes.POINTER(Completion), ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]
+        L.sdcsz_server_release.argtypes = [SP, ctypes.c_uint64]
+        L.sdcsz_server_get_stats.argtypes = [SP, ctypes.POINTER(ServerStats)]
+        L.sdcsz_server_destroy.argtypes = [SP]
+        L.sdcsz_server_destroy.restype = None
+        for f in (L.sdcsz_server_create, L.sdcsz_server_submit, L.sdcsz_server_poll, L.sdcsz_server_release,
+                  L.sdcsz_server_get_stats):
+            f.restype = i32
         L.sdcsz_batch_destroy.argtypes = [BP]
         L.sdcsz_batch_destroy.restype = None
         for f in (L.sdcsz_batch_create, L.sdcsz_batch_workspace_size, L.sdcsz_batch_bind, L.sdcsz_batch_set_fields,
@@ -484,3 +539,114 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching request server (sdcsz_server_* in the C header).
+
+    ``submit_*`` return immediately; ``poll`` returns completions as dicts with the result as
+    a device pointer and size (for server-provided outputs ``result_view`` wraps it as a uint8
+    CUDA tensor view, valid until ``release``). Caller tensors passed to a request must stay
+    alive until its completion is polled: the server keeps references until then."""
+
+    def __init__(self, hbm_budget: int, slots: int = 8):
+        cfg = ServerConfig(int(hbm_budget), int(slots), 0)
+        self.h = ctypes.c_void_p()
+        rc = lib().sdcsz_server_create(ctypes.byref(cfg), ctypes.byref(self.h))
+        if rc:
+            raise SdcszError(rc, "server_create")
+        self._keep = {}
+
+    def _submit(self, req: Request, keep):
+        rc = lib().sdcsz_server_submit(self.h, ctypes.byref(req))
+        if rc:
+            raise SdcszError(rc, "server_submit")
+        self._keep[int(req.id)] = keep
+
+    def submit_compress(self, rid, field, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
+                        out=None, flips=None):
+        r = Request()
+        r.op, r.id, r.d_in = OP_COMPRESS, rid, field.data_ptr()
+        r.params = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor)
+        if out is not None:
+            r.d_out, r.out_cap = out.data_ptr(), out.numel()
+        ft = flips_tensor(flips, field.device) if flips else None
+        if ft is not None:
+            r.d_flips, r.n_flips = ft.data_ptr(), len(flips)
+        self._submit(r, (field, out, ft))
+
+    def submit_decompress(self, rid, stream_t, out=None, flips=None):
+        r = Request()
+        r.op, r.id, r.d_in, r.in_bytes = OP_DECOMPRESS, rid, stream_t.data_ptr(), stream_t.numel()
+        if out is not None:
+            r.d_out, r.out_cap = out.data_ptr(), out.numel() * out.element_size()
+        ft = flips_tensor(flips, stream_t.device) if flips else None
+        if ft is not None:
+            r.d_flips, r.n_flips = ft.data_ptr(), len(flips)
+        self._submit(r, (stream_t, out, ft))
+
+    def submit_verify(self, rid, stream_t, original=None):
+        r = Request()
+        r.op, r.id, r.d_in, r.in_bytes = OP_VERIFY, rid, stream_t.data_ptr(), stream_t.numel()
+        if original is not None:
+            r.d_original = original.data_ptr()
+        self._submit(r, (stream_t, original))
+
+    def poll(self, max_n: int = 256, wait_us: int = 0):
+        arr = (Completion * max_n)()
+        n = ctypes.c_uint32()
+        rc = lib().sdcsz_server_poll(self.h, arr, max_n, ctypes.byref(n), wait_us)
+        if rc:
+            raise SdcszError(rc, "server_poll")
+        out = []
+        for c in arr[: n.value]:
+            self._keep.pop(int(c.id), None)
+            out.append({"id": int(c.id), "op": int(c.op), "status": int(c.status), "d_result": c.d_result,
+                        "result_bytes": int(c.result_bytes), "report": c.report.as_dict(), "t_submit": c.t_submit,
+                        "t_admit": c.t_admit, "t_done": c.t_done})
+        return out
+
+    def release(self, rid):
+        rc = lib().sdcsz_server_release(self.h, rid)
+        if rc:
+            raise SdcszError(rc, "server_release")
+
+    def stats(self):
+        st = ServerStats()
+        lib().sdcsz_server_get_stats(self.h, ctypes.byref(st))
+        return {n: int(getattr(st, n)) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().sdcsz_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def result_view(completion, device=None):
+    """A uint8 CUDA tensor view of a server-provided result (valid until Server.release)."""
+    import torch
+    n = completion["result_bytes"]
+    if not n:
+        return torch.empty(0, dtype=torch.uint8, device=device or "cuda")
+    return _device_view(completion["d_result"], n, device)
+
+
+def _device_view(ptr, nbytes, device=None):
+    """Wrap raw device memory as a uint8 tensor (no copy, no ownership)."""
+    import torch
+
+    class _Arr:
+        pass
+
+    a = _Arr()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    a.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
+                                  "version": 3, "strides": None}
+    return torch.as_tensor(a, device=dev)

@@ -10,15 +10,14 @@
 #include <mutex>
 #include <vector>
 
-#include "sdcsz_internal.cuh"
+#include "host.h"
 
 namespace sdcsz {
 
-namespace {
+inline namespace host {
 
 constexpr uint64_t kMaxPoints = 1ull << 40;
 
-inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int sm_count() {
   static int cached[64] = {0};
@@ -51,7 +50,7 @@ cudaStream_t side_stream() {
   return streams[dev];
 }
 
-namespace {
+inline namespace host {
 
 // Validate parameters and fill the padded-3D geometry.
 int make_geo(const sdcsz_params* p, Geo* g) {
@@ -98,11 +97,6 @@ int make_geo(const sdcsz_params* p, Geo* g) {
   g->e = p->eb;
   return SDCSZ_OK;
 }
-
-struct WsPlan {
-  size_t state, sum_in, isum_in, sum_q, isum_q, sum_dc, coef, est, pflag, flags, coefT, hist, codebook, lb, sort_keys,
-      node_w, node_parent, codes, ustage, total;
-};
 
 WsPlan plan_ws(const Geo& g) {
   WsPlan w;
@@ -228,7 +222,7 @@ struct Trace {
 
 int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap, size_t* out_bytes,
                   void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream, const sdcsz_flip* flips,
-                  size_t n_flips, float* stage_ms = nullptr) {
+                  size_t n_flips, float* stage_ms) {
   Geo g;
   int rc = make_geo(p, &g);
   if (rc) return rc;
@@ -333,9 +327,24 @@ int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout) 
   return SDCSZ_OK;
 }
 
+int decode_enqueue(const void* d_stream, size_t nbytes, const Hdr& h, void* d_field, size_t field_bytes,
+                   uint8_t* status, const void* d_orig, bool write, State* st, cudaStream_t s, const sdcsz_flip* flips,
+                   size_t n_flips) {
+  const uint64_t need = h.g.N * (h.g.dtype ? 8 : 4);
+  if (write && need && (!d_field || field_bytes < need)) return d_field ? SDCSZ_ECAPACITY : SDCSZ_EINVAL;
+  if (n_flips > 0xffffffffu || (n_flips && !flips)) return SDCSZ_EINVAL;
+  if (cudaMemsetAsync(st, 0, sizeof(State), s) != cudaSuccess) return SDCSZ_ECUDA;
+  Launch L;
+  L.stream = s;
+  L.sms = sm_count();
+  launch_decode(static_cast<const uint8_t*>(d_stream), nbytes, h, d_field, status, d_orig, st, write, flips,
+                (uint32_t)n_flips, L);
+  return SDCSZ_OK;
+}
+
 int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes, uint8_t* status,
                     const void* d_orig, bool write, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,
-                    const sdcsz_flip* flips, size_t n_flips, float* stage_ms = nullptr) {
+                    const sdcsz_flip* flips, size_t n_flips, float* stage_ms) {
   if (!d_stream || !d_ws) return SDCSZ_EINVAL;
   if (nbytes < (size_t)kHeaderBytes) return SDCSZ_EFORMAT;
   if (ws_bytes < sdcsz_decompress_workspace_size()) return SDCSZ_ECAPACITY;
@@ -349,19 +358,13 @@ int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t f
   Hdr h;
   int rc = parse_header(hb, nbytes, &h, nullptr);
   if (rc) return rc;
-  const uint64_t need = h.g.N * (h.g.dtype ? 8 : 4);
-  if (write && need && (!d_field || field_bytes < need)) return d_field ? SDCSZ_ECAPACITY : SDCSZ_EINVAL;
   State* st = static_cast<State*>(d_ws);
-  if (cudaMemsetAsync(st, 0, sizeof(State), s) != cudaSuccess) return SDCSZ_ECUDA;
-  Launch L;
-  L.stream = s;
-  L.sms = sm_count();
   Trace tr;
   tr.ms = stage_ms;
   tr.n = 1;
   tr.start(s);
-  launch_decode(static_cast<const uint8_t*>(d_stream), nbytes, h, d_field, status, d_orig, st, write, flips,
-                (uint32_t)n_flips, L);
+  rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips);
+  if (rc) return rc;
   tr.mark();
   if (cudaGetLastError() != cudaSuccess) return SDCSZ_ECUDA;
   tr.finish();

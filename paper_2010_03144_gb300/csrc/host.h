@@ -1,0 +1,42 @@
+// Host-side helpers of the library shared by its translation units (entry points, batches,
+// the request server). Not part of the C ABI.
+#pragma once
+
+#include "sdcsz_internal.cuh"
+
+namespace sdcsz {
+inline namespace host {
+
+// Byte offsets of the regions of a compression workspace.
+struct WsPlan {
+  size_t state, sum_in, isum_in, sum_q, isum_q, sum_dc, coef, est, pflag, flags, coefT, hist, codebook, lb, sort_keys,
+      node_w, node_parent, codes, ustage, total;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+int sm_count();
+int make_geo(const sdcsz_params* p, Geo* g);
+WsPlan plan_ws(const Geo& g);
+Ws bind_ws(void* base, const WsPlan& p);
+int map_error(unsigned int e);
+void fill_report(const State& h, uint64_t nb, sdcsz_report* r);
+int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout);
+
+// Compression of one field on `stream`. With out_bytes and report both null it only
+// enqueues work (no host synchronisation).
+int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap, size_t* out_bytes,
+                  void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream, const sdcsz_flip* flips,
+                  size_t n_flips, float* stage_ms = nullptr);
+
+// Decompression (write) or verification of a stream whose header was already parsed to the
+// host: clears the State at `st` and enqueues the decoder; no host synchronisation.
+int decode_enqueue(const void* d_stream, size_t nbytes, const Hdr& h, void* d_field, size_t field_bytes,
+                   uint8_t* status, const void* d_orig, bool write, State* st, cudaStream_t s, const sdcsz_flip* flips,
+                   size_t n_flips);
+
+int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes, uint8_t* status,
+                    const void* d_orig, bool write, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,
+                    const sdcsz_flip* flips, size_t n_flips, float* stage_ms = nullptr);
+
+}  // namespace host
+}  // namespace sdcsz
