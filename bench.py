@@ -292,13 +292,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for q in range(args.steps):
         n_s = e2e_step()
-    e1.record(stream)
+        evs[q + 1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = _reduce_max(e0.elapsed_time(e1), world, device)
+    step_ms = [evs[q].elapsed_time(evs[q + 1]) for q in range(args.steps)]
+    e2e_ms = _reduce_max(evs[0].elapsed_time(evs[-1]), world, device)
     e2e_value = world * gb * args.steps / (e2e_ms / 1e3)
 
     result = None
@@ -326,7 +327,10 @@ def run_ours(args):
             "decompress_gbs": round(gb / (dec_ms / 1e3), 2),
             "abft_overhead_pct": round(100.0 * (ms_on_max - ms_off_max) / ms_off_max, 2),
             "abft_off_value": round(world * gb * args.steps / (ms_off_max / 1e3), 2),
-            "p99_latency_ms": None,
+            "p99_latency_ms": round(float(np.percentile(step_ms, 99)), 4),
+            "latency": {"p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+                        "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+                        "what": "one end-to-end step through the public API (host field in, host field out)"},
             "kernels": kernels,
             "kernels_abft_off_ms": {k: round(v / args.steps, 4) for k, v in stages_off.items()},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
@@ -492,13 +496,128 @@ def run_batch13(args):
     batch.close()
 
 
+def _device_field(shape, seed, dtype, device, spikes=0.0):
+    """The synthetic recipe (8 sinusoids with integer frequencies 1..6 per axis, random phases,
+    Gaussian noise 1e-3, optional 1% lognormal spikes), drawn on the device with torch's
+    seeded generators: fast enough for a pool of large serving inputs."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    nd = len(shape)
+    freqs = torch.randint(1, 7, (8, nd), generator=g)
+    phases = torch.rand(8, generator=g, dtype=torch.float64) * 2 * np.pi
+    axes = [torch.arange(n, device=device, dtype=torch.float64) / n for n in shape]
+    acc = torch.zeros(shape, device=device, dtype=torch.float64)
+    for m in range(8):
+        ang = phases[m].item()
+        grid = None
+        for a in range(nd):
+            t = 2 * np.pi * freqs[m, a].item() * axes[a]
+            t = t.view(*([1] * a), -1, *([1] * (nd - a - 1)))
+            grid = t if grid is None else grid + t
+        acc += torch.sin(grid + ang)
+    gd = torch.Generator(device=device).manual_seed(seed + 1)
+    acc += 1e-3 * torch.randn(shape, device=device, dtype=torch.float64, generator=gd)
+    if spikes > 0:
+        n = acc.numel()
+        k = max(1, int(spikes * n))
+        idx = torch.randint(0, n, (k,), device=device, generator=gd)
+        sign = torch.randint(0, 2, (k,), device=device, generator=gd).to(torch.float64) * 2 - 1
+        mag = torch.exp(2.0 * torch.randn(k, device=device, dtype=torch.float64, generator=gd))
+        acc.view(-1)[idx] += sign * mag
+    return acc.to(dtype).contiguous()
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of compress / decompress / verify requests through the server."""
+    import torch
+
+    import paper_2010_03144_gb300 as sz
+    from paper_2010_03144_gb300 import build as libbuild
+
+    libbuild.build()
+    sz.lib()
+    device = torch.device("cuda", 0)
+    rng = np.random.default_rng(4)
+    # input pool resident in HBM: float32 3D, edges uniform in 32..512; float64 2D, 256..4096
+    pool = []
+    for i in range(12):
+        shp = tuple(int(v) for v in rng.integers(32, 513, size=3))
+        pool.append(_device_field(shp, 400 + i, torch.float32, device))
+    for i in range(6):
+        shp = tuple(int(v) for v in rng.integers(256, 4097, size=2))
+        pool.append(_device_field(shp, 500 + i, torch.float64, device))
+    streams = [sz.compress(f, 1e-3)[0].clone() for f in pool]
+    torch.cuda.synchronize()
+    rate, seconds, warm_s = 2000.0, max(1.0, args.steps / 10.0), 0.5
+    n_req = int(rng.poisson(rate * (seconds + warm_s)))
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    arrivals = np.cumsum(gaps)
+    ops = rng.integers(0, 3, size=n_req)
+    which = rng.integers(0, len(pool), size=n_req)
+    ebs = 10.0 ** rng.uniform(-5, -2, size=n_req)
+    flipped = rng.random(n_req) < 0.001
+    srv = sz.Server(hbm_budget=60 << 30, slots=8)
+    done, lat, nbytes_done, peak_inflight = {}, [], 0, 0
+    t0 = time.perf_counter()
+    nxt = 0
+    while len(done) < n_req:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            k, op = int(which[nxt]), int(ops[nxt])
+            fl = None
+            if flipped[nxt]:
+                fl = [("code", 1, 3, 2)] if op == 0 else ([("decomp", 1, 0, 0)] if op == 1 else None)
+            if op == 0:
+                srv.submit_compress(nxt, pool[k], float(ebs[nxt]), flips=fl)
+            elif op == 1:
+                srv.submit_decompress(nxt, streams[k], flips=fl)
+            else:
+                srv.submit_verify(nxt, streams[k])
+            nxt += 1
+        for c in srv.poll(256, wait_us=0 if nxt < n_req else 2000):
+            rid = c["id"]
+            done[rid] = c
+            if c["status"] not in (0, sz.ESDC):
+                raise RuntimeError(f"request {rid} failed: {c['status']}")
+            if c["op"] in (sz.OP_COMPRESS, sz.OP_DECOMPRESS):
+                srv.release(rid)
+            if arrivals[rid] >= warm_s:
+                lat.append(c["t_done"] - c["t_submit"])
+                nbytes_done += pool[int(which[rid])].numel() * pool[int(which[rid])].element_size()
+        st = srv.stats()
+        peak_inflight = max(peak_inflight, st["in_flight"])
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat_ms = np.array(lat) * 1e3
+    measured = [c for rid, c in done.items() if arrivals[rid] >= warm_s]
+    span = max(c["t_done"] for c in measured) - min(c["t_submit"] for c in measured)
+    print(json.dumps({
+        "metric": "serving p50/p99 latency and GB/s, Poisson compress/decompress/verify requests",
+        "value": round(nbytes_done / span / 1e9, 2), "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic",
+        "config": {"workload": "serve: Poisson 2000 req/s, thirds compress/decompress/verify, pool of 12 float32 3D "
+                               "(edges U{32..512}) and 6 float64 2D (edges U{256..4096}) fields resident in HBM, "
+                               "compress rel eb log-uniform 1e-5..1e-2, 0.1% of requests with one bit flip, "
+                               "60 GB admission budget, 8 slots",
+                   "requests": n_req, "measured_requests": len(lat), "warmup_s": warm_s, "seconds": seconds},
+        "p50_latency_ms": round(float(np.percentile(lat_ms, 50)), 3),
+        "p99_latency_ms": round(float(np.percentile(lat_ms, 99)), 3),
+        "mean_latency_ms": round(float(lat_ms.mean()), 3),
+        "achieved_req_per_s": round(len(lat) / span, 1),
+        "wall_s": round(wall, 2), "peak_in_flight": peak_inflight, "peak_bytes": st["peak_bytes"],
+        "flipped_requests": int(flipped.sum()),
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13",), default="512cube")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve"), default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -507,6 +626,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch13":
         run_batch13(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "host.h"
@@ -40,14 +42,49 @@ std::atomic<unsigned long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-cudaStream_t side_stream() {
+cudaStream_t side_stream(cudaStream_t main) {
   static std::mutex mu;
-  static cudaStream_t streams[64] = {nullptr};
+  static std::map<std::pair<int, cudaStream_t>, cudaStream_t> streams;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
-  if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
-  return streams[dev];
+  cudaStream_t& s = streams[{dev, main}];
+  if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+  return s;
+}
+
+namespace {
+std::mutex g_occ_mu;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
+std::map<std::pair<int, const void*>, size_t> g_smem;
+
+void allow_smem_locked(int dev, const void* kern, size_t smem) {
+  size_t& cur = g_smem[{dev, kern}];
+  if (smem > cur && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+    cur = smem;
+}
+}  // namespace
+
+void allow_smem(const void* kern, size_t smem) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_occ_mu);
+  allow_smem_locked(dev, kern, smem);
+}
+
+int occupancy(const void* kern, int threads, size_t smem) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_occ_mu);
+  allow_smem_locked(dev, kern, smem);
+  const auto key = std::make_tuple(dev, kern, threads, smem);
+  auto it = g_occ.find(key);
+  if (it != g_occ.end()) return it->second;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) occ = 1;
+  occ = occ < 1 ? 1 : occ;
+  g_occ[key] = occ;
+  return occ;
 }
 
 inline namespace host {

@@ -751,10 +751,7 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
 // ---------------------------------------------------------------- launch
 template <class K>
 inline unsigned persistent_grid(K kern, uint32_t threads, size_t smem, uint64_t ngroups, const Launch& L) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
-  if (occ < 1) occ = 1;
+  const int occ = occupancy(reinterpret_cast<const void*>(kern), (int)threads, smem);
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ngroups, (uint64_t)occ * L.sms));
 }
 
@@ -822,7 +819,7 @@ void run_generic(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint
     const uint64_t count = edge_count(h.g);
     if (!count) return;
     auto ke = k_decode_edges<T, NDIM>;
-    cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_smem(reinterpret_cast<const void*>(ke), smem);
     ke<<<(unsigned)((count + threads - 1) / threads), threads, smem, L.stream>>>(s, nbytes, h, field, status, orig,
                                                                                   st, flips, nflips, count);
     note_launch();

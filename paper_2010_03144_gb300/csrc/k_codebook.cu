@@ -286,14 +286,14 @@ __global__ void __launch_bounds__(1024) k_codebook_batch(const Job* __restrict__
 constexpr size_t kCodebookSmem = kSmemSort * 8 + 4096 * 8 + 8192 * 4 + 8192;
 
 void batch_codebook(const Job* jobs, uint32_t n, const Launch& L) {
-  cudaFuncSetAttribute(k_codebook_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCodebookSmem);
+  allow_smem(reinterpret_cast<const void*>(k_codebook_batch), kCodebookSmem);
   k_codebook_batch<<<n, 1024, kCodebookSmem, L.stream>>>(jobs);
   note_launch();
 }
 
 void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
   const size_t smem = kCodebookSmem;
-  cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_smem(reinterpret_cast<const void*>(k_codebook), smem);
   k_codebook<<<1, 1024, smem, L.stream>>>(g, w, out, cap);
   note_launch();
 }

@@ -328,9 +328,7 @@ __global__ void __launch_bounds__(256) k_encode_batch(BatchArgs a) {
 template <typename T, bool ABFT>
 static void batch_encode_t(const BatchArgs& a, const Launch& L) {
   auto kern = k_encode_batch<T, ABFT>;
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
-  if (occ < 1) occ = 1;
+  const int occ = occupancy(reinterpret_cast<const void*>(kern), 256, 0);
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(a.start[a.n], (uint64_t)occ * L.sms));
   kern<<<grid, 256, 0, L.stream>>>(a);
   note_launch();

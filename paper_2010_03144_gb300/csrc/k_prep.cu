@@ -425,7 +425,7 @@ static void run_generic(const void* field, const Geo& g, const Ws& w, bool all, 
   const uint64_t count = all ? g.nb : edge_count(g);
   if (!count) return;
   const size_t smem = (g.predictor == 0) ? (size_t)walker_slots(g.ndim, g.B) * threads * sizeof(float) : 0;
-  cudaFuncSetAttribute(k_prep<T, NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_smem(reinterpret_cast<const void*>(k_prep<T, NDIM>), smem);
   k_prep<T, NDIM><<<(unsigned)((count + threads - 1) / threads), threads, smem, L.stream>>>(
       static_cast<const T*>(field), g, w, all ? 1 : 0, count);
   note_launch();
@@ -451,10 +451,7 @@ static void launch_prep_t(const void* field, const Geo& g, const Ws& w, const La
 // ---------------------------------------------------------------- batched launches
 template <class K>
 static unsigned batch_grid(K kern, uint32_t threads, size_t smem, uint64_t items, const Launch& L) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
-  if (occ < 1) occ = 1;
+  const int occ = occupancy(reinterpret_cast<const void*>(kern), (int)threads, smem);
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(items, (uint64_t)occ * L.sms));
 }
 

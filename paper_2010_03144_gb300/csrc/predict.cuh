@@ -759,10 +759,7 @@ __global__ void __launch_bounds__(128, 7) k_predict_fast_batch(BatchArgs a) {
 // ---------------------------------------------------------------- launch
 template <class K>
 inline void launch_persistent(K kern, uint32_t threads, size_t smem, uint64_t nb, const Launch& L, dim3* grid_out) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)threads, smem);
-  if (occ < 1) occ = 1;
+  const int occ = occupancy(reinterpret_cast<const void*>(kern), (int)threads, smem);
   const uint64_t need = (nb + threads - 1) / threads;
   *grid_out = dim3((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)occ * L.sms)));
 }

@@ -451,8 +451,14 @@ struct Launch {
 // Counts every kernel launch the library issues (read back by sdcsz_kernel_launches).
 void note_launch();
 
-// A library-owned stream per device for work that can overlap the caller's stream.
-cudaStream_t side_stream();
+// A library-owned stream for work that overlaps the caller's stream `main`: one per
+// (device, caller stream), so concurrent callers on different streams never share one.
+cudaStream_t side_stream(cudaStream_t main);
+
+// Resident CTAs per SM of `kern` at (threads, smem), cached per device; also raises the
+// kernel's dynamic shared-memory limit to `smem` once. Host-side launch setup only.
+int occupancy(const void* kern, int threads, size_t smem);
+void allow_smem(const void* kern, size_t smem);
 
 // Fork/join: work launched on `side` runs concurrently with the caller's stream between the
 // constructor and join(); join() makes the caller's stream wait for it. Events carry the
@@ -462,7 +468,7 @@ struct Fork {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   bool on = false;
   explicit Fork(const Launch& L) : main(L.stream) {
-    side = side_stream();
+    side = side_stream(main);
     if (!side || cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess) return;
     if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) return;
     cudaEventRecord(e0, main);
