@@ -90,18 +90,27 @@ __device__ __forceinline__ void encode_group(const Geo& g, const Ws& w, uint8_t*
     unsigned long long is = 0;
     const uint32_t* pp = codes + pair_index(b, g.P, 0);
     const uint32_t P2 = P >> 1;
-#pragma unroll 4
-    for (uint32_t k2 = 0; k2 < P2; ++k2) {
-      const uint32_t wp2 = pp[32 * (uint64_t)k2];
+    // isum over a pair: (2m+1) c0 + (2m+2) c1 = (2m+1)(c0 + c1) + c1
+    auto pair = [&](uint32_t wp2, uint32_t k2) {
       const uint32_t c0 = wp2 & 0xffffu, c1 = wp2 >> 16;
       bits += (cb(c0) & 31u) + (cb(c1) & 31u);
       nun += (c0 == 0) + (c1 == 0);
       if (ABFT) {
         s += c0 + c1;
-        mad_wide(is, c0, 2 * k2 + 1);
-        mad_wide(is, c1, 2 * k2 + 2);
+        mad_wide(is, c0 + c1, 2 * k2 + 1);
+        is += c1;
       }
+    };
+    // eight independent loads in flight per thread, then their arithmetic
+    uint32_t k2 = 0;
+    for (; k2 + 8 <= P2; k2 += 8) {
+      uint32_t wq[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) wq[q] = pp[32 * (uint64_t)(k2 + q)];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) pair(wq[q], k2 + q);
     }
+    for (; k2 < P2; ++k2) pair(pp[32 * (uint64_t)k2], k2);
     if (P & 1) {  // odd point count: the last pair holds one code
       const uint32_t c0 = pp[32 * (uint64_t)P2] & 0xffffu;
       bits += cb(c0) & 31u;
@@ -265,11 +274,7 @@ __device__ __forceinline__ void encode_group(const Geo& g, const Ws& w, uint8_t*
   const uint32_t* pp = codes + pair_index(b, g.P, 0);
   const T* up = ust + code_index(b, g.P, 0);
   const uint32_t cw0 = __ldg(&w.codebook[0]);
-  uint32_t wp2 = 0;
-#pragma unroll 4
-  for (uint32_t k = 0; k < P; ++k) {
-    if (!(k & 1)) wp2 = pp[32 * (uint64_t)(k >> 1)];
-    uint32_t c = (k & 1) ? (wp2 >> 16) : (wp2 & 0xffffu);
+  auto put = [&](uint32_t c, uint32_t k) {
     if (ABFT && k == kfix) c = vfix;
     const uint32_t cw = c ? cb(c) : cw0;
     const uint32_t len = cw & 31u;
@@ -290,7 +295,22 @@ __device__ __forceinline__ void encode_group(const Geo& g, const Ws& w, uint8_t*
       if (uidx < ulim) udst[uidx] = up[32 * (uint64_t)k];
       ++uidx;
     }
+  };
+  // code pairs loaded four at a time ahead of their use
+  const uint32_t P2 = P >> 1;
+  for (uint32_t k2 = 0; k2 < P2; k2 += 4) {
+    uint32_t wq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) wq[q] = (k2 + q < P2) ? pp[32 * (uint64_t)(k2 + q)] : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (k2 + q < P2) {
+        put(wq[q] & 0xffffu, 2 * (k2 + q));
+        put(wq[q] >> 16, 2 * (k2 + q) + 1);
+      }
+    }
   }
+  if (P & 1) put(pp[32 * (uint64_t)P2] & 0xffffu, P - 1);
   if (nacc) put_word(out, wa, (uint32_t)(acc << (32 - nacc)), lo, hi, fits);
   if (bad) {
     // a block whose codes could not be repaired is reported in the header status word
