@@ -197,36 +197,53 @@ __device__ __forceinline__ void load_row(const T* __restrict__ row, bool vec2, T
   }
 }
 
+// A row of n <= B2 values (scalar loads; the rest of x is zero).
+template <typename T, int B2>
+__device__ __forceinline__ void load_row_n(const T* __restrict__ row, uint32_t n, T (&x)[B2]) {
+#pragma unroll
+  for (int l = 0; l < B2; ++l) x[l] = (uint32_t)l < n ? __ldg(row + l) : T(0);
+}
+
 // One full block with compile-time edges. `blk` points at the block origin in the field,
 // `plane` at this thread's shared-memory slot 0 (3D Lorenzo only; slot stride kCta).
-template <typename T, int NDIM, int B0, int B1, int B2, int kCta, bool REG, bool ABFT, bool HOOK>
+// EDGE: a block cut by the field boundary, extents e0 x e1 x e2 at most B0 x B1 x B2 (the
+// loops keep their compile-time bounds and skip what lies outside; codes are paired by the
+// block-local index, which need not start a row on a pair).
+template <typename T, int NDIM, int B0, int B1, int B2, int kCta, bool REG, bool ABFT, bool HOOK, bool EDGE = false>
 __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t si, uint64_t sj, bool vec2,
                                              const T* cT, T* plane, T eb, T inv2, T Rh, uint32_t R,
                                              uint32_t* __restrict__ pptr, T* __restrict__ uptr, const Hist& h,
-                                             const Hooks hk, T xfix) {
+                                             const Hooks hk, T xfix, uint32_t e0 = B0, uint32_t e1 = B1,
+                                             uint32_t e2 = B2) {
   PassRes r = {0, 0, 0, 0, 0, 0, 0};
   Run run(R);
+  const int n0 = EDGE ? (int)e0 : B0, n1 = EDGE ? (int)e1 : B1;
+  uint32_t lowe = 0;  // EDGE: pending low half of a code pair
   if (!REG && NDIM == 3) {
 #pragma unroll
     for (int s = 0; s < B1 * B2; ++s) plane[s * kCta] = T(0);
   }
   T brow[B2], arow[B2];  // Lorenzo: d[i][j-1][l] and d[i-1][j-1][l] (3D); d[j-1][l] (2D)
 #pragma unroll 1
-  for (int i = 0; i < B0; ++i) {
+  for (int i = 0; i < n0; ++i) {
 #pragma unroll
     for (int l = 0; l < B2; ++l) {
       brow[l] = T(0);
       arow[l] = T(0);
     }
     T xn[B2];
-    load_row<T, B2>(blk + (uint64_t)i * si, vec2, xn);
+    if (EDGE) load_row_n<T, B2>(blk + (uint64_t)i * si, e2, xn);
+    else load_row<T, B2>(blk + (uint64_t)i * si, vec2, xn);
 #pragma unroll 1
-    for (int j = 0; j < B1; ++j) {
+    for (int j = 0; j < n1; ++j) {
       T x[B2];
 #pragma unroll
       for (int l = 0; l < B2; ++l) x[l] = xn[l];
-      if (j + 1 < B1) load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)(j + 1) * sj, vec2, xn);  // next row
-      const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
+      if (j + 1 < n1) {  // next row
+        if (EDGE) load_row_n<T, B2>(blk + (uint64_t)i * si + (uint64_t)(j + 1) * sj, e2, xn);
+        else load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)(j + 1) * sj, vec2, xn);
+      }
+      const uint32_t k0 = EDGE ? (uint32_t)((i * n1 + j) * (int)e2) : (uint32_t)((i * B1 + j) * B2);
       uint32_t* prow = pptr + (uint64_t)(k0 >> 1) * 32;  // B2 is even: rows start on a pair
       T* urow = uptr + (uint64_t)k0 * 32;
       uint32_t lowc = 0;
@@ -245,6 +262,7 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
       T c = T(0), ac = T(0), bc = T(0), abc = T(0);
 #pragma unroll
       for (int l = 0; l < B2; ++l) {
+        if (EDGE && l >= (int)e2) break;
         const uint32_t k = k0 + l;
         T v = x[l];
         if (HOOK && k == hk.kfix) v = xfix;
@@ -298,8 +316,13 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
             HOOK && k == hk.kp, hk.bitp, r.dup);
         T xr;
         const uint32_t code = quantize<T, ABFT, HOOK>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup);
-        if (l & 1) prow[(l >> 1) * 32] = lowc | (code << 16);
-        else lowc = code;
+        if (EDGE) {
+          if (k & 1) pptr[(uint64_t)(k >> 1) * 32] = lowe | (code << 16);
+          else lowe = code;
+        } else {
+          if (l & 1) prow[(l >> 1) * 32] = lowc | (code << 16);
+          else lowc = code;
+        }
         if (!code) {
           urow[l * 32] = v;
           ++r.nun;
@@ -327,6 +350,7 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
       }
     }
   }
+  if (EDGE && ((e0 * e1 * e2) & 1)) pptr[(uint64_t)((e0 * e1 * e2) >> 1) * 32] = lowe;  // odd count: last half
   run.flush(h);
   return r;
 }
@@ -639,58 +663,76 @@ __global__ void __launch_bounds__(128) k_predict_batch(BatchArgs a) {
       });
 }
 
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool HOOK>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool HOOK, bool EDGE>
 __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_t si, uint64_t sj, bool vec2,
                                                  const T* cT, T* plane, const Consts<T>& K, uint32_t R, uint32_t* cptr,
-                                                 T* uptr, const Hist& h, const Hooks& hk, T xfix) {
+                                                 T* uptr, const Hist& h, const Hooks& hk, T xfix, const uint32_t* e) {
   if (reg)
-    return fast_pass<T, NDIM, B0, B1, B2, 128, true, ABFT, HOOK>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh, R,
-                                                                 cptr, uptr, h, hk, xfix);
-  return fast_pass<T, NDIM, B0, B1, B2, 128, false, ABFT, HOOK>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh, R,
-                                                                cptr, uptr, h, hk, xfix);
+    return fast_pass<T, NDIM, B0, B1, B2, 128, true, ABFT, HOOK, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2,
+                                                                       K.Rh, R, cptr, uptr, h, hk, xfix, e[0], e[1],
+                                                                       e[2]);
+  return fast_pass<T, NDIM, B0, B1, B2, 128, false, ABFT, HOOK, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh,
+                                                                      R, cptr, uptr, h, hk, xfix, e[0], e[1], e[2]);
 }
 
 // One full block of a compile-time shape (B0 x B1 x B2, leading 1s below 3D); edge blocks
 // are skipped (the generic path takes them).
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+// One block with the compile-time shape B0 x B1 x B2 (leading 1s below 3D). Full blocks only,
+// unless EDGE: then block b is an edge block, cut by the field boundary, walked with the same
+// code and its actual extents.
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool EDGE = false>
 __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, const Geo& g, const Ws& w,
                                                    const sdcsz_flip* __restrict__ flips, uint32_t nflips, int vec2,
                                                    uint64_t b, T* plane, const Consts<T>& K, const Hist& h,
                                                    Counters& cnt) {
   T* ustage = static_cast<T*>(w.ustage);
-  constexpr uint32_t P = B0 * B1 * B2;
+  constexpr uint32_t P = B0 * B1 * B2;  // the layout stride (g.P)
   const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
-  const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
-  const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
-  if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) return;
-  const T* blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
-  constexpr uint32_t S = NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2;
-  bool reg = choose_reg(g, w, b, S, K.noise, [&] {
+  uint32_t e[3] = {B0, B1, B2}, Pb = P;
+  const T* blk;
+  Box x;
+  if (EDGE) {
+    x = block_box(g, b);
+    e[0] = x.e[0];
+    e[1] = x.e[1];
+    e[2] = x.e[2];
+    Pb = x.P;
+    blk = field + row_base(g, x, 0, 0);
+    vec2 = 0;
+  } else {
+    const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
+    const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+    if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) return;
+    blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
+  }
+  const uint32_t S = EDGE ? sample_points(NDIM, x.e) : (NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2);
+  auto ereg = [&](uint32_t kf, T xf) {
+    if (EDGE) return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kf, xf);
+    if (kf != kNone) return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, w.coef[b], kf, xf);
     return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, w.coef[b], kNone, T(0));
-  });
+  };
+  bool reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg(kNone, T(0)); });
   T cT[4];
   Hooks hk;
   load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
   uint32_t* cptr = reinterpret_cast<uint32_t*>(w.codes) + pair_index(b, P, 0);
   T* uptr = ustage + code_index(b, P, 0);
   const bool hooked = (hk.kp != kNone) || (hk.kr != kNone);
-  PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
-                                                                      cptr, uptr, h, hk, T(0))
-                     : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, false>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
-                                                                       cptr, uptr, h, hk, T(0));
+  PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
+                                                                            cptr, uptr, h, hk, T(0), e)
+                     : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, false, EDGE>(reg, blk, si, sj, vec2, cT, plane, K,
+                                                                             g.R, cptr, uptr, h, hk, T(0), e);
   uint8_t flag = 0;
   if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
-    const Box x = block_box(g, b);
+    if (!EDGE) x = block_box(g, b);
     uint32_t kf;
     T xf;
     if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
-      withdraw(w, g, b, P, h);
+      withdraw(w, g, b, Pb, h);
       hk.kfix = kf;
-      reg = choose_reg(g, w, b, S, K.noise, [&] {
-        return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, w.coef[b], kf, xf);
-      });
-      r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
-                                                         hk, xf);
+      reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg(kf, xf); });
+      r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
+                                                               hk, xf, e);
       ++cnt.fix;
     } else {
       ++cnt.bad;
@@ -701,6 +743,32 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
   cnt.unpred += r.nun;
   cnt.reg += reg;
   cnt.dup += r.dup;
+}
+
+// Edge blocks of a field whose full blocks take the fast kernel: the same compile-time
+// walk with runtime extents, one thread per edge block (compact enumeration).
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+__global__ void __launch_bounds__(128, 7) k_predict_edge(const T* __restrict__ field, Geo g, Ws w,
+                                                      const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                      uint64_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t hist_s[kHistWindow];
+  State* st = w.st;
+  if (*(volatile unsigned int*)&st->error) return;
+  Hist h;
+  hist_init(hist_s, h, g, w);
+  __syncthreads();
+  const Consts<T> K(st->eb, g.R, NDIM);
+  T* plane = reinterpret_cast<T*>(smem) + threadIdx.x;
+  Counters cnt;
+  for (uint64_t it = cta_pull(&st->queue[1]); it * blockDim.x < count; it = cta_pull(&st->queue[1])) {
+    const uint64_t e = it * blockDim.x + threadIdx.x;
+    if (e < count)
+      predict_fast_block<T, NDIM, B0, B1, B2, ABFT, true>(field, g, w, flips, nflips, 0, edge_block(g, e), plane, K,
+                                                          h, cnt);
+  }
+  cnt.commit(st);
+  hist_flush(hist_s, h, w);
 }
 
 // Fast kernel: full blocks of a compile-time shape.
@@ -793,6 +861,42 @@ void run_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
   note_launch();
 }
 
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+void run_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+              const Launch& L) {
+  const uint64_t count = edge_count(g);
+  if (!count) return;
+  const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
+  auto kern = k_predict_edge<T, NDIM, B0, B1, B2, ABFT>;
+  dim3 grid;
+  launch_persistent(kern, 128, smem, count, L, &grid);
+  kern<<<grid, 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, count);
+  note_launch();
+}
+
+template <typename T, bool ABFT>
+void try_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+              const Launch& L) {
+  if (g.ndim == 3) {
+    switch (g.B[2]) {
+      case 4: run_edge<T, 3, 4, 4, 4, ABFT>(field, g, w, flips, nflips, L); break;
+      case 6: run_edge<T, 3, 6, 6, 6, ABFT>(field, g, w, flips, nflips, L); break;
+      case 8: run_edge<T, 3, 8, 8, 8, ABFT>(field, g, w, flips, nflips, L); break;
+      case 10: run_edge<T, 3, 10, 10, 10, ABFT>(field, g, w, flips, nflips, L); break;
+      case 12: run_edge<T, 3, 12, 12, 12, ABFT>(field, g, w, flips, nflips, L); break;
+      case 16: run_edge<T, 3, 16, 16, 16, ABFT>(field, g, w, flips, nflips, L); break;
+      default: break;
+    }
+  } else if (g.ndim == 2) {
+    switch (g.B[2]) {
+      case 8: run_edge<T, 2, 1, 8, 8, ABFT>(field, g, w, flips, nflips, L); break;
+      case 12: run_edge<T, 2, 1, 12, 12, ABFT>(field, g, w, flips, nflips, L); break;
+      case 16: run_edge<T, 2, 1, 16, 16, ABFT>(field, g, w, flips, nflips, L); break;
+      default: break;
+    }
+  }
+}
+
 // Shapes with a fast path: cubes 4..16 in 3D, squares 8/12/16 in 2D.
 inline bool has_fast(const Geo& g) {
   if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2])
@@ -829,16 +933,20 @@ bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
 template <typename T, bool ABFT>
 void launch_predict_t(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
                       const Launch& L) {
-  // edge blocks (or everything when no fast path exists for the shape) on the side stream,
-  // concurrently with the full blocks
-  Fork fk(L);
-  const bool fast = has_fast(g);
-  const Launch Lg = fast ? fk.side_launch(L) : L;
-  if (g.ndim == 3) run_generic<T, 3, ABFT>(field, g, w, flips, nflips, !fast, Lg);
-  else if (g.ndim == 2) run_generic<T, 2, ABFT>(field, g, w, flips, nflips, !fast, Lg);
-  else run_generic<T, 1, ABFT>(field, g, w, flips, nflips, !fast, Lg);
-  if (fast) try_fast<T, ABFT>(field, g, w, flips, nflips, L);
-  fk.join();
+  // shapes with a fast path: edge blocks on the side stream with the same compile-time walk,
+  // concurrently with the full blocks; other shapes: the generic kernel for every block
+  if (has_fast(g)) {
+    Fork fk(L);
+    try_edge<T, ABFT>(field, g, w, flips, nflips, fk.side_launch(L));
+    try_fast<T, ABFT>(field, g, w, flips, nflips, L);
+    fk.join();
+  } else if (g.ndim == 3) {
+    run_generic<T, 3, ABFT>(field, g, w, flips, nflips, true, L);
+  } else if (g.ndim == 2) {
+    run_generic<T, 2, ABFT>(field, g, w, flips, nflips, true, L);
+  } else {
+    run_generic<T, 1, ABFT>(field, g, w, flips, nflips, true, L);
+  }
 }
 
 // ---------------------------------------------------------------- batched launches
