@@ -113,43 +113,53 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
   __syncthreads();
 
   // 2-3. Huffman merge and leaf depths (one thread), length counts
-  uint8_t* depth = nullptr;
   if (n >= 2) {
-    // node arrays: internal weights [n-1], parents [2n-1], depths [2n-1]
+    // node arrays: internal weights [n-1], parents [2n-1]
     const bool small = n <= 4096;
     unsigned long long* iw = small ? reinterpret_cast<unsigned long long*>(smem + kSmemSort * 8) : w.node_w;
     uint32_t* parent = small ? reinterpret_cast<uint32_t*>(smem + kSmemSort * 8 + 4096 * 8) : w.node_parent;
-    depth = small ? (smem + kSmemSort * 8 + 4096 * 8 + 8192 * 4)
-                  : reinterpret_cast<uint8_t*>(w.node_parent + 2 * 65536);
     if (tid == 0) {
+      // The next leaf weights (two ahead) and the oldest unmerged internal weight stay in
+      // registers, so each pick is a compare of registers; the node just created is forwarded.
       uint32_t lp = 0, ip = 0;
+      unsigned long long lw = keys[0] >> 16, lw1 = keys[1] >> 16, hw = 0;
       for (uint32_t ni = 0; ni + 1 < n; ++ni) {
         unsigned long long wsum = 0;
+#pragma unroll
         for (int pick = 0; pick < 2; ++pick) {
-          const bool leaf = lp < n && (ip >= ni || (keys[lp] >> 16) <= iw[ip]);
+          const bool leaf = lp < n && (ip >= ni || lw <= hw);
           if (leaf) {
-            wsum += keys[lp] >> 16;
+            wsum += lw;
             parent[lp] = n + ni;
             ++lp;
+            lw = lw1;
+            lw1 = lp + 1 < n ? keys[lp + 1] >> 16 : 0ull;
           } else {
-            wsum += iw[ip];
+            wsum += hw;
             parent[n + ip] = n + ni;
             ++ip;
+            if (ip < ni) hw = iw[ip];
           }
         }
         iw[ni] = wsum;
-      }
-      const uint32_t root = 2 * n - 2;
-      depth[root] = 0;
-      for (int64_t v = (int64_t)root - 1; v >= 0; --v) {
-        uint32_t d = depth[parent[v]] + 1u;
-        depth[v] = (uint8_t)(d > 63 ? 63 : d);
+        if (ip == ni) hw = wsum;
       }
     }
     __syncthreads();
-    for (uint32_t p = tid; p < n; p += blockDim.x) {
-      atomicAdd(&cnt[depth[p]], 1u);
-      atomicMax(&s_maxlen, (uint32_t)depth[p]);
+    // leaf depths: every leaf walks to the root (a Huffman tree over at most 2^40 points is
+    // less than 64 levels deep) and counts its length
+    {
+      const uint32_t root = 2 * n - 2;
+      for (uint32_t p = tid; p < n; p += blockDim.x) {
+        uint32_t d = 0, v = p;
+        while (v != root && d < 2 * n) {
+          v = parent[v];
+          ++d;
+        }
+        const uint32_t dc = d > 63 ? 63u : d;
+        atomicAdd(&cnt[dc], 1u);
+        atomicMax(&s_maxlen, dc);
+      }
     }
     __syncthreads();
     if (tid == 0) {
