@@ -166,6 +166,7 @@ WsPlan plan_ws(const Geo& g) {
   w.node_parent = take(4 * 2 * 65536 + 2 * 65536);
   w.codes = take(4 * pair_slots);
   w.ustage = take(s * slots);
+  w.etmp = take(4 * encode_slot_words(g.P) * nb);
   w.total = o;
   return w;
 }
@@ -192,6 +193,7 @@ Ws bind_ws(void* base, const WsPlan& p) {
   w.node_parent = reinterpret_cast<uint32_t*>(b + p.node_parent);
   w.codes = reinterpret_cast<uint16_t*>(b + p.codes);
   w.ustage = b + p.ustage;
+  w.etmp = reinterpret_cast<uint32_t*>(b + p.etmp);
   return w;
 }
 
@@ -597,7 +599,7 @@ __global__ void k_batch_reset(const Job* __restrict__ jobs, unsigned long long* 
     for (uint32_t q = threadIdx.x; q < nheads; q += blockDim.x) heads[q] = 0ull;
 }
 
-enum BatchKind { BK_PREP_FAST, BK_PREP_GENERIC, BK_PREDICT_FAST, BK_PREDICT_GENERIC, BK_ENCODE };
+enum BatchKind { BK_PREP_FAST, BK_PREP_GENERIC, BK_PREDICT_FAST, BK_PREDICT_GENERIC, BK_ENCODE_BLOCKS, BK_ENCODE };
 
 struct BatchLaunch {
   BatchKind kind;
@@ -701,7 +703,8 @@ void batch_plan_launches(sdcsz_batch* b) {
     uint32_t threads = 128;
     while (threads > 32 && (size_t)slots * s * threads > 160 * 1024) threads >>= 1;
     add(BK_PREDICT_GENERIC, g.dtype, g.ndim, 0, g.abft != 0, threads, 0, j, 1);  // items set below
-    add(BK_ENCODE, g.dtype, 0, 0, g.abft != 0, 256, 0, j, ceil_div(g.nb, kGroup));
+    add(BK_ENCODE_BLOCKS, g.dtype, 0, 0, g.abft != 0, 128, 0, j, ceil_div(g.nb, 128));
+    add(BK_ENCODE, g.dtype, 0, 0, false, 256, 0, j, ceil_div(g.nb, kGroup));
   }
   // generic predict: threads are the class minimum, so the items follow it
   for (auto& L : b->launches) {
@@ -774,7 +777,9 @@ int batch_enqueue(sdcsz_batch* b, cudaStream_t s) {
   stage(BK_PREDICT_FAST, BK_PREDICT_GENERIC, 2);
   batch_codebook(b->d_table, n, L);
   for (auto& Q : b->launches)
-    if (Q.kind == BK_ENCODE) batch_encode(Q.dtype, Q.abft, Q.args, L);
+    if (Q.kind == BK_ENCODE_BLOCKS) batch_encode_blocks(Q.dtype, Q.abft, Q.args, L);
+  for (auto& Q : b->launches)
+    if (Q.kind == BK_ENCODE) batch_encode_assemble(Q.dtype, Q.args, L);
   return cudaGetLastError() == cudaSuccess ? SDCSZ_OK : SDCSZ_ECUDA;
 }
 

@@ -10,7 +10,7 @@ inline namespace host {
 // Byte offsets of the regions of a compression workspace.
 struct WsPlan {
   size_t state, sum_in, isum_in, sum_q, isum_q, sum_dc, coef, est, pflag, flags, coefT, hist, codebook, lb, sort_keys,
-      node_w, node_parent, codes, ustage, total;
+      node_w, node_parent, codes, ustage, etmp, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }

@@ -1,13 +1,21 @@
 // K4: per-block Huffman encoding and stream assembly (the encoding and output steps of
-// Algorithm 1 of the paper, without the Zstd stage).
+// Algorithm 1 of the paper, without the Zstd stage). Two kernels:
 //
-// One CTA per random-access group of 256 blocks, one thread per block. Pass 1 reads the
-// block's codes, checks them against sum_q/isum_q (Algorithm 1's check of the bin array before
-// encoding: a single corrupted code is located and repaired) and sums the code lengths. A CTA scan plus a single-pass decoupled look-back
-// across groups (group ids taken from a ticket in launch order, every wait bounded) gives each
-// block its payload, unpredictable-value and coefficient offsets. Pass 2 re-reads the codes
-// (L2 resident) and packs the bits MSB-first into 32-bit words: words wholly inside the
-// block's byte range are stored whole, the partial first and last words byte by byte.
+// K4a, one thread per block: encodes the block's codes (read from HBM once) MSB-first into a
+// fixed-size slot of the workspace, taking sum_q/isum_q on the way. When they disagree with
+// the values of K2 (Algorithm 1's check of the bin array before encoding) the single corrupted
+// code is located and repaired and the block is encoded again. Then the block's unpredictable
+// values move to the front of its staging slot, and the per-block entries that sit at fixed
+// places in the stream (payload size, unpredictable count, sum_dc, regression bitmap) are
+// written.
+//
+// K4b, one CTA per random-access group of 256 blocks: a CTA scan plus a single-pass decoupled
+// look-back across groups (group ids from a ticket in launch order, every wait bounded) gives
+// each block its payload, unpredictable-value and coefficient offsets; each thread then copies
+// its block's payload (the slot holds it in stream byte order: whole aligned words are stored
+// with a funnel shift, the partial first and last words byte by byte), its unpredictable values
+// and its coefficients. The group's table entry and, for the last group, the header totals are
+// written.
 #include <algorithm>
 
 #include "sdcsz_internal.cuh"
@@ -18,6 +26,7 @@ namespace {
 
 constexpr unsigned long long kFlagAgg = 1ull, kMaskBytes = (1ull << 22) - 1, kMaskUn = (1ull << 21) - 1;
 constexpr uint32_t kCbWindow = 2048;  // codebook entries around the centre kept in shared memory
+constexpr uint32_t kPosKept = 4;      // unpredictable positions remembered in registers per block
 
 __device__ __forceinline__ unsigned long long pack_agg(unsigned long long bytes, unsigned long long un,
                                                        unsigned long long rg) {
@@ -38,20 +47,6 @@ struct Codebook {
   }
 };
 
-// Store the 32-bit big-endian word `v` at aligned word address `wa` of the stream, keeping
-// only the bytes inside [lo, hi).
-__device__ __forceinline__ void put_word(uint8_t* out, uint64_t wa, uint32_t v, uint64_t lo, uint64_t hi, bool fits) {
-  if (!fits) return;
-  if (wa >= lo && wa + 4 <= hi) {
-    *reinterpret_cast<uint32_t*>(out + wa) = __byte_perm(v, 0, 0x0123);
-  } else {
-    for (int q = 0; q < 4; ++q)
-      if (wa + q >= lo && wa + q < hi) out[wa + q] = (uint8_t)(v >> (24 - 8 * q));
-  }
-}
-
-}  // namespace
-
 __device__ __forceinline__ uint32_t cb_lo(const Geo& g) { return g.R > kCbWindow / 2 ? g.R - kCbWindow / 2 : 0; }
 
 // Shared-memory window of the codebook around the centre bin.
@@ -61,68 +56,107 @@ __device__ __forceinline__ void cb_load(uint32_t* cb_s, const Geo& g, const Ws& 
     cb_s[q] = lo + q < g.bins ? __ldg(&w.codebook[lo + q]) : 0u;
 }
 
-// One random-access group (256 blocks, one per thread) of the stream.
-template <typename T, bool ABFT>
-__device__ __forceinline__ void encode_group(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
-                                             uint64_t gid, const uint32_t* cb_s) {
-  __shared__ unsigned long long s_wt[8][3];
-  __shared__ unsigned long long s_excl[3];
-  __shared__ unsigned long long s_tot[3];
-  State* st = w.st;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  Codebook cb;
-  cb.lo = cb_lo(g);
-  cb.s = cb_s;
-  cb.g = w.codebook;
-  const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
-  const uint64_t b = gid * kGroup + tid;
-  const bool active = b < g.nb;
-  const Layout L = st->L;
-  const uint32_t* __restrict__ codes = reinterpret_cast<const uint32_t*>(w.codes);
+// The error flag read once by the CTA, so that every thread takes the same path.
+__device__ __forceinline__ bool cta_failed(State* st) {
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = *(volatile unsigned int*)&st->error != 0;
+  __syncthreads();
+  return s_fail != 0;
+}
 
-  // pass 1: verify codes, count bits and unpredictables
-  uint32_t P = 0, bits = 0, nun = 0, kfix = 0xffffffffu, vfix = 0;
-  bool reg = false, bad = false;
+struct EncRes {
+  uint32_t bits, nun, sq;
+  unsigned long long isq;
+  uint32_t pos[kPosKept];
+};
+
+// One pass over a block's codes: the Huffman bits into `slot` (stream byte order, the last
+// word zero padded), the code checksums (ABFT), the unpredictable count and the first
+// kPosKept unpredictable positions. With FIX, code kfix reads as vfix.
+template <bool ABFT, bool FIX>
+__device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, uint32_t P, uint32_t* __restrict__ slot,
+                                               const Codebook& cb, uint32_t cw0, uint32_t kfix, uint32_t vfix) {
+  EncRes e;
+  e.bits = 0;
+  e.nun = 0;
+  e.sq = 0;
+  e.isq = 0;
+  unsigned long long acc = 0;
+  uint32_t nacc = 0, wi = 0;
+  auto put = [&](uint32_t c, uint32_t k) {
+    if (FIX && k == kfix) c = vfix;
+    const uint32_t cw = c ? cb(c) : cw0;
+    const uint32_t len = cw & 31u;
+    acc = (acc << len) | (cw >> 5);
+    nacc += len;
+    e.bits += len;
+    if (nacc >= 32) {
+      nacc -= 32;
+      slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+    }
+    if (ABFT) {
+      e.sq += c;
+      mad_wide(e.isq, c, k + 1);
+    }
+    if (c == 0) {
+      if (e.nun < kPosKept) e.pos[e.nun] = k;
+      ++e.nun;
+    }
+  };
+  // code pairs loaded four at a time ahead of their use
+  const uint32_t P2 = P >> 1;
+  for (uint32_t k2 = 0; k2 < P2; k2 += 4) {
+    uint32_t wq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) wq[q] = (k2 + q < P2) ? pp[32 * (uint64_t)(k2 + q)] : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (k2 + q < P2) {
+        put(wq[q] & 0xffffu, 2 * (k2 + q));
+        put(wq[q] >> 16, 2 * (k2 + q) + 1);
+      }
+    }
+  }
+  if (P & 1) put(pp[32 * (uint64_t)P2] & 0xffffu, P - 1);
+  if (nacc) slot[wi] = __byte_perm((uint32_t)(acc << (32 - nacc)), 0, 0x0123);
+  return e;
+}
+
+// Store the little-endian word `v` at aligned word address `wa` of the stream, keeping only
+// the bytes inside [lo, hi).
+__device__ __forceinline__ void put_bytes(uint8_t* out, uint64_t wa, uint32_t v, uint64_t lo, uint64_t hi) {
+  for (int q = 0; q < 4; ++q)
+    if (wa + q >= lo && wa + q < hi) out[wa + q] = (uint8_t)(v >> (8 * q));
+}
+
+// Payload slot of one block: 32-bit words for P codes of at most kMaxLen bits, 16-byte rounded.
+__host__ __device__ inline uint64_t slot_words_of(uint32_t P) { return ((uint64_t)P * kMaxLen + 127) / 128 * 4; }
+
+// ---------------------------------------------------------------- K4a
+template <typename T, bool ABFT>
+__device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t* __restrict__ out,
+                                             const uint32_t* cb_s, uint64_t b) {
+  State* st = w.st;
+  const Layout L = st->L;
+  const uint32_t lane = threadIdx.x & 31;
+  const bool active = b < g.nb;
+  bool reg = false;
   if (active) {
-    P = block_box(g, b).P;
+    Codebook cb;
+    cb.lo = cb_lo(g);
+    cb.s = cb_s;
+    cb.g = w.codebook;
+    const uint32_t cw0 = __ldg(&w.codebook[0]);
+    const uint32_t P = block_box(g, b).P;
     reg = w.flags[b] & 1;
-    uint32_t s = 0;
-    unsigned long long is = 0;
-    const uint32_t* pp = codes + pair_index(b, g.P, 0);
-    const uint32_t P2 = P >> 1;
-    // isum over a pair: (2m+1) c0 + (2m+2) c1 = (2m+1)(c0 + c1) + c1
-    auto pair = [&](uint32_t wp2, uint32_t k2) {
-      const uint32_t c0 = wp2 & 0xffffu, c1 = wp2 >> 16;
-      bits += (cb(c0) & 31u) + (cb(c1) & 31u);
-      nun += (c0 == 0) + (c1 == 0);
-      if (ABFT) {
-        s += c0 + c1;
-        mad_wide(is, c0 + c1, 2 * k2 + 1);
-        is += c1;
-      }
-    };
-    // eight independent loads in flight per thread, then their arithmetic
-    uint32_t k2 = 0;
-    for (; k2 + 8 <= P2; k2 += 8) {
-      uint32_t wq[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) wq[q] = pp[32 * (uint64_t)(k2 + q)];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) pair(wq[q], k2 + q);
-    }
-    for (; k2 < P2; ++k2) pair(pp[32 * (uint64_t)k2], k2);
-    if (P & 1) {  // odd point count: the last pair holds one code
-      const uint32_t c0 = pp[32 * (uint64_t)P2] & 0xffffu;
-      bits += cb(c0) & 31u;
-      nun += (c0 == 0);
-      if (ABFT) {
-        s += c0;
-        mad_wide(is, c0, P);
-      }
-    }
-    if (ABFT && (s != w.sum_q[b] || is != w.isum_q[b])) {
+    const uint32_t* pp = reinterpret_cast<const uint32_t*>(w.codes) + pair_index(b, g.P, 0);
+    uint32_t* slot = w.etmp + b * slot_words_of(g.P);
+    EncRes e = encode_codes<ABFT, false>(pp, P, slot, cb, cw0, 0u, 0u);
+    uint32_t kfix = 0xffffffffu, vfix = 0;
+    bool bad = false;
+    if (ABFT && (e.sq != w.sum_q[b] || e.isq != w.isum_q[b])) {
       long long delta = 0;
-      const long long m = locate_word(w.sum_q[b], w.isum_q[b], s, is, P, 0, &delta);
+      const long long m = locate_word(w.sum_q[b], w.isum_q[b], e.sq, e.isq, P, 0, &delta);
       bool fixed = false;
       if (m >= 0) {
         const uint32_t old = (pp[32 * (uint64_t)(m >> 1)] >> (16 * (m & 1))) & 0xffffu;
@@ -130,19 +164,75 @@ __device__ __forceinline__ void encode_group(const Geo& g, const Ws& w, uint8_t*
         if (nv >= 0 && nv < (long long)g.bins) {
           kfix = (uint32_t)m;
           vfix = (uint32_t)nv;
-          bits += (cb(vfix) & 31u) - (cb(old) & 31u);
-          nun += (vfix == 0) - (old == 0);
+          e = encode_codes<ABFT, true>(pp, P, slot, cb, cw0, kfix, vfix);  // the repaired block
           fixed = true;
         }
       }
-      if (fixed) atomicAdd(&st->codes_corrected, 1ull);
-      else {
+      if (fixed) {
+        atomicAdd(&st->codes_corrected, 1ull);
+      } else {
         bad = true;
         atomicAdd(&st->uncorrectable, 1ull);
       }
     }
+    // unpredictable values to the front of the block's staging slot, in order (in place: the
+    // j-th value moves down from its point k >= j)
+    T* up = static_cast<T*>(w.ustage) + code_index(b, g.P, 0);
+    if (e.nun <= kPosKept) {
+#pragma unroll
+      for (uint32_t j = 0; j < kPosKept; ++j)
+        if (j < e.nun && e.pos[j] != j) up[32 * (uint64_t)j] = up[32 * (uint64_t)e.pos[j]];
+    } else {
+      uint32_t j = 0;
+      for (uint32_t k = 0; k < P; ++k) {
+        uint32_t c = (pp[32 * (uint64_t)(k >> 1)] >> (16 * (k & 1))) & 0xffffu;
+        if (k == kfix) c = vfix;
+        if (c == 0) {
+          if (j != k) up[32 * (uint64_t)j] = up[32 * (uint64_t)k];
+          ++j;
+        }
+      }
+    }
+    *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * b) = (uint16_t)((e.bits + 7u) >> 3);
+    *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * b) = (uint16_t)e.nun;
+    if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * b) = w.sum_dc[b];
+    // a block whose codes could not be repaired is reported in the header status word
+    if (bad) atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
   }
-  const unsigned long long bytes = (bits + 7u) >> 3;
+  // regression bitmap word of this warp's 32 blocks
+  const unsigned int ballot = __ballot_sync(0xffffffffu, active && reg);
+  if (lane == 0 && b < g.nb) *reinterpret_cast<uint32_t*>(out + L.bitmap + 4 * (b >> 5)) = ballot;
+}
+
+template <typename T, bool ABFT>
+__global__ void __launch_bounds__(128) k_encode_blocks(Geo g, Ws w, uint8_t* __restrict__ out) {
+  __shared__ uint32_t cb_s[kCbWindow];
+  if (cta_failed(w.st)) return;
+  cb_load(cb_s, g, w);
+  __syncthreads();
+  encode_block<T, ABFT>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------- K4b
+template <typename T>
+__device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
+                                               uint64_t gid) {
+  __shared__ unsigned long long s_wt[8][3];
+  __shared__ unsigned long long s_excl[3];
+  __shared__ unsigned long long s_tot[3];
+  State* st = w.st;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
+  const uint64_t b = gid * kGroup + tid;
+  const bool active = b < g.nb;
+  const Layout L = st->L;
+  uint32_t bytes = 0, nun = 0;
+  bool reg = false;
+  if (active) {
+    bytes = *reinterpret_cast<const uint16_t*>(out + L.sizes + 2 * b);
+    nun = *reinterpret_cast<const uint16_t*>(out + L.ucounts + 2 * b);
+    reg = w.flags[b] & 1;
+  }
 
   // CTA exclusive scan of (bytes, unpredictables, regression flag)
   unsigned long long v[3] = {bytes, nun, reg ? 1ull : 0ull}, inc[3] = {v[0], v[1], v[2]};
@@ -239,101 +329,56 @@ __device__ __forceinline__ void encode_group(const Geo& g, const Ws& w, uint8_t*
       if (L.payload + pay > cap) atomicOr(&st->error, ERR_CAPACITY);
     }
   }
-  // bitmap word of this warp's 32 blocks
-  const unsigned int ballot = __ballot_sync(0xffffffffu, active && reg);
-  if (lane == 0 && (gid * kGroup + wid * 32) < g.nb)
-    *reinterpret_cast<uint32_t*>(out + L.bitmap + 4 * ((gid * kGroup) / 32 + wid)) = ballot;
   if (!active) return;
 
   const unsigned long long pay_off = s_excl[0] + s_wt[wid][0] + inc[0] - v[0];
   const unsigned long long un_off = s_excl[1] + s_wt[wid][1] + inc[1] - v[1];
   const unsigned long long rg_off = s_excl[2] + s_wt[wid][2] + inc[2] - v[2];
-  *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * b) = (uint16_t)bytes;
-  *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * b) = (uint16_t)nun;
-  if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * b) = w.sum_dc[b];
   if (reg) {
     const T* cT = static_cast<const T*>(w.coefT) + 4 * b;
     T* dst = reinterpret_cast<T*>(out + L.coef) + (uint64_t)(g.ndim + 1) * rg_off;
     for (int a = 0; a <= g.ndim; ++a) dst[a] = cT[a];
   }
-  // pass 2: pack the codes MSB-first; copy the unpredictable values in order. Every word
-  // emitted inside the loop is whole and inside the block except the first one when the block
-  // starts mid-word (its leading bytes belong to the previous block); the last, partial word
-  // is written after the loop.
-  const uint64_t lo = L.payload + pay_off, hi = lo + bytes;
-  const bool fits = hi <= cap;
-  if (!fits) atomicOr(&st->error, ERR_CAPACITY);
-  uint64_t wa = lo & ~uint64_t(3);                  // aligned word being filled
-  unsigned long long acc = 0;
-  uint32_t nacc = 8u * (uint32_t)(lo & 3);          // leading bytes of the first word are not ours
-  bool head = (lo & 3) != 0;
-  const T* ust = static_cast<const T*>(w.ustage);
+  // unpredictable values, moved by K4a to the front of the block's staging slot
+  const T* up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
   T* udst = reinterpret_cast<T*>(out + L.unpred);
-  unsigned long long uidx = un_off;
   const unsigned long long ulim = st->n_unpred;
-  const uint32_t* pp = codes + pair_index(b, g.P, 0);
-  const T* up = ust + code_index(b, g.P, 0);
-  const uint32_t cw0 = __ldg(&w.codebook[0]);
-  auto put = [&](uint32_t c, uint32_t k) {
-    if (ABFT && k == kfix) c = vfix;
-    const uint32_t cw = c ? cb(c) : cw0;
-    const uint32_t len = cw & 31u;
-    acc = (acc << len) | (cw >> 5);
-    nacc += len;
-    if (nacc >= 32) {
-      nacc -= 32;
-      const uint32_t word = (uint32_t)(acc >> nacc);
-      if (head) {
-        put_word(out, wa, word, lo, hi, fits);
-        head = false;
-      } else if (fits) {
-        *reinterpret_cast<uint32_t*>(out + wa) = __byte_perm(word, 0, 0x0123);
-      }
-      wa += 4;
-    }
-    if (c == 0) {
-      if (uidx < ulim) udst[uidx] = up[32 * (uint64_t)k];
-      ++uidx;
-    }
-  };
-  // code pairs loaded four at a time ahead of their use
-  const uint32_t P2 = P >> 1;
-  for (uint32_t k2 = 0; k2 < P2; k2 += 4) {
-    uint32_t wq[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) wq[q] = (k2 + q < P2) ? pp[32 * (uint64_t)(k2 + q)] : 0u;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (k2 + q < P2) {
-        put(wq[q] & 0xffffu, 2 * (k2 + q));
-        put(wq[q] >> 16, 2 * (k2 + q) + 1);
-      }
-    }
+  for (uint32_t j = 0; j < nun; ++j)
+    if (un_off + j < ulim) udst[un_off + j] = up[32 * (uint64_t)j];
+  // payload: stream bytes [lo, hi) = slot bytes [0, bytes). The stream word at wa = wa0 + 4i
+  // holds slot bytes 4i - r .. 4i - r + 3 (r = lo mod 4): the top r bytes of slot word i - 1
+  // and the low 4 - r bytes of slot word i. Words wholly inside [lo, hi) are stored whole;
+  // the first and last are shared with the neighbouring blocks and written byte by byte.
+  const uint64_t lo = L.payload + pay_off, hi = lo + bytes;
+  if (hi > cap) {
+    atomicOr(&st->error, ERR_CAPACITY);
+    return;
   }
-  if (P & 1) put(pp[32 * (uint64_t)P2] & 0xffffu, P - 1);
-  if (nacc) put_word(out, wa, (uint32_t)(acc << (32 - nacc)), lo, hi, fits);
-  if (bad) {
-    // a block whose codes could not be repaired is reported in the header status word
-    atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
+  const uint32_t* src = w.etmp + b * slot_words_of(g.P);
+  const uint32_t r = (uint32_t)(lo & 3), nw = (bytes + 3) / 4;
+  const uint64_t wa0 = lo - r;
+  for (uint64_t wa = wa0; wa < hi; wa += 4) {
+    const uint32_t i = (uint32_t)((wa - wa0) >> 2);
+    const uint32_t cur = i < nw ? src[i] : 0u;
+    const uint32_t prev = (r && i > 0) ? src[i - 1] : 0u;
+    const uint32_t val = r ? __funnelshift_l(prev, cur, 8 * r) : cur;
+    if (wa >= lo && wa + 4 <= hi) *reinterpret_cast<uint32_t*>(out + wa) = val;
+    else put_bytes(out, wa, val, lo, hi);
   }
 }
 
-template <typename T, bool ABFT>
-__global__ void __launch_bounds__(256) k_encode(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_encode_assemble(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
   __shared__ uint32_t s_gid;
-  __shared__ uint32_t cb_s[kCbWindow];
-  State* st = w.st;
-  if (*(volatile unsigned int*)&st->error) return;
-  if (threadIdx.x == 0) s_gid = atomicAdd(&st->ticket, 1u);
-  cb_load(cb_s, g, w);
+  if (cta_failed(w.st)) return;
+  if (threadIdx.x == 0) s_gid = atomicAdd(&w.st->ticket, 1u);
   __syncthreads();
-  encode_group<T, ABFT>(g, w, out, cap, s_gid, cb_s);
+  assemble_group<T>(g, w, out, cap, s_gid);
 }
 
-// Batched: the groups of every job; a job's groups are pulled in increasing order, so each
-// look-back only waits for groups already taken by running CTAs.
+// ---------------------------------------------------------------- batches
 template <typename T, bool ABFT>
-__global__ void __launch_bounds__(256) k_encode_batch(BatchArgs a) {
+__global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
   __shared__ uint32_t cb_s[kCbWindow];
   __shared__ Job s_job;
   batch_loop(
@@ -342,38 +387,78 @@ __global__ void __launch_bounds__(256) k_encode_batch(BatchArgs a) {
         cb_load(cb_s, s_job.g, s_job.w);
         __syncthreads();
       },
-      [&](uint64_t it) { encode_group<T, ABFT>(s_job.g, s_job.w, s_job.out, s_job.cap, it, cb_s); }, NoOp());
+      [&](uint64_t it) { encode_block<T, ABFT>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x); },
+      NoOp());
+}
+
+// A job's groups are pulled in increasing order, so each look-back only waits for groups
+// already taken by running CTAs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_encode_assemble_batch(BatchArgs a) {
+  __shared__ Job s_job;
+  batch_loop(
+      a, s_job, NoOp(), [&](uint64_t it) { assemble_group<T>(s_job.g, s_job.w, s_job.out, s_job.cap, it); }, NoOp());
+}
+
+template <class K>
+unsigned batch_grid_of(K kern, uint32_t threads, uint64_t items, const Launch& L) {
+  const int occ = occupancy(reinterpret_cast<const void*>(kern), (int)threads, 0);
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(items, (uint64_t)occ * L.sms));
 }
 
 template <typename T, bool ABFT>
-static void batch_encode_t(const BatchArgs& a, const Launch& L) {
-  auto kern = k_encode_batch<T, ABFT>;
-  const int occ = occupancy(reinterpret_cast<const void*>(kern), 256, 0);
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(a.start[a.n], (uint64_t)occ * L.sms));
-  kern<<<grid, 256, 0, L.stream>>>(a);
+void batch_blocks_t(const BatchArgs& a, const Launch& L) {
+  auto kern = k_encode_blocks_batch<T, ABFT>;
+  kern<<<batch_grid_of(kern, 128, a.start[a.n], L), 128, 0, L.stream>>>(a);
   note_launch();
 }
 
-void batch_encode(int dtype, bool abft, const BatchArgs& a, const Launch& L) {
+template <typename T>
+void batch_assemble_t(const BatchArgs& a, const Launch& L) {
+  auto kern = k_encode_assemble_batch<T>;
+  kern<<<batch_grid_of(kern, 256, a.start[a.n], L), 256, 0, L.stream>>>(a);
+  note_launch();
+}
+
+template <typename T, bool ABFT>
+void launch_encode_t(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
+  const uint64_t nchunks = (g.nb + 127) / 128, ngroups = (g.nb + kGroup - 1) / kGroup;
+  if (!ngroups) return;
+  k_encode_blocks<T, ABFT><<<(unsigned)nchunks, 128, 0, L.stream>>>(g, w, out);
+  note_launch();
+  k_encode_assemble<T><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
+  note_launch();
+}
+
+}  // namespace
+
+uint64_t encode_slot_words(uint32_t P) { return slot_words_of(P); }
+
+// items: 128-block chunks
+void batch_encode_blocks(int dtype, bool abft, const BatchArgs& a, const Launch& L) {
   if (dtype == 0) {
-    if (abft) batch_encode_t<float, true>(a, L);
-    else batch_encode_t<float, false>(a, L);
+    if (abft) batch_blocks_t<float, true>(a, L);
+    else batch_blocks_t<float, false>(a, L);
   } else {
-    if (abft) batch_encode_t<double, true>(a, L);
-    else batch_encode_t<double, false>(a, L);
+    if (abft) batch_blocks_t<double, true>(a, L);
+    else batch_blocks_t<double, false>(a, L);
   }
 }
 
+// items: 256-block groups
+void batch_encode_assemble(int dtype, const BatchArgs& a, const Launch& L) {
+  if (dtype == 0) batch_assemble_t<float>(a, L);
+  else batch_assemble_t<double>(a, L);
+}
+
 void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
-  const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
-  if (!ngroups) return;
   if (g.dtype == 0) {
-    if (g.abft) k_encode<float, true><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
-    else k_encode<float, false><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
+    if (g.abft) launch_encode_t<float, true>(g, w, out, cap, L);
+    else launch_encode_t<float, false>(g, w, out, cap, L);
   } else {
-    if (g.abft) k_encode<double, true><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
-    else k_encode<double, false><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
-  }  note_launch();
+    if (g.abft) launch_encode_t<double, true>(g, w, out, cap, L);
+    else launch_encode_t<double, false>(g, w, out, cap, L);
+  }
 }
 
 }  // namespace sdcsz

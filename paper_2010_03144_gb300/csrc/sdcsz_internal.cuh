@@ -94,6 +94,7 @@ struct Ws {
   uint32_t* node_parent;
   uint16_t* codes;     // quantization codes in warp-interleaved pairs (see pair_index)
   void* ustage;        // unpredictable values, same interleaving as codes
+  uint32_t* etmp;      // per-block payload slots of the encoder (encode_slot_words each)
 };
 
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
@@ -595,7 +596,9 @@ bool batch_predict_fast(int dtype, int ndim, uint32_t B, bool abft, const BatchA
 void batch_predict_generic(int dtype, int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
                            const Launch& L);
 void batch_codebook(const Job* jobs, uint32_t n, const Launch& L);
-void batch_encode(int dtype, bool abft, const BatchArgs& a, const Launch& L);
+void batch_encode_blocks(int dtype, bool abft, const BatchArgs& a, const Launch& L);
+void batch_encode_assemble(int dtype, const BatchArgs& a, const Launch& L);
+uint64_t encode_slot_words(uint32_t P);
 
 // Parsed stream header (host side) for the decoder.
 struct Hdr {
