@@ -203,7 +203,8 @@ int locate_and_repair(uint32_t* w, uint64_t n, uint64_t sum0, uint64_t isum0, ui
 // ---------------------------------------------------------------- predictors (Sec. 3.1)
 // Improved Lorenzo predictor on block-local values d (row-major, extents e), with zero
 // for neighbours outside the block (independent blocks, Sec. 5.1). The operand order is
-// fixed so that every implementation rounds identically.
+// fixed so that every implementation rounds identically: the neighbours in the previous
+// row and plane first, the previous point of the same row last.
 template <typename T>
 T lorenzo(const T* d, const uint32_t e[3], int ndim, uint32_t i, uint32_t j, uint32_t l) {
   auto at = [&](long ii, long jj, long ll) -> T {
@@ -213,16 +214,16 @@ T lorenzo(const T* d, const uint32_t e[3], int ndim, uint32_t i, uint32_t j, uin
   long I = i, J = j, L = l;
   if (ndim == 3) {
     T s = at(I - 1, J, L) + at(I, J - 1, L);
-    s = s + at(I, J, L - 1);
     s = s - at(I - 1, J - 1, L);
     s = s - at(I - 1, J, L - 1);
     s = s - at(I, J - 1, L - 1);
     s = s + at(I - 1, J - 1, L - 1);
+    s = s + at(I, J, L - 1);
     return s;
   }
   if (ndim == 2) {
-    T s = at(0, J - 1, L) + at(0, J, L - 1);
-    s = s - at(0, J - 1, L - 1);
+    T s = at(0, J - 1, L) - at(0, J - 1, L - 1);
+    s = s + at(0, J, L - 1);
     return s;
   }
   return at(0, 0, L - 1);

@@ -297,13 +297,13 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
           pred = FT<T>::add(FT<T>::add(ra, FT<T>::mul(cT[lc], (T)l)), cT[lc + 1]);
         } else if (NDIM == 3) {
           T sacc = FT<T>::add(a, bb);
-          sacc = FT<T>::add(sacc, c);
           sacc = FT<T>::sub(sacc, ab);
           sacc = FT<T>::sub(sacc, ac);
           sacc = FT<T>::sub(sacc, bc);
-          pred = FT<T>::add(sacc, abc);
+          sacc = FT<T>::add(sacc, abc);
+          pred = FT<T>::add(sacc, c);
         } else {
-          pred = FT<T>::sub(FT<T>::add(a, c), ac);
+          pred = FT<T>::add(FT<T>::sub(a, ac), c);
         }
         T xr = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
         if (q <= 0) {  // unpredictable value (code 0) or an undecodable block (rare)

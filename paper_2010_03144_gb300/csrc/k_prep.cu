@@ -279,15 +279,15 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
               if (NDIM == 3) {
                 const float a = pa[l], ab = hj ? pb[l] : 0.0f;
                 float t = __fadd_rn(a, bb);
-                t = __fadd_rn(t, cp);
                 t = __fsub_rn(t, ab);
                 t = __fsub_rn(t, ac);
                 t = __fsub_rn(t, bc);
-                L = __fadd_rn(t, abc);
+                t = __fadd_rn(t, abc);
+                L = __fadd_rn(t, cp);
                 ac = a;
                 abc = ab;
               } else {
-                L = __fsub_rn(__fadd_rn(bb, cp), bc);
+                L = __fadd_rn(__fsub_rn(bb, bc), cp);
               }
               bc = bb;
               cp = xr;

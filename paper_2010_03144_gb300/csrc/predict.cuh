@@ -287,13 +287,13 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
               }
               if (NDIM == 3) {
                 T s = FT<T>::add(a, bb);
-                s = FT<T>::add(s, c);
                 s = FT<T>::sub(s, ab);
                 s = FT<T>::sub(s, ac);
                 s = FT<T>::sub(s, bc);
-                return FT<T>::add(s, abc);
+                s = FT<T>::add(s, abc);
+                return FT<T>::add(s, c);
               }
-              if (NDIM == 2) return FT<T>::sub(FT<T>::add(a, c), ac);
+              if (NDIM == 2) return FT<T>::add(FT<T>::sub(a, ac), c);
               return c;
             },
             [&] {
@@ -304,13 +304,13 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
               }
               if (NDIM == 3) {
                 T s = FT<T>::add_v(a, bb);
-                s = FT<T>::add_v(s, c);
                 s = FT<T>::sub_v(s, ab);
                 s = FT<T>::sub_v(s, ac);
                 s = FT<T>::sub_v(s, bc);
-                return FT<T>::add_v(s, abc);
+                s = FT<T>::add_v(s, abc);
+                return FT<T>::add_v(s, c);
               }
-              if (NDIM == 2) return FT<T>::sub_v(FT<T>::add_v(a, c), ac);
+              if (NDIM == 2) return FT<T>::add_v(FT<T>::sub_v(a, ac), c);
               return c;
             },
             HOOK && k == hk.kp, hk.bitp, r.dup);

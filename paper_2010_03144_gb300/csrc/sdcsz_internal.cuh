@@ -328,10 +328,13 @@ __device__ __forceinline__ long long locate_word(unsigned long long sum0, unsign
 // Lorenzo predictor over reconstructed neighbours with zero outside the block, walked in the
 // block's sequential (row-major) order. The previous plane (3D) / row (2D) sits in this
 // thread's shared-memory slots; the previous point's neighbours stay in registers.
-//   3D: pred = ((((((a + b) + c) - ab) - ac) - bc) + abc) with a = d[i-1,j,l],
+//   3D: pred = ((((((a + b) - ab) - ac) - bc) + abc) + c) with a = d[i-1,j,l],
 //       b = d[i,j-1,l], c = d[i,j,l-1], ab = d[i-1,j-1,l], ac = d[i-1,j,l-1],
 //       bc = d[i,j-1,l-1], abc = d[i-1,j-1,l-1].
-//   2D: pred = (d[j-1,l] + d[j,l-1]) - d[j-1,l-1].   1D: pred = d[l-1].
+//   2D: pred = (d[j-1,l] - d[j-1,l-1]) + d[j,l-1].   1D: pred = d[l-1].
+// The previous point of the row (c) comes last: it is the only operand that depends on the
+// point just reconstructed, so the serial chain per point is a single addition before the
+// quantizer.
 template <typename V, int NDIM>
 struct Walker {
   V* base;        // this thread's slot 0
@@ -348,14 +351,14 @@ struct Walker {
   __device__ __forceinline__ V combine() const {
     if (NDIM == 3) {
       V s = Op::add(a, b);
-      s = Op::add(s, cp);
       s = Op::sub(s, ab);
       s = Op::sub(s, ap);
       s = Op::sub(s, bp);
-      return Op::add(s, abp);
+      s = Op::add(s, abp);
+      return Op::add(s, cp);
     } else if (NDIM == 2) {
-      V s = Op::add(a, cp);
-      return Op::sub(s, ap);
+      V s = Op::sub(a, ap);
+      return Op::add(s, cp);
     } else {
       return cp;
     }
