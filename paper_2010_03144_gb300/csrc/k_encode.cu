@@ -103,6 +103,41 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
       ++e.nun;
     }
   };
+  // Both codes of a pair at once when their bits fit in one word (nearly always: codes are a
+  // few bits long); the accumulator then holds at most 31 + 32 bits before its one flush.
+  auto put2 = [&](uint32_t c0, uint32_t c1, uint32_t k) {
+    if (FIX && k == kfix) c0 = vfix;
+    if (FIX && k + 1 == kfix) c1 = vfix;
+    const uint32_t w0 = c0 ? cb(c0) : cw0, w1 = c1 ? cb(c1) : cw0;
+    const uint32_t l0 = w0 & 31u, l1 = w1 & 31u, l = l0 + l1;
+    if (l > 32) {
+      put(c0, k);
+      put(c1, k + 1);
+      return;
+    }
+    acc = (acc << l) | (((unsigned long long)(w0 >> 5) << l1) | (w1 >> 5));
+    nacc += l;
+    e.bits += l;
+    if (nacc >= 32) {
+      nacc -= 32;
+      slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+    }
+    if (ABFT) {
+      e.sq += c0 + c1;
+      mad_wide(e.isq, c0 + c1, k + 1);  // (k+1) c0 + (k+2) c1
+      e.isq += c1;
+    }
+    if (c0 == 0 || c1 == 0) {
+      if (c0 == 0) {
+        if (e.nun < kPosKept) e.pos[e.nun] = k;
+        ++e.nun;
+      }
+      if (c1 == 0) {
+        if (e.nun < kPosKept) e.pos[e.nun] = k + 1;
+        ++e.nun;
+      }
+    }
+  };
   // code pairs loaded four at a time ahead of their use
   const uint32_t P2 = P >> 1;
   for (uint32_t k2 = 0; k2 < P2; k2 += 4) {
@@ -110,12 +145,8 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) wq[q] = (k2 + q < P2) ? pp[32 * (uint64_t)(k2 + q)] : 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (k2 + q < P2) {
-        put(wq[q] & 0xffffu, 2 * (k2 + q));
-        put(wq[q] >> 16, 2 * (k2 + q) + 1);
-      }
-    }
+    for (int q = 0; q < 4; ++q)
+      if (k2 + q < P2) put2(wq[q] & 0xffffu, wq[q] >> 16, 2 * (k2 + q));
   }
   if (P & 1) put(pp[32 * (uint64_t)P2] & 0xffffu, P - 1);
   if (nacc) slot[wi] = __byte_perm((uint32_t)(acc << (32 - nacc)), 0, 0x0123);
@@ -354,16 +385,26 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
     atomicOr(&st->error, ERR_CAPACITY);
     return;
   }
-  const uint32_t* src = w.etmp + b * slot_words_of(g.P);
+  // The slot is read four words (16 bytes, aligned) at a time, and the previous word carried.
+  const uint4* src4 = reinterpret_cast<const uint4*>(w.etmp + b * slot_words_of(g.P));
   const uint32_t r = (uint32_t)(lo & 3), nw = (bytes + 3) / 4;
   const uint64_t wa0 = lo - r;
-  for (uint64_t wa = wa0; wa < hi; wa += 4) {
-    const uint32_t i = (uint32_t)((wa - wa0) >> 2);
-    const uint32_t cur = i < nw ? src[i] : 0u;
-    const uint32_t prev = (r && i > 0) ? src[i - 1] : 0u;
-    const uint32_t val = r ? __funnelshift_l(prev, cur, 8 * r) : cur;
-    if (wa >= lo && wa + 4 <= hi) *reinterpret_cast<uint32_t*>(out + wa) = val;
-    else put_bytes(out, wa, val, lo, hi);
+  const uint32_t nout = (uint32_t)((hi - wa0 + 3) >> 2);  // stream words touched
+  uint32_t prev = 0;
+  for (uint32_t i0 = 0; i0 < nout; i0 += 4) {
+    const uint4 q = i0 < nw ? src4[i0 >> 2] : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t cur[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t i = i0 + t;
+      if (i >= nout) break;
+      const uint32_t c = i < nw ? cur[t] : 0u;
+      const uint32_t val = r ? __funnelshift_l(prev, c, 8 * r) : c;
+      prev = c;
+      const uint64_t wa = wa0 + 4 * (uint64_t)i;
+      if (wa >= lo && wa + 4 <= hi) *reinterpret_cast<uint32_t*>(out + wa) = val;
+      else put_bytes(out, wa, val, lo, hi);
+    }
   }
 }
 
