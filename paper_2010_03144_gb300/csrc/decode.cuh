@@ -139,6 +139,10 @@ struct FastReader {
       sym = slow_symbol((unsigned long long)peek << 32, cn, syms, n_live, &len);
       if (sym < 0) return -1;
     }
+    advance(len);
+    return sym;
+  }
+  __device__ __forceinline__ void advance(uint32_t len) {
     pos += len;
     if (pos >= 32) {  // only lanes crossing a word boundary touch memory
       pos -= 32;
@@ -147,7 +151,22 @@ struct FastReader {
       w2 = __ldg(wp);
       ++wp;
     }
-    return sym;
+  }
+  // Two symbols with one lookup when both codes lie in the 12-bit window (the pair table
+  // holds the second symbol only then), else one at a time.
+  __device__ __forceinline__ void next2(const uint2* lut2, const uint32_t* lut, const Canon& cn, const uint16_t* syms,
+                                        uint32_t n_live, int& q0, int& q1) {
+    const uint32_t peek = __funnelshift_l(w1, w0, pos);
+    const uint2 e = lut2[peek >> (32 - kLutBits)];
+    const uint32_t l0 = e.x & 0xffu, l1 = e.y & 0xffu;
+    if (l1) {
+      q0 = (int)(e.x >> 8);
+      q1 = (int)(e.y >> 8);
+      advance(l0 + l1);
+    } else {
+      q0 = next(lut, cn, syms, n_live);
+      q1 = next(lut, cn, syms, n_live);
+    }
   }
 };
 
@@ -162,7 +181,23 @@ struct Tables {
   const Canon* cn;
   const uint16_t* syms;
   uint32_t n_live;
+  const uint2* lut2;  // pair table (fast decoder only)
 };
+
+// Pair table: entry p holds lut[p] and, when that code is shorter than the window and the
+// code after it also ends inside the window, that second code's lut entry (else 0). Only the
+// window's known bits decide either symbol. Call after the lut is complete and visible.
+__device__ __forceinline__ void pair_table(uint2* lut2, const uint32_t* lut) {
+  for (uint32_t e = threadIdx.x; e < (1u << kLutBits); e += blockDim.x) {
+    const uint32_t v1 = lut[e], l1 = v1 & 0xffu;
+    uint32_t v2 = 0;
+    if (l1 && l1 < (uint32_t)kLutBits) {
+      const uint32_t u = lut[(e << l1) & ((1u << kLutBits) - 1)], l2 = u & 0xffu;
+      if (l2 && l2 <= (uint32_t)kLutBits - l1) v2 = u;
+    }
+    lut2[e] = make_uint2(v1, v2);
+  }
+}
 
 // ---------------------------------------------------------------- generic path
 template <typename T, int NDIM>
@@ -232,7 +267,9 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
 }
 
 // ---------------------------------------------------------------- fast path (full blocks)
-template <typename T, int NDIM, int B0, int B1, int B2, bool REG, bool HOOK>
+// WRITE: decompression (the block is stored to blk_out); otherwise verification (compared
+// with blk_orig when there is one).
+template <typename T, int NDIM, int B0, int B1, int B2, bool REG, bool HOOK, bool WRITE>
 __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const uint8_t* lim, const Hdr& h,
                                             const BlockIn& bi, const Tables& tb, T* plane, T* __restrict__ blk_out,
                                             const T* __restrict__ blk_orig, uint64_t si, uint64_t sj, bool vec2,
@@ -278,9 +315,16 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       T out[B2];
       T c = T(0), ac = T(0), bc = T(0), abc = T(0);
       const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
+      int qp = 0;  // second symbol of the pair decoded at even l
 #pragma unroll
       for (int l = 0; l < B2; ++l) {
-        const int q = br.next(tb.lut, *tb.cn, tb.syms, tb.n_live);
+        int q;
+        if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
+          if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp);
+          else q = qp;
+        } else {
+          q = br.next(tb.lut, *tb.cn, tb.syms, tb.n_live);
+        }
         T a = T(0), bb = T(0), ab = T(0);
         if (!REG) {
           if (NDIM == 3) {
@@ -330,7 +374,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
         sum_words<T>(xr, sum);
       }
       const uint64_t ro = (uint64_t)i * si + (uint64_t)j * sj;
-      if (blk_out) {
+      if (WRITE) {
         if ((B2 % 2) == 0 && vec2) {
           typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type V2;
           V2* p = reinterpret_cast<V2*>(blk_out + ro);
@@ -346,7 +390,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
           for (int l = 0; l < B2; ++l) blk_out[ro + l] = out[l];
         }
       }
-      if (blk_orig) {
+      if (!WRITE && blk_orig) {
 #pragma unroll
         for (int l = 0; l < B2; ++l) {
           const T xo = blk_orig[ro + l];
@@ -564,7 +608,7 @@ __global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ s, u
   uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
   const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
   if (!cta_tables(s, h, sm, lut, syms, st)) return;
-  const Tables tb = {lut, &sm.cn, syms, h.n_live};
+  const Tables tb = {lut, &sm.cn, syms, h.n_live, nullptr};
   const uint8_t* lim = s + nbytes;
   Walker<T, NDIM> wk;
   wk.base = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
@@ -621,7 +665,7 @@ __global__ void __launch_bounds__(256) k_decode_edges(const uint8_t* __restrict_
   uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
   const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
   if (!cta_tables(s, h, sm, lut, syms, st)) return;
-  const Tables tb = {lut, &sm.cn, syms, h.n_live};
+  const Tables tb = {lut, &sm.cn, syms, h.n_live, nullptr};
   const uint8_t* lim = s + nbytes;
   Walker<T, NDIM> wk;
   wk.base = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
@@ -666,20 +710,20 @@ __global__ void __launch_bounds__(256) k_decode_edges(const uint8_t* __restrict_
   acc.commit(st);
 }
 
-template <typename T, int NDIM, int B0, int B1, int B2, bool HOOK>
+template <typename T, int NDIM, int B0, int B1, int B2, bool HOOK, bool WRITE>
 __device__ __forceinline__ bool fast_dispatch(bool reg, const uint8_t* s, const uint8_t* lim, const Hdr& h,
                                               const BlockIn& bi, const Tables& tb, T* plane, T* out, const T* org,
                                               uint64_t si, uint64_t sj, bool vec2, uint32_t kinj, uint32_t bitinj,
                                               unsigned long long* sum, unsigned long long* nv, double* me) {
   if (reg)
-    return decode_fast<T, NDIM, B0, B1, B2, true, HOOK>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj, bitinj,
-                                                        sum, nv, me);
-  return decode_fast<T, NDIM, B0, B1, B2, false, HOOK>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj, bitinj,
-                                                       sum, nv, me);
+    return decode_fast<T, NDIM, B0, B1, B2, true, HOOK, WRITE>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj,
+                                                               bitinj, sum, nv, me);
+  return decode_fast<T, NDIM, B0, B1, B2, false, HOOK, WRITE>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj,
+                                                              bitinj, sum, nv, me);
 }
 
-// Fast kernel: full blocks of a compile-time shape.
-template <typename T, int NDIM, int B0, int B1, int B2>
+// Fast kernel: full blocks of a compile-time shape (WRITE: decompression, else verification).
+template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE>
 __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
                                                      uint8_t* status, const T* orig, State* st,
                                                      const sdcsz_flip* __restrict__ flips, uint32_t nflips,
@@ -689,9 +733,13 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
   uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
   const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
   if (!cta_tables(s, h, sm, lut, syms, st)) return;
-  const Tables tb = {lut, &sm.cn, syms, h.n_live};
+  uint2* lut2 = reinterpret_cast<uint2*>(smem + (4u << kLutBits));
+  __syncthreads();
+  pair_table(lut2, lut);
+  __syncthreads();
+  const Tables tb = {lut, &sm.cn, syms, h.n_live, lut2};
   const uint8_t* lim = s + nbytes;
-  T* plane = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
+  T* plane = reinterpret_cast<T*>(smem + (12u << kLutBits)) + threadIdx.x;
   Walker<T, NDIM> wk;  // for the few blocks that take the generic decoder
   wk.base = plane;
   wk.stride = blockDim.x;
@@ -715,8 +763,8 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
       const uint64_t c1 = tq % g.nbd[1], c0 = tq / g.nbd[1];
       if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) continue;
       const uint64_t bo = (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
-      T* out = field ? field + bo : nullptr;
-      const T* org = orig ? orig + bo : nullptr;
+      T* out = WRITE ? field + bo : nullptr;
+      const T* org = (!WRITE && orig) ? orig + bo : nullptr;
       BlockIn bi;
       bi.b = b;
       bi.pay_off = sm.off[t][0];
@@ -737,10 +785,10 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
           return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, field, orig, first ? kinj : kNone, bitinj, sum, nv,
                                          me);
         if (first && kinj != kNone)
-          return fast_dispatch<T, NDIM, B0, B1, B2, true>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj,
-                                                          bitinj, sum, nv, me);
-        return fast_dispatch<T, NDIM, B0, B1, B2, false>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kNone,
-                                                         0, sum, nv, me);
+          return fast_dispatch<T, NDIM, B0, B1, B2, true, WRITE>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2,
+                                                                 kinj, bitinj, sum, nv, me);
+        return fast_dispatch<T, NDIM, B0, B1, B2, false, WRITE>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2,
+                                                                kNone, 0, sum, nv, me);
       }, acc);
       if (status) status[b] = stv;
     }
@@ -758,8 +806,8 @@ inline unsigned persistent_grid(K kern, uint32_t threads, size_t smem, uint64_t 
 template <typename T, int NDIM, int B0, int B1, int B2>
 void run_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
               const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
-  const size_t smem = (4u << kLutBits) + (size_t)walker_slots(NDIM, h.g.B) * 256 * sizeof(T);
-  auto kern = k_decode_fast<T, NDIM, B0, B1, B2>;
+  const size_t smem = (12u << kLutBits) + (size_t)walker_slots(NDIM, h.g.B) * 256 * sizeof(T);  // lut, pair lut, plane
+  auto kern = field ? k_decode_fast<T, NDIM, B0, B1, B2, true> : k_decode_fast<T, NDIM, B0, B1, B2, false>;
   const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
   const unsigned grid = persistent_grid(kern, 256, smem, ngroups, L);
   const uintptr_t al = 2 * sizeof(T);
