@@ -223,10 +223,26 @@ __global__ void __launch_bounds__(128) k_prep_batch(BatchArgs a) {
   }, NoOp());
 }
 
+// 3D fast blocks whose two planes fit 1 KB per thread are read through shared memory: the
+// next plane is copied asynchronously (cp.async, 8-byte units) while the current one is walked,
+// so the row loads no longer wait on HBM one after another.
+template <typename T, int NDIM, int B1, int B2>
+struct PrepStage {
+  static constexpr int U = B2 * (int)sizeof(T) / 8;  // 8-byte units per row
+  static constexpr bool on = NDIM == 3 && (B2 * sizeof(T)) % 8 == 0 && 2 * B1 * B2 * sizeof(T) <= 1024;
+  static constexpr size_t bytes(uint32_t threads) { return on ? (size_t)2 * B1 * U * 8 * threads : 0; }
+};
+
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+
 // Fast path: full blocks of a compile-time shape B0 x B1 x B2 (leading 1 for 2D).
 template <typename T, int NDIM, int B0, int B1, int B2>
 __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo& g, const Ws& w, int vec2,
-                                          uint64_t cta) {
+                                          uint64_t cta, unsigned char* stage) {
   State* st = w.st;
   const uint32_t tid = threadIdx.x;
   const uint64_t b = cta * blockDim.x + tid;
@@ -246,15 +262,46 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
     float brow[B2], pa[B2], pb[B2], na[B2], nb[B2];
 #pragma unroll
     for (int l = 0; l < B2; ++l) pa[l] = pb[l] = na[l] = nb[l] = 0.0f;
+    using ST = PrepStage<T, NDIM, B1, B2>;
+    const bool staged = ST::on && vec2;
+    // unit u of row r of buffer f of this thread: 8 bytes at ((f*B1 + r)*U + u)*blockDim + tid
+    auto unit = [&](int f, int r, int u) {
+      return reinterpret_cast<unsigned long long*>(stage) + (((size_t)f * B1 + r) * ST::U + u) * blockDim.x + tid;
+    };
+    auto issue_plane = [&](int i) {
+#pragma unroll 1
+      for (int r = 0; r < B1; ++r)
+#pragma unroll
+        for (int u = 0; u < ST::U; ++u)
+          cp_async8(unit(i & 1, r, u), reinterpret_cast<const unsigned char*>(blk + (uint64_t)i * si + (uint64_t)r * sj) + 8 * u);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (ST::on && staged) issue_plane(0);
 #pragma unroll 1
     for (int i = 0; i < B0; ++i) {
       const float ti = __fsub_rn((float)i, c0);
       const int s_cur = i % B1, s_next = (i + 1) % B1;
+      if (ST::on && staged) {
+        if (i + 1 < B0) {
+          issue_plane(i + 1);
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+      }
 #pragma unroll 1
       for (int j = 0; j < B1; ++j) {
         const float tj = __fsub_rn((float)j, c1);
         T x[B2];
-        load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)j * sj, vec2, x);
+        if (ST::on && staged) {
+#pragma unroll
+          for (int u = 0; u < ST::U; ++u) {
+            const unsigned long long v = *unit(i & 1, j, u);
+            memcpy(reinterpret_cast<unsigned char*>(x) + 8 * u, &v, 8);
+          }
+        } else {
+          load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)j * sj, vec2, x);
+        }
         const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
         float r0 = 0.0f, rl = 0.0f;
 #pragma unroll
@@ -338,14 +385,16 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
 
 template <typename T, int NDIM, int B0, int B1, int B2>
 __global__ void __launch_bounds__(128) k_prep_fast(const T* __restrict__ field, Geo g, Ws w, int vec2) {
-  prep_fast<T, NDIM, B0, B1, B2>(field, g, w, vec2, blockIdx.x);
+  extern __shared__ __align__(16) unsigned char stage[];
+  prep_fast<T, NDIM, B0, B1, B2>(field, g, w, vec2, blockIdx.x, stage);
 }
 
 template <typename T, int NDIM, int B0, int B1, int B2>
 __global__ void __launch_bounds__(128) k_prep_fast_batch(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char stage[];
   __shared__ Job s_job;
   batch_loop(a, s_job, NoOp(), [&](uint64_t it) {
-    prep_fast<T, NDIM, B0, B1, B2>(static_cast<const T*>(s_job.field), s_job.g, s_job.w, s_job.vec2, it);
+    prep_fast<T, NDIM, B0, B1, B2>(static_cast<const T*>(s_job.field), s_job.g, s_job.w, s_job.vec2, it, stage);
   }, NoOp());
 }
 
@@ -380,8 +429,9 @@ __global__ void k_bound_batch(const Job* jobs, uint32_t n) {
 
 template <typename T, int NDIM, int B0, int B1, int B2>
 static void run_fast(const void* field, const Geo& g, const Ws& w, const Launch& L) {
-  const size_t smem = 0;
+  const size_t smem = PrepStage<T, NDIM, B1, B2>::bytes(128);
   auto kern = k_prep_fast<T, NDIM, B0, B1, B2>;
+  allow_smem(reinterpret_cast<const void*>(kern), smem);
   const bool vec2 = (B2 % 2 == 0) && (g.d[2] % 2 == 0) && (reinterpret_cast<uintptr_t>(field) % (2 * sizeof(T)) == 0);
   kern<<<(unsigned)((g.nb + 127) / 128), 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, vec2 ? 1 : 0);
   note_launch();
@@ -458,8 +508,9 @@ static unsigned batch_grid(K kern, uint32_t threads, size_t smem, uint64_t items
 template <typename T, int NDIM, int B0, int B1, int B2>
 static void batch_fast_t(const BatchArgs& a, const Launch& L) {
   auto kern = k_prep_fast_batch<T, NDIM, B0, B1, B2>;
-  const unsigned grid = batch_grid(kern, 128, 0, a.start[a.n], L);
-  kern<<<grid, 128, 0, L.stream>>>(a);
+  const size_t smem = PrepStage<T, NDIM, B1, B2>::bytes(128);
+  const unsigned grid = batch_grid(kern, 128, smem, a.start[a.n], L);
+  kern<<<grid, 128, smem, L.stream>>>(a);
   note_launch();
 }
 
