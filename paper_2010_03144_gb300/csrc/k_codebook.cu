@@ -15,33 +15,6 @@ namespace sdcsz {
 
 namespace {
 
-// Block-wide exclusive scan of one value per thread (1024 threads).
-__device__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t inc = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= (uint32_t)o) inc += n;
-  }
-  if (lane == 31) s_warp[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t t = (lane < (blockDim.x >> 5)) ? s_warp[lane] : 0;
-    uint32_t ti = t;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t n = __shfl_up_sync(0xffffffffu, ti, o);
-      if (lane >= (uint32_t)o) ti += n;
-    }
-    s_warp[lane] = ti - t;  // exclusive prefix of warp totals
-    if (lane == 31) s_warp[32] = ti;
-  }
-  __syncthreads();
-  const uint32_t r = s_warp[wid] + inc - v;
-  *total = s_warp[32];
-  __syncthreads();
-  return r;
-}
-
 // Ascending bitonic sort of n_pad (power of two) 64-bit keys, shared or global memory.
 __device__ void bitonic_sort(unsigned long long* a, uint32_t n_pad) {
   for (uint32_t size = 2; size <= n_pad; size <<= 1) {
@@ -78,29 +51,15 @@ constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this
 
 __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
                                          unsigned char* smem) {
-  __shared__ uint32_t s_warp[40];
   __shared__ uint32_t cnt[64];
   __shared__ uint32_t s_maxlen;
   __shared__ uint32_t first_code[kMaxLen + 2], first_index[kMaxLen + 2], cum[kMaxLen + 2];
   State* st = w.st;
   const uint32_t tid = threadIdx.x;
-  const uint32_t bins = g.bins;
 
-  // 1. live symbols -> keys (global scratch), codebook cleared. Thread t owns the bins
-  //    t, t + blockDim, ... (coalesced); the keys are sorted next, so their order here is free.
-  uint32_t mine = 0;
-#pragma unroll 4
-  for (uint32_t s = tid; s < bins; s += blockDim.x) {
-    mine += __ldg(&w.hist[s]) ? 1u : 0u;
-    w.codebook[s] = 0;
-  }
-  uint32_t n;
-  uint32_t pos = block_excl_scan(mine, s_warp, &n);
-#pragma unroll 4
-  for (uint32_t s = tid; s < bins; s += blockDim.x) {
-    const unsigned long long hc = __ldg(&w.hist[s]);
-    if (hc) w.sort_keys[pos++] = (hc << 16) | s;
-  }
+  // 1. the live symbols' keys (count << 16 | symbol), gathered by k_codebook_gather in no
+  //    particular order (they are sorted next) together with their number
+  const uint32_t n = *(volatile unsigned int*)&st->n_live;
   uint32_t n_pad = 1;
   while (n_pad < n) n_pad <<= 1;
   unsigned long long* keys = (n_pad <= kSmemSort) ? reinterpret_cast<unsigned long long*>(smem) : w.sort_keys;
@@ -272,6 +231,28 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
   }
 }
 
+// Step 1 of the codebook, spread over the GPU: one thread per bin clears the codebook entry and,
+// for a live bin, appends its key (warp-aggregated slot reservation on State::n_live).
+__device__ __forceinline__ void gather_bin(const Geo& g, const Ws& w, uint32_t s) {
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned long long hc = s < g.bins ? __ldg(&w.hist[s]) : 0ull;
+  if (s < g.bins) w.codebook[s] = 0;
+  const unsigned int m = __ballot_sync(0xffffffffu, hc != 0);
+  uint32_t base = 0;
+  if (lane == 0 && m) base = atomicAdd(&w.st->n_live, (unsigned int)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (hc) w.sort_keys[base + __popc(m & ((1u << lane) - 1))] = (hc << 16) | s;
+}
+
+__global__ void __launch_bounds__(1024) k_codebook_gather(Geo g, Ws w) {
+  gather_bin(g, w, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) k_codebook_gather_batch(const Job* __restrict__ jobs) {
+  const Job& jb = jobs[blockIdx.y];
+  gather_bin(jb.g, jb.w, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 __global__ void __launch_bounds__(1024) k_codebook(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (*(volatile unsigned int*)&w.st->error) return;
@@ -296,6 +277,8 @@ __global__ void __launch_bounds__(1024) k_codebook_batch(const Job* __restrict__
 constexpr size_t kCodebookSmem = kSmemSort * 8 + 4096 * 8 + 8192 * 4 + 8192;
 
 void batch_codebook(const Job* jobs, uint32_t n, const Launch& L) {
+  k_codebook_gather_batch<<<dim3(64, n), 1024, 0, L.stream>>>(jobs);
+  note_launch();
   allow_smem(reinterpret_cast<const void*>(k_codebook_batch), kCodebookSmem);
   k_codebook_batch<<<n, 1024, kCodebookSmem, L.stream>>>(jobs);
   note_launch();
@@ -303,6 +286,8 @@ void batch_codebook(const Job* jobs, uint32_t n, const Launch& L) {
 
 void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
   const size_t smem = kCodebookSmem;
+  k_codebook_gather<<<(g.bins + 1023) / 1024, 1024, 0, L.stream>>>(g, w);
+  note_launch();
   allow_smem(reinterpret_cast<const void*>(k_codebook), smem);
   k_codebook<<<1, 1024, smem, L.stream>>>(g, w, out, cap);
   note_launch();
