@@ -34,6 +34,28 @@ __device__ void bitonic_sort(unsigned long long* a, uint32_t n_pad) {
   }
 }
 
+// Ascending sort of n distinct keys (padded to n_pad with ~0). Up to one key per thread: each
+// thread counts the keys below its own (all threads read the same key at a time, a broadcast)
+// and stores it at that rank; three barriers instead of the bitonic network's many.
+__device__ void sort_keys(unsigned long long* a, uint32_t n, uint32_t n_pad) {
+  if (n <= 1) return;
+  if (n > blockDim.x) {
+    bitonic_sort(a, n_pad);
+    return;
+  }
+  const uint32_t t = threadIdx.x;
+  unsigned long long mine = 0;
+  uint32_t rank = 0;
+  __syncthreads();
+  if (t < n) {
+    mine = a[t];
+    for (uint32_t j = 0; j < n; ++j) rank += a[j] < mine;
+  }
+  __syncthreads();
+  if (t < n) a[rank] = mine;
+  __syncthreads();
+}
+
 __device__ __forceinline__ void put_u8(uint8_t* o, uint64_t off, uint8_t v) { o[off] = v; }
 __device__ __forceinline__ void put_u16(uint8_t* o, uint64_t off, uint16_t v) {
   o[off] = (uint8_t)v; o[off + 1] = (uint8_t)(v >> 8);
@@ -66,7 +88,7 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
   __syncthreads();
   for (uint32_t t = tid; t < n_pad; t += blockDim.x) keys[t] = (t < n) ? w.sort_keys[t] : ~0ull;
   __syncthreads();
-  if (n > 1) bitonic_sort(keys, n_pad);
+  sort_keys(keys, n, n_pad);
   for (uint32_t t = tid; t < 64; t += blockDim.x) cnt[t] = 0;
   if (tid == 0) s_maxlen = 0;
   __syncthreads();
@@ -162,7 +184,7 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
   __syncthreads();
   for (uint32_t t = tid; t < n_pad; t += blockDim.x) keys[t] = (t < n) ? w.sort_keys[t] : ~0ull;
   __syncthreads();
-  if (n > 1) bitonic_sort(keys, n_pad);
+  sort_keys(keys, n, n_pad);
   if (tid == 0) {
     uint32_t code = 0, idx = 0;
     for (uint32_t l = 1; l <= (uint32_t)kMaxLen; ++l) {
