@@ -748,7 +748,7 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
 // Edge blocks of a field whose full blocks take the fast kernel: the same compile-time
 // walk with runtime extents, one thread per edge block (compact enumeration).
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
-__global__ void __launch_bounds__(128, 7) k_predict_edge(const T* __restrict__ field, Geo g, Ws w,
+__global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_edge(const T* __restrict__ field, Geo g, Ws w,
                                                       const sdcsz_flip* __restrict__ flips, uint32_t nflips,
                                                       uint64_t count) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -771,9 +771,14 @@ __global__ void __launch_bounds__(128, 7) k_predict_edge(const T* __restrict__ f
   hist_flush(hist_s, h, w);
 }
 
+// Resident CTAs of 128 threads per SM the fast kernels are compiled for (register budget).
+#ifndef SDCSZ_PRED_MINB
+#define SDCSZ_PRED_MINB 7
+#endif
+
 // Fast kernel: full blocks of a compile-time shape.
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
-__global__ void __launch_bounds__(128, 7) k_predict_fast(const T* __restrict__ field, Geo g, Ws w,
+__global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast(const T* __restrict__ field, Geo g, Ws w,
                                                       const sdcsz_flip* __restrict__ flips, uint32_t nflips,
                                                       int vec2) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -796,7 +801,7 @@ __global__ void __launch_bounds__(128, 7) k_predict_fast(const T* __restrict__ f
 
 // Batched fast kernel: the full blocks of every job with this block shape.
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
-__global__ void __launch_bounds__(128, 7) k_predict_fast_batch(BatchArgs a) {
+__global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t hist_s[kHistWindow];
   __shared__ Job s_job;
