@@ -496,43 +496,13 @@ def run_batch13(args):
     batch.close()
 
 
-def _device_field(shape, seed, dtype, device, spikes=0.0):
-    """The synthetic recipe (8 sinusoids with integer frequencies 1..6 per axis, random phases,
-    Gaussian noise 1e-3, optional 1% lognormal spikes), drawn on the device with torch's
-    seeded generators: fast enough for a pool of large serving inputs."""
-    import torch
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    nd = len(shape)
-    freqs = torch.randint(1, 7, (8, nd), generator=g)
-    phases = torch.rand(8, generator=g, dtype=torch.float64) * 2 * np.pi
-    axes = [torch.arange(n, device=device, dtype=torch.float64) / n for n in shape]
-    acc = torch.zeros(shape, device=device, dtype=torch.float64)
-    for m in range(8):
-        ang = phases[m].item()
-        grid = None
-        for a in range(nd):
-            t = 2 * np.pi * freqs[m, a].item() * axes[a]
-            t = t.view(*([1] * a), -1, *([1] * (nd - a - 1)))
-            grid = t if grid is None else grid + t
-        acc += torch.sin(grid + ang)
-    gd = torch.Generator(device=device).manual_seed(seed + 1)
-    acc += 1e-3 * torch.randn(shape, device=device, dtype=torch.float64, generator=gd)
-    if spikes > 0:
-        n = acc.numel()
-        k = max(1, int(spikes * n))
-        idx = torch.randint(0, n, (k,), device=device, generator=gd)
-        sign = torch.randint(0, 2, (k,), device=device, generator=gd).to(torch.float64) * 2 - 1
-        mag = torch.exp(2.0 * torch.randn(k, device=device, dtype=torch.float64, generator=gd))
-        acc.view(-1)[idx] += sign * mag
-    return acc.to(dtype).contiguous()
-
-
 def run_serve(args):
     """Serving: a Poisson stream of compress / decompress / verify requests through the server."""
     import torch
 
     import paper_2010_03144_gb300 as sz
     from paper_2010_03144_gb300 import build as libbuild
+    import synth
 
     libbuild.build()
     sz.lib()
@@ -542,10 +512,10 @@ def run_serve(args):
     pool = []
     for i in range(12):
         shp = tuple(int(v) for v in rng.integers(32, 513, size=3))
-        pool.append(_device_field(shp, 400 + i, torch.float32, device))
+        pool.append(synth.device_field(shp, 400 + i, torch.float32, device))
     for i in range(6):
         shp = tuple(int(v) for v in rng.integers(256, 4097, size=2))
-        pool.append(_device_field(shp, 500 + i, torch.float64, device))
+        pool.append(synth.device_field(shp, 500 + i, torch.float64, device))
     streams = [sz.compress(f, 1e-3)[0].clone() for f in pool]
     torch.cuda.synchronize()
     rate, seconds, warm_s = 2000.0, max(1.0, args.steps / 10.0), 0.5
@@ -611,13 +581,115 @@ def run_serve(args):
     }), flush=True)
 
 
+def run_faults(args):
+    """Bit-flip rate sweep: soft errors in the input, the bin array and the regression
+    coefficients during compression, and persistent corruption of the compressed stream;
+    detection / correction counts, compression-ratio change and GB/s against the fault-free run."""
+    import torch
+
+    import paper_2010_03144_gb300 as sz
+    from paper_2010_03144_gb300 import build as libbuild
+    import synth
+
+    libbuild.build()
+    sz.lib()
+    dev = torch.device("cuda", 0)
+    rel, rates = 1e-4, (1e-9, 1e-7, 1e-5)
+    results = []
+    for shape, tdt, B in (((1024, 1024, 1024), torch.float32, 8), ((512, 512, 512), torch.float64, 8)):
+        W = 1 if tdt == torch.float32 else 2
+        x0 = synth.device_field(shape, 21, tdt, dev, spikes=0.01)
+        N = x0.numel()
+        nbd = [n // B for n in shape]
+        nb, P = nbd[0] * nbd[1] * nbd[2], B ** 3
+
+        def timed(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps, out
+
+        def clean():
+            s, rep = sz.compress(x0, rel, block=B)
+            rc, y, st, rd = sz.decompress(s)
+            return s, rep, y
+        base_ms, (s0, rep0, _) = timed(clean)
+        row = {"field": f"{tuple(shape)} {'f32' if W == 1 else 'f64'} block {B}^3 rel {rel}",
+               "fault_free": {"ratio": round(N * 4 * W / s0.numel(), 3),
+                              "gbs": round(N * 4 * W / (base_ms * 1e-3) / 1e9, 1)}, "rates": []}
+        for rate in rates:
+            rng = np.random.default_rng(int(round(-np.log10(rate))))
+            n_in = int(rng.binomial(N * W, rate))
+            words = np.unique(rng.integers(0, N * W, size=n_in))
+            pts = words // W
+            i, j, l = np.unravel_index(pts, shape)
+            blk = ((i // B) * nbd[1] + j // B) * nbd[2] + l // B
+            flips = [("input", int(bk), int(wd), int(bt)) for bk, wd, bt in
+                     zip(blk, words, rng.integers(0, 32, size=words.size))]
+            n_code = int(rng.binomial(N, rate))
+            flips += [("code", int(bk), int(k), int(bt)) for bk, k, bt in
+                      zip(rng.integers(0, nb, n_code), rng.integers(0, P, n_code), rng.integers(0, 16, n_code))]
+            n_coef = int(rng.binomial(nb * 4, rate))
+            flips += [("coef", int(bk), int(k), int(bt)) for bk, k, bt in
+                      zip(rng.integers(0, nb, n_coef), rng.integers(0, 4, n_coef), rng.integers(0, 32 * W, n_coef))]
+            x = x0.clone()
+
+            def faulty():
+                x.copy_(x0)
+                s, rep = sz.compress(x, rel, block=B, flips=flips)
+                rc, y, st, rd = sz.decompress(s)
+                return s, rep, y
+            ms, (s, rep, y) = timed(faulty)
+            viol = int(((x0.double() - y.double()).abs() > rep["eb_abs"]).sum()) if W == 1 else \
+                sum(int(((x0[q:q + 64].double() - y[q:q + 64].double()).abs() > rep["eb_abs"]).sum())
+                    for q in range(0, shape[0], 64))
+            # persistent corruption of the compressed stream (payload bits)
+            hb = s[:128].cpu().numpy()
+            pay_bytes = int(np.frombuffer(hb[96:104].tobytes(), "<u8")[0])
+            pay0 = int(s.numel()) - pay_bytes  # the payload is the stream's last section
+            npay = pay_bytes
+            n_st = int(rng.binomial(npay // 4, rate))
+            sc = s.clone()
+            if n_st:
+                pos = torch.from_numpy(rng.integers(pay0, s.numel(), size=n_st)).to(dev)
+                sc[pos] ^= torch.from_numpy((1 << rng.integers(0, 8, size=n_st)).astype(np.uint8)).to(dev)
+            rc2, y2, st2, rd2 = sz.decompress(sc)
+            detected = int((st2 != 0).sum())
+            ok_mask = (st2 == 0)
+            row["rates"].append({
+                "rate_per_word": rate, "input_flips": int(words.size), "code_flips": n_code, "coef_flips": n_coef,
+                "input_corrected": rep["input_corrected"], "codes_corrected": rep["codes_corrected"],
+                "uncorrectable_blocks": rep["uncorrectable_blocks"], "bound_violations_after_decompress": viol,
+                "ratio": round(N * 4 * W / s.numel(), 3),
+                "ratio_change_pct": round(100.0 * (s0.numel() - s.numel()) / s.numel(), 4),
+                "gbs": round(N * 4 * W / (ms * 1e-3) / 1e9, 1),
+                "stream_flips": n_st, "stream_blocks_flagged": detected, "stream_rc": rc2,
+                "blocks_passing": int(ok_mask.sum())})
+            del x, s, y, sc, y2
+            torch.cuda.empty_cache()
+        results.append(row)
+        del x0
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "fault sweep: detection/correction, CR change and GB/s vs fault-free",
+                      "unit": "GB/s", "data": "synthetic", "higher_is_better": True,
+                      "config": {"workload": "faults: 1024^3 f32 and 512^3 f64, spikes 1%, rel 1e-4, 8^3 blocks; "
+                                             "flips per word over input, bin array and coefficients at compression, "
+                                             "and payload bits of the stream", "steps": "3 timed runs per rate"},
+                      "sweep": results}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve"), default="512cube")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve", "faults"), default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -628,6 +700,8 @@ def main():
         run_batch13(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "faults":
+        run_faults(args)
     else:
         run_ours(args)
 

@@ -677,6 +677,11 @@ __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_
 
 // One full block of a compile-time shape (B0 x B1 x B2, leading 1s below 3D); edge blocks
 // are skipped (the generic path takes them).
+// Resident CTAs of 128 threads per SM the fast kernels are compiled for (register budget).
+#ifndef SDCSZ_PRED_MINB
+#define SDCSZ_PRED_MINB 7
+#endif
+
 // One block with the compile-time shape B0 x B1 x B2 (leading 1s below 3D). Full blocks only,
 // unless EDGE: then block b is an edge block, cut by the field boundary, walked with the same
 // code and its actual extents.
@@ -770,11 +775,6 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_edge(const T* 
   cnt.commit(st);
   hist_flush(hist_s, h, w);
 }
-
-// Resident CTAs of 128 threads per SM the fast kernels are compiled for (register budget).
-#ifndef SDCSZ_PRED_MINB
-#define SDCSZ_PRED_MINB 7
-#endif
 
 // Fast kernel: full blocks of a compile-time shape.
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>

@@ -69,3 +69,34 @@ def integer_field(shape, seed: int, lo: int = -50, hi: int = 50, dtype=np.float3
     rng = np.random.default_rng(seed)
     return rng.integers(lo, hi + 1, size=shape).astype(dtype)
 
+
+def device_field(shape, seed, dtype, device, spikes=0.0):
+    """The same recipe as ``sinusoid_field`` (8 sinusoids with integer frequencies 1..6 per axis,
+    random phases, Gaussian noise 1e-3, optional 1% lognormal spikes), computed in float64 on a
+    torch device with torch's seeded generators, for fields too large to draw on the host. The
+    values differ from ``sinusoid_field``'s for the same seed (other generators)."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    nd = len(shape)
+    freqs = torch.randint(1, 7, (8, nd), generator=g)
+    phases = torch.rand(8, generator=g, dtype=torch.float64) * 2 * np.pi
+    axes = [torch.arange(n, device=device, dtype=torch.float64) / n for n in shape]
+    acc = torch.zeros(shape, device=device, dtype=torch.float64)
+    for m in range(8):
+        ang = phases[m].item()
+        grid = None
+        for a in range(nd):
+            t = 2 * np.pi * freqs[m, a].item() * axes[a]
+            t = t.view(*([1] * a), -1, *([1] * (nd - a - 1)))
+            grid = t if grid is None else grid + t
+        acc += torch.sin(grid + ang)
+    gd = torch.Generator(device=device).manual_seed(seed + 1)
+    acc += 1e-3 * torch.randn(shape, device=device, dtype=torch.float64, generator=gd)
+    if spikes > 0:
+        n = acc.numel()
+        k = max(1, int(spikes * n))
+        idx = torch.randint(0, n, (k,), device=device, generator=gd)
+        sign = torch.randint(0, 2, (k,), device=device, generator=gd).to(torch.float64) * 2 - 1
+        mag = torch.exp(2.0 * torch.randn(k, device=device, dtype=torch.float64, generator=gd))
+        acc.view(-1)[idx] += sign * mag
+    return acc.to(dtype).contiguous()
