@@ -172,6 +172,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
   const uint32_t lane = threadIdx.x & 31;
   const bool active = b < g.nb;
   bool reg = false;
+  unsigned long long nun_enc = 0;
   if (active) {
     Codebook cb;
     cb.lo = cb_lo(g);
@@ -226,13 +227,18 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
     }
     *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * b) = (uint16_t)((e.bits + 7u) >> 3);
     *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * b) = (uint16_t)e.nun;
+    nun_enc = e.nun;
     if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * b) = w.sum_dc[b];
     // a block whose codes could not be repaired is reported in the header status word
     if (bad) atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
   }
-  // regression bitmap word of this warp's 32 blocks
+  // regression bitmap word of this warp's 32 blocks; the warp's unpredictable count
   const unsigned int ballot = __ballot_sync(0xffffffffu, active && reg);
-  if (lane == 0 && b < g.nb) *reinterpret_cast<uint32_t*>(out + L.bitmap + 4 * (b >> 5)) = ballot;
+  unsigned long long wun = warp_sum(nun_enc);
+  if (lane == 0 && b < g.nb) {
+    *reinterpret_cast<uint32_t*>(out + L.bitmap + 4 * (b >> 5)) = ballot;
+    if (wun) atomicAdd(&st->n_unpred_enc, wun);
+  }
 }
 
 template <typename T, bool ABFT>
@@ -256,7 +262,12 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
   const uint64_t b = gid * kGroup + tid;
   const bool active = b < g.nb;
-  const Layout L = st->L;
+  // The unpredictable section holds the points whose code, as encoded, is 0: the count K2 took
+  // unless a block's codes could not be repaired. The payload follows that section.
+  const unsigned long long n_unpred = st->n_unpred_enc;
+  const uint64_t s_dt = g.dtype ? 8 : 4;
+  Layout L = st->L;
+  L.payload = align16(L.unpred + s_dt * n_unpred);
   uint32_t bytes = 0, nun = 0;
   bool reg = false;
   if (active) {
@@ -353,8 +364,12 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
     for (int q = 0; q < 3; ++q) *reinterpret_cast<unsigned long long*>(out + go + 8 * q) = s_excl[q];
     if (gid == ngroups - 1) {
       const unsigned long long pay = s_excl[0] + s_tot[0];
+      *reinterpret_cast<unsigned long long*>(out + 88) = n_unpred;
       *reinterpret_cast<unsigned long long*>(out + 96) = pay;
       *reinterpret_cast<unsigned long long*>(out + 104) = L.payload + pay;
+      for (uint64_t o = L.unpred + s_dt * n_unpred; o < L.payload && o < cap; ++o) out[o] = 0;  // alignment gap
+      st->n_unpred = n_unpred;
+      st->L = L;
       st->payload_bytes = pay;
       st->total_bytes = L.payload + pay;
       if (L.payload + pay > cap) atomicOr(&st->error, ERR_CAPACITY);
@@ -373,7 +388,7 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   // unpredictable values, moved by K4a to the front of the block's staging slot
   const T* up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
   T* udst = reinterpret_cast<T*>(out + L.unpred);
-  const unsigned long long ulim = st->n_unpred;
+  const unsigned long long ulim = n_unpred;
   for (uint32_t j = 0; j < nun; ++j)
     if (un_off + j < ulim) udst[un_off + j] = up[32 * (uint64_t)j];
   // payload: stream bytes [lo, hi) = slot bytes [0, bytes). The stream word at wa = wa0 + 4i

@@ -54,6 +54,7 @@ struct State {
   unsigned long long max_err_bits;  // double bits of max |x - x'| (non-negative: ordered as u64)
   unsigned int ticket, n_live;
   unsigned long long payload_bytes, total_bytes;
+  unsigned long long n_unpred_enc;  // unpredictable points of the codes as encoded (after repairs)
   Layout L;
   unsigned long long queue[4];  // work-queue counters of the persistent kernels of one call
 };
