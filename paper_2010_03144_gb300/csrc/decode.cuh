@@ -680,10 +680,30 @@ __global__ void __launch_bounds__(256) k_decode_edges(const uint8_t* __restrict_
     const uint64_t gid = b / kGroup;
     const uint8_t* gp = s + h.L.groups + 24 * gid;
     unsigned long long pay = ld_u64(gp), un = ld_u64(gp + 8), rg = ld_u64(gp + 16);
-    for (uint64_t q = gid * kGroup; q < b; ++q) {
-      pay += *reinterpret_cast<const uint16_t*>(s + h.L.sizes + 2 * q);
-      un += *reinterpret_cast<const uint16_t*>(s + h.L.ucounts + 2 * q);
-      rg += (*reinterpret_cast<const uint32_t*>(s + h.L.bitmap + 4 * (q / 32)) >> (q % 32)) & 1u;
+    // sums over the group's blocks before b: eight 16-bit entries per 16-byte load (the
+    // sections are 16-byte aligned and a group starts at a multiple of 256 entries), then the
+    // partial last load; regression flags by whole bitmap words
+    const uint64_t q0 = gid * kGroup, nq = b - q0;
+    const uint4* sz4 = reinterpret_cast<const uint4*>(s + h.L.sizes + 2 * q0);
+    const uint4* uc4 = reinterpret_cast<const uint4*>(s + h.L.ucounts + 2 * q0);
+    auto sum16 = [](uint4 v, uint32_t n) {  // sum of the first n (<= 8) 16-bit entries
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+      uint32_t t = 0;
+#pragma unroll
+      for (uint32_t m = 0; m < 8; ++m)
+        if (m < n) t += (w[m >> 1] >> (16 * (m & 1))) & 0xffffu;
+      return t;
+    };
+    for (uint64_t q = 0; q < nq; q += 8) {
+      const uint32_t n = (uint32_t)min((uint64_t)8, nq - q);
+      pay += sum16(__ldg(sz4 + q / 8), n);
+      un += sum16(__ldg(uc4 + q / 8), n);
+    }
+    const uint32_t* bm = reinterpret_cast<const uint32_t*>(s + h.L.bitmap) + q0 / 32;
+    for (uint64_t q = 0; q < nq; q += 32) {
+      const uint32_t n = (uint32_t)min((uint64_t)32, nq - q);
+      const uint32_t word = __ldg(bm + q / 32);
+      rg += __popc(n == 32 ? word : (word & ((1u << n) - 1)));
     }
     BlockIn bi;
     bi.b = b;

@@ -406,8 +406,11 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   const uint64_t wa0 = lo - r;
   const uint32_t nout = (uint32_t)((hi - wa0 + 3) >> 2);  // stream words touched
   uint32_t prev = 0;
+  uint4 qn = nw ? src4[0] : make_uint4(0u, 0u, 0u, 0u);  // the next 16 bytes, loaded one step ahead
   for (uint32_t i0 = 0; i0 < nout; i0 += 4) {
-    const uint4 q = i0 < nw ? src4[i0 >> 2] : make_uint4(0u, 0u, 0u, 0u);
+    const uint4 q = qn;
+    if (i0 + 4 < nw) qn = src4[(i0 >> 2) + 1];
+    else qn = make_uint4(0u, 0u, 0u, 0u);
     const uint32_t cur[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
