@@ -44,14 +44,10 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 557475309, "src": "7843b15c00ff"},
-    ("384cube", "prep"): {"bytes": 235184896, "src": "7843b15c00ff"},
-    ("512cube", "predict"): {"bytes": 916736986, "src": "5b68743326e4"},
-    ("384cube", "predict"): {"bytes": 386748416, "src": "5b68743326e4"},
-    ("512cube", "encode"): {"bytes": 332079407, "src": "11f4076d8ccd"},
-    ("384cube", "encode"): {"bytes": 140096000, "src": "11f4076d8ccd"},
-    ("512cube", "decode"): {"bytes": 477491655, "src": "b97fcfccbc4a"},
-    ("384cube", "decode"): {"bytes": 201441792, "src": "b97fcfccbc4a"},
+    ("512cube", "prep"): {"bytes": 555697948, "src": "c9c1570083b1"},
+    ("384cube", "prep"): {"bytes": 234435072, "src": "c9c1570083b1"},
+    ("512cube", "predict"): {"bytes": 920000436, "src": "18891af77d96"},
+    ("384cube", "predict"): {"bytes": 388125184, "src": "18891af77d96"},
 }
 
 
