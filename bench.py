@@ -154,6 +154,11 @@ def _barrier(world):
         dist.barrier()
 
 
+def weak_scaling_value(world: int, bytes_per_rank: float, steps: int, ms_max: float) -> float:
+    """Whole-job GB/s: every rank processed `bytes_per_rank` per step; the slowest rank's time counts."""
+    return world * bytes_per_rank * steps / (ms_max / 1e3) / 1e9
+
+
 def algorithmic_bytes(N, s, nb, n_unpred, n_reg, stream_bytes, abft):
     """Bytes each kernel must move (inputs read once, outputs written once)."""
     meta_in = 16 + 16 + 8 + 1 if abft else 16 + 8 + 1
@@ -248,7 +253,7 @@ def run_ours(args):
     ms_off_max = _reduce_max(ms_off, world, device)
     per_step = ms_on_max / args.steps
     gb = N * s_dt / 1e9
-    value = world * gb * args.steps / (ms_on_max / 1e3)
+    value = weak_scaling_value(world, N * s_dt, args.steps, ms_on_max)
 
     # per-kernel averages over the timed region, roofline of the dominant kernel
     avg = {k: v / args.steps for k, v in stages.items()}
