@@ -527,7 +527,7 @@ def run_serve(args):
     which = rng.integers(0, len(pool), size=n_req)
     ebs = 10.0 ** rng.uniform(-5, -2, size=n_req)
     flipped = rng.random(n_req) < 0.001
-    srv = sz.Server(hbm_budget=60 << 30, slots=8)
+    srv = sz.Server(hbm_budget=60 << 30, slots=args.slots)
     done, lat, nbytes_done, peak_inflight = {}, [], 0, 0
     t0 = time.perf_counter()
     nxt = 0
@@ -571,7 +571,7 @@ def run_serve(args):
         "config": {"workload": "serve: Poisson 2000 req/s, thirds compress/decompress/verify, pool of 12 float32 3D "
                                "(edges U{32..512}) and 6 float64 2D (edges U{256..4096}) fields resident in HBM, "
                                "compress rel eb log-uniform 1e-5..1e-2, 0.1% of requests with one bit flip, "
-                               "60 GB admission budget, 8 slots",
+                               f"60 GB admission budget, {args.slots} slots",
                    "requests": n_req, "measured_requests": len(lat), "warmup_s": warm_s, "seconds": seconds},
         "p50_latency_ms": round(float(np.percentile(lat_ms, 50)), 3),
         "p99_latency_ms": round(float(np.percentile(lat_ms, 99)), 3),
@@ -692,6 +692,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve", "faults"), default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
