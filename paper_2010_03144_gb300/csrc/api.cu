@@ -286,15 +286,27 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
   const size_t ngroups = (g.nb + kGroup - 1) / kGroup;
   if (ngroups && cudaMemsetAsync(w.lb, 0, sizeof(LookBack) * ngroups, L.stream) != cudaSuccess) return SDCSZ_ECUDA;
   tr.mark();
-  launch_prep(d_field, g, w, L);
-  if (nf) launch_flip_input(const_cast<void*>(d_field), g, flips, nf, w, L);
+  {
+    NvtxRange r("sdcsz prep (range, checksums, regression, estimates)");
+    launch_prep(d_field, g, w, L);
+    if (nf) launch_flip_input(const_cast<void*>(d_field), g, flips, nf, w, L);
+  }
   tr.mark();
-  if (g.nb) launch_predict(d_field, g, w, flips, nf, L);
-  if (nf) launch_flip_codes(g, w, flips, nf, L);
+  {
+    NvtxRange r("sdcsz predict (prediction, quantization, checks)");
+    if (g.nb) launch_predict(d_field, g, w, flips, nf, L);
+    if (nf) launch_flip_codes(g, w, flips, nf, L);
+  }
   tr.mark();
-  launch_codebook(g, w, static_cast<uint8_t*>(d_out), out_cap, L);
+  {
+    NvtxRange r("sdcsz codebook");
+    launch_codebook(g, w, static_cast<uint8_t*>(d_out), out_cap, L);
+  }
   tr.mark();
-  launch_encode(g, w, static_cast<uint8_t*>(d_out), out_cap, L);
+  {
+    NvtxRange r("sdcsz encode");
+    launch_encode(g, w, static_cast<uint8_t*>(d_out), out_cap, L);
+  }
   tr.mark();
   if (cudaGetLastError() != cudaSuccess) return SDCSZ_ECUDA;
   tr.finish();
@@ -402,7 +414,10 @@ int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t f
   tr.ms = stage_ms;
   tr.n = 1;
   tr.start(s);
-  rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips);
+  {
+    NvtxRange r(write ? "sdcsz decode" : "sdcsz verify");
+    rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips);
+  }
   if (rc) return rc;
   tr.mark();
   if (cudaGetLastError() != cudaSuccess) return SDCSZ_ECUDA;
@@ -745,6 +760,7 @@ void batch_plan_launches(sdcsz_batch* b) {
 
 // Enqueue the whole batch on `s` (no host synchronisation).
 int batch_enqueue(sdcsz_batch* b, cudaStream_t s) {
+  NvtxRange r("sdcsz batch compress");
   Launch L;
   L.stream = s;
   L.sms = sm_count();

@@ -2,10 +2,21 @@
 // the request server). Not part of the C ABI.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sdcsz_internal.cuh"
 
 namespace sdcsz {
 inline namespace host {
+
+// NVTX range around the host-side enqueue of one stage, so that a timeline profiler groups
+// the stage's kernels under its name.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Byte offsets of the regions of a compression workspace.
 struct WsPlan {
