@@ -684,13 +684,74 @@ def run_faults(args):
                       "sweep": results}), flush=True)
 
 
+def run_region(args):
+    """Random access: boxes of 32^3, 64^3 and 128^3 at random positions decoded out of the
+    stream of a 1024^3 float32 field (6^3 blocks), each call timed end to end on the host
+    (header read, decode, verification, report), against the full decompression."""
+    import torch
+
+    import paper_2010_03144_gb300 as sz
+    from paper_2010_03144_gb300 import build as libbuild
+    import synth
+
+    libbuild.build()
+    sz.lib()
+    dev = torch.device("cuda", 0)
+    n = 1024
+    f = synth.device_field((n, n, n), 11, torch.float32, dev, spikes=0.01)
+    s, _ = sz.compress(f, 1e-4)
+    s = s.clone()
+    del f
+    out_full = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    ws = torch.empty(sz.decompress_workspace_size(), dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(12)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return np.array(ts) * 1e3
+
+    full_ms = timed(lambda: sz.decompress(s, out=out_full, ws=ws), max(3, args.steps // 4))
+    rows = []
+    for e in (32, 64, 128):
+        out = torch.empty((e, e, e), dtype=torch.float32, device=dev)
+        st = torch.empty(((e + 4) // 6 + 1) ** 3, dtype=torch.uint8, device=dev)
+        boxes = [tuple(int(v) for v in rng.integers(0, n - e + 1, size=3)) for _ in range(args.steps)]
+        it = iter(boxes * (1 + (args.warmup + args.steps) // len(boxes)))
+
+        def one():
+            lo = next(it)
+            rc, _, _, _ = sz.decompress_region(s, lo, tuple(v + e for v in lo), out=out, status=st, ws=ws)
+            assert rc == 0
+
+        ms = timed(one, args.steps)
+        rows.append({"box": f"{e}^3", "p50_ms": round(float(np.percentile(ms, 50)), 3),
+                     "p99_ms": round(float(np.percentile(ms, 99)), 3),
+                     "GB_per_s_of_box": round(e ** 3 * 4 / (np.median(ms) / 1e3) / 1e9, 2)})
+    print(json.dumps({
+        "metric": "random-access box decompression latency", "value": rows[1]["p50_ms"], "unit": "ms",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "region: 1024^3 float32 (spikes 1%), rel 1e-4, 6^3 blocks; boxes at uniform random "
+                               "positions, value = p50 of the 64^3 box, host-timed calls including the header read"},
+        "boxes": rows, "full_decompress_p50_ms": round(float(np.percentile(full_ms, 50)), 3)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve", "faults"), default="512cube")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve", "faults", "region"),
+                    default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
     args = ap.parse_args()
@@ -704,6 +765,8 @@ def main():
         run_serve(args)
     elif args.workload == "faults":
         run_faults(args)
+    elif args.workload == "region":
+        run_region(args)
     else:
         run_ours(args)
 

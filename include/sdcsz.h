@@ -178,6 +178,21 @@ int sdcsz_decompress_traced(const void* d_stream, size_t nbytes, void* d_field, 
 int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap,
                            size_t* out_bytes, sdcsz_report* report, void* stream);
 
+/*
+ * Random-access (region) decompression: only the blocks that intersect the box
+ * [lo[a], hi[a]) (a < ndim, the field's axis order, element coordinates) are decoded and
+ * verified (each block is independent, Sec. 5.1), and the box is written densely (C order,
+ * its own shape) to d_out (out_bytes >= box points * element size). d_block_status (may be
+ * NULL; else room for prod_a (floor((hi[a]-1)/B[a]) - floor(lo[a]/B[a]) + 1) bytes) receives
+ * one status per intersecting block, in row-major order of the box's block range; the report
+ * counts those blocks. lo and hi each hold ndim values; an empty or out-of-field box is
+ * SDCSZ_EINVAL. Same return codes as sdcsz_decompress; the header
+ * is read to the host first (one synchronisation).
+ */
+int sdcsz_decompress_region(const void* d_stream, size_t nbytes, const uint64_t* lo, const uint64_t* hi, void* d_out,
+                            size_t out_bytes, uint8_t* d_block_status, void* d_ws, size_t ws_bytes,
+                            sdcsz_report* report, void* stream);
+
 /* Parse a stream header held in HOST memory (the first 128 bytes suffice for dims and
  * dtype; total_bytes is the full stream length). */
 int sdcsz_read_header(const void* h_stream, size_t nbytes, sdcsz_params* out, uint64_t* total_bytes);

@@ -29,7 +29,7 @@ EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_wor
            "sdcsz_batch_workspace_size", "sdcsz_batch_bind", "sdcsz_batch_set_fields", "sdcsz_batch_compress",
            "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy",
            "sdcsz_autotune_block", "sdcsz_server_create", "sdcsz_server_submit", "sdcsz_server_poll",
-           "sdcsz_server_release", "sdcsz_server_get_stats", "sdcsz_server_destroy")
+           "sdcsz_server_release", "sdcsz_server_get_stats", "sdcsz_server_destroy", "sdcsz_decompress_region")
 
 
 class SdcszError(RuntimeError):
@@ -170,6 +170,9 @@ def lib():
         L.sdcsz_read_header.argtypes = [vp, sz, P, ctypes.POINTER(ctypes.c_uint64)]
         L.sdcsz_strerror.argtypes = [i32]
         L.sdcsz_strerror.restype = ctypes.c_char_p
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.sdcsz_decompress_region.argtypes = [vp, sz, u64p, u64p, vp, sz, vp, vp, sz, R, vp]
+        L.sdcsz_decompress_region.restype = i32
         L.sdcsz_kernel_launches.argtypes = []
         L.sdcsz_kernel_launches.restype = ctypes.c_ulonglong
         BI, BP = ctypes.POINTER(BatchItem), ctypes.c_void_p
@@ -389,6 +392,39 @@ def decompress(stream, out=None, status=None, flips=None, ws=None, cuda_stream=N
     if rc not in (OK, ESDC):
         raise SdcszError(rc, "decompress")
     return rc, field, st[:nb], (rep.as_dict() if report else None)
+
+
+def region_blocks(shape, block, lo, hi) -> int:
+    """Blocks intersecting the box [lo, hi) of a field with this shape and block size."""
+    n = 1
+    for a in range(len(shape)):
+        n *= (hi[a] - 1) // block[a] - lo[a] // block[a] + 1
+    return n
+
+
+def decompress_region(stream, lo, hi, out=None, status=None, ws=None, cuda_stream=None, report=True):
+    """Decode only the blocks that intersect the box [lo, hi) (element coordinates, the
+    field's axis order). Returns (rc, box tensor, per-block status, report dict or None)."""
+    import torch
+    h, nb, dt = _geometry(stream)
+    lo, hi = [int(v) for v in lo], [int(v) for v in hi]
+    box = tuple(max(b - a, 0) for a, b in zip(lo, hi))  # an empty box is rejected by the library
+    res = out if out is not None else torch.empty(box, dtype=dt, device=stream.device)
+    nblk = region_blocks(h["shape"], h["block"], lo, hi) if all(b > a for a, b in zip(lo, hi)) else 1
+    if status is not None and status.numel() < nblk:
+        raise SdcszError(ECAPACITY, "decompress_region status")
+    st = status if status is not None else torch.empty(max(nblk, 1), dtype=torch.uint8, device=stream.device)
+    w = ws if ws is not None else torch.empty(decompress_workspace_size(), dtype=torch.uint8, device=stream.device)
+    rep = Report()
+    lo_a = (ctypes.c_uint64 * 3)(*(lo + [0] * (3 - len(lo))))
+    hi_a = (ctypes.c_uint64 * 3)(*(hi + [0] * (3 - len(hi))))
+    rc = lib().sdcsz_decompress_region(ctypes.c_void_p(stream.data_ptr()), stream.numel(), lo_a, hi_a,
+                                       ctypes.c_void_p(res.data_ptr()), res.numel() * res.element_size(),
+                                       ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(w.data_ptr()), w.numel(),
+                                       ctypes.byref(rep) if report else None, _stream_handle(cuda_stream))
+    if rc not in (OK, ESDC):
+        raise SdcszError(rc, "decompress_region")
+    return rc, res, st[:nblk], (rep.as_dict() if report else None)
 
 
 def verify(stream, original=None, status=None, ws=None, cuda_stream=None):

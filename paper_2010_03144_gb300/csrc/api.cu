@@ -572,6 +572,59 @@ void* static_scratch_address() {
 }  // namespace
 }  // namespace sdcsz
 
+extern "C" int sdcsz_decompress_region(const void* d_stream, size_t nbytes, const uint64_t* lo, const uint64_t* hi,
+                                       void* d_out, size_t out_bytes, uint8_t* d_block_status, void* d_ws,
+                                       size_t ws_bytes, sdcsz_report* report, void* stream) {
+  using namespace sdcsz;
+  if (!d_stream || !d_ws || !lo || !hi) return SDCSZ_EINVAL;
+  if (nbytes < (size_t)kHeaderBytes) return SDCSZ_EFORMAT;
+  if (ws_bytes < sdcsz_decompress_workspace_size()) return SDCSZ_ECAPACITY;
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255) return SDCSZ_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t hb[kHeaderBytes];
+  cudaGetLastError();
+  if (cudaMemcpyAsync(hb, d_stream, kHeaderBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SDCSZ_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SDCSZ_ECUDA;
+  Hdr h;
+  int rc = parse_header(hb, nbytes, &h, nullptr);
+  if (rc) return rc;
+  // the box in padded 3D coordinates
+  uint64_t lo3[3] = {0, 0, 0}, hi3[3] = {1, 1, 1}, pts = 1, nblk = 1;
+  const int off = 3 - h.g.ndim;
+  for (int a = 0; a < h.g.ndim; ++a) {
+    if (lo[a] >= hi[a] || hi[a] > h.g.d[off + a]) return SDCSZ_EINVAL;
+    lo3[off + a] = lo[a];
+    hi3[off + a] = hi[a];
+    pts *= hi[a] - lo[a];
+    nblk *= (hi[a] - 1) / h.g.B[off + a] - lo[a] / h.g.B[off + a] + 1;
+  }
+  if (!d_out || out_bytes < pts * (h.g.dtype ? 8 : 4)) return d_out ? SDCSZ_ECAPACITY : SDCSZ_EINVAL;
+  State* st = static_cast<State*>(d_ws);
+  if (cudaMemsetAsync(st, 0, sizeof(State), s) != cudaSuccess) return SDCSZ_ECUDA;
+  Launch L;
+  L.stream = s;
+  L.sms = sm_count();
+  {
+    NvtxRange r("sdcsz decode region");
+    launch_region(static_cast<const uint8_t*>(d_stream), nbytes, h, d_out, lo3, hi3, d_block_status, st, L);
+  }
+  if (cudaGetLastError() != cudaSuccess) return SDCSZ_ECUDA;
+  if (report) {
+    State hs;
+    rc = read_state(st, s, &hs);
+    if (rc) return rc;
+    hs.n_reg = h.n_reg;
+    hs.n_unpred = h.n_unpred;
+    hs.total_bytes = h.total;
+    hs.eb = h.eb;
+    fill_report(hs, nblk, report);
+    rc = map_error(hs.error);
+    if (rc) return rc;
+    if (hs.uncorrectable) return SDCSZ_ESDC;
+  }
+  return SDCSZ_OK;
+}
+
 extern "C" int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap,
                                       size_t* out_bytes, sdcsz_report* report, void* stream) {
   Geo g;

@@ -200,10 +200,38 @@ __device__ __forceinline__ void pair_table(uint2* lut2, const uint32_t* lut) {
 }
 
 // ---------------------------------------------------------------- generic path
-template <typename T, int NDIM>
+// Where the generic decoder stores a block's values: the whole field (or nowhere when
+// verifying), or a dense sub-box of the field (region decompression).
+template <typename T>
+struct FieldSink {
+  T* field;
+  __device__ __forceinline__ T* row(const Geo& g, const Box& x, uint32_t i, uint32_t j) const {
+    return field ? field + row_base(g, x, i, j) : nullptr;
+  }
+  __device__ __forceinline__ bool col(const Box&, uint32_t) const { return true; }
+};
+
+template <typename T>
+struct RegionSink {
+  T* out;
+  uint64_t lo[3], hi[3];  // the box in padded 3D coordinates, [lo, hi)
+  // element l of the block row is at row(...)[l] (dereferenced only where col() holds)
+  __device__ __forceinline__ T* row(const Geo&, const Box& x, uint32_t i, uint32_t j) const {
+    const uint64_t gi = x.org[0] + i, gj = x.org[1] + j;
+    if (gi < lo[0] || gi >= hi[0] || gj < lo[1] || gj >= hi[1]) return nullptr;
+    const int64_t r = (int64_t)(((gi - lo[0]) * (hi[1] - lo[1]) + (gj - lo[1])) * (hi[2] - lo[2]));
+    return out + (r + ((int64_t)x.org[2] - (int64_t)lo[2]));
+  }
+  __device__ __forceinline__ bool col(const Box& x, uint32_t l) const {
+    const uint64_t gl = x.org[2] + l;
+    return gl >= lo[2] && gl < hi[2];
+  }
+};
+
+template <typename T, int NDIM, class Sink = FieldSink<T>>
 __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const uint8_t* lim, const Hdr& h,
                                             const BlockIn& bi, const Tables& tb, Walker<T, NDIM>& wk,
-                                            T* __restrict__ field, const T* __restrict__ orig, uint32_t kinj,
+                                            const Sink sink, const T* __restrict__ orig, uint32_t kinj,
                                             uint32_t bitinj, unsigned long long* sum_out, unsigned long long* viol,
                                             double* maxerr) {
   const Geo& g = h.g;
@@ -225,6 +253,7 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
   for (uint32_t i = 0; i < x.e[0]; ++i) {
     for (uint32_t j = 0; j < x.e[1]; ++j) {
       const uint64_t rb = row_base(g, x, i, j);
+      T* dst = sink.row(g, x, i, j);
       wk.row_start();
       for (uint32_t l = 0; l < x.e[2]; ++l, ++k) {
         const int q = ok ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : -1;
@@ -242,7 +271,7 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
         }
         if (k == kinj) xr = FT<T>::flip(xr, bitinj);
         if (!reg) wk.commit(j, l, xr);
-        if (field) field[rb + l] = xr;
+        if (dst && sink.col(x, l)) dst[l] = xr;
         if (orig) {
           const T xo = orig[rb + l];
           bool bad;
@@ -598,6 +627,51 @@ __device__ __forceinline__ void find_inj(const sdcsz_flip* flips, uint32_t nflip
   if (nflips && find_flip(flips, nflips, SDCSZ_SITE_DECOMP, b, &idx, bit)) *k = (uint32_t)min(idx, (uint64_t)kNone - 1);
 }
 
+// The payload, unpredictable and coefficient offsets of block b from its group's table entry
+// plus the block-table entries before it in the group: eight 16-bit entries per 16-byte load
+// (the sections are 16-byte aligned and a group starts at a multiple of 256 entries) and the
+// regression flags by whole bitmap words. False when the entries point outside the stream.
+__device__ __forceinline__ bool place_block(const uint8_t* __restrict__ s, const Hdr& h, uint64_t b, BlockIn* out) {
+  (void)h.g;
+  const uint64_t gid = b / kGroup;
+  const uint8_t* gp = s + h.L.groups + 24 * gid;
+  unsigned long long pay = ld_u64(gp), un = ld_u64(gp + 8), rg = ld_u64(gp + 16);
+  // sums over the group's blocks before b: eight 16-bit entries per 16-byte load (the
+  // sections are 16-byte aligned and a group starts at a multiple of 256 entries), then the
+  // partial last load; regression flags by whole bitmap words
+  const uint64_t q0 = gid * kGroup, nq = b - q0;
+  const uint4* sz4 = reinterpret_cast<const uint4*>(s + h.L.sizes + 2 * q0);
+  const uint4* uc4 = reinterpret_cast<const uint4*>(s + h.L.ucounts + 2 * q0);
+  auto sum16 = [](uint4 v, uint32_t n) {  // sum of the first n (<= 8) 16-bit entries
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t t = 0;
+#pragma unroll
+    for (uint32_t m = 0; m < 8; ++m)
+      if (m < n) t += (w[m >> 1] >> (16 * (m & 1))) & 0xffffu;
+    return t;
+  };
+  for (uint64_t q = 0; q < nq; q += 8) {
+    const uint32_t n = (uint32_t)min((uint64_t)8, nq - q);
+    pay += sum16(__ldg(sz4 + q / 8), n);
+    un += sum16(__ldg(uc4 + q / 8), n);
+  }
+  const uint32_t* bm = reinterpret_cast<const uint32_t*>(s + h.L.bitmap) + q0 / 32;
+  for (uint64_t q = 0; q < nq; q += 32) {
+    const uint32_t n = (uint32_t)min((uint64_t)32, nq - q);
+    const uint32_t word = __ldg(bm + q / 32);
+    rg += __popc(n == 32 ? word : (word & ((1u << n) - 1)));
+  }
+  BlockIn& bi = *out;
+  bi.b = b;
+  bi.pay_off = pay;
+  bi.un_off = un;
+  bi.size = *reinterpret_cast<const uint16_t*>(s + h.L.sizes + 2 * b);
+  bi.ucnt = *reinterpret_cast<const uint16_t*>(s + h.L.ucounts + 2 * b);
+  const bool reg = (*reinterpret_cast<const uint32_t*>(s + h.L.bitmap + 4 * (b / 32)) >> (b % 32)) & 1u;
+  bi.reg_idx = reg ? (int64_t)rg : -1;
+  return !(pay + bi.size > h.payload_bytes || un + bi.ucnt > h.n_unpred || (reg && rg >= h.n_reg));
+}
+
 // Generic kernel: edge blocks (or all blocks when `all`).
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
@@ -645,7 +719,7 @@ __global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ s, u
       find_inj(flips, nflips, b, &kinj, &bitinj);
       const uint8_t stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv,
                                                      double* me) {
-        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, field, orig, first ? kinj : kNone, bitinj, sum, nv, me);
+        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone, bitinj, sum, nv, me);
       }, acc);
       if (status) status[b] = stv;
     }
@@ -677,44 +751,10 @@ __global__ void __launch_bounds__(256) k_decode_edges(const uint8_t* __restrict_
   if (e < count) {
     const Geo& g = h.g;
     const uint64_t b = edge_block(g, e);
-    const uint64_t gid = b / kGroup;
-    const uint8_t* gp = s + h.L.groups + 24 * gid;
-    unsigned long long pay = ld_u64(gp), un = ld_u64(gp + 8), rg = ld_u64(gp + 16);
-    // sums over the group's blocks before b: eight 16-bit entries per 16-byte load (the
-    // sections are 16-byte aligned and a group starts at a multiple of 256 entries), then the
-    // partial last load; regression flags by whole bitmap words
-    const uint64_t q0 = gid * kGroup, nq = b - q0;
-    const uint4* sz4 = reinterpret_cast<const uint4*>(s + h.L.sizes + 2 * q0);
-    const uint4* uc4 = reinterpret_cast<const uint4*>(s + h.L.ucounts + 2 * q0);
-    auto sum16 = [](uint4 v, uint32_t n) {  // sum of the first n (<= 8) 16-bit entries
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-      uint32_t t = 0;
-#pragma unroll
-      for (uint32_t m = 0; m < 8; ++m)
-        if (m < n) t += (w[m >> 1] >> (16 * (m & 1))) & 0xffffu;
-      return t;
-    };
-    for (uint64_t q = 0; q < nq; q += 8) {
-      const uint32_t n = (uint32_t)min((uint64_t)8, nq - q);
-      pay += sum16(__ldg(sz4 + q / 8), n);
-      un += sum16(__ldg(uc4 + q / 8), n);
-    }
-    const uint32_t* bm = reinterpret_cast<const uint32_t*>(s + h.L.bitmap) + q0 / 32;
-    for (uint64_t q = 0; q < nq; q += 32) {
-      const uint32_t n = (uint32_t)min((uint64_t)32, nq - q);
-      const uint32_t word = __ldg(bm + q / 32);
-      rg += __popc(n == 32 ? word : (word & ((1u << n) - 1)));
-    }
     BlockIn bi;
-    bi.b = b;
-    bi.pay_off = pay;
-    bi.un_off = un;
-    bi.size = *reinterpret_cast<const uint16_t*>(s + h.L.sizes + 2 * b);
-    bi.ucnt = *reinterpret_cast<const uint16_t*>(s + h.L.ucounts + 2 * b);
-    const bool reg = (*reinterpret_cast<const uint32_t*>(s + h.L.bitmap + 4 * (b / 32)) >> (b % 32)) & 1u;
-    bi.reg_idx = reg ? (int64_t)rg : -1;
+    const bool placed = place_block(s, h, b, &bi);
     uint8_t stv;
-    if (pay + bi.size > h.payload_bytes || un + bi.ucnt > h.n_unpred || (reg && rg >= h.n_reg)) {
+    if (!placed) {
       atomicOr(&st->error, ERR_FORMAT);
       stv = SDCSZ_BLOCK_BAD;
       ++acc.bad;
@@ -722,10 +762,63 @@ __global__ void __launch_bounds__(256) k_decode_edges(const uint8_t* __restrict_
       uint32_t kinj, bitinj;
       find_inj(flips, nflips, b, &kinj, &bitinj);
       stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv, double* me) {
-        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, field, orig, first ? kinj : kNone, bitinj, sum, nv, me);
+        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone, bitinj,
+                                       sum, nv, me);
       }, acc);
     }
     if (status) status[b] = stv;
+  }
+  acc.commit(st);
+}
+
+// Region decompression: the blocks that intersect a box, one thread each (enumerated over the
+// box's block range), decoded and verified on their own (Sec. 5.1 random access) and stored
+// into a dense array of the box's shape.
+struct Region {
+  uint64_t lo[3], hi[3];  // the box, padded 3D coordinates, [lo, hi)
+  uint64_t c0[3], nc[3];  // its block range: first block coordinate and count per axis
+};
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_decode_region(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* out,
+                                                       Region rgn, uint8_t* status, State* st, uint64_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Smem sm;
+  uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
+  const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
+  if (!cta_tables(s, h, sm, lut, syms, st)) return;
+  const Tables tb = {lut, &sm.cn, syms, h.n_live, nullptr};
+  const uint8_t* lim = s + nbytes;
+  Walker<T, NDIM> wk;
+  wk.base = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
+  wk.stride = blockDim.x;
+  wk.B2 = h.g.B[2];
+  wk.sr = h.g.B[1] * h.g.B[2];
+  Acc acc;
+  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) {
+    const Geo& g = h.g;
+    const uint64_t r2 = e % rgn.nc[2], r = e / rgn.nc[2];
+    const uint64_t r1 = r % rgn.nc[1], r0 = r / rgn.nc[1];
+    const uint64_t b = ((rgn.c0[0] + r0) * g.nbd[1] + (rgn.c0[1] + r1)) * g.nbd[2] + (rgn.c0[2] + r2);
+    RegionSink<T> sink;
+    sink.out = out;
+    for (int a = 0; a < 3; ++a) {
+      sink.lo[a] = rgn.lo[a];
+      sink.hi[a] = rgn.hi[a];
+    }
+    BlockIn bi;
+    uint8_t stv;
+    if (!place_block(s, h, b, &bi)) {
+      atomicOr(&st->error, ERR_FORMAT);
+      stv = SDCSZ_BLOCK_BAD;
+      ++acc.bad;
+    } else {
+      stv = verify_block(s, h, b, [&](bool, unsigned long long* sum, unsigned long long* nv, double* me) {
+        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, sink, nullptr, kNone, 0, sum, nv, me);
+      }, acc);
+    }
+    if (status) status[e] = stv;
   }
   acc.commit(st);
 }
@@ -802,7 +895,7 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
       const uint8_t stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv,
                                                      double* me) {
         if (!safe)
-          return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, field, orig, first ? kinj : kNone, bitinj, sum, nv,
+          return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone, bitinj, sum, nv,
                                          me);
         if (first && kinj != kNone)
           return fast_dispatch<T, NDIM, B0, B1, B2, true, WRITE>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2,
@@ -915,6 +1008,30 @@ void launch_decode_t(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* fiel
   else run_generic<T, 1>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, Lg);
   if (fast) try_fast<T>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
   fk.join();
+}
+
+template <typename T>
+void launch_region_t(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const Region& rgn, uint8_t* status,
+                     State* st, const Launch& L) {
+  const uint64_t count = rgn.nc[0] * rgn.nc[1] * rgn.nc[2];
+  if (!count) return;
+  const size_t per = (size_t)walker_slots(h.g.ndim, h.g.B) * sizeof(T);
+  uint32_t threads = 256;
+  while (threads > 64 && per * threads > 192 * 1024) threads >>= 1;
+  const size_t smem = (4u << kLutBits) + per * threads;
+  const unsigned grid = (unsigned)((count + threads - 1) / threads);
+  T* o = static_cast<T*>(out);
+  if (h.g.ndim == 3) {
+    allow_smem(reinterpret_cast<const void*>(k_decode_region<T, 3>), smem);
+    k_decode_region<T, 3><<<grid, threads, smem, L.stream>>>(s, nbytes, h, o, rgn, status, st, count);
+  } else if (h.g.ndim == 2) {
+    allow_smem(reinterpret_cast<const void*>(k_decode_region<T, 2>), smem);
+    k_decode_region<T, 2><<<grid, threads, smem, L.stream>>>(s, nbytes, h, o, rgn, status, st, count);
+  } else {
+    allow_smem(reinterpret_cast<const void*>(k_decode_region<T, 1>), smem);
+    k_decode_region<T, 1><<<grid, threads, smem, L.stream>>>(s, nbytes, h, o, rgn, status, st, count);
+  }
+  note_launch();
 }
 
 }  // namespace

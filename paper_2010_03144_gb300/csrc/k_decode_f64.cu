@@ -9,4 +9,16 @@ void launch_decode_f64(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* fi
   kdec::launch_decode_t<double>(s, nbytes, h, field, status, original, st, write, flips, nflips, L);
 }
 
+void launch_region_f64(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
+                        const uint64_t hi[3], uint8_t* status, State* st, const Launch& L) {
+  kdec::Region r;
+  for (int a = 0; a < 3; ++a) {
+    r.lo[a] = lo[a];
+    r.hi[a] = hi[a];
+    r.c0[a] = lo[a] / h.g.B[a];
+    r.nc[a] = hi[a] > lo[a] ? (hi[a] - 1) / h.g.B[a] - r.c0[a] + 1 : 0;
+  }
+  kdec::launch_region_t<double>(s, nbytes, h, out, r, status, st, L);
+}
+
 }  // namespace sdcsz

@@ -80,6 +80,17 @@ void launch_decode_f64(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* fi
                        const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
                        const Launch& L);
 
+void launch_region_f32(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
+                       const uint64_t hi[3], uint8_t* status, State* st, const Launch& L);
+void launch_region_f64(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
+                       const uint64_t hi[3], uint8_t* status, State* st, const Launch& L);
+
+void launch_region(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
+                   const uint64_t hi[3], uint8_t* status, State* st, const Launch& L) {
+  if (h.g.dtype == 0) launch_region_f32(s, nbytes, h, out, lo, hi, status, st, L);
+  else launch_region_f64(s, nbytes, h, out, lo, hi, status, st, L);
+}
+
 void launch_decode(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
                    const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
                    const Launch& L) {

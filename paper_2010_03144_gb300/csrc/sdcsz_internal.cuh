@@ -612,6 +612,9 @@ struct Hdr {
   uint64_t n_reg, n_unpred, payload_bytes, total;
   double eb;
 };
+// Blocks intersecting the box [lo, hi) (padded 3D coordinates) into a dense array of its shape.
+void launch_region(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
+                   const uint64_t hi[3], uint8_t* status, State* st, const Launch& L);
 void launch_decode(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
                    const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
                    const Launch& L);
