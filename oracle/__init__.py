@@ -28,6 +28,7 @@ _lib = None
 OK, EINVAL, ECAPACITY, EFORMAT, ESDC = 0, -1, -2, -3, -4
 SITES = {"input": 1, "code": 2, "coef": 3, "pred": 4, "recon": 5, "decomp": 6}
 PREDICTORS = {"auto": 0, "lorenzo": 1, "regression": 2}
+ENCODINGS = {"raw": 0, "compact": 1}
 DEFAULT_BLOCK = {1: 128, 2: 12, 3: 6}
 
 
@@ -42,7 +43,7 @@ class Params(ctypes.Structure):
         ("quant_bins", ctypes.c_uint32),
         ("abft", ctypes.c_uint32),
         ("predictor", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("encoding", ctypes.c_uint32),
     ]
 
 
@@ -107,6 +108,9 @@ def lib():
         L.orc_canonical_codes.restype = None
         L.orc_regression.argtypes = [vp, u32, u32, vp, vp]
         L.orc_compress_block.argtypes = [vp, P, ctypes.c_double, u64, vp, vp, vp, vp, ctypes.POINTER(u64)]
+        L.orc_truncate_unpredictable.argtypes = [vp, u32, ctypes.c_double, vp]
+        L.orc_quantize_coefficient.argtypes = [ctypes.c_float, u32, u32, vp, ctypes.c_double, u32,
+                                               ctypes.POINTER(ctypes.c_int32), vp]
         L.orc_error_bound.argtypes = [vp, P]
         L.orc_error_bound.restype = ctypes.c_double
         _lib = L
@@ -117,7 +121,8 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto") -> Params:
+def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
+                encoding="raw") -> Params:
     ndim = len(shape)
     p = Params()
     p.ndim = ndim
@@ -135,6 +140,7 @@ def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=Tr
     p.quant_bins = int(bins)
     p.abft = 1 if abft else 0
     p.predictor = PREDICTORS[predictor]
+    p.encoding = ENCODINGS[encoding]
     return p
 
 
@@ -160,11 +166,13 @@ def compress_bound(p: Params) -> int:
 
 
 def compress(field: np.ndarray, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-             flips=None):
+             flips=None, encoding="raw"):
     """Alg. 1. Returns (stream bytes as uint8 array, report dict). ``flips`` is a list of
-    (site, block, index, bit) soft errors to simulate (see the site list in the C source)."""
+    (site, block, index, bit) soft errors to simulate (see the site list in the C source);
+    ``encoding`` is "raw" (coefficients and unpredictable values in sections of their own) or
+    "compact" (both quantized / truncated and kept in the block's payload)."""
     field = np.ascontiguousarray(field)
-    p = make_params(field.shape, field.dtype, eb, eb_mode, block, bins, abft, predictor)
+    p = make_params(field.shape, field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
     cap = compress_bound(p)
     out = np.zeros(cap, dtype=np.uint8)
     nbytes = ctypes.c_uint64()
@@ -186,7 +194,8 @@ def read_header(stream: np.ndarray):
         return None
     shape = tuple(int(p.dims[a]) for a in range(p.ndim))
     return {"shape": shape, "dtype": np.float32 if p.dtype == 0 else np.float64,
-            "block": tuple(int(p.block[a]) for a in range(p.ndim)), "total": total.value, "abft": bool(p.abft)}
+            "block": tuple(int(p.block[a]) for a in range(p.ndim)), "total": total.value, "abft": bool(p.abft),
+            "encoding": "compact" if p.encoding == 1 else "raw"}
 
 
 def decompress(stream: np.ndarray, flips=None):
@@ -243,10 +252,11 @@ def regression(block_values: np.ndarray):
     return bool(ok), coef[: v.ndim + 1]
 
 
-def compress_block(field: np.ndarray, eb_abs: float, b: int, block=None, bins=65536, predictor="auto"):
+def compress_block(field: np.ndarray, eb_abs: float, b: int, block=None, bins=65536, predictor="auto",
+                   encoding="raw"):
     """One block of Algorithm 1's prediction loop at a given absolute bound (no ABFT verification)."""
     field = np.ascontiguousarray(field)
-    p = make_params(field.shape, field.dtype, eb_abs, "abs", block, bins, False, predictor)
+    p = make_params(field.shape, field.dtype, eb_abs, "abs", block, bins, False, predictor, encoding)
     codes = np.zeros(4096, dtype=np.uint16)
     coef = np.zeros(4, dtype=field.dtype)
     is_reg = np.zeros(1, dtype=np.uint8)
@@ -259,6 +269,28 @@ def compress_block(field: np.ndarray, eb_abs: float, b: int, block=None, bins=65
     n = npts.value
     return {"codes": codes[:n].copy(), "coef": coef[: field.ndim + 1].copy(), "regression": bool(is_reg[0]),
             "sum_q": int(sums[0]), "isum_q": int(sums[1]), "sum_dc": int(sums[2])}
+
+
+def truncate_unpredictable(x, eb, dtype):
+    """Compact encoding: (value an unpredictable x decompresses to, mantissa bits kept)."""
+    dt = np.dtype(dtype)
+    v = np.array([x], dtype=dt)
+    out = np.zeros(1, dtype=dt)
+    m = lib().orc_truncate_unpredictable(_ptr(v), 0 if dt == np.float32 else 1, float(eb), _ptr(out))
+    return out[0], m
+
+
+def quantize_coefficient(c, eb, dtype, block, a):
+    """Compact encoding: (ok, integer, dequantized value) of coefficient a of a block shape."""
+    dt = np.dtype(dtype)
+    blk = np.ascontiguousarray(block, dtype=np.uint32)
+    k = ctypes.c_int32()
+    out = np.zeros(1, dtype=dt)
+    ok = lib().orc_quantize_coefficient(float(np.float32(c)), 0 if dt == np.float32 else 1, blk.size, _ptr(blk),
+                                        float(eb), int(a), ctypes.byref(k), _ptr(out))
+    if ok < 0:
+        raise ValueError("bad block shape or coefficient index")
+    return bool(ok), int(k.value), out[0]
 
 
 def error_bound(field: np.ndarray, eb, eb_mode="rel") -> float:

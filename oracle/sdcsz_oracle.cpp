@@ -34,7 +34,13 @@
 //     the code checksums protect);
 //   * Huffman: (weight, creation order) tie-break, lengths limited to 24 bits by the
 //     JPEG (ITU T.81 Annex K.3) adjustment, canonical codes, MSB-first bit order;
-//   * the byte layout of the stream.
+//   * the byte layout of the stream;
+//   * the compact encoding (SZ's own coefficient and unpredictable-value encodings, kept
+//     block-local): regression coefficients as integer multiples of a step tied to the bound
+//     (slopes eb/(16 B_a), intercept eb/16, round half away from zero in double), written
+//     as length-prefixed zigzag integers at the head of the block's payload; unpredictable
+//     values truncated to the mantissa bits the bound needs and written right after their
+//     code 0.
 // Parity unpinned: the predictor-selection estimate (kappa, sample set) only changes the
 // compression ratio (Sec. 4.1.1) and is pinned by determinism and GPU/oracle equality only.
 
@@ -58,7 +64,7 @@ typedef struct {
   uint32_t quant_bins;  // even, 2..65536
   uint32_t abft;        // 1 = fault tolerant (ftrsz), 0 = plain independent blocks (rsz)
   uint32_t predictor;   // 0 = select per block, 1 = Lorenzo only, 2 = regression only
-  uint32_t reserved;
+  uint32_t encoding;    // 0 = raw coefficient / unpredictable sections, 1 = compact
 } orc_params;
 
 typedef struct {
@@ -333,11 +339,92 @@ bool select_regression(float Ereg, float Elor, uint64_t S, int ndim, float ebf) 
   return Ereg < total;
 }
 
+// ---------------------------------------------------------------- compact encoding
+// Steps of the coefficient quantization for an absolute bound E (the dtype value): slope a
+// moves the prediction by at most (B_a - 1) * step_a / 2 across the block and the intercept by
+// step / 2, so the rounded coefficients shift a prediction by less than eb / 8 in total.
+struct CoefSteps {
+  double step[4], inv[4];
+};
+
+CoefSteps coef_steps(const Geom& g, double E) {
+  CoefSteps q;
+  const int off = 3 - g.ndim;
+  for (int a = 0; a < 4; ++a) q.step[a] = q.inv[a] = 0.0;
+  for (int a = 0; a < g.ndim; ++a) {
+    const double d = 16.0 * (double)g.B[off + a];
+    q.step[a] = E / d;
+    q.inv[a] = d / E;
+  }
+  q.step[g.ndim] = E / 16.0;
+  q.inv[g.ndim] = 16.0 / E;
+  return q;
+}
+
+// Nearest multiple of the step (halves away from zero); false when it is not finite or not
+// below 2^30 steps, which makes the block use Lorenzo.
+bool quantize_coef(float c, double inv, int32_t* k) {
+  const double t = (double)c * inv;
+  if (!(std::fabs(t) < 1073741824.0)) return false;
+  const double m = std::floor(std::fabs(t) + 0.5);
+  *k = (int32_t)(t < 0.0 ? -m : m);
+  return true;
+}
+
+template <typename T> T dequantize_coef(int32_t k, double step) { return (T)((double)k * step); }
+
+// Bit fields of the dtype: mantissa bits, exponent bits, exponent bias.
+template <typename T> struct Fmt;
+template <> struct Fmt<float> {
+  typedef uint32_t U;
+  static constexpr int M = 23, E = 8, BIAS = 127;
+};
+template <> struct Fmt<double> {
+  typedef uint64_t U;
+  static constexpr int M = 52, E = 11, BIAS = 1023;
+};
+
+template <typename T> typename Fmt<T>::U raw_bits(T x) {
+  typename Fmt<T>::U u;
+  std::memcpy(&u, &x, sizeof(T));
+  return u;
+}
+
+template <typename T> T from_raw(typename Fmt<T>::U u) {
+  T x;
+  std::memcpy(&x, &u, sizeof(T));
+  return x;
+}
+
+// floor(log2(eb)) of a normal bound
+template <typename T> int bound_exponent(T eb) {
+  return (int)((raw_bits<T>(eb) >> Fmt<T>::M) & ((1u << Fmt<T>::E) - 1)) - Fmt<T>::BIAS;
+}
+
+// Mantissa bits an unpredictable value keeps: with x in [2^ex, 2^(ex+1)), dropping all but m
+// mantissa bits errs by less than 2^(ex-m), which is at most 2^eexp <= eb once m >= ex - eexp.
+// Zeros, subnormals, infinities and NaNs keep every bit.
+template <typename T> int kept_mantissa_bits(T x, int eexp) {
+  const int Ex = (int)((raw_bits<T>(x) >> Fmt<T>::M) & ((1u << Fmt<T>::E) - 1));
+  if (Ex == 0 || Ex == (1 << Fmt<T>::E) - 1) return Fmt<T>::M;
+  const int m = Ex - Fmt<T>::BIAS - eexp;
+  return m < 0 ? 0 : (m > Fmt<T>::M ? Fmt<T>::M : m);
+}
+
+// The value an unpredictable point decompresses to: x with the dropped mantissa bits zero.
+template <typename T> T truncate_unpredictable(T x, int eexp) {
+  const int drop = Fmt<T>::M - kept_mantissa_bits<T>(x, eexp);
+  typename Fmt<T>::U u = raw_bits<T>(x);
+  if (drop > 0) u &= ~((((typename Fmt<T>::U)1) << drop) - 1);
+  return from_raw<T>(u);
+}
+
 // ---------------------------------------------------------------- per-block compression
 struct Ctx {
   Geom g;
   int predictor_mode = 0;
   bool abft = true;
+  bool compact = false;
   uint32_t bins = 65536, R = 32768;
   const orc_flip* flips = nullptr;
   int nflips = 0;
@@ -348,6 +435,7 @@ struct BlockResult {
   uint32_t ext[3];
   bool regression = false;
   T coef[4] = {0, 0, 0, 0};
+  int32_t kq[4] = {0, 0, 0, 0};  // compact encoding: the stored coefficient integers
   std::vector<uint16_t> code;  // q_bin[] (Sec. 4.2.3): 0 = unpredictable, else q + R
   std::vector<T> vin;          // verified input values, the source of unpredictable values
   uint64_t sum_q = 0, isum_q = 0, sum_dc = 0;
@@ -368,6 +456,7 @@ struct Prep {
   float coef[4] = {0, 0, 0, 0};
   bool finite = false;
   float Ereg = 0.0f, Elor = 0.0f;
+  int32_t kq[4] = {0, 0, 0, 0};  // compact encoding: the coefficients as multiples of their steps
 };
 
 template <typename T>
@@ -399,6 +488,30 @@ bool indicator_of(const Ctx& c, const Prep& pr, const uint32_t e[3], float ebf) 
   return select_regression(pr.Ereg, pr.Elor, sample_points(c.g.ndim, e), c.g.ndim, ebf);
 }
 
+// Compact encoding, once the bound is known: the coefficients become integers (a coefficient
+// that cannot be one makes the block use Lorenzo), and the selection estimate of regression is
+// taken with the coefficients the block would predict with, on the values of the first pass.
+template <typename T>
+void quantize_prep(const Ctx& c, const T* field, uint64_t b, T eb, Prep* pr) {
+  if (!pr->finite) return;
+  const CoefSteps qs = coef_steps(c.g, (double)eb);
+  float cq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int a = 0; a <= c.g.ndim; ++a) {
+    if (!quantize_coef(pr->coef[a], qs.inv[a], &pr->kq[a])) {
+      pr->finite = false;
+      return;
+    }
+    cq[a] = (float)dequantize_coef<T>(pr->kq[a], qs.step[a]);
+  }
+  for (int a = 0; a < 4; ++a) pr->coef[a] = cq[a];
+  if (c.predictor_mode == 0) {
+    std::vector<T> v;
+    uint32_t e[3];
+    load_block<T>(c.g, field, b, &v, e);
+    selection_estimates<T>(v.data(), e, c.g.ndim, pr->coef, &pr->Ereg, &pr->Elor);
+  }
+}
+
 // Algorithm 1's prediction loop for one block: verify the input with sum_in/isum_in, pick f()
 // from the indicator, then predict every point with duplicated prediction and
 // reconstruction (f_dup, dec_dup) and take the block checksums (sum_q/isum_q, sum_dc).
@@ -424,11 +537,23 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
 
   const bool use_reg = indicator_of(c, pr, e, (float)eb);
   out->regression = use_reg;
-  for (int a = 0; a < 4; ++a) out->coef[a] = (T)pr.coef[a];
-  for (int a = 0; a <= g.ndim; ++a) {
-    const orc_flip* f = find_flip(c, SITE_COEF, b, (uint64_t)a);
-    if (f) out->coef[a] = Bits<T>::flip(out->coef[a], f->bit);
+  if (c.compact) {
+    // the stored integers are what a memory error strikes; both sides dequantize them
+    const CoefSteps qs = coef_steps(g, (double)eb);
+    for (int a = 0; a < 4; ++a) out->kq[a] = pr.kq[a];
+    for (int a = 0; a <= g.ndim; ++a) {
+      const orc_flip* f = find_flip(c, SITE_COEF, b, (uint64_t)a);
+      if (f) out->kq[a] = (int32_t)((uint32_t)out->kq[a] ^ (1u << (f->bit & 31)));
+    }
+    for (int a = 0; a < 4; ++a) out->coef[a] = a <= g.ndim ? dequantize_coef<T>(out->kq[a], qs.step[a]) : (T)0;
+  } else {
+    for (int a = 0; a < 4; ++a) out->coef[a] = (T)pr.coef[a];
+    for (int a = 0; a <= g.ndim; ++a) {
+      const orc_flip* f = find_flip(c, SITE_COEF, b, (uint64_t)a);
+      if (f) out->coef[a] = Bits<T>::flip(out->coef[a], f->bit);
+    }
   }
+  const int eexp = bound_exponent<T>(eb);
 
   // the per-point loop
   const T Rh = (T)c.R - (T)0.5;
@@ -479,7 +604,10 @@ void compress_block(const Ctx& c, const T* field, uint64_t b, T eb, T inv2, uint
             xr = xd;
           }
         }
-        if (code == 0) out->n_unpred++;             // unpredictable, stored raw
+        if (code == 0) {                            // unpredictable: stored raw, or truncated
+          out->n_unpred++;
+          if (c.compact) xr = truncate_unpredictable<T>(x, eexp);
+        }
         out->code[k] = code;
         xrec[k] = xr;
         out->sum_q += code;                         // sum_q, isum_q
@@ -590,7 +718,7 @@ void canon_from_lengths(const uint8_t* len, uint32_t nsym, Canon* c, std::vector
 struct BitWriter {
   std::vector<uint8_t> bytes;
   uint64_t nbits = 0;
-  void put(uint32_t code, uint32_t len) {  // MSB-first
+  void put(uint64_t code, uint32_t len) {  // the low len bits of code, MSB-first
     for (int s = (int)len - 1; s >= 0; --s) {
       if (nbits % 8 == 0) bytes.push_back(0);
       if ((code >> s) & 1u) bytes.back() |= (uint8_t)(0x80u >> (nbits % 8));
@@ -599,6 +727,24 @@ struct BitWriter {
   }
 };
 
+// Compact encoding: a coefficient integer as its zigzag value z (0, -1, 1, -2, ... -> 0, 1, 2,
+// 3, ...), written as the bit length n of z in 6 bits, then the n - 1 bits of z below its
+// leading one.
+void put_coef_int(BitWriter* bw, int32_t k) {
+  const uint32_t z = ((uint32_t)k << 1) ^ (k < 0 ? 0xffffffffu : 0u);
+  uint32_t n = 0;
+  while (n < 32 && (z >> n) != 0) ++n;
+  bw->put(n, 6);
+  if (n > 1) bw->put(z & ((1u << (n - 1)) - 1u), n - 1);
+}
+
+// Compact encoding: an unpredictable value as its sign, exponent and kept mantissa bits.
+template <typename T>
+void put_unpredictable(BitWriter* bw, T x, int eexp) {
+  const int m = kept_mantissa_bits<T>(x, eexp);
+  bw->put((uint64_t)(raw_bits<T>(x) >> (Fmt<T>::M - m)), (uint32_t)(1 + Fmt<T>::E + m));
+}
+
 // ---------------------------------------------------------------- stream layout
 uint64_t align16(uint64_t x) { return (x + 15) & ~(uint64_t)15; }
 
@@ -606,7 +752,9 @@ struct Layout {
   uint64_t table, groups, sizes, ucounts, bitmap, sumdc, coef, unpred, payload;
 };
 
-Layout make_layout(const Geom& g, bool abft, uint64_t n_live, uint64_t n_reg, uint64_t n_unpred) {
+// The compact encoding keeps coefficients and unpredictable values in the payload, so its
+// coefficient and unpredictable sections are empty.
+Layout make_layout(const Geom& g, bool abft, bool compact, uint64_t n_live, uint64_t n_reg, uint64_t n_unpred) {
   const uint64_t s = g.dtype ? 8 : 4;
   const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
   Layout L;
@@ -617,8 +765,8 @@ Layout make_layout(const Geom& g, bool abft, uint64_t n_live, uint64_t n_reg, ui
   L.bitmap = align16(L.ucounts + 2 * g.nb);
   L.sumdc = align16(L.bitmap + 4 * ((g.nb + 31) / 32));
   L.coef = align16(L.sumdc + (abft ? 8 * g.nb : 0));
-  L.unpred = align16(L.coef + s * (uint64_t)(g.ndim + 1) * n_reg);
-  L.payload = align16(L.unpred + s * n_unpred);
+  L.unpred = align16(L.coef + (compact ? 0 : s * (uint64_t)(g.ndim + 1) * n_reg));
+  L.payload = align16(L.unpred + (compact ? 0 : s * n_unpred));
   return L;
 }
 
@@ -634,7 +782,8 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   const Geom& g = c.g;
   if (!(p->eb > 0.0) || !std::isfinite(p->eb) || p->eb_mode > 1) return EINVAL_;
   if (p->quant_bins < 2 || p->quant_bins > 65536 || (p->quant_bins & 1)) return EINVAL_;
-  if (p->predictor > 2) return EINVAL_;
+  if (p->predictor > 2 || p->encoding > 1) return EINVAL_;
+  c.compact = p->encoding == 1;
   c.bins = p->quant_bins;
   c.R = p->quant_bins / 2;
   c.abft = p->abft != 0;
@@ -675,6 +824,8 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   const T eb = (T)ebd;
   if (!(eb > (T)0) || !std::isfinite(eb) || !std::isnormal(eb)) return EINVAL_;
   const T inv2 = (T)(1.0 / (2.0 * (double)eb));
+  if (c.compact)
+    for (uint64_t b = 0; b < g.nb; ++b) quantize_prep<T>(c, field_in, b, eb, &prep[b]);
 
   std::vector<T> field(field_in, field_in + g.N);  // working copy that soft errors may strike
   // memory errors in the input strike here, after its checksums (Sec. 6.1.2, mode A)
@@ -733,10 +884,14 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
       }
     }
     BitWriter bw;
+    if (c.compact && B.regression)
+      for (int a = 0; a <= g.ndim; ++a) put_coef_int(&bw, B.kq[a]);
+    const int eexp = bound_exponent<T>(eb);
     for (uint64_t k = 0; k < P; ++k) {
       uint16_t q = B.code[k];
       if (q == 0) ucount[b]++;
       bw.put(code_of[q], len[q]);
+      if (q == 0 && c.compact) put_unpredictable<T>(&bw, B.vin[k], eexp);
     }
     payload[b] = bw.bytes;
     payload_bytes += bw.bytes.size();
@@ -749,7 +904,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   // write the stream (Algorithm 1's output step, without the Zstd stage)
   const uint64_t s = sizeof(T);
   const uint64_t n_live = canon.symbols.size();
-  Layout L = make_layout(g, c.abft, n_live, n_reg, n_unpred);
+  Layout L = make_layout(g, c.abft, c.compact, n_live, n_reg, n_unpred);
   const uint64_t total = L.payload + payload_bytes;
   if (total > cap) return ECAPACITY;
   std::memset(out, 0, total);
@@ -763,6 +918,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   put<uint8_t>(out, 48, (uint8_t)c.abft);
   put<uint8_t>(out, 49, (uint8_t)p->predictor);
   put<uint8_t>(out, 50, (uint8_t)p->eb_mode);
+  put<uint8_t>(out, 51, (uint8_t)p->encoding);
   put<uint32_t>(out, 52, (uint32_t)n_live);
   put<double>(out, 56, (double)eb);
   put<double>(out, 64, p->eb);
@@ -788,12 +944,15 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
     if (B.regression) {
       uint32_t word = get<uint32_t>(out, L.bitmap + 4 * (b / 32));
       put<uint32_t>(out, L.bitmap + 4 * (b / 32), word | (1u << (b % 32)));
-      for (int a = 0; a <= g.ndim; ++a) put<T>(out, L.coef + s * ((g.ndim + 1) * rg + a), B.coef[a]);
+      if (!c.compact)
+        for (int a = 0; a <= g.ndim; ++a) put<T>(out, L.coef + s * ((g.ndim + 1) * rg + a), B.coef[a]);
       rg++;
     }
     if (c.abft) put<uint64_t>(out, L.sumdc + 8 * b, B.sum_dc);
-    for (uint64_t k = 0; k < B.code.size(); ++k)
-      if (B.code[k] == 0) put<T>(out, L.unpred + s * un++, B.vin[k]);
+    if (c.compact) un += ucount[b];
+    else
+      for (uint64_t k = 0; k < B.code.size(); ++k)
+        if (B.code[k] == 0) put<T>(out, L.unpred + s * un++, B.vin[k]);
     if (!payload[b].empty()) std::memcpy(out + L.payload + pay, payload[b].data(), payload[b].size());
     pay += payload[b].size();
   }
@@ -808,7 +967,7 @@ struct Parsed {
   Geom g;
   orc_params p;
   uint32_t bins, R, n_live;
-  bool abft;
+  bool abft, compact;
   double eb;
   uint64_t n_reg, n_unpred, payload_bytes, total;
   Layout L;
@@ -831,6 +990,9 @@ int parse(const uint8_t* s, uint64_t n, Parsed* P) {
   P->p.abft = P->abft;
   P->p.predictor = get<uint8_t>(s, 49);
   P->p.eb_mode = get<uint8_t>(s, 50);
+  P->p.encoding = get<uint8_t>(s, 51);
+  if (P->p.encoding > 1) return EFORMAT;
+  P->compact = P->p.encoding == 1;
   P->n_live = get<uint32_t>(s, 52);
   P->eb = get<double>(s, 56);
   P->p.eb = get<double>(s, 64);
@@ -841,7 +1003,7 @@ int parse(const uint8_t* s, uint64_t n, Parsed* P) {
   P->payload_bytes = get<uint64_t>(s, 96);
   P->total = get<uint64_t>(s, 104);
   if (P->n_live > P->bins || P->n_reg > P->g.nb || P->n_unpred > P->g.N) return EFORMAT;
-  P->L = make_layout(P->g, P->abft, P->n_live, P->n_reg, P->n_unpred);
+  P->L = make_layout(P->g, P->abft, P->compact, P->n_live, P->n_reg, P->n_unpred);
   if (P->total != P->L.payload + P->payload_bytes || P->total > n) return EFORMAT;
   uint64_t kraft = 0, cnt = 0;
   for (uint32_t l = 0; l <= kMaxLen; ++l) {
@@ -875,6 +1037,53 @@ int decode_symbol(const uint8_t* pay, uint64_t* bit, uint64_t end, const Canon& 
   return -1;
 }
 
+// n raw bits (n <= 32) MSB-first from [bit, end); false when the block's bytes run out.
+bool read_bits(const uint8_t* pay, uint64_t* bit, uint64_t end, uint32_t n, uint32_t* v) {
+  uint32_t x = 0;
+  for (uint32_t t = 0; t < n; ++t) {
+    if (*bit >= end) return false;
+    x = (x << 1) | ((pay[*bit / 8] >> (7 - (*bit % 8))) & 1u);
+    ++*bit;
+  }
+  *v = x;
+  return true;
+}
+
+// Compact encoding: one length-prefixed zigzag coefficient integer.
+bool read_coef_int(const uint8_t* pay, uint64_t* bit, uint64_t end, int32_t* k) {
+  uint32_t n, low = 0;
+  if (!read_bits(pay, bit, end, 6, &n) || n > 32) return false;
+  if (n > 1 && !read_bits(pay, bit, end, n - 1, &low)) return false;
+  const uint32_t z = n == 0 ? 0u : ((n > 1 ? (1u << (n - 1)) : 1u) | low);
+  *k = (int32_t)((z >> 1) ^ (0u - (z & 1u)));
+  return true;
+}
+
+// Compact encoding: one truncated unpredictable value (sign, exponent, kept mantissa bits).
+template <typename T>
+bool read_unpredictable(const uint8_t* pay, uint64_t* bit, uint64_t end, int eexp, T* x) {
+  typedef typename Fmt<T>::U U;
+  uint32_t se;
+  if (!read_bits(pay, bit, end, 1 + Fmt<T>::E, &se)) return false;
+  const int Ex = (int)(se & ((1u << Fmt<T>::E) - 1));
+  int m = Fmt<T>::M;
+  if (Ex != 0 && Ex != (1 << Fmt<T>::E) - 1) {
+    m = Ex - Fmt<T>::BIAS - eexp;
+    m = m < 0 ? 0 : (m > Fmt<T>::M ? Fmt<T>::M : m);
+  }
+  U mant = 0;
+  for (int got = 0; got < m;) {
+    const uint32_t n = (uint32_t)std::min(32, m - got);
+    uint32_t v;
+    if (!read_bits(pay, bit, end, n, &v)) return false;
+    mant = (mant << n) | v;
+    got += (int)n;
+  }
+  const U u = ((U)se << Fmt<T>::M) | (mant << (Fmt<T>::M - m));
+  *x = from_raw<T>(u);
+  return true;
+}
+
 // One block of Algorithm 2's decompression loop: Huffman decode, then Lorenzo or regression.
 // Returns false on a malformed block.
 template <typename T>
@@ -891,13 +1100,22 @@ bool decompress_block(const Parsed& P, const uint8_t* s, uint64_t b, uint64_t pa
   const T eb = (T)P.eb;
   const uint64_t sz = sizeof(T);
   T coef[4] = {0, 0, 0, 0};
-  if (reg_idx >= 0)
-    for (int a = 0; a <= g.ndim; ++a) coef[a] = get<T>(s, P.L.coef + sz * ((g.ndim + 1) * (uint64_t)reg_idx + a));
   const uint8_t* pay = s + P.L.payload + pay_off;
   uint64_t bit = 0;
   const uint64_t end = 8 * size;
   uint64_t used = 0, k = 0;
   bool ok = true;
+  const int eexp = bound_exponent<T>(eb);
+  if (reg_idx >= 0 && P.compact) {
+    const CoefSteps qs = coef_steps(g, (double)eb);
+    for (int a = 0; a <= g.ndim && ok; ++a) {
+      int32_t kq;
+      ok = read_coef_int(pay, &bit, end, &kq);
+      if (ok) coef[a] = dequantize_coef<T>(kq, qs.step[a]);
+    }
+  } else if (reg_idx >= 0) {
+    for (int a = 0; a <= g.ndim; ++a) coef[a] = get<T>(s, P.L.coef + sz * ((g.ndim + 1) * (uint64_t)reg_idx + a));
+  }
   uint64_t sum = 0;
   for (uint32_t i = 0; i < e[0]; ++i)
     for (uint32_t j = 0; j < e[1]; ++j)
@@ -907,8 +1125,10 @@ bool decompress_block(const Parsed& P, const uint8_t* s, uint64_t b, uint64_t pa
         if (q < 0) {
           ok = false;
         } else if (q == 0) {
-          if (used < ucnt) xr = get<T>(s, P.L.unpred + sz * (un_off + used));
-          else ok = false;
+          if (used >= ucnt) ok = false;
+          else if (P.compact) ok = read_unpredictable<T>(pay, &bit, end, eexp, &xr);
+          else xr = get<T>(s, P.L.unpred + sz * (un_off + used));
+          if (!ok) xr = 0;
           ++used;
         } else {
           uint32_t c3[3] = {i, j, l};
@@ -1025,11 +1245,15 @@ int orc_compress(const void* field, const orc_params* p, const orc_flip* flips, 
 }
 
 // Worst case: every point unpredictable and coded with kMaxLen bits, every block regression.
+// Compact encoding: each point may also carry a whole value and each block 4 coefficients of
+// at most 38 bits.
 int orc_compress_bound(const orc_params* p, uint64_t* bytes) {
   Geom g;
   if (!p || !make_geom(p, &g)) return EINVAL_;
-  Layout L = make_layout(g, p->abft != 0, p->quant_bins ? p->quant_bins : 65536, g.nb, g.N);
-  *bytes = L.payload + g.nb * (((uint64_t)g.P * kMaxLen + 7) / 8);
+  const bool compact = p->encoding == 1;
+  Layout L = make_layout(g, p->abft != 0, compact, p->quant_bins ? p->quant_bins : 65536, g.nb, g.N);
+  const uint64_t bits = compact ? (uint64_t)g.P * (kMaxLen + 8 * (g.dtype ? 8 : 4)) + 4 * 38 : (uint64_t)g.P * kMaxLen;
+  *bytes = L.payload + g.nb * ((bits + 7) / 8);
   return OK;
 }
 
@@ -1089,6 +1313,7 @@ int orc_compress_block(const void* field, const orc_params* p, double eb_abs, ui
   c.R = p->quant_bins / 2;
   c.abft = p->abft != 0;
   c.predictor_mode = (int)p->predictor;
+  c.compact = p->encoding == 1;
   uint64_t sum_in = 0, isum_in = 0;
   auto run = [&](auto* f, auto tag) -> int {
     typedef decltype(tag) T;
@@ -1098,6 +1323,7 @@ int orc_compress_block(const void* field, const orc_params* p, double eb_abs, ui
     Ctx c2 = c;
     c2.abft = false;  // no stored input checksums to verify against
     Prep pr = prepare_block<T>(c2, (const T*)f, b);
+    if (c2.compact) quantize_prep<T>(c2, (const T*)f, b, eb, &pr);
     compress_block<T>(c2, (const T*)f, b, eb, inv2, sum_in, isum_in, pr, &r);
     std::memcpy(codes, r.code.data(), 2 * r.code.size());
     std::memcpy(coef, r.coef, sizeof(T) * 4);
@@ -1110,6 +1336,42 @@ int orc_compress_block(const void* field, const orc_params* p, double eb_abs, ui
   };
   if (p->dtype == 0) return run((const float*)field, 0.0f);
   return run((const double*)field, 0.0);
+}
+
+// Compact encoding, for pinning: the value an unpredictable point x decompresses to at the
+// absolute bound eb (both of the dtype); returns the mantissa bits kept.
+int orc_truncate_unpredictable(const void* x, uint32_t dtype, double eb, void* out) {
+  if (dtype == 0) {
+    const float v = *(const float*)x, e = (float)eb;
+    *(float*)out = truncate_unpredictable<float>(v, bound_exponent<float>(e));
+    return kept_mantissa_bits<float>(v, bound_exponent<float>(e));
+  }
+  const double v = *(const double*)x;
+  *(double*)out = truncate_unpredictable<double>(v, bound_exponent<double>(eb));
+  return kept_mantissa_bits<double>(v, bound_exponent<double>(eb));
+}
+
+// Compact encoding, for pinning: coefficient a (ndim = intercept) of a block geometry with
+// edges block[0..ndim-1] at the absolute bound eb (of the dtype) as an integer k and its
+// dequantized dtype value; returns 0 when it cannot be stored (the block uses Lorenzo).
+int orc_quantize_coefficient(float c, uint32_t dtype, uint32_t ndim, const uint32_t* block, double eb, uint32_t a,
+                             int32_t* k, void* deq) {
+  orc_params p;
+  std::memset(&p, 0, sizeof(p));
+  p.ndim = ndim;
+  p.dtype = dtype;
+  for (uint32_t d = 0; d < ndim; ++d) {
+    p.dims[d] = block[d];
+    p.block[d] = block[d];
+  }
+  Geom g;
+  if (!make_geom(&p, &g) || a > ndim) return -1;
+  const double E = dtype == 0 ? (double)(float)eb : eb;
+  const CoefSteps qs = coef_steps(g, E);
+  if (!quantize_coef(c, qs.inv[a], k)) return 0;
+  if (dtype == 0) *(float*)deq = dequantize_coef<float>(*k, qs.step[a]);
+  else *(double*)deq = dequantize_coef<double>(*k, qs.step[a]);
+  return 1;
 }
 
 // The value-range relative bound of the field, as the compressor computes it.
