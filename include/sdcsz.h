@@ -80,7 +80,12 @@ typedef struct {
   uint32_t quant_bins;
   uint32_t abft;
   uint32_t predictor;
-  uint32_t reserved; /* must be 0 */
+  /* 0 = raw: regression coefficients and unpredictable values in sections of their own, as
+   * stored values; 1 = compact: coefficients as integer multiples of eb/(16 B_a) (slopes) and
+   * eb/16 (intercept), written as length-prefixed zigzag integers at the head of the block's
+   * payload, and each unpredictable value right after its code 0 with only the mantissa bits
+   * the bound needs (SZ's own encodings, kept block-local). */
+  uint32_t encoding;
 } sdcsz_params;
 
 /* Counters of one call (Algorithm 2 reports corrected errors and SDCs to the user). */

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libsdcsz.so")
 OK, EINVAL, ECAPACITY, EFORMAT, ESDC, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
 SITES = {"input": 1, "code": 2, "coef": 3, "pred": 4, "recon": 5, "decomp": 6}
 PREDICTORS = {"auto": 0, "lorenzo": 1, "regression": 2}
+ENCODINGS = {"raw": 0, "compact": 1}
 BLOCK_OK, BLOCK_CORRECTED, BLOCK_SDC, BLOCK_BAD = 0, 1, 2, 3
 
 # Symbols the header declares (checked by tests against the shared object's exports).
@@ -49,7 +50,7 @@ class Params(ctypes.Structure):
         ("quant_bins", ctypes.c_uint32),
         ("abft", ctypes.c_uint32),
         ("predictor", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("encoding", ctypes.c_uint32),
     ]
 
 
@@ -221,7 +222,8 @@ def strerror(code: int) -> str:
     return lib().sdcsz_strerror(int(code)).decode()
 
 
-def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto") -> Params:
+def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
+                encoding="raw") -> Params:
     import torch
     ndim = len(shape)
     p = Params()
@@ -244,6 +246,7 @@ def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=Tr
     p.quant_bins = int(bins)
     p.abft = 1 if abft else 0
     p.predictor = PREDICTORS[predictor]
+    p.encoding = ENCODINGS[encoding]
     return p
 
 
@@ -298,13 +301,17 @@ class Workspace:
 
 
 def compress(field, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto", flips=None,
-             workspace: Workspace | None = None, stream=None, sync=True):
+             workspace: Workspace | None = None, stream=None, sync=True, encoding="raw"):
     """Compress a CUDA tensor (float32/float64, 1-3 dims, contiguous). Returns
-    (stream bytes as a uint8 CUDA tensor view, report dict or None)."""
+    (stream bytes as a uint8 CUDA tensor view, report dict or None). ``encoding`` "compact"
+    keeps the regression coefficients as bound-relative integers and the unpredictable values
+    truncated to the bits the bound needs, both inside the block payloads."""
     import torch
     if not field.is_cuda or not field.is_contiguous():
         raise ValueError("field must be a contiguous CUDA tensor")
-    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor)
+    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
+    if workspace is not None and workspace.p.encoding != p.encoding:
+        raise ValueError("workspace was sized for another encoding")
     w = workspace if workspace is not None else Workspace(p, field.device)
     rep = Report()
     nbytes = ctypes.c_size_t()
@@ -342,7 +349,8 @@ def read_header(stream_bytes):
     shape = tuple(int(p.dims[a]) for a in range(p.ndim))
     block = tuple(int(p.block[a]) for a in range(p.ndim))
     return {"shape": shape, "dtype": "float32" if p.dtype == 0 else "float64", "block": block,
-            "total": int(total.value), "abft": bool(p.abft), "bins": int(p.quant_bins)}
+            "total": int(total.value), "abft": bool(p.abft), "bins": int(p.quant_bins),
+            "encoding": "compact" if p.encoding == 1 else "raw"}
 
 
 def _geometry(stream):
@@ -468,10 +476,10 @@ def decompress_traced(stream_t, out, ws, stream=None):
 
 
 def compress_noalloc(field, out, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-                     stream=None):
+                     stream=None, encoding="raw"):
     """Compress into the caller's uint8 CUDA tensor `out` with the library's fixed scratch
     (no device allocation by the library). Returns (stream bytes view, report dict)."""
-    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor)
+    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
     n = ctypes.c_size_t()
     rep = Report()
     rc = lib().sdcsz_compress_noalloc(ctypes.c_void_p(field.data_ptr()), ctypes.byref(p),
@@ -489,17 +497,19 @@ class Batch:
     per field; ``block`` is None, an int or a tuple for every field, or a list with one entry
     per field. Each field's stream is byte-identical to ``compress`` of that field."""
 
-    def __init__(self, fields, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto", stream=None):
+    def __init__(self, fields, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto", stream=None,
+                 encoding="raw"):
         import torch
         n = len(fields)
+        encs = list(encoding) if isinstance(encoding, (list, tuple)) else [encoding] * n
         ebs = list(eb) if isinstance(eb, (list, tuple)) else [eb] * n
         modes = list(eb_mode) if isinstance(eb_mode, (list, tuple)) else [eb_mode] * n
         blocks = list(block) if isinstance(block, list) else [block] * n
         abfts = list(abft) if isinstance(abft, (list, tuple)) else [abft] * n
         preds = list(predictor) if isinstance(predictor, (list, tuple)) else [predictor] * n
         self.fields = list(fields)
-        self.params = [make_params(tuple(f.shape), f.dtype, ebs[i], modes[i], blocks[i], bins, abfts[i], preds[i])
-                       for i, f in enumerate(self.fields)]
+        self.params = [make_params(tuple(f.shape), f.dtype, ebs[i], modes[i], blocks[i], bins, abfts[i], preds[i],
+                                   encs[i]) for i, f in enumerate(self.fields)]
         self.caps = [compress_bound(p) for p in self.params]
         dev = self.fields[0].device
         self.outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in self.caps]
@@ -600,10 +610,10 @@ class Server:
         self._keep[int(req.id)] = keep
 
     def submit_compress(self, rid, field, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-                        out=None, flips=None):
+                        out=None, flips=None, encoding="raw"):
         r = Request()
         r.op, r.id, r.d_in = OP_COMPRESS, rid, field.data_ptr()
-        r.params = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor)
+        r.params = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
         if out is not None:
             r.d_out, r.out_cap = out.data_ptr(), out.numel()
         ft = flips_tensor(flips, field.device) if flips else None

@@ -93,7 +93,7 @@ inline namespace host {
 int make_geo(const sdcsz_params* p, Geo* g) {
   if (!p) return SDCSZ_EINVAL;
   if (p->ndim < 1 || p->ndim > 3 || p->dtype > 1 || p->eb_mode > 1 || p->abft > 1 || p->predictor > 2 ||
-      p->reserved != 0)
+      p->encoding > 1)
     return SDCSZ_EINVAL;
   if (!(p->eb > 0.0) || !(p->eb < 1.0 / 0.0)) return SDCSZ_EINVAL;
   const uint32_t bins = p->quant_bins ? p->quant_bins : 65536u;
@@ -131,6 +131,7 @@ int make_geo(const sdcsz_params* p, Geo* g) {
   g->abft = (int)p->abft;
   g->predictor = (int)p->predictor;
   g->eb_mode = (int)p->eb_mode;
+  g->enc = (int)p->encoding;
   g->e = p->eb;
   return SDCSZ_OK;
 }
@@ -166,7 +167,7 @@ WsPlan plan_ws(const Geo& g) {
   w.node_parent = take(4 * 2 * 65536 + 2 * 65536);
   w.codes = take(4 * pair_slots);
   w.ustage = take(s * slots);
-  w.etmp = take(4 * encode_slot_words(g.P) * nb);
+  w.etmp = take(4 * encode_slot_words(g) * nb);
   w.total = o;
   return w;
 }
@@ -342,6 +343,7 @@ int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout) 
   p.abft = s[48];
   p.predictor = s[49];
   p.eb_mode = s[50];
+  p.encoding = s[51];
   std::memcpy(&p.eb, s + 64, 8);
   if (!(p.eb > 0.0)) p.eb = 1.0;  // the user bound is informational for decoding
   Geo g;
@@ -373,6 +375,18 @@ int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout) 
     h->payload_bytes = payload;
     h->total = total;
     h->eb = eb;
+    if (p.dtype == 0) {
+      const float ebf = (float)eb;
+      uint32_t u;
+      std::memcpy(&u, &ebf, 4);
+      h->texp = (int)((u >> 23) & 0xffu) - 127;
+    } else {
+      uint64_t u;
+      std::memcpy(&u, &eb, 8);
+      h->texp = (int)((u >> 52) & 0x7ffu) - 1023;
+    }
+    const CoefSteps cs = coef_steps(g, eb);
+    for (int a = 0; a < 4; ++a) h->cstep[a] = cs.step[a];
   }
   if (pout) *pout = p;
   return SDCSZ_OK;
@@ -452,7 +466,7 @@ int sdcsz_compress_bound(const sdcsz_params* p, size_t* max_bytes) {
   if (rc) return rc;
   if (!max_bytes) return SDCSZ_EINVAL;
   const Layout L = make_layout(g, g.bins, g.nb, g.N);
-  *max_bytes = (size_t)(L.payload + g.nb * (((uint64_t)g.P * kMaxLen + 7) / 8));
+  *max_bytes = (size_t)(L.payload + g.nb * 4 * encode_slot_words(g));
   return SDCSZ_OK;
 }
 

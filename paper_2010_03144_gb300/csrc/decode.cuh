@@ -9,7 +9,9 @@
 // compared with sum_dc; on a mismatch the block is decompressed once more from its compressed
 // bytes (random-access re-execution) and reported corrected or as an SDC in compression.
 // As in compression, full blocks of the common shapes take a fast kernel with compile-time
-// edges and edge blocks a generic kernel.
+// edges and edge blocks a generic kernel. In the compact encoding a regression block's
+// payload starts with its coefficient integers and each code 0 is followed by the point's
+// truncated value.
 #pragma once
 
 #include <algorithm>
@@ -22,6 +24,7 @@ namespace kdec {
 namespace {
 
 constexpr uint32_t kNone = 0xffffffffu;
+constexpr int kDefer = -2;  // second symbol of a pair not decoded yet (compact encoding: a value comes first)
 
 struct Canon {
   uint32_t fc[kMaxLen + 2];  // first code of each length
@@ -88,6 +91,18 @@ struct BitReader {
     nb = 64 - skip;
     used = 0;
   }
+  // the next n (1..32) raw bits
+  __device__ __forceinline__ uint32_t bits(uint32_t n) {
+    if (nb <= 32) {
+      buf |= (unsigned long long)word() << (32 - nb);
+      nb += 32;
+    }
+    const uint32_t v = (uint32_t)(buf >> (64 - n));
+    buf <<= n;
+    nb -= (int)n;
+    used += n;
+    return v;
+  }
   // next symbol, or -1 for an invalid code
   __device__ __forceinline__ int next(const uint32_t* lut, const Canon& cn, const uint16_t* syms, uint32_t n_live) {
     if (nb <= 32) {
@@ -142,6 +157,12 @@ struct FastReader {
     advance(len);
     return sym;
   }
+  // the next n (1..32) raw bits
+  __device__ __forceinline__ uint32_t bits(uint32_t n) {
+    const uint32_t peek = __funnelshift_l(w1, w0, pos);
+    advance(n);
+    return n == 32 ? peek : peek >> (32 - n);
+  }
   __device__ __forceinline__ void advance(uint32_t len) {
     pos += len;
     if (pos >= 32) {  // only lanes crossing a word boundary touch memory
@@ -153,9 +174,10 @@ struct FastReader {
     }
   }
   // Two symbols with one lookup when both codes lie in the 12-bit window (the pair table
-  // holds the second symbol only then), else one at a time.
+  // holds the second symbol only then), else one at a time. In the compact encoding a code 0
+  // is followed by its value, so after a first symbol 0 the second is left for later (kDefer).
   __device__ __forceinline__ void next2(const uint2* lut2, const uint32_t* lut, const Canon& cn, const uint16_t* syms,
-                                        uint32_t n_live, int& q0, int& q1) {
+                                        uint32_t n_live, int& q0, int& q1, bool compact) {
     const uint32_t peek = __funnelshift_l(w1, w0, pos);
     const uint2 e = lut2[peek >> (32 - kLutBits)];
     const uint32_t l0 = e.x & 0xffu, l1 = e.y & 0xffu;
@@ -165,10 +187,60 @@ struct FastReader {
       advance(l0 + l1);
     } else {
       q0 = next(lut, cn, syms, n_live);
-      q1 = next(lut, cn, syms, n_live);
+      q1 = (compact && q0 == 0) ? kDefer : next(lut, cn, syms, n_live);
     }
   }
 };
+
+// Compact encoding: one coefficient integer (bit length of its zigzag value in 6 bits, then the
+// bits below the leading one); false for a length above 32.
+template <class Reader>
+__device__ __forceinline__ bool read_coef(Reader& br, int* k) {
+  const uint32_t n = br.bits(6);
+  if (n > 32) return false;
+  uint32_t z = 0;
+  if (n > 0) z = (n > 1 ? br.bits(n - 1) : 0u) | (1u << (n - 1));
+  *k = (int)((z >> 1) ^ (0u - (z & 1u)));
+  return true;
+}
+
+// Compact encoding: one unpredictable value (sign and exponent, then the kept mantissa bits).
+template <typename T, class Reader>
+__device__ __forceinline__ T read_unpred(Reader& br, int texp) {
+  typedef typename Bitsof<T>::U U;
+  const uint32_t se = br.bits(1 + Bitsof<T>::E);
+  const int Ex = (int)(se & ((1u << Bitsof<T>::E) - 1));
+  int m = Bitsof<T>::M;
+  if (Ex != 0 && Ex != (1 << Bitsof<T>::E) - 1) m = min(max(Ex - Bitsof<T>::BIAS - texp, 0), Bitsof<T>::M);
+  U mant = 0;
+  if (m > 32) {
+    mant = (U)br.bits((uint32_t)m - 32) << 32;
+    mant |= br.bits(32);
+  } else if (m > 0) {
+    mant = br.bits((uint32_t)m);
+  }
+  return Bitsof<T>::val(((U)se << Bitsof<T>::M) | (mant << (Bitsof<T>::M - m)));
+}
+
+// The coefficients of a regression block: stored dtype values, or (compact encoding) the
+// integers at the head of its payload times their steps.
+template <typename T, int NDIM, class Reader>
+__device__ __forceinline__ bool block_coefs(const uint8_t* s, const Hdr& h, int64_t reg_idx, Reader& br, T cT[4]) {
+  if (h.g.enc) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a <= NDIM; ++a) {
+      int k = 0;
+      if (ok) ok = read_coef(br, &k);
+      cT[a] = coef_from_int<T>(k, h.cstep[a]);
+    }
+    return ok;
+  }
+  const T* c = reinterpret_cast<const T*>(s + h.L.coef) + (uint64_t)(NDIM + 1) * reg_idx;
+#pragma unroll
+  for (int a = 0; a <= NDIM; ++a) cT[a] = c[a];
+  return true;
+}
 
 struct BlockIn {
   uint64_t b, pay_off, un_off;
@@ -186,12 +258,13 @@ struct Tables {
 
 // Pair table: entry p holds lut[p] and, when that code is shorter than the window and the
 // code after it also ends inside the window, that second code's lut entry (else 0). Only the
-// window's known bits decide either symbol. Call after the lut is complete and visible.
-__device__ __forceinline__ void pair_table(uint2* lut2, const uint32_t* lut) {
+// window's known bits decide either symbol. In the compact encoding a code 0 is followed by a
+// value, not a code, so it never starts a pair. Call after the lut is complete and visible.
+__device__ __forceinline__ void pair_table(uint2* lut2, const uint32_t* lut, bool compact) {
   for (uint32_t e = threadIdx.x; e < (1u << kLutBits); e += blockDim.x) {
     const uint32_t v1 = lut[e], l1 = v1 & 0xffu;
     uint32_t v2 = 0;
-    if (l1 && l1 < (uint32_t)kLutBits) {
+    if (l1 && l1 < (uint32_t)kLutBits && !(compact && (v1 >> 8) == 0)) {
       const uint32_t u = lut[(e << l1) & ((1u << kLutBits) - 1)], l2 = u & 0xffu;
       if (l2 && l2 <= (uint32_t)kLutBits - l1) v2 = u;
     }
@@ -239,14 +312,11 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
   const T eb = (T)h.eb;
   T cT[4] = {T(0), T(0), T(0), T(0)};
   const bool reg = bi.reg_idx >= 0;
-  if (reg) {
-    const T* c = reinterpret_cast<const T*>(s + h.L.coef) + (uint64_t)(NDIM + 1) * bi.reg_idx;
-    for (int a = 0; a <= NDIM; ++a) cT[a] = c[a];
-  }
   const T* un = reinterpret_cast<const T*>(s + h.L.unpred) + bi.un_off;
   BitReader br;
   br.init(s + h.L.payload + bi.pay_off, lim);
   bool ok = true;
+  if (reg) ok = block_coefs<T, NDIM>(s, h, bi.reg_idx, br, cT);
   uint32_t used_u = 0, k = 0;
   unsigned long long sum = 0, nv = 0;
   double me = 0.0;
@@ -262,8 +332,9 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
         if (q < 0 || (uint32_t)q >= g.bins) {
           ok = false;
         } else if (q == 0) {
-          if (used_u < bi.ucnt) xr = un[used_u];
-          else ok = false;
+          if (used_u >= bi.ucnt) ok = false;
+          else if (h.g.enc) xr = read_unpred<T>(br, h.texp);
+          else xr = un[used_u];
           ++used_u;
         } else {
           const T pred = reg ? regress<T, NDIM, OpRN<T>>(cT, i, j, l) : wk.template combine<OpRN<T>>();
@@ -308,16 +379,12 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
   const T eb = (T)h.eb;
   const int R = (int)g.R;
   T cT[4] = {T(0), T(0), T(0), T(0)};
-  if (REG) {
-    const T* c = reinterpret_cast<const T*>(s + h.L.coef) + (uint64_t)(NDIM + 1) * bi.reg_idx;
-#pragma unroll
-    for (int a = 0; a <= NDIM; ++a) cT[a] = c[a];
-  }
   const T* un = reinterpret_cast<const T*>(s + h.L.unpred) + bi.un_off;
   FastReader br;
   br.init(s + h.L.payload + bi.pay_off);
   (void)lim;
   bool ok = true;
+  if (REG) ok = block_coefs<T, NDIM>(s, h, bi.reg_idx, br, cT);
   uint32_t used_u = 0;
   unsigned long long sum = 0, nv = 0;
   double me = 0.0;
@@ -349,8 +416,8 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       for (int l = 0; l < B2; ++l) {
         int q;
         if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
-          if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp);
-          else q = qp;
+          if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp, h.g.enc != 0);
+          else q = qp == kDefer ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : qp;
         } else {
           q = br.next(tb.lut, *tb.cn, tb.syms, tb.n_live);
         }
@@ -381,7 +448,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
         T xr = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
         if (q <= 0) {  // unpredictable value (code 0) or an undecodable block (rare)
           xr = T(0);
-          if (q == 0 && used_u < bi.ucnt) xr = un[used_u];
+          if (q == 0 && used_u < bi.ucnt) xr = h.g.enc ? read_unpred<T>(br, h.texp) : un[used_u];
           else ok = false;
           ++used_u;
         }
@@ -848,7 +915,7 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
   if (!cta_tables(s, h, sm, lut, syms, st)) return;
   uint2* lut2 = reinterpret_cast<uint2*>(smem + (4u << kLutBits));
   __syncthreads();
-  pair_table(lut2, lut);
+  pair_table(lut2, lut, h.g.enc != 0);
   __syncthreads();
   const Tables tb = {lut, &sm.cn, syms, h.n_live, lut2};
   const uint8_t* lim = s + nbytes;
@@ -888,10 +955,12 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
       bi.ucnt = sm.uc[t];
       uint32_t kinj, bitinj;
       find_inj(flips, nflips, b, &kinj, &bitinj);
-      // The unchecked reader consumes at most 24 bits per point whatever the data, reads at
+      // The unchecked reader consumes at most 24 bits per point whatever the data (in the compact
+      // encoding also a whole value per point and 4 coefficients of at most 38 bits), reads at
       // most 12 bytes ahead of what it consumed and starts up to 3 bytes early; blocks whose
       // worst case could reach the end of the stream take the bounds-checked reader.
-      const bool safe = (uint64_t)(lim - (s + h.L.payload)) >= bi.pay_off + 3ull * (B0 * B1 * B2) + 16;
+      const uint64_t worst = h.g.enc ? (3ull + sizeof(T)) * (B0 * B1 * B2) + 19 : 3ull * (B0 * B1 * B2);
+      const bool safe = (uint64_t)(lim - (s + h.L.payload)) >= bi.pay_off + worst + 16;
       const uint8_t stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv,
                                                      double* me) {
         if (!safe)

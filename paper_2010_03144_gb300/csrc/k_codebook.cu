@@ -230,6 +230,7 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
     put_u8(out, 48, (uint8_t)g.abft);
     put_u8(out, 49, (uint8_t)g.predictor);
     put_u8(out, 50, (uint8_t)g.eb_mode);
+    put_u8(out, 51, (uint8_t)g.enc);
     put_u32(out, 52, n);
     put_u64(out, 56, (unsigned long long)__double_as_longlong(st->eb));
     put_u64(out, 64, (unsigned long long)__double_as_longlong(g.e));
@@ -244,8 +245,9 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
     const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
     const uint64_t ends[8] = {L.table + 4 * (kMaxLen + 1) + 2 * (uint64_t)n, L.groups + 24 * ngroups,
                               L.sizes + 2 * g.nb, L.ucounts + 2 * g.nb, L.bitmap + 4 * ((g.nb + 31) / 32),
-                              L.sumdc + (g.abft ? 8 * g.nb : 0), L.coef + s * (uint64_t)(g.ndim + 1) * st->n_reg,
-                              L.unpred + s * st->n_unpred};
+                              L.sumdc + (g.abft ? 8 * g.nb : 0),
+                              L.coef + (g.enc ? 0 : s * (uint64_t)(g.ndim + 1) * st->n_reg),
+                              L.unpred + (g.enc ? 0 : s * st->n_unpred)};
     const uint64_t starts[8] = {L.groups, L.sizes, L.ucounts, L.bitmap, L.sumdc, L.coef, L.unpred, L.payload};
     for (int q = 0; q < 8; ++q)
       for (uint64_t o = ends[q]; o < starts[q]; ++o) out[o] = 0;

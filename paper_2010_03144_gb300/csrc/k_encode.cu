@@ -2,7 +2,9 @@
 // Algorithm 1 of the paper, without the Zstd stage). Two kernels:
 //
 // K4a, one thread per block: encodes the block's codes (read from HBM once) MSB-first into a
-// fixed-size slot of the workspace, taking sum_q/isum_q on the way. When they disagree with
+// fixed-size slot of the workspace, taking sum_q/isum_q on the way. In the compact encoding
+// the block's coefficient integers come first and each unpredictable value follows its code
+// 0, truncated to the mantissa bits the bound needs. When they disagree with
 // the values of K2 (Algorithm 1's check of the bin array before encoding) the single corrupted
 // code is located and repaired and the block is encoded again. Then the block's unpredictable
 // values move to the front of its staging slot, and the per-block entries that sit at fixed
@@ -24,13 +26,15 @@ namespace sdcsz {
 
 namespace {
 
-constexpr unsigned long long kFlagAgg = 1ull, kMaskBytes = (1ull << 22) - 1, kMaskUn = (1ull << 21) - 1;
+// look-back aggregate of a group: bytes (25 bits: 256 blocks of at most 65535), unpredictable
+// points (21 bits: 256 blocks of at most 4096), regression blocks (16 bits), and a flag
+constexpr unsigned long long kFlagAgg = 1ull, kMaskBytes = (1ull << 25) - 1, kMaskUn = (1ull << 21) - 1;
 constexpr uint32_t kCbWindow = 2048;  // codebook entries around the centre kept in shared memory
 constexpr uint32_t kPosKept = 4;      // unpredictable positions remembered in registers per block
 
 __device__ __forceinline__ unsigned long long pack_agg(unsigned long long bytes, unsigned long long un,
                                                        unsigned long long rg) {
-  return (kFlagAgg << 62) | (rg << 43) | (un << 22) | bytes;
+  return (kFlagAgg << 62) | (rg << 46) | (un << 25) | bytes;
 }
 
 __device__ __forceinline__ void mad_wide(unsigned long long& acc, uint32_t a, uint32_t b) {
@@ -70,12 +74,24 @@ struct EncRes {
   uint32_t pos[kPosKept];
 };
 
+// What the compact encoding adds to a block's payload: its coefficient integers (nco of
+// them, none for a Lorenzo block) and, after each code 0, the point's value from the
+// unpredictable staging (stride 32) truncated at exponent texp.
+template <typename T>
+struct Extra {
+  const int* kq;
+  int nco;
+  const T* up;
+  int texp;
+};
+
 // One pass over a block's codes: the Huffman bits into `slot` (stream byte order, the last
 // word zero padded), the code checksums (ABFT), the unpredictable count and the first
-// kPosKept unpredictable positions. With FIX, code kfix reads as vfix.
-template <bool ABFT, bool FIX>
+// kPosKept unpredictable positions. With FIX, code kfix reads as vfix. CMP: compact encoding.
+template <bool ABFT, bool FIX, bool CMP, typename T>
 __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, uint32_t P, uint32_t* __restrict__ slot,
-                                               const Codebook& cb, uint32_t cw0, uint32_t kfix, uint32_t vfix) {
+                                               const Codebook& cb, uint32_t cw0, uint32_t kfix, uint32_t vfix,
+                                               const Extra<T>& ex) {
   EncRes e;
   e.bits = 0;
   e.nun = 0;
@@ -83,6 +99,33 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
   e.isq = 0;
   unsigned long long acc = 0;
   uint32_t nacc = 0, wi = 0;
+  // len (<= 32) low bits of v
+  auto put_bits = [&](uint32_t v, uint32_t len) {
+    acc = (acc << len) | (len < 32 ? (v & ((1u << len) - 1u)) : v);
+    nacc += len;
+    e.bits += len;
+    if (nacc >= 32) {
+      nacc -= 32;
+      slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+    }
+  };
+  auto put_value = [&](uint32_t k) {
+    typedef typename Bitsof<T>::U U;
+    const T v = ex.up[32 * (uint64_t)k];
+    const int m = kept_bits<T>(v, ex.texp);
+    const uint32_t len = 1u + Bitsof<T>::E + (uint32_t)m;
+    const U u = Bitsof<T>::raw(v) >> (Bitsof<T>::M - m);
+    if (len > 32) put_bits((uint32_t)((unsigned long long)u >> 32), len - 32);
+    put_bits((uint32_t)u, len > 32 ? 32u : len);
+  };
+  if (CMP)
+    for (int a = 0; a < ex.nco; ++a) {  // zigzag, its bit length in 6 bits, the bits below the leading one
+      const int kv = ex.kq[a];
+      const uint32_t z = ((uint32_t)kv << 1) ^ (kv < 0 ? 0xffffffffu : 0u);
+      const uint32_t n = 32u - (uint32_t)__clz(z);
+      put_bits(n, 6);
+      if (n > 1) put_bits(z, n - 1);
+    }
   auto put = [&](uint32_t c, uint32_t k) {
     if (FIX && k == kfix) c = vfix;
     const uint32_t cw = c ? cb(c) : cw0;
@@ -101,6 +144,7 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
     if (c == 0) {
       if (e.nun < kPosKept) e.pos[e.nun] = k;
       ++e.nun;
+      if (CMP) put_value(k);
     }
   };
   // Both codes of a pair at once when their bits fit in one word (nearly always: codes are a
@@ -110,7 +154,7 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
     if (FIX && k + 1 == kfix) c1 = vfix;
     const uint32_t w0 = c0 ? cb(c0) : cw0, w1 = c1 ? cb(c1) : cw0;
     const uint32_t l0 = w0 & 31u, l1 = w1 & 31u, l = l0 + l1;
-    if (l > 32) {
+    if (l > 32 || (CMP && (c0 == 0 || c1 == 0))) {
       put(c0, k);
       put(c1, k + 1);
       return;
@@ -160,11 +204,15 @@ __device__ __forceinline__ void put_bytes(uint8_t* out, uint64_t wa, uint32_t v,
     if (wa + q >= lo && wa + q < hi) out[wa + q] = (uint8_t)(v >> (8 * q));
 }
 
-// Payload slot of one block: 32-bit words for P codes of at most kMaxLen bits, 16-byte rounded.
-__host__ __device__ inline uint64_t slot_words_of(uint32_t P) { return ((uint64_t)P * kMaxLen + 127) / 128 * 4; }
+// Payload slot of one block, 16-byte rounded: P codes of at most kMaxLen bits; in the compact
+// encoding also a whole value per point and 4 coefficient integers of at most 38 bits.
+__host__ __device__ inline uint64_t slot_words_of(const Geo& g) {
+  const uint64_t bits = (uint64_t)g.P * (kMaxLen + (g.enc ? 8 * (g.dtype ? 8 : 4) : 0)) + (g.enc ? 4 * 38 : 0);
+  return (bits + 127) / 128 * 4;
+}
 
 // ---------------------------------------------------------------- K4a
-template <typename T, bool ABFT>
+template <typename T, bool ABFT, bool CMP>
 __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t* __restrict__ out,
                                              const uint32_t* cb_s, uint64_t b) {
   State* st = w.st;
@@ -182,8 +230,14 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
     const uint32_t P = block_box(g, b).P;
     reg = w.flags[b] & 1;
     const uint32_t* pp = reinterpret_cast<const uint32_t*>(w.codes) + pair_index(b, g.P, 0);
-    uint32_t* slot = w.etmp + b * slot_words_of(g.P);
-    EncRes e = encode_codes<ABFT, false>(pp, P, slot, cb, cw0, 0u, 0u);
+    uint32_t* slot = w.etmp + b * slot_words_of(g);
+    T* up = static_cast<T*>(w.ustage) + code_index(b, g.P, 0);
+    Extra<T> ex;
+    ex.kq = static_cast<const int*>(w.coefT) + 4 * b;
+    ex.nco = reg ? g.ndim + 1 : 0;
+    ex.up = up;
+    ex.texp = CMP ? bound_exponent<T>((T)st->eb) : kNoTrunc;
+    EncRes e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, 0u, 0u, ex);
     uint32_t kfix = 0xffffffffu, vfix = 0;
     bool bad = false;
     if (ABFT && (e.sq != w.sum_q[b] || e.isq != w.isum_q[b])) {
@@ -196,7 +250,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
         if (nv >= 0 && nv < (long long)g.bins) {
           kfix = (uint32_t)m;
           vfix = (uint32_t)nv;
-          e = encode_codes<ABFT, true>(pp, P, slot, cb, cw0, kfix, vfix);  // the repaired block
+          e = encode_codes<ABFT, true, CMP, T>(pp, P, slot, cb, cw0, kfix, vfix, ex);  // the repaired block
           fixed = true;
         }
       }
@@ -208,20 +262,21 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
       }
     }
     // unpredictable values to the front of the block's staging slot, in order (in place: the
-    // j-th value moves down from its point k >= j)
-    T* up = static_cast<T*>(w.ustage) + code_index(b, g.P, 0);
-    if (e.nun <= kPosKept) {
+    // j-th value moves down from its point k >= j); the compact encoding has them in the payload
+    if (!CMP) {
+      if (e.nun <= kPosKept) {
 #pragma unroll
-      for (uint32_t j = 0; j < kPosKept; ++j)
-        if (j < e.nun && e.pos[j] != j) up[32 * (uint64_t)j] = up[32 * (uint64_t)e.pos[j]];
-    } else {
-      uint32_t j = 0;
-      for (uint32_t k = 0; k < P; ++k) {
-        uint32_t c = (pp[32 * (uint64_t)(k >> 1)] >> (16 * (k & 1))) & 0xffffu;
-        if (k == kfix) c = vfix;
-        if (c == 0) {
-          if (j != k) up[32 * (uint64_t)j] = up[32 * (uint64_t)k];
-          ++j;
+        for (uint32_t j = 0; j < kPosKept; ++j)
+          if (j < e.nun && e.pos[j] != j) up[32 * (uint64_t)j] = up[32 * (uint64_t)e.pos[j]];
+      } else {
+        uint32_t j = 0;
+        for (uint32_t k = 0; k < P; ++k) {
+          uint32_t c = (pp[32 * (uint64_t)(k >> 1)] >> (16 * (k & 1))) & 0xffffu;
+          if (k == kfix) c = vfix;
+          if (c == 0) {
+            if (j != k) up[32 * (uint64_t)j] = up[32 * (uint64_t)k];
+            ++j;
+          }
         }
       }
     }
@@ -241,13 +296,13 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
   }
 }
 
-template <typename T, bool ABFT>
+template <typename T, bool ABFT, bool CMP>
 __global__ void __launch_bounds__(128) k_encode_blocks(Geo g, Ws w, uint8_t* __restrict__ out) {
   __shared__ uint32_t cb_s[kCbWindow];
   if (cta_failed(w.st)) return;
   cb_load(cb_s, g, w);
   __syncthreads();
-  encode_block<T, ABFT>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  encode_block<T, ABFT, CMP>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------- K4b
@@ -263,11 +318,12 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   const uint64_t b = gid * kGroup + tid;
   const bool active = b < g.nb;
   // The unpredictable section holds the points whose code, as encoded, is 0: the count K2 took
-  // unless a block's codes could not be repaired. The payload follows that section.
+  // unless a block's codes could not be repaired. The payload follows that section (which the
+  // compact encoding leaves empty).
   const unsigned long long n_unpred = st->n_unpred_enc;
   const uint64_t s_dt = g.dtype ? 8 : 4;
   Layout L = st->L;
-  L.payload = align16(L.unpred + s_dt * n_unpred);
+  L.payload = align16(L.unpred + (g.enc ? 0 : s_dt * n_unpred));
   uint32_t bytes = 0, nun = 0;
   bool reg = false;
   if (active) {
@@ -325,8 +381,8 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
             const unsigned long long a = *(volatile const unsigned long long*)&pr->agg;
             if (a >> 62) {
               va[0] = a & kMaskBytes;
-              va[1] = (a >> 22) & kMaskUn;
-              va[2] = (a >> 43) & 0x7ffffull;
+              va[1] = (a >> 25) & kMaskUn;
+              va[2] = (a >> 46) & 0xffffull;
               ready = true;
             }
           }
@@ -367,7 +423,7 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
       *reinterpret_cast<unsigned long long*>(out + 88) = n_unpred;
       *reinterpret_cast<unsigned long long*>(out + 96) = pay;
       *reinterpret_cast<unsigned long long*>(out + 104) = L.payload + pay;
-      for (uint64_t o = L.unpred + s_dt * n_unpred; o < L.payload && o < cap; ++o) out[o] = 0;  // alignment gap
+      for (uint64_t o = L.unpred + (g.enc ? 0 : s_dt * n_unpred); o < L.payload && o < cap; ++o) out[o] = 0;  // gap
       st->n_unpred = n_unpred;
       st->L = L;
       st->payload_bytes = pay;
@@ -380,17 +436,19 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   const unsigned long long pay_off = s_excl[0] + s_wt[wid][0] + inc[0] - v[0];
   const unsigned long long un_off = s_excl[1] + s_wt[wid][1] + inc[1] - v[1];
   const unsigned long long rg_off = s_excl[2] + s_wt[wid][2] + inc[2] - v[2];
-  if (reg) {
+  if (reg && !g.enc) {
     const T* cT = static_cast<const T*>(w.coefT) + 4 * b;
     T* dst = reinterpret_cast<T*>(out + L.coef) + (uint64_t)(g.ndim + 1) * rg_off;
     for (int a = 0; a <= g.ndim; ++a) dst[a] = cT[a];
   }
   // unpredictable values, moved by K4a to the front of the block's staging slot
-  const T* up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
-  T* udst = reinterpret_cast<T*>(out + L.unpred);
-  const unsigned long long ulim = n_unpred;
-  for (uint32_t j = 0; j < nun; ++j)
-    if (un_off + j < ulim) udst[un_off + j] = up[32 * (uint64_t)j];
+  if (!g.enc) {
+    const T* up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
+    T* udst = reinterpret_cast<T*>(out + L.unpred);
+    const unsigned long long ulim = n_unpred;
+    for (uint32_t j = 0; j < nun; ++j)
+      if (un_off + j < ulim) udst[un_off + j] = up[32 * (uint64_t)j];
+  }
   // payload: stream bytes [lo, hi) = slot bytes [0, bytes). The stream word at wa = wa0 + 4i
   // holds slot bytes 4i - r .. 4i - r + 3 (r = lo mod 4): the top r bytes of slot word i - 1
   // and the low 4 - r bytes of slot word i. Words wholly inside [lo, hi) are stored whole;
@@ -401,7 +459,7 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
     return;
   }
   // The slot is read four words (16 bytes, aligned) at a time, and the previous word carried.
-  const uint4* src4 = reinterpret_cast<const uint4*>(w.etmp + b * slot_words_of(g.P));
+  const uint4* src4 = reinterpret_cast<const uint4*>(w.etmp + b * slot_words_of(g));
   const uint32_t r = (uint32_t)(lo & 3), nw = (bytes + 3) / 4;
   const uint64_t wa0 = lo - r;
   const uint32_t nout = (uint32_t)((hi - wa0 + 3) >> 2);  // stream words touched
@@ -446,7 +504,10 @@ __global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
         cb_load(cb_s, s_job.g, s_job.w);
         __syncthreads();
       },
-      [&](uint64_t it) { encode_block<T, ABFT>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x); },
+      [&](uint64_t it) {
+        if (s_job.g.enc) encode_block<T, ABFT, true>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x);
+        else encode_block<T, ABFT, false>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x);
+      },
       NoOp());
 }
 
@@ -483,7 +544,8 @@ template <typename T, bool ABFT>
 void launch_encode_t(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
   const uint64_t nchunks = (g.nb + 127) / 128, ngroups = (g.nb + kGroup - 1) / kGroup;
   if (!ngroups) return;
-  k_encode_blocks<T, ABFT><<<(unsigned)nchunks, 128, 0, L.stream>>>(g, w, out);
+  if (g.enc) k_encode_blocks<T, ABFT, true><<<(unsigned)nchunks, 128, 0, L.stream>>>(g, w, out);
+  else k_encode_blocks<T, ABFT, false><<<(unsigned)nchunks, 128, 0, L.stream>>>(g, w, out);
   note_launch();
   k_encode_assemble<T><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
   note_launch();
@@ -491,7 +553,7 @@ void launch_encode_t(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, cons
 
 }  // namespace
 
-uint64_t encode_slot_words(uint32_t P) { return slot_words_of(P); }
+uint64_t encode_slot_words(const Geo& g) { return slot_words_of(g); }
 
 // items: 128-block chunks
 void batch_encode_blocks(int dtype, bool abft, const BatchArgs& a, const Launch& L) {

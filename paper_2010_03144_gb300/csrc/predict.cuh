@@ -94,9 +94,11 @@ __device__ __forceinline__ void sum_words(T v, unsigned long long& sum) {
 // Algorithm 1 for one point with its (already duplicated) prediction: linear-scaling
 // quantization, reconstruction with dec_dup, and the machine-epsilon double check.
 // Returns the code (0 = unpredictable) and the value later points are predicted from.
+// An unpredictable point decompresses to its value, truncated to the mantissa bits the bound
+// needs in the compact encoding (texp = floor(log2 eb)); texp = kNoTrunc keeps it whole.
 template <typename T, bool ABFT, bool HOOK>
 __device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, uint32_t R, bool hit_r, uint32_t bitr,
-                                             T& xr, uint32_t& dup) {
+                                             T& xr, uint32_t& dup, int texp) {
   const T diff = FT<T>::sub(v, pred);
   const T t = FT<T>::mul(FT<T>::absv(diff), inv2);
   const bool inr = t < Rh;
@@ -113,7 +115,8 @@ __device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, ui
     }
   }
   const bool ok = inr && (FT<T>::absv(FT<T>::sub(v, xd)) <= eb);
-  xr = ok ? xd : v;
+  if (ok) xr = xd;
+  else xr = truncated<T>(v, texp);
   return ok ? (uint32_t)(q + (int)R) : 0u;
 }
 
@@ -134,6 +137,7 @@ __device__ __forceinline__ T dup_pred(F1 prim, F2 dupf, bool hit_p, uint32_t bit
 
 struct Hooks {
   uint32_t kp, bitp, kr, bitr, kfix;
+  int texp;  // truncation exponent of unpredictable values (kNoTrunc: raw encoding)
 };
 
 // ---------------------------------------------------------------- generic path
@@ -159,7 +163,8 @@ __device__ __noinline__ PassRes generic_pass(const T* __restrict__ field, const 
             [&] { return REG ? regress<T, NDIM, OpV<T>>(cT, i, j, l) : wk.template combine<OpV<T>>(); },
             k == hk.kp, hk.bitp, r.dup);
         T xr;
-        const uint32_t code = quantize<T, ABFT, true>(v, pred, eb, inv2, Rh, g.R, k == hk.kr, hk.bitr, xr, r.dup);
+        const uint32_t code = quantize<T, ABFT, true>(v, pred, eb, inv2, Rh, g.R, k == hk.kr, hk.bitr, xr, r.dup,
+                                                      hk.texp);
         codes[code_pos(b, g.P, k)] = (uint16_t)code;
         if (!code) {
           ustage[ci] = v;
@@ -315,7 +320,8 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
             },
             HOOK && k == hk.kp, hk.bitp, r.dup);
         T xr;
-        const uint32_t code = quantize<T, ABFT, HOOK>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup);
+        const uint32_t code =
+            quantize<T, ABFT, HOOK>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup, hk.texp);
         if (EDGE) {
           if (k & 1) pptr[(uint64_t)(k >> 1) * 32] = lowe | (code << 16);
           else lowe = code;
@@ -365,8 +371,9 @@ struct Prologue {
 // (which needs the coefficients) is summed here by `ereg()` just before the block is
 // predicted, so its re-read of the block hits the cache.
 template <class F>
-__device__ __forceinline__ bool choose_reg(const Geo& g, const Ws& w, uint64_t b, uint32_t S, float noise, F ereg) {
-  if (!(w.pflag[b] & 1)) return false;
+__device__ __forceinline__ bool choose_reg(const Geo& g, const Ws& w, uint64_t b, bool usable, uint32_t S, float noise,
+                                           F ereg) {
+  if (!usable) return false;
   if (g.predictor == 2) return true;
   if (g.predictor == 1) return false;
   const float Elor = w.est[b].y;
@@ -432,16 +439,67 @@ __device__ __forceinline__ float ereg_fast(const T* __restrict__ blk, uint64_t s
   return E;
 }
 
+// The coefficients a block is selected and predicted with. Raw encoding: the fitted fp32
+// values. Compact encoding: each becomes the nearest multiple of its step (a coefficient
+// that cannot be stored makes the block use Lorenzo), and the selection estimate uses the
+// dequantized values rounded to fp32.
+template <typename T>
+struct Consts;
+
+struct CoefSel {
+  float4 c4;  // for the selection estimate
+  bool ok;    // regression is possible
+  int k[4];   // compact encoding: the coefficient integers
+};
+
 template <typename T, int NDIM>
-__device__ __forceinline__ void load_coefs(const Ws& w, uint64_t b, const sdcsz_flip* flips, uint32_t nflips, T cT[4],
-                                           Hooks& hk) {
+__device__ __forceinline__ CoefSel coef_select(const Geo& g, const Ws& w, uint64_t b, const Consts<T>& K) {
+  CoefSel r;
+  r.c4 = w.coef[b];
+  r.ok = (w.pflag[b] & 1) != 0;
+  r.k[0] = r.k[1] = r.k[2] = r.k[3] = 0;
+  if (g.enc && r.ok) {
+    const float cf[4] = {r.c4.x, r.c4.y, r.c4.z, r.c4.w};
+    float cs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a <= NDIM; ++a) {
+      if (!r.ok) break;
+      r.ok = coef_to_int(cf[a], K.cs.inv[a], &r.k[a]);
+      cs[a] = FT<T>::tofloat(coef_from_int<T>(r.k[a], K.cs.step[a]));
+    }
+    r.c4 = make_float4(cs[0], cs[1], cs[2], cs[3]);
+  }
+  return r;
+}
+
+// Coefficients for prediction, with simulated memory errors applied to what is stored (the
+// dtype values, or the compact encoding's integers), and the block's other error hooks.
+template <typename T, int NDIM>
+__device__ __forceinline__ void load_coefs(const Geo& g, const Ws& w, uint64_t b, const sdcsz_flip* flips,
+                                           uint32_t nflips, T cT[4], Hooks& hk, CoefSel& cq, const Consts<T>& K) {
   const float4 c4 = w.coef[b];
   cT[0] = FT<T>::fromfloat(c4.x);
   cT[1] = FT<T>::fromfloat(c4.y);
   cT[2] = FT<T>::fromfloat(c4.z);
   cT[3] = FT<T>::fromfloat(c4.w);
+  hk.texp = K.texp;
   hk.kp = hk.kr = hk.kfix = kNone;
   hk.bitp = hk.bitr = 0;
+  if (g.enc) {
+    if (nflips) {
+      uint32_t lo = 0, hi = nflips;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (flips[mid].block < b) lo = mid + 1;
+        else hi = mid;
+      }
+      for (uint32_t t = lo; t < nflips && flips[t].block == b; ++t)
+        if (flips[t].site == SDCSZ_SITE_COEF && flips[t].index <= (uint64_t)NDIM)
+          cq.k[flips[t].index] = (int)((uint32_t)cq.k[flips[t].index] ^ (1u << (flips[t].bit & 31)));
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) cT[a] = a <= NDIM ? coef_from_int<T>(cq.k[a], K.cs.step[a]) : T(0);
+  }
   if (!nflips) return;
   uint32_t lo = 0, hi = nflips;
   while (lo < hi) {
@@ -451,7 +509,7 @@ __device__ __forceinline__ void load_coefs(const Ws& w, uint64_t b, const sdcsz_
   }
   for (uint32_t t = lo; t < nflips && flips[t].block == b; ++t) {
     const sdcsz_flip f = flips[t];
-    if (f.site == SDCSZ_SITE_COEF && f.index <= (uint64_t)NDIM) cT[f.index] = FT<T>::flip(cT[f.index], f.bit);
+    if (!g.enc && f.site == SDCSZ_SITE_COEF && f.index <= (uint64_t)NDIM) cT[f.index] = FT<T>::flip(cT[f.index], f.bit);
     if (f.site == SDCSZ_SITE_PRED && hk.kp == kNone) {
       hk.kp = (uint32_t)min(f.index, (uint64_t)kNone - 1);
       hk.bitp = f.bit;
@@ -463,16 +521,22 @@ __device__ __forceinline__ void load_coefs(const Ws& w, uint64_t b, const sdcsz_
   }
 }
 
+// The coefficients of a regression block are kept for the encoder: dtype values, or the
+// compact encoding's integers.
 template <typename T>
 __device__ __forceinline__ void block_epilogue(const Ws& w, uint64_t b, bool reg, int ndim, const T cT[4],
-                                               const PassRes& r, bool abft, uint8_t flag) {
+                                               const PassRes& r, bool abft, uint8_t flag, const Geo& g,
+                                               const CoefSel& cq) {
   if (abft) {
     w.sum_q[b] = r.sq;
     w.isum_q[b] = r.isq;
     w.sum_dc[b] = r.sdc;
   }
   w.flags[b] = flag | (reg ? 1 : 0);
-  if (reg) {
+  if (reg && g.enc) {
+    int* ki = static_cast<int*>(w.coefT) + 4 * b;
+    for (int a = 0; a <= ndim; ++a) ki[a] = cq.k[a];
+  } else if (reg) {
     T* coefT = static_cast<T*>(w.coefT) + 4 * b;
     for (int a = 0; a <= ndim; ++a) coefT[a] = cT[a];
   }
@@ -500,8 +564,13 @@ template <typename T>
 struct Consts {
   T eb, inv2, Rh;
   float noise;
-  __device__ __forceinline__ Consts(double ebd, uint32_t R, int ndim) {
+  int texp;      // compact encoding: truncation exponent of unpredictable values, else kNoTrunc
+  CoefSteps cs;  // compact encoding: coefficient steps
+  __device__ __forceinline__ Consts(double ebd, const Geo& g, int ndim) {
+    const uint32_t R = g.R;
     eb = (T)ebd;
+    texp = g.enc ? bound_exponent<T>(eb) : kNoTrunc;
+    if (g.enc) cs = coef_steps(g, (double)eb);
     if (sizeof(T) == 4) inv2 = (T)__double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, ebd)));
     else inv2 = (T)__ddiv_rn(1.0, __dmul_rn(2.0, ebd));
     Rh = FT<T>::sub(FT<T>::fromi((int)R), T(0.5));
@@ -564,11 +633,12 @@ __device__ __forceinline__ void predict_generic_block(const T* __restrict__ fiel
   T* ustage = static_cast<T*>(w.ustage);
   const Box x = block_box(g, b);
   const uint32_t S = sample_points(NDIM, x.e);
-  bool reg = choose_reg(g, w, b, S, K.noise,
-                        [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kNone, T(0)); });
+  CoefSel cq = coef_select<T, NDIM>(g, w, b, K);
+  bool reg = choose_reg(g, w, b, cq.ok, S, K.noise,
+                        [&] { return ereg_generic<T, NDIM>(field, g, x, cq.c4, kNone, T(0)); });
   T cT[4];
   Hooks hk;
-  load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
+  load_coefs<T, NDIM>(g, w, b, flips, nflips, cT, hk, cq, K);
   PassRes r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
                                                       h, hk, T(0))
                   : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage,
@@ -581,7 +651,7 @@ __device__ __forceinline__ void predict_generic_block(const T* __restrict__ fiel
       withdraw(w, g, b, x.P, h);
       hk.kfix = kf;
       // the selection estimate and the prediction both see the repaired value
-      reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kf, xf); });
+      reg = choose_reg(g, w, b, cq.ok, S, K.noise, [&] { return ereg_generic<T, NDIM>(field, g, x, cq.c4, kf, xf); });
       r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
                                                   hk, xf)
               : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
@@ -592,7 +662,7 @@ __device__ __forceinline__ void predict_generic_block(const T* __restrict__ fiel
       flag = 2;
     }
   }
-  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
+  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag, g, cq);
   cnt.unpred += r.nun;
   cnt.reg += reg;
   cnt.dup += r.dup;
@@ -618,7 +688,7 @@ __global__ void __launch_bounds__(128) k_predict(const T* __restrict__ field, Ge
   Hist h;
   hist_init(hist_s, h, g, w);
   __syncthreads();
-  const Consts<T> K(st->eb, g.R, NDIM);
+  const Consts<T> K(st->eb, g, NDIM);
   Walker<T, NDIM> wk;
   walker_init(wk, smem, g);
   Counters cnt;
@@ -649,7 +719,7 @@ __global__ void __launch_bounds__(128) k_predict_batch(BatchArgs a) {
         const uint64_t e = it * blockDim.x + threadIdx.x;
         if (e < s_job.gcount) {
           const Geo& g = s_job.g;
-          const Consts<T> K(s_job.w.st->eb, g.R, NDIM);
+          const Consts<T> K(s_job.w.st->eb, g, NDIM);
           Walker<T, NDIM> wk;
           walker_init(wk, smem, g);
           predict_generic_block<T, NDIM, ABFT>(static_cast<const T*>(s_job.field), g, s_job.w, nullptr, 0,
@@ -711,15 +781,16 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
     blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
   }
   const uint32_t S = EDGE ? sample_points(NDIM, x.e) : (NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2);
+  CoefSel cq = coef_select<T, NDIM>(g, w, b, K);
   auto ereg = [&](uint32_t kf, T xf) {
-    if (EDGE) return ereg_generic<T, NDIM>(field, g, x, w.coef[b], kf, xf);
-    if (kf != kNone) return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, w.coef[b], kf, xf);
-    return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, w.coef[b], kNone, T(0));
+    if (EDGE) return ereg_generic<T, NDIM>(field, g, x, cq.c4, kf, xf);
+    if (kf != kNone) return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, cq.c4, kf, xf);
+    return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, cq.c4, kNone, T(0));
   };
-  bool reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg(kNone, T(0)); });
+  bool reg = choose_reg(g, w, b, cq.ok, S, K.noise, [&] { return ereg(kNone, T(0)); });
   T cT[4];
   Hooks hk;
-  load_coefs<T, NDIM>(w, b, flips, nflips, cT, hk);
+  load_coefs<T, NDIM>(g, w, b, flips, nflips, cT, hk, cq, K);
   uint32_t* cptr = reinterpret_cast<uint32_t*>(w.codes) + pair_index(b, P, 0);
   T* uptr = ustage + code_index(b, P, 0);
   const bool hooked = (hk.kp != kNone) || (hk.kr != kNone);
@@ -735,7 +806,7 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
     if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
       withdraw(w, g, b, Pb, h);
       hk.kfix = kf;
-      reg = choose_reg(g, w, b, S, K.noise, [&] { return ereg(kf, xf); });
+      reg = choose_reg(g, w, b, cq.ok, S, K.noise, [&] { return ereg(kf, xf); });
       r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
                                                                hk, xf, e);
       ++cnt.fix;
@@ -744,7 +815,7 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
       flag = 2;
     }
   }
-  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag);
+  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag, g, cq);
   cnt.unpred += r.nun;
   cnt.reg += reg;
   cnt.dup += r.dup;
@@ -763,7 +834,7 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_edge(const T* 
   Hist h;
   hist_init(hist_s, h, g, w);
   __syncthreads();
-  const Consts<T> K(st->eb, g.R, NDIM);
+  const Consts<T> K(st->eb, g, NDIM);
   T* plane = reinterpret_cast<T*>(smem) + threadIdx.x;
   Counters cnt;
   for (uint64_t it = cta_pull(&st->queue[1]); it * blockDim.x < count; it = cta_pull(&st->queue[1])) {
@@ -788,7 +859,7 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast(const T* 
   Hist h;
   hist_init(hist_s, h, g, w);
   __syncthreads();
-  const Consts<T> K(st->eb, g.R, NDIM);
+  const Consts<T> K(st->eb, g, NDIM);
   T* plane = reinterpret_cast<T*>(smem) + threadIdx.x;
   Counters cnt;
   for (uint64_t it = cta_pull(&st->queue[0]); it * blockDim.x < g.nb; it = cta_pull(&st->queue[0])) {
@@ -817,7 +888,7 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast_batch(Bat
       [&](uint64_t it) {
         const uint64_t b = it * blockDim.x + threadIdx.x;
         if (b < s_job.g.nb) {
-          const Consts<T> K(s_job.w.st->eb, s_job.g.R, NDIM);
+          const Consts<T> K(s_job.w.st->eb, s_job.g, NDIM);
           predict_fast_block<T, NDIM, B0, B1, B2, ABFT>(static_cast<const T*>(s_job.field), s_job.g, s_job.w,
                                                         nullptr, 0, s_job.vec2, b, plane, K, h, cnt);
         }

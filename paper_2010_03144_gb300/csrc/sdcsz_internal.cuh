@@ -35,6 +35,7 @@ struct Geo {
   uint32_t P;  // points in a full block
   uint32_t bins, R;
   int abft, predictor, eb_mode;
+  int enc;  // 1: compact encoding (coefficients and unpredictable values in the payload)
   double e;
 };
 
@@ -111,8 +112,8 @@ __host__ __device__ inline Layout make_layout(const Geo& g, uint64_t n_live, uin
   L.bitmap = align16(L.ucounts + 2 * g.nb);
   L.sumdc = align16(L.bitmap + 4 * ((g.nb + 31) / 32));
   L.coef = align16(L.sumdc + (g.abft ? 8 * g.nb : 0));
-  L.unpred = align16(L.coef + s * (uint64_t)(g.ndim + 1) * n_reg);
-  L.payload = align16(L.unpred + s * n_unpred);
+  L.unpred = align16(L.coef + (g.enc ? 0 : s * (uint64_t)(g.ndim + 1) * n_reg));
+  L.payload = align16(L.unpred + (g.enc ? 0 : s * n_unpred));
   return L;
 }
 
@@ -285,6 +286,82 @@ template <> struct FT<double> {
   }
   __device__ static __forceinline__ bool is_normal_pos(double v) { return v >= 2.2250738585072014e-308 && v <= 1.7976931348623157e308; }
 };
+
+// ---------------------------------------------------------------- compact encoding
+// Bit fields of the dtype (mantissa bits, exponent bits, bias) and the value as an integer.
+template <typename T> struct Bitsof;
+template <> struct Bitsof<float> {
+  typedef uint32_t U;
+  static constexpr int M = 23, E = 8, BIAS = 127;
+  __device__ static __forceinline__ U raw(float v) { return __float_as_uint(v); }
+  __device__ static __forceinline__ float val(U u) { return __uint_as_float(u); }
+};
+template <> struct Bitsof<double> {
+  typedef unsigned long long U;
+  static constexpr int M = 52, E = 11, BIAS = 1023;
+  __device__ static __forceinline__ U raw(double v) { return (U)__double_as_longlong(v); }
+  __device__ static __forceinline__ double val(U u) { return __longlong_as_double((long long)u); }
+};
+
+// floor(log2(eb)) of the dtype bound eb (normal); kNoTrunc keeps every mantissa bit.
+constexpr int kNoTrunc = -100000;
+template <typename T>
+__device__ __forceinline__ int bound_exponent(T eb) {
+  return (int)((Bitsof<T>::raw(eb) >> Bitsof<T>::M) & ((1u << Bitsof<T>::E) - 1)) - Bitsof<T>::BIAS;
+}
+
+// Mantissa bits an unpredictable value keeps so that dropping the rest errs by less than
+// 2^texp <= eb: with v in [2^ex, 2^(ex+1)) that is ex - texp bits, clamped to [0, M]; zeros,
+// subnormals, infinities and NaNs keep all of them.
+template <typename T>
+__device__ __forceinline__ int kept_bits(T v, int texp) {
+  const int Ex = (int)((Bitsof<T>::raw(v) >> Bitsof<T>::M) & ((1u << Bitsof<T>::E) - 1));
+  if (Ex == 0 || Ex == (1 << Bitsof<T>::E) - 1) return Bitsof<T>::M;
+  return min(max(Ex - Bitsof<T>::BIAS - texp, 0), Bitsof<T>::M);
+}
+
+// The value an unpredictable point decompresses to (v itself when texp is kNoTrunc).
+template <typename T>
+__device__ __forceinline__ T truncated(T v, int texp) {
+  const int drop = Bitsof<T>::M - kept_bits<T>(v, texp);
+  typedef typename Bitsof<T>::U U;
+  return Bitsof<T>::val(Bitsof<T>::raw(v) & ~((((U)1) << drop) - (U)1));
+}
+
+// Steps of the coefficient integers: slope a (of ndim) eb / (16 B_a), intercept eb / 16, for
+// the absolute bound E (the dtype value widened); inverse steps for the rounding.
+struct CoefSteps {
+  double step[4], inv[4];
+};
+__host__ __device__ inline CoefSteps coef_steps(const Geo& g, double E) {
+  CoefSteps q;
+  const int off = 3 - g.ndim;
+  for (int a = 0; a < 4; ++a) q.step[a] = q.inv[a] = 0.0;
+  for (int a = 0; a < g.ndim; ++a) {
+    const double d = 16.0 * (double)g.B[off + a];
+    q.step[a] = E / d;
+    q.inv[a] = d / E;
+  }
+  q.step[g.ndim] = E / 16.0;
+  q.inv[g.ndim] = 16.0 / E;
+  return q;
+}
+
+// Nearest multiple of the step, halves away from zero; false unless below 2^30 steps.
+__device__ __forceinline__ bool coef_to_int(float c, double inv, int* k) {
+  const double t = __dmul_rn((double)c, inv);
+  if (!(fabs(t) < 1073741824.0)) return false;
+  const double m = floor(__dadd_rn(fabs(t), 0.5));
+  *k = (int)(t < 0.0 ? -m : m);
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T coef_from_int(int k, double step) {
+  const double v = __dmul_rn((double)k, step);
+  if (sizeof(T) == 4) return (T)__double2float_rn(v);
+  return (T)v;
+}
 
 // Checksum words of one value at point k: sum += words, isum += (word index + 1) * word
 // (Sec. 3.2 and 5.4; float64 = two 32-bit words, low word first).
@@ -602,7 +679,7 @@ void batch_predict_generic(int dtype, int ndim, bool abft, const BatchArgs& a, u
 void batch_codebook(const Job* jobs, uint32_t n, const Launch& L);
 void batch_encode_blocks(int dtype, bool abft, const BatchArgs& a, const Launch& L);
 void batch_encode_assemble(int dtype, const BatchArgs& a, const Launch& L);
-uint64_t encode_slot_words(uint32_t P);
+uint64_t encode_slot_words(const Geo& g);
 
 // Parsed stream header (host side) for the decoder.
 struct Hdr {
@@ -611,6 +688,8 @@ struct Hdr {
   uint32_t n_live;
   uint64_t n_reg, n_unpred, payload_bytes, total;
   double eb;
+  int texp;         // compact encoding: floor(log2 eb), the truncation exponent of unpredictable values
+  double cstep[4];  // compact encoding: steps of the coefficient integers
 };
 // Blocks intersecting the box [lo, hi) (padded 3D coordinates) into a dense array of its shape.
 void launch_region(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
