@@ -195,8 +195,9 @@ def run_ours(args):
     x = synth.sinusoid_field(shape, wl["seed"] + rank, spikes=wl["spikes"])
     N, s_dt = x.size, 4
     d = torch.from_numpy(x).to(device)
-    p_on = sz.make_params(shape, np.float32, REL_EB, block=block, abft=True)
-    p_off = sz.make_params(shape, np.float32, REL_EB, block=block, abft=False)
+    enc = args.encoding
+    p_on = sz.make_params(shape, np.float32, REL_EB, block=block, abft=True, encoding=enc)
+    p_off = sz.make_params(shape, np.float32, REL_EB, block=block, abft=False, encoding=enc)
     ws_on = sz.Workspace(p_on, device)
     ws_off = sz.Workspace(p_off, device)
     out = torch.empty(shape, dtype=torch.float32, device=device)
@@ -213,7 +214,7 @@ def run_ours(args):
         return nbytes
 
     # reports of one run for counts and the compression ratio
-    s_t, rep = sz.compress(d, REL_EB, block=block, workspace=ws_on)
+    s_t, rep = sz.compress(d, REL_EB, block=block, workspace=ws_on, encoding=enc)
     stream_bytes = int(rep["compressed_bytes"])
     rc, y, st, rep_d = sz.decompress(s_t, out=out, ws=dws)
     assert rc == 0
@@ -280,7 +281,7 @@ def run_ours(args):
 
     def e2e_step():
         d_in.copy_(h_field, non_blocking=True)
-        s_out, r = sz.compress(d_in, REL_EB, block=block, workspace=ws_on)
+        s_out, r = sz.compress(d_in, REL_EB, block=block, workspace=ws_on, encoding=enc)
         n = int(r["compressed_bytes"])
         h_stream[:n].copy_(s_out, non_blocking=True)
         d_s[:n].copy_(h_stream[:n], non_blocking=True)
@@ -320,7 +321,8 @@ def run_ours(args):
             "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload} float32 {shape} sinusoids+noise+{wl['spikes']:.0%} spikes, "
-                                   f"rel eb {REL_EB}, block {block}^3, ABFT on; one step = compress + decompress",
+                                   f"rel eb {REL_EB}, block {block}^3, ABFT on, {enc} encoding; "
+                                   "one step = compress + decompress",
                        "field_bytes": N * s_dt, "compressed_bytes": stream_bytes,
                        "compression_ratio": round(N * s_dt / stream_bytes, 3),
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"{world} independent replicas"},
@@ -366,7 +368,7 @@ def cpu_baseline(args):
     x, slab = _oracle_sample(args)
     oracle.lib()
     t0 = time.perf_counter()
-    s, rep = oracle.compress(x, REL_EB, block=WORKLOADS[args.workload]["block"])
+    s, rep = oracle.compress(x, REL_EB, block=WORKLOADS[args.workload]["block"], encoding=args.encoding)
     rc, y, st, _ = oracle.decompress(s)
     dt = time.perf_counter() - t0
     return {"value": round(x.nbytes / 1e9 / dt, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
@@ -384,10 +386,10 @@ def run_reference(args):
     oracle.lib()
     block = WORKLOADS[args.workload]["block"]
     for _ in range(args.warmup):
-        oracle.compress(x[:8], REL_EB, block=block)
+        oracle.compress(x[:8], REL_EB, block=block, encoding=args.encoding)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, rep = oracle.compress(x, REL_EB, block=block)
+        s, rep = oracle.compress(x, REL_EB, block=block, encoding=args.encoding)
         oracle.decompress(s)
     dt = time.perf_counter() - t0
     value = x.nbytes * args.steps / 1e9 / dt
@@ -395,7 +397,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"{args.workload} recipe, slab {slab} per step, rel eb {REL_EB}, block {block}^3, "
-                                  f"ABFT on; one step = compress + decompress"},
+                                  f"ABFT on, {args.encoding} encoding; one step = compress + decompress"},
            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                             "sample": f"{slab} slab per step"},
            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -754,6 +756,8 @@ def main():
                     default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
+    ap.add_argument("--encoding", choices=("raw", "compact"), default="raw",
+                    help="stream encoding: raw coefficient/unpredictable sections, or compact (in the payload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -688,6 +688,7 @@ struct BatchLaunch {
   int dtype, ndim;
   uint32_t B;
   bool abft;
+  bool enc;  // compact encoding (the fast predict kernels are instantiated per encoding)
   uint32_t threads;
   size_t smem;
   std::vector<uint32_t> jobs;
@@ -749,10 +750,10 @@ void batch_fill_jobs(sdcsz_batch* b) {
 void batch_plan_launches(sdcsz_batch* b) {
   b->launches.clear();
   auto add = [&](BatchKind kind, int dtype, int ndim, uint32_t B, bool abft, uint32_t threads, size_t smem,
-                 uint32_t j, uint64_t items) {
+                 uint32_t j, uint64_t items, bool enc = false) {
     if (!items) return;
     for (auto& L : b->launches)
-      if (L.kind == kind && L.dtype == dtype && L.ndim == ndim && L.B == B && L.abft == abft) {
+      if (L.kind == kind && L.dtype == dtype && L.ndim == ndim && L.B == B && L.abft == abft && L.enc == enc) {
         L.jobs.push_back(j);
         L.items.push_back(items);
         L.threads = std::min(L.threads, threads);
@@ -765,6 +766,7 @@ void batch_plan_launches(sdcsz_batch* b) {
     L.ndim = ndim;
     L.B = B;
     L.abft = abft;
+    L.enc = enc;
     L.threads = threads;
     L.smem = smem;
     L.jobs.push_back(j);
@@ -778,7 +780,7 @@ void batch_plan_launches(sdcsz_batch* b) {
     const uint32_t slots = walker_slots(g.ndim, g.B);
     if (jb.fast) {
       add(BK_PREP_FAST, g.dtype, g.ndim, g.B[2], false, 128, 0, j, ceil_div(g.nb, 128));
-      add(BK_PREDICT_FAST, g.dtype, g.ndim, g.B[2], g.abft != 0, 128, 0, j, ceil_div(g.nb, 128));
+      add(BK_PREDICT_FAST, g.dtype, g.ndim, g.B[2], g.abft != 0, 128, 0, j, ceil_div(g.nb, 128), g.enc != 0);
     }
     add(BK_PREP_GENERIC, g.dtype, g.ndim, 0, false, 128, g.predictor == 0 ? (size_t)slots * 128 * 4 : 0, j,
         ceil_div(jb.gcount, 128));
@@ -849,7 +851,7 @@ int batch_enqueue(sdcsz_batch* b, cudaStream_t s) {
     for (auto& Q : b->launches) {
       if (Q.kind == fast_kind) {
         if (fast_kind == BK_PREP_FAST) batch_prep_fast(Q.dtype, Q.ndim, Q.B, Q.args, L);
-        else batch_predict_fast(Q.dtype, Q.ndim, Q.B, Q.abft, Q.args, L);
+        else batch_predict_fast(Q.dtype, Q.ndim, Q.B, Q.abft, Q.enc, Q.args, L);
       }
     }
     cudaEventRecord(b->ev[e + 1], b->side);

@@ -225,8 +225,9 @@ __device__ __forceinline__ T read_unpred(Reader& br, int texp) {
 // The coefficients of a regression block: stored dtype values, or (compact encoding) the
 // integers at the head of its payload times their steps.
 template <typename T, int NDIM, class Reader>
-__device__ __forceinline__ bool block_coefs(const uint8_t* s, const Hdr& h, int64_t reg_idx, Reader& br, T cT[4]) {
-  if (h.g.enc) {
+__device__ __forceinline__ bool block_coefs(const uint8_t* s, const Hdr& h, int64_t reg_idx, Reader& br, T cT[4],
+                                            bool compact) {
+  if (compact) {
     bool ok = true;
 #pragma unroll
     for (int a = 0; a <= NDIM; ++a) {
@@ -316,7 +317,7 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
   BitReader br;
   br.init(s + h.L.payload + bi.pay_off, lim);
   bool ok = true;
-  if (reg) ok = block_coefs<T, NDIM>(s, h, bi.reg_idx, br, cT);
+  if (reg) ok = block_coefs<T, NDIM>(s, h, bi.reg_idx, br, cT, h.g.enc != 0);
   uint32_t used_u = 0, k = 0;
   unsigned long long sum = 0, nv = 0;
   double me = 0.0;
@@ -369,7 +370,7 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
 // ---------------------------------------------------------------- fast path (full blocks)
 // WRITE: decompression (the block is stored to blk_out); otherwise verification (compared
 // with blk_orig when there is one).
-template <typename T, int NDIM, int B0, int B1, int B2, bool REG, bool HOOK, bool WRITE>
+template <typename T, int NDIM, int B0, int B1, int B2, bool REG, bool HOOK, bool WRITE, bool CMP>
 __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const uint8_t* lim, const Hdr& h,
                                             const BlockIn& bi, const Tables& tb, T* plane, T* __restrict__ blk_out,
                                             const T* __restrict__ blk_orig, uint64_t si, uint64_t sj, bool vec2,
@@ -384,7 +385,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
   br.init(s + h.L.payload + bi.pay_off);
   (void)lim;
   bool ok = true;
-  if (REG) ok = block_coefs<T, NDIM>(s, h, bi.reg_idx, br, cT);
+  if (REG) ok = block_coefs<T, NDIM>(s, h, bi.reg_idx, br, cT, CMP);
   uint32_t used_u = 0;
   unsigned long long sum = 0, nv = 0;
   double me = 0.0;
@@ -416,8 +417,8 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       for (int l = 0; l < B2; ++l) {
         int q;
         if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
-          if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp, h.g.enc != 0);
-          else q = qp == kDefer ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : qp;
+          if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp, CMP);
+          else q = (CMP && qp == kDefer) ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : qp;
         } else {
           q = br.next(tb.lut, *tb.cn, tb.syms, tb.n_live);
         }
@@ -448,7 +449,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
         T xr = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
         if (q <= 0) {  // unpredictable value (code 0) or an undecodable block (rare)
           xr = T(0);
-          if (q == 0 && used_u < bi.ucnt) xr = h.g.enc ? read_unpred<T>(br, h.texp) : un[used_u];
+          if (q == 0 && used_u < bi.ucnt) xr = CMP ? read_unpred<T>(br, h.texp) : un[used_u];
           else ok = false;
           ++used_u;
         }
@@ -890,20 +891,21 @@ __global__ void __launch_bounds__(256) k_decode_region(const uint8_t* __restrict
   acc.commit(st);
 }
 
-template <typename T, int NDIM, int B0, int B1, int B2, bool HOOK, bool WRITE>
+template <typename T, int NDIM, int B0, int B1, int B2, bool HOOK, bool WRITE, bool CMP>
 __device__ __forceinline__ bool fast_dispatch(bool reg, const uint8_t* s, const uint8_t* lim, const Hdr& h,
                                               const BlockIn& bi, const Tables& tb, T* plane, T* out, const T* org,
                                               uint64_t si, uint64_t sj, bool vec2, uint32_t kinj, uint32_t bitinj,
                                               unsigned long long* sum, unsigned long long* nv, double* me) {
   if (reg)
-    return decode_fast<T, NDIM, B0, B1, B2, true, HOOK, WRITE>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj,
-                                                               bitinj, sum, nv, me);
-  return decode_fast<T, NDIM, B0, B1, B2, false, HOOK, WRITE>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2, kinj,
-                                                              bitinj, sum, nv, me);
+    return decode_fast<T, NDIM, B0, B1, B2, true, HOOK, WRITE, CMP>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2,
+                                                                    kinj, bitinj, sum, nv, me);
+  return decode_fast<T, NDIM, B0, B1, B2, false, HOOK, WRITE, CMP>(s, lim, h, bi, tb, plane, out, org, si, sj, vec2,
+                                                                   kinj, bitinj, sum, nv, me);
 }
 
-// Fast kernel: full blocks of a compile-time shape (WRITE: decompression, else verification).
-template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE>
+// Fast kernel: full blocks of a compile-time shape (WRITE: decompression, else verification;
+// CMP: compact encoding).
+template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE, bool CMP>
 __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
                                                      uint8_t* status, const T* orig, State* st,
                                                      const sdcsz_flip* __restrict__ flips, uint32_t nflips,
@@ -915,7 +917,7 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
   if (!cta_tables(s, h, sm, lut, syms, st)) return;
   uint2* lut2 = reinterpret_cast<uint2*>(smem + (4u << kLutBits));
   __syncthreads();
-  pair_table(lut2, lut, h.g.enc != 0);
+  pair_table(lut2, lut, CMP);
   __syncthreads();
   const Tables tb = {lut, &sm.cn, syms, h.n_live, lut2};
   const uint8_t* lim = s + nbytes;
@@ -959,7 +961,7 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
       // encoding also a whole value per point and 4 coefficients of at most 38 bits), reads at
       // most 12 bytes ahead of what it consumed and starts up to 3 bytes early; blocks whose
       // worst case could reach the end of the stream take the bounds-checked reader.
-      const uint64_t worst = h.g.enc ? (3ull + sizeof(T)) * (B0 * B1 * B2) + 19 : 3ull * (B0 * B1 * B2);
+      const uint64_t worst = CMP ? (3ull + sizeof(T)) * (B0 * B1 * B2) + 19 : 3ull * (B0 * B1 * B2);
       const bool safe = (uint64_t)(lim - (s + h.L.payload)) >= bi.pay_off + worst + 16;
       const uint8_t stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv,
                                                      double* me) {
@@ -967,9 +969,11 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
           return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone, bitinj, sum, nv,
                                          me);
         if (first && kinj != kNone)
-          return fast_dispatch<T, NDIM, B0, B1, B2, true, WRITE>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2,
+          return fast_dispatch<T, NDIM, B0, B1, B2, true, WRITE, CMP>(reg, s, lim, h, bi, tb, plane, out, org, si, sj,
+                                                                      vec2,
                                                                  kinj, bitinj, sum, nv, me);
-        return fast_dispatch<T, NDIM, B0, B1, B2, false, WRITE>(reg, s, lim, h, bi, tb, plane, out, org, si, sj, vec2,
+        return fast_dispatch<T, NDIM, B0, B1, B2, false, WRITE, CMP>(reg, s, lim, h, bi, tb, plane, out, org, si, sj,
+                                                                      vec2,
                                                                 kNone, 0, sum, nv, me);
       }, acc);
       if (status) status[b] = stv;
@@ -989,7 +993,8 @@ template <typename T, int NDIM, int B0, int B1, int B2>
 void run_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
               const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
   const size_t smem = (12u << kLutBits) + (size_t)walker_slots(NDIM, h.g.B) * 256 * sizeof(T);  // lut, pair lut, plane
-  auto kern = field ? k_decode_fast<T, NDIM, B0, B1, B2, true> : k_decode_fast<T, NDIM, B0, B1, B2, false>;
+  auto kern = h.g.enc ? (field ? k_decode_fast<T, NDIM, B0, B1, B2, true, true> : k_decode_fast<T, NDIM, B0, B1, B2, false, true>)
+                      : (field ? k_decode_fast<T, NDIM, B0, B1, B2, true, false> : k_decode_fast<T, NDIM, B0, B1, B2, false, false>);
   const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
   const unsigned grid = persistent_grid(kern, 256, smem, ngroups, L);
   const uintptr_t al = 2 * sizeof(T);

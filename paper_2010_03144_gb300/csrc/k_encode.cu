@@ -231,12 +231,13 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
     reg = w.flags[b] & 1;
     const uint32_t* pp = reinterpret_cast<const uint32_t*>(w.codes) + pair_index(b, g.P, 0);
     uint32_t* slot = w.etmp + b * slot_words_of(g);
-    T* up = static_cast<T*>(w.ustage) + code_index(b, g.P, 0);
-    Extra<T> ex;
-    ex.kq = static_cast<const int*>(w.coefT) + 4 * b;
-    ex.nco = reg ? g.ndim + 1 : 0;
-    ex.up = up;
-    ex.texp = CMP ? bound_exponent<T>((T)st->eb) : kNoTrunc;
+    Extra<T> ex = {nullptr, 0, nullptr, kNoTrunc};
+    if (CMP) {
+      ex.kq = static_cast<const int*>(w.coefT) + 4 * b;
+      ex.nco = reg ? g.ndim + 1 : 0;
+      ex.up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
+      ex.texp = bound_exponent<T>((T)st->eb);
+    }
     EncRes e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, 0u, 0u, ex);
     uint32_t kfix = 0xffffffffu, vfix = 0;
     bool bad = false;
@@ -264,6 +265,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
     // unpredictable values to the front of the block's staging slot, in order (in place: the
     // j-th value moves down from its point k >= j); the compact encoding has them in the payload
     if (!CMP) {
+      T* up = static_cast<T*>(w.ustage) + code_index(b, g.P, 0);
       if (e.nun <= kPosKept) {
 #pragma unroll
         for (uint32_t j = 0; j < kPosKept; ++j)

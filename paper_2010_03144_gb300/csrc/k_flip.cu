@@ -56,15 +56,15 @@ void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint3
 }
 
 
-bool batch_predict_fast_f32(int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L);
-bool batch_predict_fast_f64(int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L);
+bool batch_predict_fast_f32(int ndim, uint32_t B, bool abft, bool enc, const BatchArgs& a, const Launch& L);
+bool batch_predict_fast_f64(int ndim, uint32_t B, bool abft, bool enc, const BatchArgs& a, const Launch& L);
 void batch_predict_generic_f32(int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
                                const Launch& L);
 void batch_predict_generic_f64(int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
                                const Launch& L);
 
-bool batch_predict_fast(int dtype, int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L) {
-  return dtype == 0 ? batch_predict_fast_f32(ndim, B, abft, a, L) : batch_predict_fast_f64(ndim, B, abft, a, L);
+bool batch_predict_fast(int dtype, int ndim, uint32_t B, bool abft, bool enc, const BatchArgs& a, const Launch& L) {
+  return dtype == 0 ? batch_predict_fast_f32(ndim, B, abft, enc, a, L) : batch_predict_fast_f64(ndim, B, abft, enc, a, L);
 }
 
 void batch_predict_generic(int dtype, int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,

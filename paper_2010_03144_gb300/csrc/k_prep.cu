@@ -413,6 +413,13 @@ __device__ __forceinline__ void bound_of(const Geo& g, State* st) {
   else eb = (T)ebd;
   if (!FT<T>::is_normal_pos(eb)) atomicOr(&st->error, ERR_EB);
   st->eb = (double)eb;
+  if (g.enc) {
+    const CoefSteps cs = coef_steps(g, (double)eb);
+    for (int a = 0; a < 4; ++a) {
+      st->cstep[a] = cs.step[a];
+      st->cinv[a] = cs.inv[a];
+    }
+  }
 }
 
 template <typename T>

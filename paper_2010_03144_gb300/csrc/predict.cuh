@@ -96,7 +96,7 @@ __device__ __forceinline__ void sum_words(T v, unsigned long long& sum) {
 // Returns the code (0 = unpredictable) and the value later points are predicted from.
 // An unpredictable point decompresses to its value, truncated to the mantissa bits the bound
 // needs in the compact encoding (texp = floor(log2 eb)); texp = kNoTrunc keeps it whole.
-template <typename T, bool ABFT, bool HOOK>
+template <typename T, bool ABFT, bool HOOK, bool CMP>
 __device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, uint32_t R, bool hit_r, uint32_t bitr,
                                              T& xr, uint32_t& dup, int texp) {
   const T diff = FT<T>::sub(v, pred);
@@ -116,7 +116,7 @@ __device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, ui
   }
   const bool ok = inr && (FT<T>::absv(FT<T>::sub(v, xd)) <= eb);
   if (ok) xr = xd;
-  else xr = truncated<T>(v, texp);
+  else xr = CMP ? truncated<T>(v, texp) : v;
   return ok ? (uint32_t)(q + (int)R) : 0u;
 }
 
@@ -163,7 +163,7 @@ __device__ __noinline__ PassRes generic_pass(const T* __restrict__ field, const 
             [&] { return REG ? regress<T, NDIM, OpV<T>>(cT, i, j, l) : wk.template combine<OpV<T>>(); },
             k == hk.kp, hk.bitp, r.dup);
         T xr;
-        const uint32_t code = quantize<T, ABFT, true>(v, pred, eb, inv2, Rh, g.R, k == hk.kr, hk.bitr, xr, r.dup,
+        const uint32_t code = quantize<T, ABFT, true, true>(v, pred, eb, inv2, Rh, g.R, k == hk.kr, hk.bitr, xr, r.dup,
                                                       hk.texp);
         codes[code_pos(b, g.P, k)] = (uint16_t)code;
         if (!code) {
@@ -214,7 +214,8 @@ __device__ __forceinline__ void load_row_n(const T* __restrict__ row, uint32_t n
 // EDGE: a block cut by the field boundary, extents e0 x e1 x e2 at most B0 x B1 x B2 (the
 // loops keep their compile-time bounds and skip what lies outside; codes are paired by the
 // block-local index, which need not start a row on a pair).
-template <typename T, int NDIM, int B0, int B1, int B2, int kCta, bool REG, bool ABFT, bool HOOK, bool EDGE = false>
+template <typename T, int NDIM, int B0, int B1, int B2, int kCta, bool REG, bool ABFT, bool HOOK, bool CMP,
+          bool EDGE = false>
 __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t si, uint64_t sj, bool vec2,
                                              const T* cT, T* plane, T eb, T inv2, T Rh, uint32_t R,
                                              uint32_t* __restrict__ pptr, T* __restrict__ uptr, const Hist& h,
@@ -321,7 +322,7 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
             HOOK && k == hk.kp, hk.bitp, r.dup);
         T xr;
         const uint32_t code =
-            quantize<T, ABFT, HOOK>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup, hk.texp);
+            quantize<T, ABFT, HOOK, CMP>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup, hk.texp);
         if (EDGE) {
           if (k & 1) pptr[(uint64_t)(k >> 1) * 32] = lowe | (code << 16);
           else lowe = code;
@@ -452,8 +453,9 @@ struct CoefSel {
   int k[4];   // compact encoding: the coefficient integers
 };
 
+// (the steps come from the call's State, where the bound kernel put them)
 template <typename T, int NDIM>
-__device__ __forceinline__ CoefSel coef_select(const Geo& g, const Ws& w, uint64_t b, const Consts<T>& K) {
+__device__ __forceinline__ CoefSel coef_select(const Geo& g, const Ws& w, uint64_t b) {
   CoefSel r;
   r.c4 = w.coef[b];
   r.ok = (w.pflag[b] & 1) != 0;
@@ -464,8 +466,8 @@ __device__ __forceinline__ CoefSel coef_select(const Geo& g, const Ws& w, uint64
 #pragma unroll
     for (int a = 0; a <= NDIM; ++a) {
       if (!r.ok) break;
-      r.ok = coef_to_int(cf[a], K.cs.inv[a], &r.k[a]);
-      cs[a] = FT<T>::tofloat(coef_from_int<T>(r.k[a], K.cs.step[a]));
+      r.ok = coef_to_int(cf[a], w.st->cinv[a], &r.k[a]);
+      cs[a] = FT<T>::tofloat(coef_from_int<T>(r.k[a], w.st->cstep[a]));
     }
     r.c4 = make_float4(cs[0], cs[1], cs[2], cs[3]);
   }
@@ -473,7 +475,9 @@ __device__ __forceinline__ CoefSel coef_select(const Geo& g, const Ws& w, uint64
 }
 
 // Coefficients for prediction, with simulated memory errors applied to what is stored (the
-// dtype values, or the compact encoding's integers), and the block's other error hooks.
+// dtype values, or the compact encoding's integers), and the block's other error hooks. The
+// compact encoding's integers are kept for the encoder here (it reads them for regression
+// blocks only), so that nothing of the selection stays live through the block's pass.
 template <typename T, int NDIM>
 __device__ __forceinline__ void load_coefs(const Geo& g, const Ws& w, uint64_t b, const sdcsz_flip* flips,
                                            uint32_t nflips, T cT[4], Hooks& hk, CoefSel& cq, const Consts<T>& K) {
@@ -497,8 +501,12 @@ __device__ __forceinline__ void load_coefs(const Geo& g, const Ws& w, uint64_t b
         if (flips[t].site == SDCSZ_SITE_COEF && flips[t].index <= (uint64_t)NDIM)
           cq.k[flips[t].index] = (int)((uint32_t)cq.k[flips[t].index] ^ (1u << (flips[t].bit & 31)));
     }
+    int* ki = static_cast<int*>(w.coefT) + 4 * b;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) cT[a] = a <= NDIM ? coef_from_int<T>(cq.k[a], K.cs.step[a]) : T(0);
+    for (int a = 0; a < 4; ++a) {
+      cT[a] = a <= NDIM ? coef_from_int<T>(cq.k[a], w.st->cstep[a]) : T(0);
+      if (a <= NDIM) ki[a] = cq.k[a];
+    }
   }
   if (!nflips) return;
   uint32_t lo = 0, hi = nflips;
@@ -521,22 +529,18 @@ __device__ __forceinline__ void load_coefs(const Geo& g, const Ws& w, uint64_t b
   }
 }
 
-// The coefficients of a regression block are kept for the encoder: dtype values, or the
-// compact encoding's integers.
+// The coefficients of a regression block are kept for the encoder (the compact encoding's
+// integers were kept by load_coefs).
 template <typename T>
 __device__ __forceinline__ void block_epilogue(const Ws& w, uint64_t b, bool reg, int ndim, const T cT[4],
-                                               const PassRes& r, bool abft, uint8_t flag, const Geo& g,
-                                               const CoefSel& cq) {
+                                               const PassRes& r, bool abft, uint8_t flag, const Geo& g) {
   if (abft) {
     w.sum_q[b] = r.sq;
     w.isum_q[b] = r.isq;
     w.sum_dc[b] = r.sdc;
   }
   w.flags[b] = flag | (reg ? 1 : 0);
-  if (reg && g.enc) {
-    int* ki = static_cast<int*>(w.coefT) + 4 * b;
-    for (int a = 0; a <= ndim; ++a) ki[a] = cq.k[a];
-  } else if (reg) {
+  if (reg && !g.enc) {
     T* coefT = static_cast<T*>(w.coefT) + 4 * b;
     for (int a = 0; a <= ndim; ++a) coefT[a] = cT[a];
   }
@@ -564,13 +568,11 @@ template <typename T>
 struct Consts {
   T eb, inv2, Rh;
   float noise;
-  int texp;      // compact encoding: truncation exponent of unpredictable values, else kNoTrunc
-  CoefSteps cs;  // compact encoding: coefficient steps
+  int texp;  // compact encoding: truncation exponent of unpredictable values, else kNoTrunc
   __device__ __forceinline__ Consts(double ebd, const Geo& g, int ndim) {
     const uint32_t R = g.R;
     eb = (T)ebd;
     texp = g.enc ? bound_exponent<T>(eb) : kNoTrunc;
-    if (g.enc) cs = coef_steps(g, (double)eb);
     if (sizeof(T) == 4) inv2 = (T)__double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, ebd)));
     else inv2 = (T)__ddiv_rn(1.0, __dmul_rn(2.0, ebd));
     Rh = FT<T>::sub(FT<T>::fromi((int)R), T(0.5));
@@ -633,7 +635,7 @@ __device__ __forceinline__ void predict_generic_block(const T* __restrict__ fiel
   T* ustage = static_cast<T*>(w.ustage);
   const Box x = block_box(g, b);
   const uint32_t S = sample_points(NDIM, x.e);
-  CoefSel cq = coef_select<T, NDIM>(g, w, b, K);
+  CoefSel cq = coef_select<T, NDIM>(g, w, b);
   bool reg = choose_reg(g, w, b, cq.ok, S, K.noise,
                         [&] { return ereg_generic<T, NDIM>(field, g, x, cq.c4, kNone, T(0)); });
   T cT[4];
@@ -651,7 +653,8 @@ __device__ __forceinline__ void predict_generic_block(const T* __restrict__ fiel
       withdraw(w, g, b, x.P, h);
       hk.kfix = kf;
       // the selection estimate and the prediction both see the repaired value
-      reg = choose_reg(g, w, b, cq.ok, S, K.noise, [&] { return ereg_generic<T, NDIM>(field, g, x, cq.c4, kf, xf); });
+      const CoefSel cq2 = coef_select<T, NDIM>(g, w, b);
+      reg = choose_reg(g, w, b, cq2.ok, S, K.noise, [&] { return ereg_generic<T, NDIM>(field, g, x, cq2.c4, kf, xf); });
       r = reg ? generic_pass<T, NDIM, true, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
                                                   hk, xf)
               : generic_pass<T, NDIM, false, ABFT>(field, g, x, b, cT, wk, K.eb, K.inv2, K.Rh, w.codes, ustage, h,
@@ -662,7 +665,7 @@ __device__ __forceinline__ void predict_generic_block(const T* __restrict__ fiel
       flag = 2;
     }
   }
-  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag, g, cq);
+  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag, g);
   cnt.unpred += r.nun;
   cnt.reg += reg;
   cnt.dup += r.dup;
@@ -733,15 +736,15 @@ __global__ void __launch_bounds__(128) k_predict_batch(BatchArgs a) {
       });
 }
 
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool HOOK, bool EDGE>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP, bool HOOK, bool EDGE>
 __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_t si, uint64_t sj, bool vec2,
                                                  const T* cT, T* plane, const Consts<T>& K, uint32_t R, uint32_t* cptr,
                                                  T* uptr, const Hist& h, const Hooks& hk, T xfix, const uint32_t* e) {
   if (reg)
-    return fast_pass<T, NDIM, B0, B1, B2, 128, true, ABFT, HOOK, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2,
+    return fast_pass<T, NDIM, B0, B1, B2, 128, true, ABFT, HOOK, CMP, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2,
                                                                        K.Rh, R, cptr, uptr, h, hk, xfix, e[0], e[1],
                                                                        e[2]);
-  return fast_pass<T, NDIM, B0, B1, B2, 128, false, ABFT, HOOK, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh,
+  return fast_pass<T, NDIM, B0, B1, B2, 128, false, ABFT, HOOK, CMP, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh,
                                                                       R, cptr, uptr, h, hk, xfix, e[0], e[1], e[2]);
 }
 
@@ -755,7 +758,7 @@ __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_
 // One block with the compile-time shape B0 x B1 x B2 (leading 1s below 3D). Full blocks only,
 // unless EDGE: then block b is an edge block, cut by the field boundary, walked with the same
 // code and its actual extents.
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool EDGE = false>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP, bool EDGE = false>
 __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, const Geo& g, const Ws& w,
                                                    const sdcsz_flip* __restrict__ flips, uint32_t nflips, int vec2,
                                                    uint64_t b, T* plane, const Consts<T>& K, const Hist& h,
@@ -781,22 +784,22 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
     blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
   }
   const uint32_t S = EDGE ? sample_points(NDIM, x.e) : (NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2);
-  CoefSel cq = coef_select<T, NDIM>(g, w, b, K);
-  auto ereg = [&](uint32_t kf, T xf) {
-    if (EDGE) return ereg_generic<T, NDIM>(field, g, x, cq.c4, kf, xf);
-    if (kf != kNone) return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, cq.c4, kf, xf);
-    return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, cq.c4, kNone, T(0));
+  CoefSel cq = coef_select<T, NDIM>(g, w, b);
+  auto ereg = [&](float4 c4, uint32_t kf, T xf) {
+    if (EDGE) return ereg_generic<T, NDIM>(field, g, x, c4, kf, xf);
+    if (kf != kNone) return ereg_fast<T, NDIM, B0, B1, B2, true>(blk, si, sj, vec2, c4, kf, xf);
+    return ereg_fast<T, NDIM, B0, B1, B2, false>(blk, si, sj, vec2, c4, kNone, T(0));
   };
-  bool reg = choose_reg(g, w, b, cq.ok, S, K.noise, [&] { return ereg(kNone, T(0)); });
+  bool reg = choose_reg(g, w, b, cq.ok, S, K.noise, [&] { return ereg(cq.c4, kNone, T(0)); });
   T cT[4];
   Hooks hk;
   load_coefs<T, NDIM>(g, w, b, flips, nflips, cT, hk, cq, K);
   uint32_t* cptr = reinterpret_cast<uint32_t*>(w.codes) + pair_index(b, P, 0);
   T* uptr = ustage + code_index(b, P, 0);
   const bool hooked = (hk.kp != kNone) || (hk.kr != kNone);
-  PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
+  PassRes r = hooked ? fast_dispatch<T, NDIM, B0, B1, B2, ABFT, CMP, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R,
                                                                             cptr, uptr, h, hk, T(0), e)
-                     : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, false, EDGE>(reg, blk, si, sj, vec2, cT, plane, K,
+                     : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, CMP, false, EDGE>(reg, blk, si, sj, vec2, cT, plane, K,
                                                                              g.R, cptr, uptr, h, hk, T(0), e);
   uint8_t flag = 0;
   if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
@@ -806,8 +809,9 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
     if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
       withdraw(w, g, b, Pb, h);
       hk.kfix = kf;
-      reg = choose_reg(g, w, b, cq.ok, S, K.noise, [&] { return ereg(kf, xf); });
-      r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
+      const CoefSel cq2 = coef_select<T, NDIM>(g, w, b);
+      reg = choose_reg(g, w, b, cq2.ok, S, K.noise, [&] { return ereg(cq2.c4, kf, xf); });
+      r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, CMP, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
                                                                hk, xf, e);
       ++cnt.fix;
     } else {
@@ -815,7 +819,7 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
       flag = 2;
     }
   }
-  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag, g, cq);
+  block_epilogue<T>(w, b, reg, NDIM, cT, r, ABFT, flag, g);
   cnt.unpred += r.nun;
   cnt.reg += reg;
   cnt.dup += r.dup;
@@ -823,7 +827,7 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
 
 // Edge blocks of a field whose full blocks take the fast kernel: the same compile-time
 // walk with runtime extents, one thread per edge block (compact enumeration).
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP>
 __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_edge(const T* __restrict__ field, Geo g, Ws w,
                                                       const sdcsz_flip* __restrict__ flips, uint32_t nflips,
                                                       uint64_t count) {
@@ -840,7 +844,7 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_edge(const T* 
   for (uint64_t it = cta_pull(&st->queue[1]); it * blockDim.x < count; it = cta_pull(&st->queue[1])) {
     const uint64_t e = it * blockDim.x + threadIdx.x;
     if (e < count)
-      predict_fast_block<T, NDIM, B0, B1, B2, ABFT, true>(field, g, w, flips, nflips, 0, edge_block(g, e), plane, K,
+      predict_fast_block<T, NDIM, B0, B1, B2, ABFT, CMP, true>(field, g, w, flips, nflips, 0, edge_block(g, e), plane, K,
                                                           h, cnt);
   }
   cnt.commit(st);
@@ -848,7 +852,7 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_edge(const T* 
 }
 
 // Fast kernel: full blocks of a compile-time shape.
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP>
 __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast(const T* __restrict__ field, Geo g, Ws w,
                                                       const sdcsz_flip* __restrict__ flips, uint32_t nflips,
                                                       int vec2) {
@@ -864,14 +868,14 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast(const T* 
   Counters cnt;
   for (uint64_t it = cta_pull(&st->queue[0]); it * blockDim.x < g.nb; it = cta_pull(&st->queue[0])) {
     const uint64_t b = it * blockDim.x + threadIdx.x;
-    if (b < g.nb) predict_fast_block<T, NDIM, B0, B1, B2, ABFT>(field, g, w, flips, nflips, vec2, b, plane, K, h, cnt);
+    if (b < g.nb) predict_fast_block<T, NDIM, B0, B1, B2, ABFT, CMP>(field, g, w, flips, nflips, vec2, b, plane, K, h, cnt);
   }
   cnt.commit(st);
   hist_flush(hist_s, h, w);
 }
 
 // Batched fast kernel: the full blocks of every job with this block shape.
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP>
 __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t hist_s[kHistWindow];
@@ -889,7 +893,7 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast_batch(Bat
         const uint64_t b = it * blockDim.x + threadIdx.x;
         if (b < s_job.g.nb) {
           const Consts<T> K(s_job.w.st->eb, s_job.g, NDIM);
-          predict_fast_block<T, NDIM, B0, B1, B2, ABFT>(static_cast<const T*>(s_job.field), s_job.g, s_job.w,
+          predict_fast_block<T, NDIM, B0, B1, B2, ABFT, CMP>(static_cast<const T*>(s_job.field), s_job.g, s_job.w,
                                                         nullptr, 0, s_job.vec2, b, plane, K, h, cnt);
         }
       },
@@ -924,11 +928,11 @@ void run_generic(const void* field, const Geo& g, const Ws& w, const sdcsz_flip*
   note_launch();
 }
 
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP>
 void run_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
               const Launch& L) {
   const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
-  auto kern = k_predict_fast<T, NDIM, B0, B1, B2, ABFT>;
+  auto kern = k_predict_fast<T, NDIM, B0, B1, B2, ABFT, CMP>;
   dim3 grid;
   launch_persistent(kern, 128, smem, g.nb, L, &grid);
   const bool vec2 = (B2 % 2 == 0) && (g.d[2] % 2 == 0) &&
@@ -937,37 +941,37 @@ void run_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
   note_launch();
 }
 
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP>
 void run_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
               const Launch& L) {
   const uint64_t count = edge_count(g);
   if (!count) return;
   const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
-  auto kern = k_predict_edge<T, NDIM, B0, B1, B2, ABFT>;
+  auto kern = k_predict_edge<T, NDIM, B0, B1, B2, ABFT, CMP>;
   dim3 grid;
   launch_persistent(kern, 128, smem, count, L, &grid);
   kern<<<grid, 128, smem, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, count);
   note_launch();
 }
 
-template <typename T, bool ABFT>
+template <typename T, bool ABFT, bool CMP>
 void try_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
               const Launch& L) {
   if (g.ndim == 3) {
     switch (g.B[2]) {
-      case 4: run_edge<T, 3, 4, 4, 4, ABFT>(field, g, w, flips, nflips, L); break;
-      case 6: run_edge<T, 3, 6, 6, 6, ABFT>(field, g, w, flips, nflips, L); break;
-      case 8: run_edge<T, 3, 8, 8, 8, ABFT>(field, g, w, flips, nflips, L); break;
-      case 10: run_edge<T, 3, 10, 10, 10, ABFT>(field, g, w, flips, nflips, L); break;
-      case 12: run_edge<T, 3, 12, 12, 12, ABFT>(field, g, w, flips, nflips, L); break;
-      case 16: run_edge<T, 3, 16, 16, 16, ABFT>(field, g, w, flips, nflips, L); break;
+      case 4: run_edge<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 6: run_edge<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 8: run_edge<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 10: run_edge<T, 3, 10, 10, 10, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 12: run_edge<T, 3, 12, 12, 12, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 16: run_edge<T, 3, 16, 16, 16, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       default: break;
     }
   } else if (g.ndim == 2) {
     switch (g.B[2]) {
-      case 8: run_edge<T, 2, 1, 8, 8, ABFT>(field, g, w, flips, nflips, L); break;
-      case 12: run_edge<T, 2, 1, 12, 12, ABFT>(field, g, w, flips, nflips, L); break;
-      case 16: run_edge<T, 2, 1, 16, 16, ABFT>(field, g, w, flips, nflips, L); break;
+      case 8: run_edge<T, 2, 1, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 12: run_edge<T, 2, 1, 12, 12, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 16: run_edge<T, 2, 1, 16, 16, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       default: break;
     }
   }
@@ -981,40 +985,40 @@ inline bool has_fast(const Geo& g) {
   return false;
 }
 
-template <typename T, bool ABFT>
+template <typename T, bool ABFT, bool CMP>
 bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
               const Launch& L) {
   if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2]) {
     switch (g.B[2]) {
-      case 4: run_fast<T, 3, 4, 4, 4, ABFT>(field, g, w, flips, nflips, L); return true;
-      case 6: run_fast<T, 3, 6, 6, 6, ABFT>(field, g, w, flips, nflips, L); return true;
-      case 8: run_fast<T, 3, 8, 8, 8, ABFT>(field, g, w, flips, nflips, L); return true;
-      case 10: run_fast<T, 3, 10, 10, 10, ABFT>(field, g, w, flips, nflips, L); return true;
-      case 12: run_fast<T, 3, 12, 12, 12, ABFT>(field, g, w, flips, nflips, L); return true;
-      case 16: run_fast<T, 3, 16, 16, 16, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 4: run_fast<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 6: run_fast<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 8: run_fast<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 10: run_fast<T, 3, 10, 10, 10, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 12: run_fast<T, 3, 12, 12, 12, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 16: run_fast<T, 3, 16, 16, 16, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       default: return false;
     }
   }
   if (g.ndim == 2 && g.B[1] == g.B[2]) {
     switch (g.B[2]) {
-      case 8: run_fast<T, 2, 1, 8, 8, ABFT>(field, g, w, flips, nflips, L); return true;
-      case 12: run_fast<T, 2, 1, 12, 12, ABFT>(field, g, w, flips, nflips, L); return true;
-      case 16: run_fast<T, 2, 1, 16, 16, ABFT>(field, g, w, flips, nflips, L); return true;
+      case 8: run_fast<T, 2, 1, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 12: run_fast<T, 2, 1, 12, 12, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 16: run_fast<T, 2, 1, 16, 16, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       default: return false;
     }
   }
   return false;
 }
 
-template <typename T, bool ABFT>
+template <typename T, bool ABFT, bool CMP>
 void launch_predict_t(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
                       const Launch& L) {
   // shapes with a fast path: edge blocks on the side stream with the same compile-time walk,
   // concurrently with the full blocks; other shapes: the generic kernel for every block
   if (has_fast(g)) {
     Fork fk(L);
-    try_edge<T, ABFT>(field, g, w, flips, nflips, fk.side_launch(L));
-    try_fast<T, ABFT>(field, g, w, flips, nflips, L);
+    try_edge<T, ABFT, CMP>(field, g, w, flips, nflips, fk.side_launch(L));
+    try_fast<T, ABFT, CMP>(field, g, w, flips, nflips, L);
     fk.join();
   } else if (g.ndim == 3) {
     run_generic<T, 3, ABFT>(field, g, w, flips, nflips, true, L);
@@ -1026,34 +1030,34 @@ void launch_predict_t(const void* field, const Geo& g, const Ws& w, const sdcsz_
 }
 
 // ---------------------------------------------------------------- batched launches
-template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT>
+template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP>
 void batch_fast(const BatchArgs& a, const Launch& L) {
   const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
-  auto kern = k_predict_fast_batch<T, NDIM, B0, B1, B2, ABFT>;
+  auto kern = k_predict_fast_batch<T, NDIM, B0, B1, B2, ABFT, CMP>;
   dim3 grid;
   launch_persistent(kern, 128, smem, a.start[a.n] * 128, L, &grid);
   kern<<<grid, 128, smem, L.stream>>>(a);
   note_launch();
 }
 
-template <typename T, bool ABFT>
+template <typename T, bool ABFT, bool CMP>
 bool batch_fast_shape(int ndim, uint32_t B, const BatchArgs& a, const Launch& L) {
   if (ndim == 3) {
     switch (B) {
-      case 4: batch_fast<T, 3, 4, 4, 4, ABFT>(a, L); return true;
-      case 6: batch_fast<T, 3, 6, 6, 6, ABFT>(a, L); return true;
-      case 8: batch_fast<T, 3, 8, 8, 8, ABFT>(a, L); return true;
-      case 10: batch_fast<T, 3, 10, 10, 10, ABFT>(a, L); return true;
-      case 12: batch_fast<T, 3, 12, 12, 12, ABFT>(a, L); return true;
-      case 16: batch_fast<T, 3, 16, 16, 16, ABFT>(a, L); return true;
+      case 4: batch_fast<T, 3, 4, 4, 4, ABFT, CMP>(a, L); return true;
+      case 6: batch_fast<T, 3, 6, 6, 6, ABFT, CMP>(a, L); return true;
+      case 8: batch_fast<T, 3, 8, 8, 8, ABFT, CMP>(a, L); return true;
+      case 10: batch_fast<T, 3, 10, 10, 10, ABFT, CMP>(a, L); return true;
+      case 12: batch_fast<T, 3, 12, 12, 12, ABFT, CMP>(a, L); return true;
+      case 16: batch_fast<T, 3, 16, 16, 16, ABFT, CMP>(a, L); return true;
       default: return false;
     }
   }
   if (ndim == 2) {
     switch (B) {
-      case 8: batch_fast<T, 2, 1, 8, 8, ABFT>(a, L); return true;
-      case 12: batch_fast<T, 2, 1, 12, 12, ABFT>(a, L); return true;
-      case 16: batch_fast<T, 2, 1, 16, 16, ABFT>(a, L); return true;
+      case 8: batch_fast<T, 2, 1, 8, 8, ABFT, CMP>(a, L); return true;
+      case 12: batch_fast<T, 2, 1, 12, 12, ABFT, CMP>(a, L); return true;
+      case 16: batch_fast<T, 2, 1, 16, 16, ABFT, CMP>(a, L); return true;
       default: return false;
     }
   }

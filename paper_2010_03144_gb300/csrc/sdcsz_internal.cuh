@@ -56,6 +56,7 @@ struct State {
   unsigned int ticket, n_live;
   unsigned long long payload_bytes, total_bytes;
   unsigned long long n_unpred_enc;  // unpredictable points of the codes as encoded (after repairs)
+  double cstep[4], cinv[4];         // compact encoding: coefficient steps (set with the bound)
   Layout L;
   unsigned long long queue[4];  // work-queue counters of the persistent kernels of one call
 };
@@ -673,7 +674,7 @@ bool prep_has_fast(const Geo& g);
 bool batch_prep_fast(int dtype, int ndim, uint32_t B, const BatchArgs& a, const Launch& L);
 void batch_prep_generic(int dtype, int ndim, const BatchArgs& a, size_t smem, const Launch& L);
 void batch_bound(const Job* jobs, uint32_t n, const Launch& L);
-bool batch_predict_fast(int dtype, int ndim, uint32_t B, bool abft, const BatchArgs& a, const Launch& L);
+bool batch_predict_fast(int dtype, int ndim, uint32_t B, bool abft, bool enc, const BatchArgs& a, const Launch& L);
 void batch_predict_generic(int dtype, int ndim, bool abft, const BatchArgs& a, uint32_t threads, size_t smem,
                            const Launch& L);
 void batch_codebook(const Job* jobs, uint32_t n, const Launch& L);
