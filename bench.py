@@ -44,10 +44,12 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 555697948, "src": "c9c1570083b1"},
-    ("384cube", "prep"): {"bytes": 234435072, "src": "c9c1570083b1"},
-    ("512cube", "predict"): {"bytes": 920000436, "src": "18891af77d96"},
-    ("384cube", "predict"): {"bytes": 388125184, "src": "18891af77d96"},
+    ("512cube", "prep"): {"bytes": 555008000, "src": "97ae17051a6f"},
+    ("384cube", "prep"): {"bytes": 234144000, "src": "97ae17051a6f"},
+    ("512cube", "predict"): {"bytes": 945076452, "src": "ed93904bd6e9"},
+    ("384cube", "predict"): {"bytes": 398704128, "src": "ed93904bd6e9"},
+    ("512cube", "decode"): {"bytes": 481188371, "src": "91c58ed5e4b7"},
+    ("384cube", "decode"): {"bytes": 203001344, "src": "91c58ed5e4b7"},
 }
 
 
