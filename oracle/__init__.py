@@ -111,6 +111,12 @@ def lib():
         L.orc_truncate_unpredictable.argtypes = [vp, u32, ctypes.c_double, vp]
         L.orc_quantize_coefficient.argtypes = [ctypes.c_float, u32, u32, vp, ctypes.c_double, u32,
                                                ctypes.POINTER(ctypes.c_int32), vp]
+        L.orc_ll_frequencies.argtypes = [vp, vp]
+        L.orc_ll_frequencies.restype = None
+        L.orc_ll_encode.argtypes = [vp, u32, vp, vp, u64]
+        L.orc_ll_encode.restype = u64
+        L.orc_ll_decode.argtypes = [vp, u64, u32, vp, vp]
+        L.orc_ll_decode.restype = None
         L.orc_error_bound.argtypes = [vp, P]
         L.orc_error_bound.restype = ctypes.c_double
         _lib = L
@@ -122,7 +128,7 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-                encoding="raw") -> Params:
+                encoding="raw", lossless=False) -> Params:
     ndim = len(shape)
     p = Params()
     p.ndim = ndim
@@ -140,7 +146,7 @@ def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=Tr
     p.quant_bins = int(bins)
     p.abft = 1 if abft else 0
     p.predictor = PREDICTORS[predictor]
-    p.encoding = ENCODINGS[encoding]
+    p.encoding = ENCODINGS[encoding] | (2 if lossless else 0)
     return p
 
 
@@ -166,13 +172,14 @@ def compress_bound(p: Params) -> int:
 
 
 def compress(field: np.ndarray, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-             flips=None, encoding="raw"):
+             flips=None, encoding="raw", lossless=False):
     """Alg. 1. Returns (stream bytes as uint8 array, report dict). ``flips`` is a list of
     (site, block, index, bit) soft errors to simulate (see the site list in the C source);
     ``encoding`` is "raw" (coefficients and unpredictable values in sections of their own) or
-    "compact" (both quantized / truncated and kept in the block's payload)."""
+    "compact" (both quantized / truncated and kept in the block's payload); ``lossless`` adds the
+    final lossless stage (an order-0 rANS coder over everything after the block tables)."""
     field = np.ascontiguousarray(field)
-    p = make_params(field.shape, field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
+    p = make_params(field.shape, field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding, lossless)
     cap = compress_bound(p)
     out = np.zeros(cap, dtype=np.uint8)
     nbytes = ctypes.c_uint64()
@@ -195,7 +202,7 @@ def read_header(stream: np.ndarray):
     shape = tuple(int(p.dims[a]) for a in range(p.ndim))
     return {"shape": shape, "dtype": np.float32 if p.dtype == 0 else np.float64,
             "block": tuple(int(p.block[a]) for a in range(p.ndim)), "total": total.value, "abft": bool(p.abft),
-            "encoding": "compact" if p.encoding == 1 else "raw"}
+            "encoding": "compact" if p.encoding & 1 else "raw", "lossless": bool(p.encoding & 2)}
 
 
 def decompress(stream: np.ndarray, flips=None):
@@ -291,6 +298,31 @@ def quantize_coefficient(c, eb, dtype, block, a):
     if ok < 0:
         raise ValueError("bad block shape or coefficient index")
     return bool(ok), int(k.value), out[0]
+
+
+def ll_frequencies(counts) -> np.ndarray:
+    """Lossless stage: the 12-bit frequencies of a 256-bin byte histogram."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    f = np.zeros(256, dtype=np.uint16)
+    lib().orc_ll_frequencies(_ptr(c), _ptr(f))
+    return f
+
+
+def ll_encode(data, freqs) -> np.ndarray:
+    """Lossless stage: one chunk (at most 16384 bytes) coded with the given frequencies."""
+    d = np.ascontiguousarray(data, dtype=np.uint8)
+    f = np.ascontiguousarray(freqs, dtype=np.uint16)
+    out = np.zeros(128 + 2 * d.size + 4, dtype=np.uint8)
+    n = lib().orc_ll_encode(_ptr(d), d.size, _ptr(f), _ptr(out), out.size)
+    return out[:n].copy()
+
+
+def ll_decode(chunk, n, freqs) -> np.ndarray:
+    c = np.ascontiguousarray(chunk, dtype=np.uint8)
+    f = np.ascontiguousarray(freqs, dtype=np.uint16)
+    out = np.zeros(n, dtype=np.uint8)
+    lib().orc_ll_decode(_ptr(c), c.size, n, _ptr(f), _ptr(out))
+    return out
 
 
 def error_bound(field: np.ndarray, eb, eb_mode="rel") -> float:

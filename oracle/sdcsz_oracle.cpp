@@ -40,7 +40,11 @@
 //     (slopes eb/(16 B_a), intercept eb/16, round half away from zero in double), written
 //     as length-prefixed zigzag integers at the head of the block's payload; unpredictable
 //     values truncated to the mantissa bits the bound needs and written right after their
-//     code 0.
+//     code 0;
+//   * the lossless stage (Algorithm 1's final step, Zstd in the paper) is an order-0 range
+//     asymmetric numeral system coder of our own over the bytes after the block tables
+//     (sum_dc, coefficients, unpredictable values, payload), in independent 16 KiB chunks
+//     of 32 interleaved states.
 // Parity unpinned: the predictor-selection estimate (kappa, sample set) only changes the
 // compression ratio (Sec. 4.1.1) and is pinned by determinism and GPU/oracle equality only.
 
@@ -64,7 +68,7 @@ typedef struct {
   uint32_t quant_bins;  // even, 2..65536
   uint32_t abft;        // 1 = fault tolerant (ftrsz), 0 = plain independent blocks (rsz)
   uint32_t predictor;   // 0 = select per block, 1 = Lorenzo only, 2 = regression only
-  uint32_t encoding;    // 0 = raw coefficient / unpredictable sections, 1 = compact
+  uint32_t encoding;    // bit 0: compact coefficient / unpredictable encoding; bit 1: lossless stage
 } orc_params;
 
 typedef struct {
@@ -782,8 +786,8 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   const Geom& g = c.g;
   if (!(p->eb > 0.0) || !std::isfinite(p->eb) || p->eb_mode > 1) return EINVAL_;
   if (p->quant_bins < 2 || p->quant_bins > 65536 || (p->quant_bins & 1)) return EINVAL_;
-  if (p->predictor > 2 || p->encoding > 1) return EINVAL_;
-  c.compact = p->encoding == 1;
+  if (p->predictor > 2 || p->encoding > 3) return EINVAL_;
+  c.compact = (p->encoding & 1) != 0;
   c.bins = p->quant_bins;
   c.R = p->quant_bins / 2;
   c.abft = p->abft != 0;
@@ -918,7 +922,7 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   put<uint8_t>(out, 48, (uint8_t)c.abft);
   put<uint8_t>(out, 49, (uint8_t)p->predictor);
   put<uint8_t>(out, 50, (uint8_t)p->eb_mode);
-  put<uint8_t>(out, 51, (uint8_t)p->encoding);
+  put<uint8_t>(out, 51, (uint8_t)(p->encoding & 1));  // the lossless stage sets bit 1 itself
   put<uint32_t>(out, 52, (uint32_t)n_live);
   put<double>(out, 56, (double)eb);
   put<double>(out, 64, p->eb);
@@ -962,14 +966,184 @@ int compress_impl(const T* field_in, const orc_params* p, const orc_flip* flips,
   return OK;
 }
 
+// ---------------------------------------------------------------- lossless stage
+// Algorithm 1 ends by compressing the encoded bin array (and sum_dc) losslessly, Algorithm 2
+// starts by undoing that; the paper uses Zstd. Here: an order-0 range asymmetric numeral system
+// (rANS) coder over the bytes from the sum_dc section to the end of the stream. Everything
+// before it (header, code table and the random-access tables) stays as it is.
+//   * symbol frequencies: the byte counts scaled to 4096 (12 bits); a byte that occurs gets at
+//     least 1; the sum is then brought to 4096 one step at a time, taking from the largest
+//     frequency above 1 (ties: smaller byte) or giving to the most frequent byte (ties:
+//     smaller byte);
+//   * the bytes are cut into chunks of 16384; in a chunk, byte i belongs to state i mod 32;
+//   * state x in [2^16, 2^32); coding s (frequency f, cumulative c) first renormalises,
+//     emitting the low 16 bits while x >= 2^20 f, then x <- (x / f) 2^12 + x mod f + c;
+//     decoding is the inverse: slot = x mod 2^12, s = the byte whose range holds slot,
+//     x <- f (x / 2^12) + slot - c, then x <- x 2^16 + the next word while x < 2^16;
+//   * the coder runs over the chunk from its last byte to its first; the 16-bit words are
+//     stored in the order the decoder takes them (byte order, states in increasing index at
+//     each byte group), after the 32 final states;
+//   * section layout at the sum_dc offset: 256 frequencies (u16), the end offset of each
+//     chunk (u32, relative to the first chunk, whose start is 16-byte aligned), then the
+//     chunks, each padded to 4 bytes. Header: byte 51 bit 1 set, the total at 104 is the
+//     stream's, the total without the stage at 120.
+constexpr uint32_t kLLChunk = 16384, kLLScale = 12, kLLM = 1u << kLLScale, kLLWays = 32;
+constexpr uint64_t kRansLow = 1ull << 16;
+
+void ll_frequencies(const uint64_t cnt[256], uint16_t f[256]) {
+  uint64_t total = 0;
+  for (int b = 0; b < 256; ++b) total += cnt[b];
+  std::memset(f, 0, 256 * sizeof(uint16_t));
+  if (!total) return;
+  int64_t sum = 0;
+  uint32_t fw[256];
+  for (int b = 0; b < 256; ++b) {
+    fw[b] = 0;
+    if (cnt[b]) {
+      const uint64_t v = cnt[b] * kLLM / total;
+      fw[b] = v < 1 ? 1u : (uint32_t)v;
+    }
+    sum += fw[b];
+  }
+  while (sum > (int64_t)kLLM) {
+    int best = -1;
+    for (int b = 0; b < 256; ++b)
+      if (fw[b] > 1 && (best < 0 || fw[b] > fw[best])) best = b;
+    --fw[best];
+    --sum;
+  }
+  while (sum < (int64_t)kLLM) {
+    int best = 0;
+    for (int b = 1; b < 256; ++b)
+      if (cnt[b] > cnt[best]) best = b;
+    ++fw[best];
+    ++sum;
+  }
+  for (int b = 0; b < 256; ++b) f[b] = (uint16_t)fw[b];
+}
+
+void ll_cumulative(const uint16_t f[256], uint32_t c[257]) {
+  c[0] = 0;
+  for (int b = 0; b < 256; ++b) c[b + 1] = c[b] + f[b];
+}
+
+// One chunk: 32 final states (u32) then the words in decoding order, padded to 4 bytes.
+void ll_encode_chunk(const uint8_t* in, uint32_t n, const uint16_t f[256], const uint32_t c[257],
+                     std::vector<uint8_t>* out) {
+  uint64_t x[kLLWays];
+  for (uint32_t j = 0; j < kLLWays; ++j) x[j] = kRansLow;
+  std::vector<uint16_t> pushed;  // in the order the coder emits them
+  const uint32_t T = (n + kLLWays - 1) / kLLWays;
+  for (uint32_t t = T; t-- > 0;)
+    for (uint32_t j = kLLWays; j-- > 0;) {
+      const uint32_t i = t * kLLWays + j;
+      if (i >= n) continue;
+      const uint32_t s = in[i], fs = f[s];
+      const uint64_t xmax = (uint64_t)((kRansLow >> kLLScale) << 16) * fs;
+      if (x[j] >= xmax) {
+        pushed.push_back((uint16_t)(x[j] & 0xffff));
+        x[j] >>= 16;
+      }
+      x[j] = ((x[j] / fs) << kLLScale) + (x[j] % fs) + c[s];
+    }
+  const size_t at = out->size();
+  out->resize(at + 4 * kLLWays + 2 * pushed.size());
+  for (uint32_t j = 0; j < kLLWays; ++j) put<uint32_t>(out->data(), at + 4 * j, (uint32_t)x[j]);
+  for (size_t q = 0; q < pushed.size(); ++q)
+    put<uint16_t>(out->data(), at + 4 * kLLWays + 2 * q, pushed[pushed.size() - 1 - q]);
+  if (out->size() & 3) out->resize(out->size() + 2, 0);
+}
+
+// Decode n bytes of one chunk of `len` bytes; words past the chunk read as 0.
+void ll_decode_chunk(const uint8_t* in, uint64_t len, uint32_t n, const uint16_t f[256], const uint32_t c[257],
+                     const uint8_t* sym, uint8_t* out) {
+  uint64_t x[kLLWays];
+  for (uint32_t j = 0; j < kLLWays; ++j) x[j] = 4 * (j + 1) <= len ? get<uint32_t>(in, 4 * j) : 0;
+  const uint64_t nw = len > 4 * kLLWays ? (len - 4 * kLLWays) / 2 : 0;
+  uint64_t p = 0;
+  const uint32_t T = (n + kLLWays - 1) / kLLWays;
+  for (uint32_t t = 0; t < T; ++t)
+    for (uint32_t j = 0; j < kLLWays; ++j) {
+      const uint32_t i = t * kLLWays + j;
+      if (i >= n) continue;
+      const uint32_t slot = (uint32_t)(x[j] & (kLLM - 1));
+      const uint32_t s = sym[slot];
+      out[i] = (uint8_t)s;
+      x[j] = (uint64_t)f[s] * (x[j] >> kLLScale) + slot - c[s];
+      if (x[j] < kRansLow) {
+        const uint64_t w = p < nw ? get<uint16_t>(in, 4 * kLLWays + 2 * p) : 0;
+        ++p;
+        x[j] = ((x[j] << 16) | w) & 0xffffffffull;
+      }
+    }
+}
+
+// The lossless stage over a finished stream R whose coded region starts at `from`.
+void ll_pack(const uint8_t* R, uint64_t nR, uint64_t from, uint8_t encoding, std::vector<uint8_t>* S) {
+  uint64_t cnt[256] = {0};
+  for (uint64_t q = from; q < nR; ++q) cnt[R[q]]++;
+  uint16_t f[256];
+  uint32_t c[257];
+  ll_frequencies(cnt, f);
+  ll_cumulative(f, c);
+  const uint64_t n = nR - from, nchunks = (n + kLLChunk - 1) / kLLChunk;
+  const uint64_t data = align16(from + 512 + 4 * nchunks);
+  std::vector<uint8_t> chunks;
+  std::vector<uint32_t> ends(nchunks);
+  for (uint64_t k = 0; k < nchunks; ++k) {
+    const uint32_t len = (uint32_t)std::min<uint64_t>(kLLChunk, n - k * kLLChunk);
+    ll_encode_chunk(R + from + k * kLLChunk, len, f, c, &chunks);
+    ends[k] = (uint32_t)chunks.size();
+  }
+  S->assign(data + chunks.size(), 0);
+  std::memcpy(S->data(), R, from);
+  put<uint8_t>(S->data(), 51, (uint8_t)(encoding | 2));
+  put<uint64_t>(S->data(), 104, (uint64_t)S->size());
+  put<uint64_t>(S->data(), 120, nR);
+  for (int b = 0; b < 256; ++b) put<uint16_t>(S->data(), from + 2 * b, f[b]);
+  for (uint64_t k = 0; k < nchunks; ++k) put<uint32_t>(S->data(), from + 512 + 4 * k, ends[k]);
+  if (!chunks.empty()) std::memcpy(S->data() + data, chunks.data(), chunks.size());
+}
+
+// Undo the lossless stage: R is the stream without it. False when the section is malformed.
+bool ll_unpack(const uint8_t* S, uint64_t nS, uint64_t from, uint64_t nR, std::vector<uint8_t>* R) {
+  if (nR < from || from + 512 > nS) return false;
+  const uint64_t n = nR - from, nchunks = (n + kLLChunk - 1) / kLLChunk;
+  const uint64_t data = align16(from + 512 + 4 * nchunks);
+  if (data > nS) return false;
+  uint16_t f[256];
+  for (int b = 0; b < 256; ++b) f[b] = get<uint16_t>(S, from + 2 * b);
+  uint32_t c[257];
+  ll_cumulative(f, c);
+  if (n && c[256] != kLLM) return false;
+  std::vector<uint8_t> sym(kLLM, 0);
+  for (int b = 0; b < 256; ++b)
+    for (uint32_t q = c[b]; q < c[b + 1]; ++q) sym[q] = (uint8_t)b;
+  R->assign(nR, 0);
+  std::memcpy(R->data(), S, from);
+  put<uint8_t>(R->data(), 51, (uint8_t)(S[51] & 1));
+  put<uint64_t>(R->data(), 104, nR);
+  put<uint64_t>(R->data(), 120, 0);
+  uint64_t start = 0;
+  for (uint64_t k = 0; k < nchunks; ++k) {
+    const uint64_t end = get<uint32_t>(S, from + 512 + 4 * k);
+    if (end < start || data + end > nS) return false;
+    const uint32_t len = (uint32_t)std::min<uint64_t>(kLLChunk, n - k * kLLChunk);
+    ll_decode_chunk(S + data + start, end - start, len, f, c, sym.data(), R->data() + from + k * kLLChunk);
+    start = end;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- Alg. 2
 struct Parsed {
   Geom g;
   orc_params p;
   uint32_t bins, R, n_live;
-  bool abft, compact;
+  bool abft, compact, lossless;
   double eb;
   uint64_t n_reg, n_unpred, payload_bytes, total;
+  uint64_t raw_total;  // size of the stream without the lossless stage (= total without it)
   Layout L;
   Canon canon;
 };
@@ -991,8 +1165,9 @@ int parse(const uint8_t* s, uint64_t n, Parsed* P) {
   P->p.predictor = get<uint8_t>(s, 49);
   P->p.eb_mode = get<uint8_t>(s, 50);
   P->p.encoding = get<uint8_t>(s, 51);
-  if (P->p.encoding > 1) return EFORMAT;
-  P->compact = P->p.encoding == 1;
+  if (P->p.encoding > 3) return EFORMAT;
+  P->compact = (P->p.encoding & 1) != 0;
+  P->lossless = (P->p.encoding & 2) != 0;
   P->n_live = get<uint32_t>(s, 52);
   P->eb = get<double>(s, 56);
   P->p.eb = get<double>(s, 64);
@@ -1004,7 +1179,8 @@ int parse(const uint8_t* s, uint64_t n, Parsed* P) {
   P->total = get<uint64_t>(s, 104);
   if (P->n_live > P->bins || P->n_reg > P->g.nb || P->n_unpred > P->g.N) return EFORMAT;
   P->L = make_layout(P->g, P->abft, P->compact, P->n_live, P->n_reg, P->n_unpred);
-  if (P->total != P->L.payload + P->payload_bytes || P->total > n) return EFORMAT;
+  P->raw_total = P->lossless ? get<uint64_t>(s, 120) : P->total;
+  if (P->raw_total != P->L.payload + P->payload_bytes || P->total > n) return EFORMAT;
   uint64_t kraft = 0, cnt = 0;
   for (uint32_t l = 0; l <= kMaxLen; ++l) {
     P->canon.bl_count[l] = get<uint32_t>(s, P->L.table + 4 * l);
@@ -1155,6 +1331,13 @@ int decompress_impl(const uint8_t* s, uint64_t n, T* field, uint8_t* status, con
   Parsed P;
   int rc = parse(s, n, &P);
   if (rc) return rc;
+  if (P.lossless) {  // Algorithm 2's first step: undo the lossless stage, then decompress
+    std::vector<uint8_t> R;
+    if (!ll_unpack(s, n, P.L.sumdc, P.raw_total, &R)) return EFORMAT;
+    rc = decompress_impl<T>(R.data(), R.size(), field, status, flips, nflips, rep);
+    if (rep) rep->compressed_bytes = P.total;
+    return rc;
+  }
   const Geom& g = P.g;
   orc_report r;
   std::memset(&r, 0, sizeof(r));
@@ -1236,24 +1419,53 @@ int decompress_impl(const uint8_t* s, uint64_t n, T* field, uint8_t* status, con
 // ---------------------------------------------------------------- exported entry points
 extern "C" {
 
+int orc_compress_bound(const orc_params* p, uint64_t* bytes);
+
 int orc_compress(const void* field, const orc_params* p, const orc_flip* flips, int nflips, uint8_t* out,
                  uint64_t cap, uint64_t* out_bytes, orc_report* rep) {
   if (!p || !out) return EINVAL_;
-  if (p->dtype == 0) return compress_impl<float>((const float*)field, p, flips, nflips, out, cap, out_bytes, rep);
-  if (p->dtype == 1) return compress_impl<double>((const double*)field, p, flips, nflips, out, cap, out_bytes, rep);
-  return EINVAL_;
+  if (p->dtype > 1 || p->encoding > 3) return EINVAL_;
+  if (!(p->encoding & 2)) {
+    if (p->dtype == 0) return compress_impl<float>((const float*)field, p, flips, nflips, out, cap, out_bytes, rep);
+    return compress_impl<double>((const double*)field, p, flips, nflips, out, cap, out_bytes, rep);
+  }
+  // the stream without the lossless stage first, then the stage over it
+  uint64_t bound = 0;
+  if (orc_compress_bound(p, &bound)) return EINVAL_;
+  std::vector<uint8_t> R(bound);
+  uint64_t nR = 0;
+  orc_report r;
+  int rc = p->dtype == 0 ? compress_impl<float>((const float*)field, p, flips, nflips, R.data(), bound, &nR, &r)
+                         : compress_impl<double>((const double*)field, p, flips, nflips, R.data(), bound, &nR, &r);
+  if (rc) return rc;
+  Parsed P;
+  if (parse(R.data(), nR, &P)) return EFORMAT;
+  std::vector<uint8_t> S;
+  ll_pack(R.data(), nR, P.L.sumdc, (uint8_t)(p->encoding & 1), &S);
+  if (S.size() > cap) return ECAPACITY;
+  std::memcpy(out, S.data(), S.size());
+  r.compressed_bytes = S.size();
+  if (out_bytes) *out_bytes = S.size();
+  if (rep) *rep = r;
+  return OK;
 }
 
 // Worst case: every point unpredictable and coded with kMaxLen bits, every block regression.
 // Compact encoding: each point may also carry a whole value and each block 4 coefficients of
 // at most 38 bits.
+// The lossless stage can add up to 2 bytes per coded byte plus its tables and states.
 int orc_compress_bound(const orc_params* p, uint64_t* bytes) {
   Geom g;
   if (!p || !make_geom(p, &g)) return EINVAL_;
-  const bool compact = p->encoding == 1;
+  const bool compact = (p->encoding & 1) != 0;
   Layout L = make_layout(g, p->abft != 0, compact, p->quant_bins ? p->quant_bins : 65536, g.nb, g.N);
   const uint64_t bits = compact ? (uint64_t)g.P * (kMaxLen + 8 * (g.dtype ? 8 : 4)) + 4 * 38 : (uint64_t)g.P * kMaxLen;
-  *bytes = L.payload + g.nb * ((bits + 7) / 8);
+  uint64_t b = L.payload + g.nb * ((bits + 7) / 8);
+  if (p->encoding & 2) {
+    const uint64_t n = b - L.sumdc, nchunks = (n + kLLChunk - 1) / kLLChunk;
+    b = L.sumdc + 512 + 4 * nchunks + 16 + 2 * n + nchunks * (4 * kLLWays + 4);
+  }
+  *bytes = b;
   return OK;
 }
 
@@ -1372,6 +1584,28 @@ int orc_quantize_coefficient(float c, uint32_t dtype, uint32_t ndim, const uint3
   if (dtype == 0) *(float*)deq = dequantize_coef<float>(*k, qs.step[a]);
   else *(double*)deq = dequantize_coef<double>(*k, qs.step[a]);
   return 1;
+}
+
+// Lossless stage, for pinning: frequencies of a byte histogram; one chunk coded and decoded.
+void orc_ll_frequencies(const uint64_t* cnt, uint16_t* f) { ll_frequencies(cnt, f); }
+
+uint64_t orc_ll_encode(const uint8_t* in, uint32_t n, const uint16_t* f, uint8_t* out, uint64_t cap) {
+  uint32_t c[257];
+  ll_cumulative(f, c);
+  std::vector<uint8_t> o;
+  ll_encode_chunk(in, n, f, c, &o);
+  if (o.size() > cap) return 0;
+  std::memcpy(out, o.data(), o.size());
+  return o.size();
+}
+
+void orc_ll_decode(const uint8_t* in, uint64_t len, uint32_t n, const uint16_t* f, uint8_t* out) {
+  uint32_t c[257];
+  ll_cumulative(f, c);
+  std::vector<uint8_t> sym(kLLM, 0);
+  for (int b = 0; b < 256; ++b)
+    for (uint32_t q = c[b]; q < c[b + 1] && q < kLLM; ++q) sym[q] = (uint8_t)b;
+  ll_decode_chunk(in, len, n, f, c, sym.data(), out);
 }
 
 // The value-range relative bound of the field, as the compressor computes it.
