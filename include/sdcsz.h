@@ -80,11 +80,16 @@ typedef struct {
   uint32_t quant_bins;
   uint32_t abft;
   uint32_t predictor;
-  /* 0 = raw: regression coefficients and unpredictable values in sections of their own, as
-   * stored values; 1 = compact: coefficients as integer multiples of eb/(16 B_a) (slopes) and
-   * eb/16 (intercept), written as length-prefixed zigzag integers at the head of the block's
-   * payload, and each unpredictable value right after its code 0 with only the mantissa bits
-   * the bound needs (SZ's own encodings, kept block-local). */
+  /* bit 0 -- 0 = raw: regression coefficients and unpredictable values in sections of their
+   * own, as stored values; 1 = compact: coefficients as integer multiples of eb/(16 B_a)
+   * (slopes) and eb/16 (intercept), written as length-prefixed zigzag integers at the head of
+   * the block's payload, and each unpredictable value right after its code 0 with only the
+   * mantissa bits the bound needs (SZ's own encodings, kept block-local).
+   * bit 1 -- the lossless stage that ends Algorithm 1 (Zstd in the paper): an order-0 rANS
+   * coder over everything after the block tables (sum_dc, coefficients, unpredictable values,
+   * payload) in 16 KiB chunks; the header and random-access tables stay as they are. Needs a
+   * 16-byte aligned output (and stream, when decompressing) and a larger decompression
+   * workspace (sdcsz_decompress_workspace_size_for); not available in batches. */
   uint32_t encoding;
 } sdcsz_params;
 
@@ -117,8 +122,14 @@ int sdcsz_compress_bound(const sdcsz_params* p, size_t* max_bytes);
  * histogram, codebook, scan state). 256-byte aligned base required. */
 int sdcsz_workspace_size(const sdcsz_params* p, size_t* bytes);
 
-/* Device workspace bytes needed by sdcsz_decompress and sdcsz_verify (any stream). */
+/* Device workspace bytes needed by sdcsz_decompress, sdcsz_verify and
+ * sdcsz_decompress_region for any stream without the lossless stage. */
 size_t sdcsz_decompress_workspace_size(void);
+
+/* Device workspace bytes needed to decompress, verify or take a region of the stream whose
+ * first 128 bytes (the header) are at h_header in HOST memory; nbytes is the stream's size.
+ * With the lossless stage this includes the stream without it. SDCSZ_EFORMAT for a bad header. */
+int sdcsz_decompress_workspace_size_for(const void* h_header, size_t nbytes, size_t* bytes);
 
 /*
  * Compress one field (Alg. 1 without the Zstd stage).

@@ -1127,7 +1127,7 @@ bool ll_unpack(const uint8_t* S, uint64_t nS, uint64_t from, uint64_t nR, std::v
   uint64_t start = 0;
   for (uint64_t k = 0; k < nchunks; ++k) {
     const uint64_t end = get<uint32_t>(S, from + 512 + 4 * k);
-    if (end < start || data + end > nS) return false;
+    if (end < start || (end & 3) || data + end > nS) return false;
     const uint32_t len = (uint32_t)std::min<uint64_t>(kLLChunk, n - k * kLLChunk);
     ll_decode_chunk(S + data + start, end - start, len, f, c, sym.data(), R->data() + from + k * kLLChunk);
     start = end;

@@ -30,7 +30,8 @@ EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_wor
            "sdcsz_batch_workspace_size", "sdcsz_batch_bind", "sdcsz_batch_set_fields", "sdcsz_batch_compress",
            "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy",
            "sdcsz_autotune_block", "sdcsz_server_create", "sdcsz_server_submit", "sdcsz_server_poll",
-           "sdcsz_server_release", "sdcsz_server_get_stats", "sdcsz_server_destroy", "sdcsz_decompress_region")
+           "sdcsz_server_release", "sdcsz_server_get_stats", "sdcsz_server_destroy", "sdcsz_decompress_region",
+           "sdcsz_decompress_workspace_size_for")
 
 
 class SdcszError(RuntimeError):
@@ -174,6 +175,8 @@ def lib():
         u64p = ctypes.POINTER(ctypes.c_uint64)
         L.sdcsz_decompress_region.argtypes = [vp, sz, u64p, u64p, vp, sz, vp, vp, sz, R, vp]
         L.sdcsz_decompress_region.restype = i32
+        L.sdcsz_decompress_workspace_size_for.argtypes = [vp, sz, ctypes.POINTER(sz)]
+        L.sdcsz_decompress_workspace_size_for.restype = i32
         L.sdcsz_kernel_launches.argtypes = []
         L.sdcsz_kernel_launches.restype = ctypes.c_ulonglong
         BI, BP = ctypes.POINTER(BatchItem), ctypes.c_void_p
@@ -223,7 +226,7 @@ def strerror(code: int) -> str:
 
 
 def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-                encoding="raw") -> Params:
+                encoding="raw", lossless=False) -> Params:
     import torch
     ndim = len(shape)
     p = Params()
@@ -246,7 +249,7 @@ def make_params(shape, dtype, eb, eb_mode="rel", block=None, bins=65536, abft=Tr
     p.quant_bins = int(bins)
     p.abft = 1 if abft else 0
     p.predictor = PREDICTORS[predictor]
-    p.encoding = ENCODINGS[encoding]
+    p.encoding = ENCODINGS[encoding] | (2 if lossless else 0)
     return p
 
 
@@ -266,8 +269,22 @@ def workspace_size(p: Params) -> int:
     return out.value
 
 
-def decompress_workspace_size() -> int:
-    return int(lib().sdcsz_decompress_workspace_size())
+def decompress_workspace_size(stream=None) -> int:
+    """Decompression workspace bytes: for any stream without the lossless stage, or for the
+    given stream (a uint8 CUDA tensor or host bytes)."""
+    if stream is None:
+        return int(lib().sdcsz_decompress_workspace_size())
+    import torch
+    n = stream.numel() if isinstance(stream, torch.Tensor) else len(stream)
+    hb = (stream[:128].cpu().numpy() if isinstance(stream, torch.Tensor) else np.frombuffer(bytes(stream[:128]),
+                                                                                                dtype=np.uint8))
+    buf = np.zeros(128, dtype=np.uint8)
+    buf[: hb.size] = hb
+    out = ctypes.c_size_t()
+    rc = lib().sdcsz_decompress_workspace_size_for(buf.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(out))
+    if rc:
+        raise SdcszError(rc, "decompress_workspace_size_for")
+    return int(out.value)
 
 
 def _stream_handle(stream):
@@ -301,15 +318,16 @@ class Workspace:
 
 
 def compress(field, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto", flips=None,
-             workspace: Workspace | None = None, stream=None, sync=True, encoding="raw"):
+             workspace: Workspace | None = None, stream=None, sync=True, encoding="raw", lossless=False):
     """Compress a CUDA tensor (float32/float64, 1-3 dims, contiguous). Returns
     (stream bytes as a uint8 CUDA tensor view, report dict or None). ``encoding`` "compact"
     keeps the regression coefficients as bound-relative integers and the unpredictable values
-    truncated to the bits the bound needs, both inside the block payloads."""
+    truncated to the bits the bound needs, both inside the block payloads; ``lossless`` adds the
+    final lossless stage (an order-0 rANS coder over everything after the block tables)."""
     import torch
     if not field.is_cuda or not field.is_contiguous():
         raise ValueError("field must be a contiguous CUDA tensor")
-    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
+    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding, lossless)
     if workspace is not None and workspace.p.encoding != p.encoding:
         raise ValueError("workspace was sized for another encoding")
     w = workspace if workspace is not None else Workspace(p, field.device)
@@ -350,7 +368,7 @@ def read_header(stream_bytes):
     block = tuple(int(p.block[a]) for a in range(p.ndim))
     return {"shape": shape, "dtype": "float32" if p.dtype == 0 else "float64", "block": block,
             "total": int(total.value), "abft": bool(p.abft), "bins": int(p.quant_bins),
-            "encoding": "compact" if p.encoding == 1 else "raw"}
+            "encoding": "compact" if p.encoding & 1 else "raw", "lossless": bool(p.encoding & 2)}
 
 
 def _geometry(stream):
@@ -386,7 +404,7 @@ def decompress(stream, out=None, status=None, flips=None, ws=None, cuda_stream=N
     h, nb, dt = _geometry(stream)
     field = out if out is not None else torch.empty(h["shape"], dtype=dt, device=stream.device)
     st = status if status is not None else torch.empty(max(nb, 1), dtype=torch.uint8, device=stream.device)
-    w = ws if ws is not None else torch.empty(decompress_workspace_size(), dtype=torch.uint8, device=stream.device)
+    w = ws if ws is not None else torch.empty(decompress_workspace_size(stream), dtype=torch.uint8, device=stream.device)
     rep = Report()
     hs = _stream_handle(cuda_stream)
     args = [ctypes.c_void_p(stream.data_ptr()), stream.numel(), ctypes.c_void_p(field.data_ptr()),
@@ -422,7 +440,7 @@ def decompress_region(stream, lo, hi, out=None, status=None, ws=None, cuda_strea
     if status is not None and status.numel() < nblk:
         raise SdcszError(ECAPACITY, "decompress_region status")
     st = status if status is not None else torch.empty(max(nblk, 1), dtype=torch.uint8, device=stream.device)
-    w = ws if ws is not None else torch.empty(decompress_workspace_size(), dtype=torch.uint8, device=stream.device)
+    w = ws if ws is not None else torch.empty(decompress_workspace_size(stream), dtype=torch.uint8, device=stream.device)
     rep = Report()
     lo_a = (ctypes.c_uint64 * 3)(*(lo + [0] * (3 - len(lo))))
     hi_a = (ctypes.c_uint64 * 3)(*(hi + [0] * (3 - len(hi))))
@@ -441,7 +459,7 @@ def verify(stream, original=None, status=None, ws=None, cuda_stream=None):
     import torch
     h, nb, dt = _geometry(stream)
     st = status if status is not None else torch.empty(max(nb, 1), dtype=torch.uint8, device=stream.device)
-    w = ws if ws is not None else torch.empty(decompress_workspace_size(), dtype=torch.uint8, device=stream.device)
+    w = ws if ws is not None else torch.empty(decompress_workspace_size(stream), dtype=torch.uint8, device=stream.device)
     rep = Report()
     orig = ctypes.c_void_p(original.data_ptr()) if original is not None else None
     rc = lib().sdcsz_verify(ctypes.c_void_p(stream.data_ptr()), stream.numel(), orig, ctypes.c_void_p(st.data_ptr()),
@@ -476,10 +494,10 @@ def decompress_traced(stream_t, out, ws, stream=None):
 
 
 def compress_noalloc(field, out, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-                     stream=None, encoding="raw"):
+                     stream=None, encoding="raw", lossless=False):
     """Compress into the caller's uint8 CUDA tensor `out` with the library's fixed scratch
     (no device allocation by the library). Returns (stream bytes view, report dict)."""
-    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
+    p = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding, lossless)
     n = ctypes.c_size_t()
     rep = Report()
     rc = lib().sdcsz_compress_noalloc(ctypes.c_void_p(field.data_ptr()), ctypes.byref(p),
@@ -610,10 +628,11 @@ class Server:
         self._keep[int(req.id)] = keep
 
     def submit_compress(self, rid, field, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",
-                        out=None, flips=None, encoding="raw"):
+                        out=None, flips=None, encoding="raw", lossless=False):
         r = Request()
         r.op, r.id, r.d_in = OP_COMPRESS, rid, field.data_ptr()
-        r.params = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding)
+        r.params = make_params(tuple(field.shape), field.dtype, eb, eb_mode, block, bins, abft, predictor, encoding,
+                               lossless)
         if out is not None:
             r.d_out, r.out_cap = out.data_ptr(), out.numel()
         ft = flips_tensor(flips, field.device) if flips else None

@@ -93,7 +93,7 @@ inline namespace host {
 int make_geo(const sdcsz_params* p, Geo* g) {
   if (!p) return SDCSZ_EINVAL;
   if (p->ndim < 1 || p->ndim > 3 || p->dtype > 1 || p->eb_mode > 1 || p->abft > 1 || p->predictor > 2 ||
-      p->encoding > 1)
+      p->encoding > 3)
     return SDCSZ_EINVAL;
   if (!(p->eb > 0.0) || !(p->eb < 1.0 / 0.0)) return SDCSZ_EINVAL;
   const uint32_t bins = p->quant_bins ? p->quant_bins : 65536u;
@@ -131,7 +131,8 @@ int make_geo(const sdcsz_params* p, Geo* g) {
   g->abft = (int)p->abft;
   g->predictor = (int)p->predictor;
   g->eb_mode = (int)p->eb_mode;
-  g->enc = (int)p->encoding;
+  g->enc = (int)(p->encoding & 1);
+  g->lossless = (int)((p->encoding >> 1) & 1);
   g->e = p->eb;
   return SDCSZ_OK;
 }
@@ -168,8 +169,26 @@ WsPlan plan_ws(const Geo& g) {
   w.codes = take(4 * pair_slots);
   w.ustage = take(s * slots);
   w.etmp = take(4 * encode_slot_words(g) * nb);
+  w.raw = w.raw_cap = w.llw = w.llst = w.llsz = w.lltop = w.lloff = w.llhist = w.llcum = 0;
+  if (g.lossless) {
+    w.raw_cap = raw_stream_bound(g);
+    const size_t chunks = (w.raw_cap + kLLChunk - 1) / kLLChunk;
+    w.raw = take(w.raw_cap);
+    w.llw = take(2 * (size_t)kLLChunk * chunks);
+    w.llst = take(128 * chunks);
+    w.llsz = take(4 * chunks);
+    w.lltop = take(4 * chunks);
+    w.lloff = take(8 * chunks);
+    w.llhist = take(8 * 256);
+    w.llcum = take(4 * 257);
+  }
   w.total = o;
   return w;
+}
+
+uint64_t raw_stream_bound(const Geo& g) {
+  const Layout L = make_layout(g, g.bins, g.nb, g.N);
+  return L.payload + g.nb * 4 * encode_slot_words(g);
 }
 
 Ws bind_ws(void* base, const WsPlan& p) {
@@ -195,6 +214,15 @@ Ws bind_ws(void* base, const WsPlan& p) {
   w.codes = reinterpret_cast<uint16_t*>(b + p.codes);
   w.ustage = b + p.ustage;
   w.etmp = reinterpret_cast<uint32_t*>(b + p.etmp);
+  w.raw = p.raw_cap ? b + p.raw : nullptr;
+  w.raw_cap = p.raw_cap;
+  w.llw = reinterpret_cast<uint16_t*>(b + p.llw);
+  w.llst = reinterpret_cast<uint32_t*>(b + p.llst);
+  w.llsz = reinterpret_cast<uint32_t*>(b + p.llsz);
+  w.lltop = reinterpret_cast<uint32_t*>(b + p.lltop);
+  w.lloff = reinterpret_cast<unsigned long long*>(b + p.lloff);
+  w.llhist = reinterpret_cast<unsigned long long*>(b + p.llhist);
+  w.llcum = reinterpret_cast<uint32_t*>(b + p.llcum);
   return w;
 }
 
@@ -272,7 +300,11 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
   const WsPlan plan = plan_ws(g);
   if (ws_bytes < plan.total) return SDCSZ_ECAPACITY;
   if (out_cap < (size_t)kHeaderBytes) return SDCSZ_ECAPACITY;
+  if (g.lossless && (reinterpret_cast<uintptr_t>(d_out) & 15)) return SDCSZ_EINVAL;
   const Ws w = bind_ws(d_ws, plan);
+  // with the lossless stage the stream is first assembled in the workspace
+  uint8_t* kout = g.lossless ? w.raw : static_cast<uint8_t*>(d_out);
+  const uint64_t kcap = g.lossless ? w.raw_cap : out_cap;
   Launch L;
   L.stream = static_cast<cudaStream_t>(stream);
   L.sms = sm_count();
@@ -301,12 +333,16 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
   tr.mark();
   {
     NvtxRange r("sdcsz codebook");
-    launch_codebook(g, w, static_cast<uint8_t*>(d_out), out_cap, L);
+    launch_codebook(g, w, kout, kcap, L);
   }
   tr.mark();
   {
     NvtxRange r("sdcsz encode");
-    launch_encode(g, w, static_cast<uint8_t*>(d_out), out_cap, L);
+    launch_encode(g, w, kout, kcap, L);
+  }
+  if (g.lossless) {
+    NvtxRange r("sdcsz lossless stage");
+    launch_ll_pack(g, w, static_cast<uint8_t*>(d_out), out_cap, L);
   }
   tr.mark();
   if (cudaGetLastError() != cudaSuccess) return SDCSZ_ECUDA;
@@ -365,7 +401,10 @@ int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout) 
   }
   if (!(eb > 0.0) || !(eb < 1.0 / 0.0)) return SDCSZ_EFORMAT;
   const Layout L = make_layout(g, n_live, n_reg, n_unpred);
-  if (payload > total || total != L.payload + payload || total > nbytes) return SDCSZ_EFORMAT;
+  uint64_t raw_total = total;
+  if (g.lossless) std::memcpy(&raw_total, s + 120, 8);
+  if (payload > raw_total || raw_total != L.payload + payload || total > nbytes) return SDCSZ_EFORMAT;
+  if (g.lossless && ll_data(L.sumdc, ll_chunks(L.sumdc, raw_total)) > total) return SDCSZ_EFORMAT;
   if (h) {
     h->g = g;
     h->L = L;
@@ -374,6 +413,7 @@ int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout) 
     h->n_unpred = n_unpred;
     h->payload_bytes = payload;
     h->total = total;
+    h->raw_total = raw_total;
     h->eb = eb;
     if (p.dtype == 0) {
       const float ebf = (float)eb;
@@ -394,17 +434,31 @@ int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout) 
 
 int decode_enqueue(const void* d_stream, size_t nbytes, const Hdr& h, void* d_field, size_t field_bytes,
                    uint8_t* status, const void* d_orig, bool write, State* st, cudaStream_t s, const sdcsz_flip* flips,
-                   size_t n_flips) {
+                   size_t n_flips, uint8_t* raw) {
   const uint64_t need = h.g.N * (h.g.dtype ? 8 : 4);
   if (write && need && (!d_field || field_bytes < need)) return d_field ? SDCSZ_ECAPACITY : SDCSZ_EINVAL;
   if (n_flips > 0xffffffffu || (n_flips && !flips)) return SDCSZ_EINVAL;
+  if (h.g.lossless && (!raw || (reinterpret_cast<uintptr_t>(raw) & 15) ||
+                       (reinterpret_cast<uintptr_t>(d_stream) & 15)))
+    return SDCSZ_EINVAL;
   if (cudaMemsetAsync(st, 0, sizeof(State), s) != cudaSuccess) return SDCSZ_ECUDA;
   Launch L;
   L.stream = s;
   L.sms = sm_count();
-  launch_decode(static_cast<const uint8_t*>(d_stream), nbytes, h, d_field, status, d_orig, st, write, flips,
-                (uint32_t)n_flips, L);
+  const uint8_t* src = static_cast<const uint8_t*>(d_stream);
+  uint64_t n = nbytes;
+  if (h.g.lossless) {  // Algorithm 2's first step: undo the lossless stage into `raw`
+    launch_ll_unpack(src, nbytes, h, raw, st, L);
+    src = raw;
+    n = h.raw_total;
+  }
+  launch_decode(src, n, h, d_field, status, d_orig, st, write, flips, (uint32_t)n_flips, L);
   return SDCSZ_OK;
+}
+
+// Decompression workspace: the State, then (lossless stage) the stream without the stage.
+size_t decode_ws_bytes(const Hdr& h) {
+  return align256(sizeof(State)) + (h.g.lossless ? align256(h.raw_total) : 0);
 }
 
 int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes, uint8_t* status,
@@ -423,14 +477,16 @@ int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t f
   Hdr h;
   int rc = parse_header(hb, nbytes, &h, nullptr);
   if (rc) return rc;
+  if (ws_bytes < decode_ws_bytes(h)) return SDCSZ_ECAPACITY;
   State* st = static_cast<State*>(d_ws);
+  uint8_t* raw = static_cast<uint8_t*>(d_ws) + align256(sizeof(State));
   Trace tr;
   tr.ms = stage_ms;
   tr.n = 1;
   tr.start(s);
   {
     NvtxRange r(write ? "sdcsz decode" : "sdcsz verify");
-    rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips);
+    rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips, raw);
   }
   if (rc) return rc;
   tr.mark();
@@ -465,8 +521,13 @@ int sdcsz_compress_bound(const sdcsz_params* p, size_t* max_bytes) {
   const int rc = make_geo(p, &g);
   if (rc) return rc;
   if (!max_bytes) return SDCSZ_EINVAL;
-  const Layout L = make_layout(g, g.bins, g.nb, g.N);
-  *max_bytes = (size_t)(L.payload + g.nb * 4 * encode_slot_words(g));
+  uint64_t b = raw_stream_bound(g);
+  if (g.lossless) {  // up to 2 bytes per coded byte, the tables and each chunk's states
+    const Layout L = make_layout(g, g.bins, g.nb, g.N);
+    const uint64_t n = b - L.sumdc, nch = ll_chunks(L.sumdc, b);
+    b = ll_data(L.sumdc, nch) + 2 * n + nch * 132;
+  }
+  *max_bytes = (size_t)b;
   return SDCSZ_OK;
 }
 
@@ -480,6 +541,15 @@ int sdcsz_workspace_size(const sdcsz_params* p, size_t* bytes) {
 }
 
 size_t sdcsz_decompress_workspace_size(void) { return align256(sizeof(State)); }
+
+int sdcsz_decompress_workspace_size_for(const void* h_header, size_t nbytes, size_t* bytes) {
+  if (!h_header || !bytes) return SDCSZ_EINVAL;
+  Hdr h;
+  const int rc = parse_header(static_cast<const uint8_t*>(h_header), nbytes, &h, nullptr);
+  if (rc) return rc;
+  *bytes = decode_ws_bytes(h);
+  return SDCSZ_OK;
+}
 
 int sdcsz_compress(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap, size_t* out_bytes,
                    void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream) {
@@ -602,6 +672,8 @@ extern "C" int sdcsz_decompress_region(const void* d_stream, size_t nbytes, cons
   Hdr h;
   int rc = parse_header(hb, nbytes, &h, nullptr);
   if (rc) return rc;
+  if (ws_bytes < decode_ws_bytes(h)) return SDCSZ_ECAPACITY;
+  if (h.g.lossless && (reinterpret_cast<uintptr_t>(d_stream) & 15)) return SDCSZ_EINVAL;
   // the box in padded 3D coordinates
   uint64_t lo3[3] = {0, 0, 0}, hi3[3] = {1, 1, 1}, pts = 1, nblk = 1;
   const int off = 3 - h.g.ndim;
@@ -620,7 +692,15 @@ extern "C" int sdcsz_decompress_region(const void* d_stream, size_t nbytes, cons
   L.sms = sm_count();
   {
     NvtxRange r("sdcsz decode region");
-    launch_region(static_cast<const uint8_t*>(d_stream), nbytes, h, d_out, lo3, hi3, d_block_status, st, L);
+    const uint8_t* src = static_cast<const uint8_t*>(d_stream);
+    uint64_t n = nbytes;
+    if (h.g.lossless) {  // the whole stage is undone (its chunks do not follow block boundaries)
+      uint8_t* raw = static_cast<uint8_t*>(d_ws) + align256(sizeof(State));
+      launch_ll_unpack(src, nbytes, h, raw, st, L);
+      src = raw;
+      n = h.raw_total;
+    }
+    launch_region(src, n, h, d_out, lo3, hi3, d_block_status, st, L);
   }
   if (cudaGetLastError() != cudaSuccess) return SDCSZ_ECUDA;
   if (report) {
@@ -887,9 +967,9 @@ int sdcsz_batch_create(const sdcsz_batch_item* items, uint32_t n, sdcsz_batch** 
   for (uint32_t j = 0; j < n; ++j) {
     Geo g;
     const int rc = make_geo(&items[j].params, &g);
-    if (rc) {
+    if (rc || g.lossless) {  // the lossless stage runs per field (sdcsz_compress), not in batches
       delete b;
-      return rc;
+      return rc ? rc : SDCSZ_EINVAL;
     }
     b->geo.push_back(g);
     b->plan.push_back(plan_ws(g));

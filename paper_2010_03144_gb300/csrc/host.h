@@ -22,7 +22,12 @@ struct NvtxRange {
 struct WsPlan {
   size_t state, sum_in, isum_in, sum_q, isum_q, sum_dc, coef, est, pflag, flags, coefT, hist, codebook, lb, sort_keys,
       node_w, node_parent, codes, ustage, etmp, total;
+  // lossless stage
+  size_t raw, raw_cap, llw, llst, llsz, lltop, lloff, llhist, llcum;
 };
+
+// Worst-case size of a stream before the lossless stage.
+uint64_t raw_stream_bound(const Geo& g);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 int sm_count();
@@ -41,10 +46,13 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
 
 // Decompression (write) or verification of a stream whose header was already parsed to the
 // host: clears the State at `st` and enqueues the decoder; no host synchronisation.
+// A stream with the lossless stage is first decoded into `raw` (h.raw_total bytes, 16-byte
+// aligned; unused otherwise).
 int decode_enqueue(const void* d_stream, size_t nbytes, const Hdr& h, void* d_field, size_t field_bytes,
                    uint8_t* status, const void* d_orig, bool write, State* st, cudaStream_t s, const sdcsz_flip* flips,
-                   size_t n_flips);
+                   size_t n_flips, uint8_t* raw = nullptr);
 
+size_t decode_ws_bytes(const Hdr& h);
 int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes, uint8_t* status,
                     const void* d_orig, bool write, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,
                     const sdcsz_flip* flips, size_t n_flips, float* stage_ms = nullptr);

@@ -35,7 +35,8 @@ struct Geo {
   uint32_t P;  // points in a full block
   uint32_t bins, R;
   int abft, predictor, eb_mode;
-  int enc;  // 1: compact encoding (coefficients and unpredictable values in the payload)
+  int enc;       // 1: compact encoding (coefficients and unpredictable values in the payload)
+  int lossless;  // 1: the lossless stage codes the stream after its block tables
   double e;
 };
 
@@ -57,6 +58,7 @@ struct State {
   unsigned long long payload_bytes, total_bytes;
   unsigned long long n_unpred_enc;  // unpredictable points of the codes as encoded (after repairs)
   double cstep[4], cinv[4];         // compact encoding: coefficient steps (set with the bound)
+  unsigned long long raw_total;     // lossless stage: size of the stream before the stage
   Layout L;
   unsigned long long queue[4];  // work-queue counters of the persistent kernels of one call
 };
@@ -98,7 +100,21 @@ struct Ws {
   uint16_t* codes;     // quantization codes in warp-interleaved pairs (see pair_index)
   void* ustage;        // unpredictable values, same interleaving as codes
   uint32_t* etmp;      // per-block payload slots of the encoder (encode_slot_words each)
+  // lossless stage (compression): the stream before the stage and the coder's scratch
+  uint8_t* raw;                    // the stream before the stage (raw_cap bytes)
+  unsigned long long raw_cap;
+  uint16_t* llw;                   // per chunk: kLLChunk words, filled from the end
+  uint32_t* llst;                  // per chunk: 32 final states
+  uint32_t* llsz;                  // per chunk: coded bytes (padded to 4); then the first word used
+  uint32_t* lltop;
+  unsigned long long* lloff;       // per chunk: offset in the output
+  unsigned long long* llhist;      // byte histogram (256)
+  uint32_t* llcum;                 // cumulative frequencies (257)
 };
+
+// Lossless stage: order-0 rANS over the bytes after the block tables, in independent chunks
+// of kLLChunk bytes, 32 interleaved states each (byte i of a chunk belongs to state i mod 32).
+constexpr uint32_t kLLChunk = 16384, kLLScale = 12, kLLM = 1u << kLLScale, kLLTable = 512;
 
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 
@@ -691,7 +707,22 @@ struct Hdr {
   double eb;
   int texp;         // compact encoding: floor(log2 eb), the truncation exponent of unpredictable values
   double cstep[4];  // compact encoding: steps of the coefficient integers
+  uint64_t raw_total;  // the stream's size without the lossless stage (== total without it)
 };
+
+// Lossless stage. Compression: over the finished stream in w.raw (its layout and size in the
+// State), into `out`; sets the State's total to the coded size. Decompression: the stream `s`
+// (nbytes) back into `raw` (h.raw_total bytes).
+void launch_ll_pack(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
+void launch_ll_unpack(const uint8_t* s, uint64_t nbytes, const Hdr& h, uint8_t* raw, State* st, const Launch& L);
+// Chunks of a stream whose coded region starts at `from` and whose stream without the stage has
+// raw_total bytes.
+__host__ __device__ inline uint64_t ll_chunks(uint64_t from, uint64_t raw_total) {
+  return raw_total > from ? (raw_total - from + kLLChunk - 1) / kLLChunk : 0;
+}
+__host__ __device__ inline uint64_t ll_data(uint64_t from, uint64_t nchunks) {
+  return align16(from + kLLTable + 4 * nchunks);
+}
 // Blocks intersecting the box [lo, hi) (padded 3D coordinates) into a dense array of its shape.
 void launch_region(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
                    const uint64_t hi[3], uint8_t* status, State* st, const Launch& L);

@@ -95,7 +95,7 @@ int request_need(sdcsz_server* S, Req& q) {
     q.parsed = true;
   }
   const uint64_t field = q.h.g.N * (q.h.g.dtype ? 8 : 4);
-  q.ws_bytes = align256(sizeof(State)) + (r.op == SDCSZ_OP_VERIFY ? align256(q.h.g.nb) : 0);
+  q.ws_bytes = decode_ws_bytes(q.h) + (r.op == SDCSZ_OP_VERIFY ? align256(q.h.g.nb) : 0);
   q.out_bytes = (r.op == SDCSZ_OP_DECOMPRESS && !r.d_out) ? align256(field) : 0;
   if (r.op == SDCSZ_OP_DECOMPRESS && r.d_out && r.out_cap < field) return SDCSZ_ECAPACITY;
   return SDCSZ_OK;
@@ -160,9 +160,11 @@ int launch(sdcsz_server* S, Slot& sl) {
     const bool write = r.op == SDCSZ_OP_DECOMPRESS;
     void* field = write ? (r.d_out ? r.d_out : q.out) : nullptr;
     const size_t fb = write ? (r.d_out ? r.out_cap : q.out_bytes) : 0;
-    uint8_t* status = write ? nullptr : static_cast<uint8_t*>(q.ws) + align256(sizeof(State));
+    uint8_t* base = static_cast<uint8_t*>(q.ws);
+    uint8_t* raw = base + align256(sizeof(State));  // the lossless stage's scratch, when there is one
+    uint8_t* status = write ? nullptr : base + decode_ws_bytes(q.h);
     rc = decode_enqueue(r.d_in, r.in_bytes, q.h, field, fb, status, write ? nullptr : r.d_original, write, st, s,
-                        r.d_flips, r.n_flips);
+                        r.d_flips, r.n_flips, raw);
   }
   if (rc) return rc;
   if (cudaMemcpyAsync(sl.h_state, st, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SDCSZ_ECUDA;
