@@ -197,9 +197,9 @@ def run_ours(args):
     x = synth.sinusoid_field(shape, wl["seed"] + rank, spikes=wl["spikes"])
     N, s_dt = x.size, 4
     d = torch.from_numpy(x).to(device)
-    enc = args.encoding
-    p_on = sz.make_params(shape, np.float32, REL_EB, block=block, abft=True, encoding=enc)
-    p_off = sz.make_params(shape, np.float32, REL_EB, block=block, abft=False, encoding=enc)
+    enc, ll = args.encoding, args.lossless
+    p_on = sz.make_params(shape, np.float32, REL_EB, block=block, abft=True, encoding=enc, lossless=ll)
+    p_off = sz.make_params(shape, np.float32, REL_EB, block=block, abft=False, encoding=enc, lossless=ll)
     ws_on = sz.Workspace(p_on, device)
     ws_off = sz.Workspace(p_off, device)
     out = torch.empty(shape, dtype=torch.float32, device=device)
@@ -216,7 +216,8 @@ def run_ours(args):
         return nbytes
 
     # reports of one run for counts and the compression ratio
-    s_t, rep = sz.compress(d, REL_EB, block=block, workspace=ws_on, encoding=enc)
+    s_t, rep = sz.compress(d, REL_EB, block=block, workspace=ws_on, encoding=enc, lossless=ll)
+    dws = torch.empty(sz.decompress_workspace_size(s_t), dtype=torch.uint8, device=device)
     stream_bytes = int(rep["compressed_bytes"])
     rc, y, st, rep_d = sz.decompress(s_t, out=out, ws=dws)
     assert rc == 0
@@ -283,7 +284,7 @@ def run_ours(args):
 
     def e2e_step():
         d_in.copy_(h_field, non_blocking=True)
-        s_out, r = sz.compress(d_in, REL_EB, block=block, workspace=ws_on, encoding=enc)
+        s_out, r = sz.compress(d_in, REL_EB, block=block, workspace=ws_on, encoding=enc, lossless=ll)
         n = int(r["compressed_bytes"])
         h_stream[:n].copy_(s_out, non_blocking=True)
         d_s[:n].copy_(h_stream[:n], non_blocking=True)
@@ -323,7 +324,8 @@ def run_ours(args):
             "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload} float32 {shape} sinusoids+noise+{wl['spikes']:.0%} spikes, "
-                                   f"rel eb {REL_EB}, block {block}^3, ABFT on, {enc} encoding; "
+                                   f"rel eb {REL_EB}, block {block}^3, ABFT on, {enc} encoding"
+                                   f"{' + lossless stage' if ll else ''}; "
                                    "one step = compress + decompress",
                        "field_bytes": N * s_dt, "compressed_bytes": stream_bytes,
                        "compression_ratio": round(N * s_dt / stream_bytes, 3),
@@ -370,7 +372,8 @@ def cpu_baseline(args):
     x, slab = _oracle_sample(args)
     oracle.lib()
     t0 = time.perf_counter()
-    s, rep = oracle.compress(x, REL_EB, block=WORKLOADS[args.workload]["block"], encoding=args.encoding)
+    s, rep = oracle.compress(x, REL_EB, block=WORKLOADS[args.workload]["block"], encoding=args.encoding,
+                             lossless=args.lossless)
     rc, y, st, _ = oracle.decompress(s)
     dt = time.perf_counter() - t0
     return {"value": round(x.nbytes / 1e9 / dt, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
@@ -388,10 +391,10 @@ def run_reference(args):
     oracle.lib()
     block = WORKLOADS[args.workload]["block"]
     for _ in range(args.warmup):
-        oracle.compress(x[:8], REL_EB, block=block, encoding=args.encoding)
+        oracle.compress(x[:8], REL_EB, block=block, encoding=args.encoding, lossless=args.lossless)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, rep = oracle.compress(x, REL_EB, block=block, encoding=args.encoding)
+        s, rep = oracle.compress(x, REL_EB, block=block, encoding=args.encoding, lossless=args.lossless)
         oracle.decompress(s)
     dt = time.perf_counter() - t0
     value = x.nbytes * args.steps / 1e9 / dt
@@ -760,6 +763,7 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
     ap.add_argument("--encoding", choices=("raw", "compact"), default="raw",
                     help="stream encoding: raw coefficient/unpredictable sections, or compact (in the payload)")
+    ap.add_argument("--lossless", action="store_true", help="add the lossless stage (rANS over the block data)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -169,7 +169,8 @@ int sdcsz_verify(const void* d_stream, size_t nbytes, const void* d_original, ui
  * recorded on `stream` between the stages; the call synchronizes and writes the elapsed
  * milliseconds of each stage to stage_ms (host). Compression has 5 stages: buffer reset,
  * K1 preparation (range, sum_in/isum_in, regression, estimates), K2 prediction/quantization,
- * K3 Huffman code, K4 encoding. Decompression has 1 stage: K5.
+ * K3 Huffman code, K4 encoding (with the lossless stage, when on). Decompression has 1
+ * stage: K5 (after undoing the lossless stage, when on).
  */
 int sdcsz_compress_traced(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap, size_t* out_bytes,
                           void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream, float* stage_ms);
