@@ -906,11 +906,10 @@ __device__ __forceinline__ bool fast_dispatch(bool reg, const uint8_t* s, const 
 // Fast kernel: full blocks of a compile-time shape (WRITE: decompression, else verification;
 // CMP: compact encoding).
 template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE, bool CMP>
-__global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
-                                                     uint8_t* status, const T* orig, State* st,
-                                                     const sdcsz_flip* __restrict__ flips, uint32_t nflips,
-                                                     int vec2) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, uint64_t nbytes, const Hdr& h, T* field,
+                                                uint8_t* status, const T* orig, State* st,
+                                                const sdcsz_flip* __restrict__ flips, uint32_t nflips, int vec2,
+                                                unsigned char* smem) {
   __shared__ Smem sm;
   uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
   const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
@@ -982,6 +981,26 @@ __global__ void __launch_bounds__(256) k_decode_fast(const uint8_t* __restrict__
   acc.commit(st);
 }
 
+// The raw and compact kernels, held to two CTAs per SM (128 registers): left to itself the
+// compiler spills some variants at 80 registers.
+template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE>
+__global__ void __launch_bounds__(256, 2) k_decode_fast(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
+                                                     uint8_t* status, const T* orig, State* st,
+                                                     const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                     int vec2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  decode_fast_cta<T, NDIM, B0, B1, B2, WRITE, false>(s, nbytes, h, field, status, orig, st, flips, nflips, vec2, smem);
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE>
+__global__ void __launch_bounds__(256, 2) k_decode_fast_c(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h,
+                                                          T* field, uint8_t* status, const T* orig, State* st,
+                                                          const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                          int vec2) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  decode_fast_cta<T, NDIM, B0, B1, B2, WRITE, true>(s, nbytes, h, field, status, orig, st, flips, nflips, vec2, smem);
+}
+
 // ---------------------------------------------------------------- launch
 template <class K>
 inline unsigned persistent_grid(K kern, uint32_t threads, size_t smem, uint64_t ngroups, const Launch& L) {
@@ -993,8 +1012,8 @@ template <typename T, int NDIM, int B0, int B1, int B2>
 void run_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
               const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
   const size_t smem = (12u << kLutBits) + (size_t)walker_slots(NDIM, h.g.B) * 256 * sizeof(T);  // lut, pair lut, plane
-  auto kern = h.g.enc ? (field ? k_decode_fast<T, NDIM, B0, B1, B2, true, true> : k_decode_fast<T, NDIM, B0, B1, B2, false, true>)
-                      : (field ? k_decode_fast<T, NDIM, B0, B1, B2, true, false> : k_decode_fast<T, NDIM, B0, B1, B2, false, false>);
+  auto kern = h.g.enc ? (field ? k_decode_fast_c<T, NDIM, B0, B1, B2, true> : k_decode_fast_c<T, NDIM, B0, B1, B2, false>)
+                      : (field ? k_decode_fast<T, NDIM, B0, B1, B2, true> : k_decode_fast<T, NDIM, B0, B1, B2, false>);
   const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
   const unsigned grid = persistent_grid(kern, 256, smem, ngroups, L);
   const uintptr_t al = 2 * sizeof(T);

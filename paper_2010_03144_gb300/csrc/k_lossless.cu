@@ -26,10 +26,6 @@ namespace {
 
 constexpr uint32_t kRansLow = 1u << 16;
 
-__device__ __forceinline__ void put_u64(uint8_t* o, uint64_t off, unsigned long long v) {
-  for (int q = 0; q < 8; ++q) o[off + q] = (uint8_t)(v >> (8 * q));
-}
-
 // ---------------------------------------------------------------- K6a
 __global__ void __launch_bounds__(256) k_ll_hist(const uint8_t* __restrict__ raw, State* st,
                                                  unsigned long long* hist) {
@@ -99,20 +95,43 @@ __global__ void k_ll_freq(State* st, const unsigned long long* __restrict__ hist
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (total) {
-    while (sum > (long long)kLLM) {
-      // the largest frequency above 1, smaller byte on ties: key = f << 8 | (255 - byte)
-      uint32_t key = 0;
+    if (sum > (long long)kLLM) {
+      // Taking one at a time from the largest frequency (smaller byte on ties) D = sum - 4096
+      // times ends with every frequency above v capped at v, where v is the smallest level
+      // whose cap removes at most D (A(v) = sum of max(0, f - v) <= D), and the R = D - A(v)
+      // smallest bytes at level v taken down to v - 1 (v >= 2: A(1) >= 4096 - 256 > D).
+      const long long D = sum - (long long)kLLM;
+      auto above = [&](uint32_t v) {
+        long long a = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a += f[q] > v ? (long long)(f[q] - v) : 0;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        return a;
+      };
+      uint32_t lo = 1, hi = kLLM;  // A(hi) = 0 <= D; find the smallest v with A(v) <= D
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (above(mid) <= D) hi = mid;
+        else lo = mid + 1;
+      }
+      const uint32_t v = lo;
+      const long long R = D - above(v);
+      uint32_t mine = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) mine += f[q] >= v;
+      uint32_t incl = mine;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+      }
+      uint32_t rank = incl - mine;
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        if (f[q] > 1) key = max(key, (f[q] << 8) | (255u - (8 * lane + q)));
-      for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
-      const uint32_t b = 255u - (key & 255u);
-      if (b / 8 == lane) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if ((uint32_t)q == b % 8) --f[q];
-      }
-      --sum;
+        if (f[q] >= v) {
+          f[q] = (long long)rank < R ? v - 1 : v;
+          ++rank;
+        }
+      sum = kLLM;
     }
     if (sum < (long long)kLLM) {
       // the most frequent byte, smaller byte on ties
@@ -161,10 +180,32 @@ __global__ void k_ll_freq(State* st, const unsigned long long* __restrict__ hist
 }
 
 // ---------------------------------------------------------------- K6c
-// One warp per chunk, from its last group of 32 bytes to its first.
+// Per byte: cumulative frequency and frequency packed (c | f << 16), and m = ceil(2^32 / f)
+// (0 for f = 1), so that x / f is umulhi(x, m) or one less (checked with the remainder).
+__device__ __forceinline__ void ll_divmod(uint32_t x, uint32_t f, uint32_t m, uint32_t& q, uint32_t& r) {
+  if (f == 1) {
+    q = x;
+    r = 0;
+    return;
+  }
+  q = __umulhi(x, m);
+  long long rr = (long long)x - (long long)q * f;
+  if (rr < 0) {
+    --q;
+    rr += f;
+  }
+  r = (uint32_t)rr;
+}
+
+// One warp per chunk, from its last group of 32 bytes to its first. The bytes are read 128 at a
+// time (lane l holds bytes 4l..4l+3 of a group of four steps), two groups ahead of their use,
+// and handed to the lane that codes them with a shuffle.
 __global__ void __launch_bounds__(256) k_ll_encode(const uint8_t* __restrict__ raw, State* st, Ws w) {
-  __shared__ uint32_t cum[257];
-  for (uint32_t t = threadIdx.x; t < 257; t += blockDim.x) cum[t] = w.llcum[t];
+  __shared__ uint2 tab[256];
+  for (uint32_t t = threadIdx.x; t < 256; t += blockDim.x) {
+    const uint32_t c = w.llcum[t], f = w.llcum[t + 1] - c;
+    tab[t] = make_uint2(c | (f << 16), f > 1 ? (uint32_t)((0x100000000ull + f - 1) / f) : 0u);
+  }
   __syncthreads();
   if (*(volatile unsigned int*)&st->error) return;
   const uint64_t from = st->L.sumdc, end = st->raw_total;
@@ -172,24 +213,50 @@ __global__ void __launch_bounds__(256) k_ll_encode(const uint8_t* __restrict__ r
   const uint64_t k = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31;
   if (k >= nch) return;
-  const uint64_t base = from + k * kLLChunk;
+  const uint64_t base = from + k * kLLChunk;  // 16-byte aligned
   const uint32_t n = (uint32_t)min((uint64_t)kLLChunk, end - base);
   uint16_t* slot = w.llw + k * kLLChunk;
   uint32_t x = kRansLow, top = kLLChunk;
   const uint32_t above = lane == 31 ? 0u : (0xffffffffu << (lane + 1));  // lanes above this one
-  for (uint32_t t = (n + 31) / 32; t-- > 0;) {
-    const uint32_t i = t * 32 + lane;
-    const bool act = i < n;
-    const uint32_t s = act ? raw[base + i] : 0u;
-    const uint32_t c = cum[s], f = cum[s + 1] - c;
-    const bool need = act && (unsigned long long)x >= ((unsigned long long)f << 20);
-    const unsigned mask = __ballot_sync(0xffffffffu, need);
-    if (need) {
-      slot[top - 1 - __popc(mask & above)] = (uint16_t)(x & 0xffffu);
-      x >>= 16;
+  auto group = [&](int g) -> uint32_t {  // bytes 128 g + 4 lane .. + 3 of the chunk
+    if (g < 0) return 0u;
+    const uint32_t o = 128u * (uint32_t)g + 4u * lane;
+    if (o + 4 <= n) return *reinterpret_cast<const uint32_t*>(raw + base + o);
+    uint32_t v = 0;
+    for (uint32_t u = 0; u < 4; ++u)
+      if (o + u < n) v |= (uint32_t)raw[base + o + u] << (8 * u);
+    return v;
+  };
+  const uint32_t T = (n + 31) / 32;
+  const int G = (int)((T + 3) / 4);
+  uint32_t cur = group(G - 1), nx1 = group(G - 2), nx2 = group(G - 3);
+  for (int g = G - 1; g >= 0; --g) {
+#pragma unroll
+    for (int tt = 3; tt >= 0; --tt) {
+      const uint32_t t = 4u * (uint32_t)g + (uint32_t)tt;
+      if (t >= T) continue;  // warp-uniform
+      const uint32_t i = t * 32 + lane;
+      const bool act = i < n;
+      const uint32_t wv = __shfl_sync(0xffffffffu, cur, 8 * tt + (lane >> 2));
+      const uint32_t sbyte = (wv >> (8 * (lane & 3))) & 0xffu;
+      const uint2 e = tab[sbyte];
+      const uint32_t c = e.x & 0xffffu, f = e.x >> 16;
+      const bool need = act && (unsigned long long)x >= ((unsigned long long)f << 20);
+      const unsigned mask = __ballot_sync(0xffffffffu, need);
+      if (need) {
+        slot[top - 1 - __popc(mask & above)] = (uint16_t)(x & 0xffffu);
+        x >>= 16;
+      }
+      top -= __popc(mask);
+      if (act) {
+        uint32_t q, r;
+        ll_divmod(x, f, e.y, q, r);
+        x = (q << kLLScale) + r + c;
+      }
     }
-    top -= __popc(mask);
-    if (act) x = ((x / f) << kLLScale) + (x % f) + c;
+    cur = nx1;
+    nx1 = nx2;
+    nx2 = group(g - 3);
   }
   w.llst[k * 32 + lane] = x;
   if (lane == 0) {
@@ -365,7 +432,11 @@ __global__ void __launch_bounds__(256) k_ll_unpack(const uint8_t* __restrict__ s
   const uint64_t base = from + k * kLLChunk;
   const uint32_t n = (uint32_t)min((uint64_t)kLLChunk, raw_total - base);
   const uint32_t below = (1u << lane) - 1u;
-  uint64_t p = 0;
+  // the words are taken in order, at most 32 per step: a window of 128 of them in registers
+  // (lane l holds words wb + l, wb + 32 + l, ...), the last two groups loaded ahead of use
+  auto word = [&](uint64_t q) -> uint32_t { return q < nw ? (uint32_t)words[q] : 0u; };
+  uint64_t wb = 0, p = 0;
+  uint32_t w0 = word(lane), w1 = word(32 + lane), w2 = word(64 + lane), w3 = word(96 + lane);
   for (uint32_t t = 0; t < (n + 31) / 32; ++t) {
     const uint32_t i = t * 32 + lane;
     const bool act = i < n;
@@ -378,11 +449,17 @@ __global__ void __launch_bounds__(256) k_ll_unpack(const uint8_t* __restrict__ s
       need = x < kRansLow;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, need);
-    if (need) {
-      const uint64_t q = p + __popc(mask & below);
-      x = (x << 16) | (q < nw ? (uint32_t)words[q] : 0u);
-    }
+    const uint32_t src = (uint32_t)(p - wb) + __popc(mask & below);  // < 64
+    const uint32_t a = __shfl_sync(0xffffffffu, w0, src & 31), bw = __shfl_sync(0xffffffffu, w1, src & 31);
+    if (need) x = (x << 16) | (src < 32 ? a : bw);
     p += __popc(mask);
+    if (p - wb >= 32) {  // warp-uniform
+      wb += 32;
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = word(wb + 96 + lane);
+    }
   }
 }
 

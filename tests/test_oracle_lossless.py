@@ -64,6 +64,40 @@ def test_frequencies_invariants(orc, seed):
     assert np.all(np.abs(f - scaled)[c > 0] <= 256)
 
 
+def _closed_form_frequencies(cnt):
+    """The frequency rule in closed form (as the GPU computes it): after scaling, a surplus D is
+    removed by capping every frequency at the smallest level v whose cap removes at most D and
+    taking the R = D - (removed) smallest bytes at level v down to v - 1; a shortfall goes to
+    the most frequent byte."""
+    total = int(cnt.sum())
+    f = np.array([max(1, int(c) * 4096 // total) if c else 0 for c in cnt], dtype=np.int64)
+    s = int(f.sum())
+    if s > 4096:
+        D = s - 4096
+        removed = lambda v: int(np.maximum(f - v, 0).sum())
+        v = next(v for v in range(1, 4097) if removed(v) <= D)
+        R = D - removed(v)
+        rank = 0
+        for b in range(256):
+            if f[b] >= v:
+                f[b] = v - 1 if rank < R else v
+                rank += 1
+    elif s < 4096:
+        f[int(np.argmax(cnt))] += 4096 - s
+    return f
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_frequency_rule_closed_form(orc, seed):
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(40):
+        k = int(rng.integers(1, 257))
+        c = np.zeros(256, dtype=np.uint64)
+        idx = rng.choice(256, size=k, replace=False)
+        c[idx] = (rng.pareto(rng.uniform(0.3, 2.0), size=k) * rng.uniform(1, 1e4) + 1).astype(np.uint64)
+        assert np.array_equal(orc.ll_frequencies(c).astype(np.int64), _closed_form_frequencies(c))
+
+
 def _ideal_bits(data, f):
     return sum(-math.log2(f[b] / 4096.0) for b in np.asarray(data, dtype=np.uint8))
 
