@@ -44,12 +44,12 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 555008000, "src": "97ae17051a6f"},
-    ("384cube", "prep"): {"bytes": 234144000, "src": "97ae17051a6f"},
-    ("512cube", "predict"): {"bytes": 945076452, "src": "ed93904bd6e9"},
-    ("384cube", "predict"): {"bytes": 398704128, "src": "ed93904bd6e9"},
-    ("512cube", "decode"): {"bytes": 481188371, "src": "91c58ed5e4b7"},
-    ("384cube", "decode"): {"bytes": 203001344, "src": "91c58ed5e4b7"},
+    ("512cube", "prep"): {"bytes": 553699100, "src": "6cfdb4f3d876"},
+    ("384cube", "prep"): {"bytes": 233591808, "src": "6cfdb4f3d876"},
+    ("512cube", "predict"): {"bytes": 936414170, "src": "beb3c158bd5a"},
+    ("384cube", "predict"): {"bytes": 395049728, "src": "beb3c158bd5a"},
+    ("512cube", "decode"): {"bytes": 475409067, "src": "9e984b91206b"},
+    ("384cube", "decode"): {"bytes": 200563200, "src": "9e984b91206b"},
 }
 
 
