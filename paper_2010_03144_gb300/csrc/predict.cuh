@@ -33,7 +33,8 @@ constexpr uint32_t kNone = 0xffffffffu;
 struct PassRes {
   unsigned long long sw, isw;  // checksums of the input words used
   unsigned long long isq, sdc; // isum_q, sum_dc
-  uint32_t sq, nun, dup;       // sum_q (< 2^28), unpredictables, duplicate mismatches
+  uint32_t sq, nun, dup;       // sum_q (< 2^28), unpredictables, duplicate mismatches (voting walk)
+  uint32_t mm;                 // OR of (primary ^ duplicate) bits over the block (unvoted walk)
 };
 
 struct Hist {
@@ -96,9 +97,16 @@ __device__ __forceinline__ void sum_words(T v, unsigned long long& sum) {
 // Returns the code (0 = unpredictable) and the value later points are predicted from.
 // An unpredictable point decompresses to its value, truncated to the mantissa bits the bound
 // needs in the compact encoding (texp = floor(log2 eb)); texp = kNoTrunc keeps it whole.
-template <typename T, bool ABFT, bool HOOK, bool CMP>
+//
+// Two forms of the duplicate checks (f_dup, dec_dup). VOTE (the walk that soft-error records
+// reach, and every re-run): a disagreement is settled at once by a third evaluation and
+// counted. Otherwise the walk only ORs the XOR of the two results into `mm`, without a branch;
+// the caller runs a block whose mask is not zero again with VOTE, which settles the
+// disagreement the same way. Both results come from the same operations on the same operands,
+// so without a fault they agree bit for bit, in range or not.
+template <typename T, bool ABFT, bool VOTE, bool CMP>
 __device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, uint32_t R, bool hit_r, uint32_t bitr,
-                                             T& xr, uint32_t& dup, int texp) {
+                                             T& xr, uint32_t& dup, uint32_t& mm, int texp) {
   const T diff = FT<T>::sub(v, pred);
   const T t = FT<T>::mul(FT<T>::absv(diff), inv2);
   const bool inr = t < Rh;
@@ -107,11 +115,15 @@ __device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, ui
   const T tq = FT<T>::fromi(2 * q);
   T xd = FT<T>::add(pred, FT<T>::mul(tq, eb));
   if (ABFT) {
-    if (HOOK && hit_r) xd = FT<T>::flip(xd, bitr);
+    if (VOTE && hit_r) xd = FT<T>::flip(xd, bitr);
     const T x2 = FT<T>::add_v(pred, FT<T>::mul_v(tq, eb));
-    if (inr && !FT<T>::same(xd, x2)) {
-      xd = FT<T>::add_v(pred, FT<T>::mul_v(tq, eb));
-      ++dup;
+    if (VOTE) {
+      if (inr && !FT<T>::same(xd, x2)) {
+        xd = FT<T>::add_v(pred, FT<T>::mul_v(tq, eb));
+        ++dup;
+      }
+    } else {
+      mm |= FT<T>::diffbits(xd, x2);
     }
   }
   const bool ok = inr && (FT<T>::absv(FT<T>::sub(v, xd)) <= eb);
@@ -120,16 +132,21 @@ __device__ __forceinline__ uint32_t quantize(T v, T pred, T eb, T inv2, T Rh, ui
   return ok ? (uint32_t)(q + (int)R) : 0u;
 }
 
-// f_dup for a prediction computed by `prim` (rounded intrinsics) and `dupf` (volatile PTX).
-template <typename T, bool ABFT, bool HOOK, class F1, class F2>
-__device__ __forceinline__ T dup_pred(F1 prim, F2 dupf, bool hit_p, uint32_t bitp, uint32_t& dup) {
+// f_dup for a prediction computed by `prim` (rounded intrinsics) and `dupf` (volatile PTX);
+// VOTE as for quantize.
+template <typename T, bool ABFT, bool VOTE, class F1, class F2>
+__device__ __forceinline__ T dup_pred(F1 prim, F2 dupf, bool hit_p, uint32_t bitp, uint32_t& dup, uint32_t& mm) {
   T pred = prim();
   if (ABFT) {
-    if (HOOK && hit_p) pred = FT<T>::flip(pred, bitp);
+    if (VOTE && hit_p) pred = FT<T>::flip(pred, bitp);
     const T p2 = dupf();
-    if (!FT<T>::same(pred, p2)) {
-      pred = dupf();
-      ++dup;
+    if (VOTE) {
+      if (!FT<T>::same(pred, p2)) {
+        pred = dupf();
+        ++dup;
+      }
+    } else {
+      mm |= FT<T>::diffbits(pred, p2);
     }
   }
   return pred;
@@ -146,7 +163,7 @@ __device__ __noinline__ PassRes generic_pass(const T* __restrict__ field, const 
                                              const T* cT, Walker<T, NDIM>& wk, T eb, T inv2, T Rh,
                                              uint16_t* __restrict__ codes, T* __restrict__ ustage, const Hist& h,
                                              const Hooks hk, T xfix) {
-  PassRes r = {0, 0, 0, 0, 0, 0, 0};
+  PassRes r = {0, 0, 0, 0, 0, 0, 0, 0};
   Run run(g.R);
   uint64_t ci = code_index(b, g.P, 0);  // unpredictable staging (one slot per point)
   uint32_t k = 0;
@@ -161,10 +178,10 @@ __device__ __noinline__ PassRes generic_pass(const T* __restrict__ field, const 
         const T pred = dup_pred<T, ABFT, true>(
             [&] { return REG ? regress<T, NDIM, OpRN<T>>(cT, i, j, l) : wk.template combine<OpRN<T>>(); },
             [&] { return REG ? regress<T, NDIM, OpV<T>>(cT, i, j, l) : wk.template combine<OpV<T>>(); },
-            k == hk.kp, hk.bitp, r.dup);
+            k == hk.kp, hk.bitp, r.dup, r.mm);
         T xr;
         const uint32_t code = quantize<T, ABFT, true, true>(v, pred, eb, inv2, Rh, g.R, k == hk.kr, hk.bitr, xr, r.dup,
-                                                      hk.texp);
+                                                      r.mm, hk.texp);
         codes[code_pos(b, g.P, k)] = (uint16_t)code;
         if (!code) {
           ustage[ci] = v;
@@ -211,6 +228,8 @@ __device__ __forceinline__ void load_row_n(const T* __restrict__ row, uint32_t n
 
 // One full block with compile-time edges. `blk` points at the block origin in the field,
 // `plane` at this thread's shared-memory slot 0 (3D Lorenzo only; slot stride kCta).
+// HOOK: the voting walk that also applies the soft-error records in `hk` (VOTE of quantize);
+// otherwise duplicate disagreements only collect in the result's mask.
 // EDGE: a block cut by the field boundary, extents e0 x e1 x e2 at most B0 x B1 x B2 (the
 // loops keep their compile-time bounds and skip what lies outside; codes are paired by the
 // block-local index, which need not start a row on a pair).
@@ -221,7 +240,7 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
                                              uint32_t* __restrict__ pptr, T* __restrict__ uptr, const Hist& h,
                                              const Hooks hk, T xfix, uint32_t e0 = B0, uint32_t e1 = B1,
                                              uint32_t e2 = B2) {
-  PassRes r = {0, 0, 0, 0, 0, 0, 0};
+  PassRes r = {0, 0, 0, 0, 0, 0, 0, 0};
   Run run(R);
   const int n0 = EDGE ? (int)e0 : B0, n1 = EDGE ? (int)e1 : B1;
   uint32_t lowe = 0;  // EDGE: pending low half of a code pair
@@ -319,10 +338,10 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
               if (NDIM == 2) return FT<T>::add_v(FT<T>::sub_v(a, ac), c);
               return c;
             },
-            HOOK && k == hk.kp, hk.bitp, r.dup);
+            HOOK && k == hk.kp, hk.bitp, r.dup, r.mm);
         T xr;
-        const uint32_t code =
-            quantize<T, ABFT, HOOK, CMP>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr, r.dup, hk.texp);
+        const uint32_t code = quantize<T, ABFT, HOOK, CMP>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr,
+                                                           r.dup, r.mm, hk.texp);
         if (EDGE) {
           if (k & 1) pptr[(uint64_t)(k >> 1) * 32] = lowe | (code << 16);
           else lowe = code;
@@ -330,10 +349,8 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
           if (l & 1) prow[(l >> 1) * 32] = lowc | (code << 16);
           else lowc = code;
         }
-        if (!code) {
-          urow[l * 32] = v;
-          ++r.nun;
-        }
+        if (!code) urow[l * 32] = v;
+        r.nun += (code == 0u);
         if (ABFT) {
           r.sq += code;
           mad_wide(r.isq, code, k + 1);
@@ -801,6 +818,15 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
                                                                             cptr, uptr, h, hk, T(0), e)
                      : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, CMP, false, EDGE>(reg, blk, si, sj, vec2, cT, plane, K,
                                                                              g.R, cptr, uptr, h, hk, T(0), e);
+  if (ABFT && r.mm) {
+    // a duplicate evaluation disagreed in the unvoted walk: take the block's codes back out of
+    // the histogram and walk it again with per-point voting (the same result as voting at
+    // once; at least one correction counted)
+    withdraw(w, g, b, Pb, h);
+    r = fast_dispatch<T, NDIM, B0, B1, B2, ABFT, CMP, true, EDGE>(reg, blk, si, sj, vec2, cT, plane, K, g.R, cptr, uptr, h,
+                                                             hk, T(0), e);
+    r.dup = r.dup ? r.dup : 1u;
+  }
   uint8_t flag = 0;
   if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
     if (!EDGE) x = block_box(g, b);

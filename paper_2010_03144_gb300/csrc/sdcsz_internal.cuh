@@ -246,6 +246,8 @@ template <> struct FT<float> {
   __device__ static __forceinline__ int trunc_i(float v) { return __float2int_rz(v); }
   __device__ static __forceinline__ float absv(float v) { return fabsf(v); }
   __device__ static __forceinline__ bool same(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+  // zero iff a and b have the same bits
+  __device__ static __forceinline__ uint32_t diffbits(float a, float b) { return __float_as_uint(a) ^ __float_as_uint(b); }
   __device__ static __forceinline__ float flip(float v, uint32_t bit) { return __uint_as_float(__float_as_uint(v) ^ (1u << (bit & 31))); }
   __device__ static __forceinline__ uint32_t lo(float v) { return __float_as_uint(v); }
   __device__ static __forceinline__ uint32_t hi(float) { return 0u; }
@@ -283,6 +285,10 @@ template <> struct FT<double> {
   __device__ static __forceinline__ int trunc_i(double v) { return __double2int_rz(v); }
   __device__ static __forceinline__ double absv(double v) { return fabs(v); }
   __device__ static __forceinline__ bool same(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+  __device__ static __forceinline__ uint32_t diffbits(double a, double b) {
+    const unsigned long long d = (unsigned long long)(__double_as_longlong(a) ^ __double_as_longlong(b));
+    return (uint32_t)d | (uint32_t)(d >> 32);
+  }
   __device__ static __forceinline__ double flip(double v, uint32_t bit) {
     return __longlong_as_double(__double_as_longlong(v) ^ (1ll << (bit & 63)));
   }
