@@ -53,28 +53,36 @@ __device__ __forceinline__ float denom(uint32_t P, uint32_t ed) {
   return __double2float_rn(__ddiv_rn(__dmul_rn((double)P, __dsub_rn(__dmul_rn((double)ed, (double)ed), 1.0)), 12.0));
 }
 
-// Coefficients from the block sums (slopes of the active axes, then the intercept).
+// The same denominator for a block shape known at compile time. P (e^2 - 1) / 12 is an integer
+// below 2^24 for every compile-time shape (cubes 4..16, squares 8..16), so the double
+// arithmetic is exact and the value equals denom's bit for bit.
+__host__ __device__ constexpr float denom_c(uint32_t P, uint32_t ed) {
+  return (float)((double)P * ((double)ed * (double)ed - 1.0) / 12.0);
+}
+
+// Coefficients from the block sums (slopes of the active axes, then the intercept); D[a] is
+// the denominator of axis a (denom of its extent), used only where the extent exceeds 1.
 template <int NDIM>
-__device__ __forceinline__ bool coefficients(uint32_t P, const uint32_t e[3], float S0, float Si, float Sj, float Sl,
-                                             float c0, float c1, float c2, float cf[4]) {
+__device__ __forceinline__ bool coefficients(uint32_t P, const uint32_t e[3], const float D[3], float S0, float Si,
+                                             float Sj, float Sl, float c0, float c1, float c2, float cf[4]) {
   const float mean = __fdiv_rn(S0, (float)P);
   if (NDIM == 3) {
-    cf[0] = e[0] > 1 ? __fdiv_rn(Si, denom(P, e[0])) : 0.0f;
-    cf[1] = e[1] > 1 ? __fdiv_rn(Sj, denom(P, e[1])) : 0.0f;
-    cf[2] = e[2] > 1 ? __fdiv_rn(Sl, denom(P, e[2])) : 0.0f;
+    cf[0] = e[0] > 1 ? __fdiv_rn(Si, D[0]) : 0.0f;
+    cf[1] = e[1] > 1 ? __fdiv_rn(Sj, D[1]) : 0.0f;
+    cf[2] = e[2] > 1 ? __fdiv_rn(Sl, D[2]) : 0.0f;
     float acc = __fmul_rn(cf[0], c0);
     acc = __fadd_rn(acc, __fmul_rn(cf[1], c1));
     acc = __fadd_rn(acc, __fmul_rn(cf[2], c2));
     cf[3] = __fsub_rn(mean, acc);
   } else if (NDIM == 2) {
-    cf[0] = e[1] > 1 ? __fdiv_rn(Sj, denom(P, e[1])) : 0.0f;
-    cf[1] = e[2] > 1 ? __fdiv_rn(Sl, denom(P, e[2])) : 0.0f;
+    cf[0] = e[1] > 1 ? __fdiv_rn(Sj, D[1]) : 0.0f;
+    cf[1] = e[2] > 1 ? __fdiv_rn(Sl, D[2]) : 0.0f;
     float acc = __fmul_rn(cf[0], c1);
     acc = __fadd_rn(acc, __fmul_rn(cf[1], c2));
     cf[2] = __fsub_rn(mean, acc);
     cf[3] = 0.0f;
   } else {
-    cf[0] = e[2] > 1 ? __fdiv_rn(Sl, denom(P, e[2])) : 0.0f;
+    cf[0] = e[2] > 1 ? __fdiv_rn(Sl, D[2]) : 0.0f;
     cf[1] = __fsub_rn(mean, __fmul_rn(cf[0], c2));
     cf[2] = cf[3] = 0.0f;
   }
@@ -195,7 +203,9 @@ __device__ __forceinline__ void prep_generic(const T* __restrict__ field, const 
       }
     }
     float cf[4];
-    const bool finite = coefficients<NDIM>(x.P, x.e, S0, Si, Sj, Sl, c0, c1, c2, cf);
+    const float D[3] = {x.e[0] > 1 ? denom(x.P, x.e[0]) : 0.0f, x.e[1] > 1 ? denom(x.P, x.e[1]) : 0.0f,
+                        x.e[2] > 1 ? denom(x.P, x.e[2]) : 0.0f};
+    const bool finite = coefficients<NDIM>(x.P, x.e, D, S0, Si, Sj, Sl, c0, c1, c2, cf);
     if (g.abft) {
       w.sum_in[b] = sum;
       w.isum_in[b] = isum;
@@ -371,7 +381,9 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
     }
     const uint32_t e[3] = {B0, B1, B2};
     float cf[4];
-    const bool finite = coefficients<NDIM>(P, e, S0, Si, Sj, Sl, c0, c1, c2, cf);
+    constexpr float D0 = denom_c(P, B0), D1 = denom_c(P, B1), D2 = denom_c(P, B2);
+    const float D[3] = {D0, D1, D2};
+    const bool finite = coefficients<NDIM>(P, e, D, S0, Si, Sj, Sl, c0, c1, c2, cf);
     if (g.abft) {
       w.sum_in[b] = sum;
       w.isum_in[b] = isum;
