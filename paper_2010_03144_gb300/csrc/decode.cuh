@@ -157,6 +157,8 @@ struct FastReader {
     advance(len);
     return sym;
   }
+  // the next 32 bits, not consumed
+  __device__ __forceinline__ uint32_t peek() const { return __funnelshift_l(w1, w0, pos); }
   // the next n (1..32) raw bits
   __device__ __forceinline__ uint32_t bits(uint32_t n) {
     const uint32_t peek = __funnelshift_l(w1, w0, pos);
@@ -255,6 +257,9 @@ struct Tables {
   const uint16_t* syms;
   uint32_t n_live;
   const uint2* lut2;  // pair table (fast decoder only)
+  // fast decoder only: a row of central codes (prediction within half a bin) is the central
+  // codeword repeated, rpat, rbits bits long; rbits = 0 when that does not fit a word
+  uint32_t rbits, rpat;
 };
 
 // Pair table: entry p holds lut[p] and, when that code is shorter than the window and the
@@ -413,10 +418,18 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       T c = T(0), ac = T(0), bc = T(0), abc = T(0);
       const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
       int qp = 0;  // second symbol of the pair decoded at even l
+      // a row of central codes (the common case of a smooth field) in one comparison
+      bool crow = false;
+      if (tb.rbits && (br.peek() >> (32 - tb.rbits)) == tb.rpat) {
+        crow = true;
+        br.advance(tb.rbits);
+      }
 #pragma unroll
       for (int l = 0; l < B2; ++l) {
         int q;
-        if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
+        if (crow) {
+          q = R;
+        } else if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
           if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp, CMP);
           else q = (CMP && qp == kDefer) ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : qp;
         } else {
@@ -913,12 +926,27 @@ __device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, u
   __shared__ Smem sm;
   uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
   const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
+  __shared__ uint32_t s_central;  // central codeword: bits << 8 | length (0: none in the window)
+  if (threadIdx.x == 0) s_central = 0;
   if (!cta_tables(s, h, sm, lut, syms, st)) return;
   uint2* lut2 = reinterpret_cast<uint2*>(smem + (4u << kLutBits));
   __syncthreads();
   pair_table(lut2, lut, CMP);
+  for (uint32_t e = threadIdx.x; e < (1u << kLutBits); e += blockDim.x) {  // every writer writes the same
+    const uint32_t v = lut[e], l = v & 0xffu;
+    if (l && (v >> 8) == h.g.R) s_central = ((e >> (kLutBits - l)) << 8) | l;
+  }
   __syncthreads();
-  const Tables tb = {lut, &sm.cn, syms, h.n_live, lut2};
+  uint32_t rbits = 0, rpat = 0;
+  {
+    const uint32_t lc = s_central & 0xffu, cc = s_central >> 8;
+    if (lc && B2 * lc <= 32u) {
+      rbits = B2 * lc;
+#pragma unroll
+      for (int l = 0; l < B2; ++l) rpat = (lc * (B2 - 1 - l) < 32u) ? (rpat | (cc << (lc * (B2 - 1 - l)))) : rpat;
+    }
+  }
+  const Tables tb = {lut, &sm.cn, syms, h.n_live, lut2, rbits, rpat};
   const uint8_t* lim = s + nbytes;
   T* plane = reinterpret_cast<T*>(smem + (12u << kLutBits)) + threadIdx.x;
   Walker<T, NDIM> wk;  // for the few blocks that take the generic decoder

@@ -88,10 +88,11 @@ struct Extra {
 // One pass over a block's codes: the Huffman bits into `slot` (stream byte order, the last
 // word zero padded), the code checksums (ABFT), the unpredictable count and the first
 // kPosKept unpredictable positions. With FIX, code kfix reads as vfix. CMP: compact encoding.
+// R is the central code (prediction within half a bin).
 template <bool ABFT, bool FIX, bool CMP, typename T>
 __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, uint32_t P, uint32_t* __restrict__ slot,
-                                               const Codebook& cb, uint32_t cw0, uint32_t kfix, uint32_t vfix,
-                                               const Extra<T>& ex) {
+                                               const Codebook& cb, uint32_t cw0, uint32_t R, uint32_t kfix,
+                                               uint32_t vfix, const Extra<T>& ex) {
   EncRes e;
   e.bits = 0;
   e.nun = 0;
@@ -182,12 +183,37 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
       }
     }
   };
+  // Eight central codes in a row (the common case of a smooth field) go in with one append of
+  // the central codeword repeated eight times, their checksums in closed form: sum_q gains 8 R
+  // and isum_q gains R (8k + 36) for codes k .. k+7. The bits are those of eight single appends
+  // (one flush suffices: fewer than 32 bits were pending and the run adds at most 32).
+  const uint32_t cwc = cb(R), lc = cwc & 31u, lrun = 8 * lc;
+  const bool runs = !FIX && lc != 0 && lc <= 4;
+  uint32_t rep = 0;
+  if (runs)
+#pragma unroll
+    for (int t = 0; t < 8; ++t) rep = (rep << lc) | (cwc >> 5);
+  const uint32_t pc = R | (R << 16);  // a pair word of two central codes
   // code pairs loaded four at a time ahead of their use
   const uint32_t P2 = P >> 1;
   for (uint32_t k2 = 0; k2 < P2; k2 += 4) {
     uint32_t wq[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) wq[q] = (k2 + q < P2) ? pp[32 * (uint64_t)(k2 + q)] : 0u;
+    if (runs && k2 + 3 < P2 && ((wq[0] ^ pc) | (wq[1] ^ pc) | (wq[2] ^ pc) | (wq[3] ^ pc)) == 0u) {
+      acc = (acc << lrun) | rep;
+      nacc += lrun;
+      e.bits += lrun;
+      if (nacc >= 32) {
+        nacc -= 32;
+        slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+      }
+      if (ABFT) {
+        e.sq += 8 * R;
+        mad_wide(e.isq, R, 16 * k2 + 36);  // codes k = 2 k2 .. k + 7: 8 k + 36
+      }
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (k2 + q < P2) put2(wq[q] & 0xffffu, wq[q] >> 16, 2 * (k2 + q));
@@ -238,7 +264,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
       ex.up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
       ex.texp = bound_exponent<T>((T)st->eb);
     }
-    EncRes e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, 0u, 0u, ex);
+    EncRes e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, g.R, 0u, 0u, ex);
     uint32_t kfix = 0xffffffffu, vfix = 0;
     bool bad = false;
     if (ABFT && (e.sq != w.sum_q[b] || e.isq != w.isum_q[b])) {
@@ -251,7 +277,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
         if (nv >= 0 && nv < (long long)g.bins) {
           kfix = (uint32_t)m;
           vfix = (uint32_t)nv;
-          e = encode_codes<ABFT, true, CMP, T>(pp, P, slot, cb, cw0, kfix, vfix, ex);  // the repaired block
+          e = encode_codes<ABFT, true, CMP, T>(pp, P, slot, cb, cw0, g.R, kfix, vfix, ex);  // the repaired block
           fixed = true;
         }
       }
