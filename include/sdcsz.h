@@ -303,6 +303,13 @@ unsigned long long sdcsz_kernel_launches(void);
  *  SDCSZ_SITE_PRED   block, index = point; the first evaluation of the prediction.
  *  SDCSZ_SITE_RECON  block, index = point; the first evaluation of the reconstruction.
  *  SDCSZ_SITE_DECOMP block, index = point; the reconstructed value in the first decompression.
+ *  SDCSZ_SITE_REWALK block (index and bit unused); changes no value. A block of the
+ *                    compile-time shapes walked without per-point voting is handled as if its
+ *                    duplicate evaluations had disagreed: its codes are withdrawn from the
+ *                    histogram and it is walked again with voting, which counts one
+ *                    dup_mismatch_corrected. No effect with ABFT off, in blocks that also
+ *                    have a PRED or RECON record (those are walked with voting from the
+ *                    start) and in blocks of other shapes. The output equals the clean run's.
  * d_flips is a device array of n records sorted by (block, site, index).
  */
 #define SDCSZ_SITE_INPUT 1
@@ -311,6 +318,7 @@ unsigned long long sdcsz_kernel_launches(void);
 #define SDCSZ_SITE_PRED 4
 #define SDCSZ_SITE_RECON 5
 #define SDCSZ_SITE_DECOMP 6
+#define SDCSZ_SITE_REWALK 7
 typedef struct {
   uint32_t site;
   uint32_t bit;

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsdcsz.so")
 
 OK, EINVAL, ECAPACITY, EFORMAT, ESDC, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
-SITES = {"input": 1, "code": 2, "coef": 3, "pred": 4, "recon": 5, "decomp": 6}
+SITES = {"input": 1, "code": 2, "coef": 3, "pred": 4, "recon": 5, "decomp": 6, "rewalk": 7}
 PREDICTORS = {"auto": 0, "lorenzo": 1, "regression": 2}
 ENCODINGS = {"raw": 0, "compact": 1}
 BLOCK_OK, BLOCK_CORRECTED, BLOCK_SDC, BLOCK_BAD = 0, 1, 2, 3

@@ -154,6 +154,7 @@ __device__ __forceinline__ T dup_pred(F1 prim, F2 dupf, bool hit_p, uint32_t bit
 
 struct Hooks {
   uint32_t kp, bitp, kr, bitr, kfix;
+  bool rewalk;  // test record: take the re-walk of a disagreeing block without a disagreement
   int texp;  // truncation exponent of unpredictable values (kNoTrunc: raw encoding)
 };
 
@@ -506,6 +507,7 @@ __device__ __forceinline__ void load_coefs(const Geo& g, const Ws& w, uint64_t b
   hk.texp = K.texp;
   hk.kp = hk.kr = hk.kfix = kNone;
   hk.bitp = hk.bitr = 0;
+  hk.rewalk = false;
   if (g.enc) {
     if (nflips) {
       uint32_t lo = 0, hi = nflips;
@@ -543,6 +545,7 @@ __device__ __forceinline__ void load_coefs(const Geo& g, const Ws& w, uint64_t b
       hk.kr = (uint32_t)min(f.index, (uint64_t)kNone - 1);
       hk.bitr = f.bit;
     }
+    if (f.site == SDCSZ_SITE_REWALK) hk.rewalk = true;
   }
 }
 
@@ -818,7 +821,7 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
                                                                             cptr, uptr, h, hk, T(0), e)
                      : fast_dispatch<T, NDIM, B0, B1, B2, ABFT, CMP, false, EDGE>(reg, blk, si, sj, vec2, cT, plane, K,
                                                                              g.R, cptr, uptr, h, hk, T(0), e);
-  if (ABFT && r.mm) {
+  if (ABFT && (r.mm || (hk.rewalk && !hooked))) {
     // a duplicate evaluation disagreed in the unvoted walk: take the block's codes back out of
     // the histogram and walk it again with per-point voting (the same result as voting at
     // once; at least one correction counted)
