@@ -44,12 +44,12 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 553699100, "src": "6cfdb4f3d876"},
-    ("384cube", "prep"): {"bytes": 233591808, "src": "6cfdb4f3d876"},
-    ("512cube", "predict"): {"bytes": 936414170, "src": "beb3c158bd5a"},
-    ("384cube", "predict"): {"bytes": 395049728, "src": "beb3c158bd5a"},
-    ("512cube", "decode"): {"bytes": 475409067, "src": "9e984b91206b"},
-    ("384cube", "decode"): {"bytes": 200563200, "src": "9e984b91206b"},
+    ("512cube", "prep"): {"bytes": 555866068, "src": "2c49ff0da773"},
+    ("384cube", "prep"): {"bytes": 234505998, "src": "2c49ff0da773"},
+    ("512cube", "predict"): {"bytes": 941574529, "src": "30f4f57490d8"},
+    ("384cube", "predict"): {"bytes": 397226754, "src": "30f4f57490d8"},
+    ("512cube", "decode"): {"bytes": 482648448, "src": "7a174b65ea5e"},
+    ("384cube", "decode"): {"bytes": 203617314, "src": "7a174b65ea5e"},
 }
 
 

@@ -194,29 +194,40 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
 #pragma unroll
     for (int t = 0; t < 8; ++t) rep = (rep << lc) | (cwc >> 5);
   const uint32_t pc = R | (R << 16);  // a pair word of two central codes
-  // code pairs loaded four at a time ahead of their use
+  // code pairs eight at a time, the next eight loaded while these are encoded
   const uint32_t P2 = P >> 1;
-  for (uint32_t k2 = 0; k2 < P2; k2 += 4) {
-    uint32_t wq[4];
+  uint32_t wq[8], wn[8];
+  auto load8 = [&](uint32_t base, uint32_t (&w)[8]) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) wq[q] = (k2 + q < P2) ? pp[32 * (uint64_t)(k2 + q)] : 0u;
-    if (runs && k2 + 3 < P2 && ((wq[0] ^ pc) | (wq[1] ^ pc) | (wq[2] ^ pc) | (wq[3] ^ pc)) == 0u) {
-      acc = (acc << lrun) | rep;
-      nacc += lrun;
-      e.bits += lrun;
-      if (nacc >= 32) {
-        nacc -= 32;
-        slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+    for (int q = 0; q < 8; ++q) w[q] = (base + q < P2) ? pp[32 * (uint64_t)(base + q)] : 0u;
+  };
+  load8(0, wq);
+  for (uint32_t k8 = 0; k8 < P2; k8 += 8) {
+    if (k8 + 8 < P2) load8(k8 + 8, wn);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t k2 = k8 + 4 * h;
+      if (runs && k2 + 3 < P2 &&
+          ((wq[4 * h] ^ pc) | (wq[4 * h + 1] ^ pc) | (wq[4 * h + 2] ^ pc) | (wq[4 * h + 3] ^ pc)) == 0u) {
+        acc = (acc << lrun) | rep;
+        nacc += lrun;
+        e.bits += lrun;
+        if (nacc >= 32) {
+          nacc -= 32;
+          slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+        }
+        if (ABFT) {
+          e.sq += 8 * R;
+          mad_wide(e.isq, R, 16 * k2 + 36);  // codes k = 2 k2 .. k + 7: 8 k + 36
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (k2 + q < P2) put2(wq[4 * h + q] & 0xffffu, wq[4 * h + q] >> 16, 2 * (k2 + q));
       }
-      if (ABFT) {
-        e.sq += 8 * R;
-        mad_wide(e.isq, R, 16 * k2 + 36);  // codes k = 2 k2 .. k + 7: 8 k + 36
-      }
-      continue;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (k2 + q < P2) put2(wq[q] & 0xffffu, wq[q] >> 16, 2 * (k2 + q));
+    for (int q = 0; q < 8; ++q) wq[q] = wn[q];
   }
   if (P & 1) put(pp[32 * (uint64_t)P2] & 0xffffu, P - 1);
   if (nacc) slot[wi] = __byte_perm((uint32_t)(acc << (32 - nacc)), 0, 0x0123);
