@@ -162,7 +162,7 @@ WsPlan plan_ws(const Geo& g) {
   w.coefT = take(4 * s * nb);
   w.hist = take(8 * 65536);
   w.codebook = take(4 * 65536);
-  w.lb = take(sizeof(LookBack) * std::max<size_t>(ngroups, 1));
+  w.gt = take(8 * std::max<size_t>(group_total_words(ngroups), 1));
   w.sort_keys = take(8 * 65536);
   w.node_w = take(8 * 65536);
   w.node_parent = take(4 * 2 * 65536 + 2 * 65536);
@@ -207,7 +207,7 @@ Ws bind_ws(void* base, const WsPlan& p) {
   w.coefT = b + p.coefT;
   w.hist = reinterpret_cast<unsigned long long*>(b + p.hist);
   w.codebook = reinterpret_cast<uint32_t*>(b + p.codebook);
-  w.lb = reinterpret_cast<LookBack*>(b + p.lb);
+  w.gt = reinterpret_cast<unsigned long long*>(b + p.gt);
   w.sort_keys = reinterpret_cast<unsigned long long*>(b + p.sort_keys);
   w.node_w = reinterpret_cast<unsigned long long*>(b + p.node_w);
   w.node_parent = reinterpret_cast<uint32_t*>(b + p.node_parent);
@@ -317,7 +317,7 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
   if (cudaMemsetAsync(w.st, 0, sizeof(State), L.stream) != cudaSuccess) return SDCSZ_ECUDA;
   if (cudaMemsetAsync(w.hist, 0, 8 * (size_t)g.bins, L.stream) != cudaSuccess) return SDCSZ_ECUDA;
   const size_t ngroups = (g.nb + kGroup - 1) / kGroup;
-  if (ngroups && cudaMemsetAsync(w.lb, 0, sizeof(LookBack) * ngroups, L.stream) != cudaSuccess) return SDCSZ_ECUDA;
+  if (ngroups && cudaMemsetAsync(w.gt, 0, 8 * group_total_words(ngroups), L.stream) != cudaSuccess) return SDCSZ_ECUDA;
   tr.mark();
   {
     NvtxRange r("sdcsz prep (range, checksums, regression, estimates)");
@@ -748,14 +748,14 @@ namespace {
 __global__ void k_batch_reset(const Job* __restrict__ jobs, unsigned long long* heads, uint32_t nheads) {
   const Job& jb = jobs[blockIdx.x];
   const uint64_t ngroups = (jb.g.nb + kGroup - 1) / kGroup;
-  const uint64_t nst = sizeof(State) / 8, nh = jb.g.bins, nl = ngroups * (sizeof(LookBack) / 8);
+  const uint64_t nst = sizeof(State) / 8, nh = jb.g.bins, nl = group_total_words(ngroups);
   unsigned long long* st = reinterpret_cast<unsigned long long*>(jb.w.st);
-  unsigned long long* lb = reinterpret_cast<unsigned long long*>(jb.w.lb);
+  unsigned long long* gt = jb.w.gt;
   for (uint64_t q = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; q < nst + nh + nl;
        q += (uint64_t)gridDim.y * blockDim.x) {
     if (q < nst) st[q] = 0ull;
     else if (q < nst + nh) jb.w.hist[q - nst] = 0ull;
-    else lb[q - nst - nh] = 0ull;
+    else gt[q - nst - nh] = 0ull;
   }
   if (blockIdx.x == 0 && blockIdx.y == 0)
     for (uint32_t q = threadIdx.x; q < nheads; q += blockDim.x) heads[q] = 0ull;

@@ -20,7 +20,7 @@ struct NvtxRange {
 
 // Byte offsets of the regions of a compression workspace.
 struct WsPlan {
-  size_t state, sum_in, isum_in, sum_q, isum_q, sum_dc, coef, est, pflag, flags, coefT, hist, codebook, lb, sort_keys,
+  size_t state, sum_in, isum_in, sum_q, isum_q, sum_dc, coef, est, pflag, flags, coefT, hist, codebook, gt, sort_keys,
       node_w, node_parent, codes, ustage, etmp, total;
   // lossless stage
   size_t raw, raw_cap, llw, llst, llsz, lltop, lloff, llhist, llcum;

@@ -9,11 +9,12 @@
 // code is located and repaired and the block is encoded again. Then the block's unpredictable
 // values move to the front of its staging slot, and the per-block entries that sit at fixed
 // places in the stream (payload size, unpredictable count, sum_dc, regression bitmap) are
-// written.
+// written; each warp adds its 32 blocks' payload bytes, unpredictables and regression blocks
+// to its group's totals (one 64-bit atomic).
 //
-// K4b, one CTA per random-access group of 256 blocks: a CTA scan plus a single-pass decoupled
-// look-back across groups (group ids from a ticket in launch order, every wait bounded) gives
-// each block its payload, unpredictable-value and coefficient offsets; each thread then copies
+// K4b, one CTA per random-access group of 256 blocks: a CTA scan plus the sum of the earlier
+// groups' totals (no CTA waits on another) gives each block its payload, unpredictable-value
+// and coefficient offsets; each thread then copies
 // its block's payload (the slot holds it in stream byte order: whole aligned words are stored
 // with a funnel shift, the partial first and last words byte by byte), its unpredictable values
 // and its coefficients. The group's table entry and, for the last group, the header totals are
@@ -26,15 +27,15 @@ namespace sdcsz {
 
 namespace {
 
-// look-back aggregate of a group: bytes (25 bits: 256 blocks of at most 65535), unpredictable
-// points (21 bits: 256 blocks of at most 4096), regression blocks (16 bits), and a flag
-constexpr unsigned long long kFlagAgg = 1ull, kMaskBytes = (1ull << 25) - 1, kMaskUn = (1ull << 21) - 1;
+// totals of a group (group_total_words): bytes (25 bits: 256 blocks of at most 65535), unpredictable
+// points (21 bits: 256 blocks of at most 4096), regression blocks (16 bits)
+constexpr unsigned long long kMaskBytes = (1ull << 25) - 1, kMaskUn = (1ull << 21) - 1;
 constexpr uint32_t kCbWindow = 2048;  // codebook entries around the centre kept in shared memory
 constexpr uint32_t kPosKept = 4;      // unpredictable positions remembered in registers per block
 
-__device__ __forceinline__ unsigned long long pack_agg(unsigned long long bytes, unsigned long long un,
+__device__ __forceinline__ unsigned long long pack_tot(unsigned long long bytes, unsigned long long un,
                                                        unsigned long long rg) {
-  return (kFlagAgg << 62) | (rg << 46) | (un << 25) | bytes;
+  return (rg << 46) | (un << 25) | bytes;
 }
 
 __device__ __forceinline__ void mad_wide(unsigned long long& acc, uint32_t a, uint32_t b) {
@@ -258,6 +259,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
   const bool active = b < g.nb;
   bool reg = false;
   unsigned long long nun_enc = 0;
+  uint32_t nbytes = 0;
   if (active) {
     Codebook cb;
     cb.lo = cb_lo(g);
@@ -319,19 +321,27 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
         }
       }
     }
-    *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * b) = (uint16_t)((e.bits + 7u) >> 3);
+    nbytes = (uint16_t)((e.bits + 7u) >> 3);
+    *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * b) = (uint16_t)nbytes;
     *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * b) = (uint16_t)e.nun;
     nun_enc = e.nun;
     if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * b) = w.sum_dc[b];
     // a block whose codes could not be repaired is reported in the header status word
     if (bad) atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
   }
-  // regression bitmap word of this warp's 32 blocks; the warp's unpredictable count
+  // regression bitmap word of this warp's 32 blocks; the warp's unpredictable count; the
+  // warp's share of its group's totals (the 32 blocks lie in one group of kGroup)
   const unsigned int ballot = __ballot_sync(0xffffffffu, active && reg);
   unsigned long long wun = warp_sum(nun_enc);
+  const unsigned long long wtot = warp_sum(active ? pack_tot(nbytes, nun_enc, reg ? 1u : 0u) : 0ull);
   if (lane == 0 && b < g.nb) {
     *reinterpret_cast<uint32_t*>(out + L.bitmap + 4 * (b >> 5)) = ballot;
     if (wun) atomicAdd(&st->n_unpred_enc, wun);
+    const uint64_t gid = b / kGroup, ng = (g.nb + kGroup - 1) / kGroup;
+    atomicAdd(&w.gt[gid], wtot);
+    unsigned long long* sg = w.gt + ng + 2 * (gid / kSuper);
+    atomicAdd(&sg[0], wtot & kMaskBytes);
+    atomicAdd(&sg[1], (((wtot >> 25) & kMaskUn) << 17) | (wtot >> 46));
   }
 }
 
@@ -349,6 +359,7 @@ template <typename T>
 __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
                                                uint64_t gid) {
   __shared__ unsigned long long s_wt[8][3];
+  __shared__ unsigned long long s_pre[8][3];
   __shared__ unsigned long long s_excl[3];
   __shared__ unsigned long long s_tot[3];
   State* st = w.st;
@@ -380,76 +391,39 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
     }
   if (lane == 31)
     for (int q = 0; q < 3; ++q) s_wt[wid][q] = inc[q];
+  // the group's exclusive prefix: the totals of the earlier super-groups and of the earlier
+  // groups of its own super-group (summed by K4a, complete when this kernel starts), read
+  // straight from memory without waiting on other CTAs
+  unsigned long long pre[3] = {0, 0, 0};
+  const uint64_t s0 = gid / kSuper;
+  for (uint64_t p = tid; p < s0; p += blockDim.x) {
+    const unsigned long long* sg = w.gt + ngroups + 2 * p;
+    pre[0] += sg[0];
+    pre[1] += sg[1] >> 17;
+    pre[2] += sg[1] & 0x1ffffull;
+  }
+  for (uint64_t p = s0 * kSuper + tid; p < gid; p += blockDim.x) {
+    const unsigned long long t = w.gt[p];
+    pre[0] += t & kMaskBytes;
+    pre[1] += (t >> 25) & kMaskUn;
+    pre[2] += t >> 46;
+  }
+  for (int q = 0; q < 3; ++q) pre[q] = warp_sum(pre[q]);
+  if (lane == 0)
+    for (int q = 0; q < 3; ++q) s_pre[wid][q] = pre[q];
   __syncthreads();
-  if (wid == 0) {
-    // warp totals -> exclusive prefixes (lane 0), then a warp-wide decoupled look-back
-    unsigned long long run[3] = {0, 0, 0};
-    if (lane == 0) {
-      for (int q2 = 0; q2 < 8; ++q2)
-        for (int q = 0; q < 3; ++q) {
-          const unsigned long long t = s_wt[q2][q];
-          s_wt[q2][q] = run[q];
-          run[q] += t;
-        }
-      for (int q = 0; q < 3; ++q) s_tot[q] = run[q];
-    }
-    for (int q = 0; q < 3; ++q) run[q] = __shfl_sync(0xffffffffu, run[q], 0);
-    LookBack* me = &w.lb[gid];
-    unsigned long long excl[3] = {0, 0, 0};
-    if (gid > 0 && lane == 0) {
-      *(volatile unsigned long long*)&me->agg = pack_agg(run[0], run[1], run[2]);
-      __threadfence();
-    }
-    // lane l looks at predecessor gid-1-l-32r; the nearest one with an inclusive prefix ends it
-    bool finished = gid == 0;
-    for (int64_t base = (int64_t)gid - 1; !finished; base -= 32) {
-      const int64_t p = base - (int64_t)lane;
-      unsigned long long va[3] = {0, 0, 0};
-      bool incl = p < 0, ready = p < 0;
-      uint32_t spins = 0;
-      while (true) {
-        if (!ready) {
-          const LookBack* pr = &w.lb[p];
-          if (*(volatile const unsigned int*)&pr->incl_flag) {
-            __threadfence();
-            va[0] = *(volatile const unsigned long long*)&pr->incl[0];
-            va[1] = *(volatile const unsigned long long*)&pr->incl[1];
-            va[2] = *(volatile const unsigned long long*)&pr->incl[2];
-            incl = ready = true;
-          } else {
-            const unsigned long long a = *(volatile const unsigned long long*)&pr->agg;
-            if (a >> 62) {
-              va[0] = a & kMaskBytes;
-              va[1] = (a >> 25) & kMaskUn;
-              va[2] = (a >> 46) & 0xffffull;
-              ready = true;
-            }
-          }
-        }
-        if (__all_sync(0xffffffffu, ready)) break;
-        if (++spins > kSpinLimit) {
-          if (lane == 0) atomicOr(&st->error, ERR_TIMEOUT);
-          ready = incl = true;  // give up: the stream is then reported as failed
-        }
-        __nanosleep(32);
-      }
-      // lanes up to the nearest inclusive prefix contribute
-      const unsigned int im = __ballot_sync(0xffffffffu, incl);
-      const uint32_t stop = im ? (uint32_t)(__ffs(im) - 1) : 31u;
+  if (tid == 0) {
+    unsigned long long run[3] = {0, 0, 0}, excl[3] = {0, 0, 0};
+    for (int q2 = 0; q2 < 8; ++q2)
       for (int q = 0; q < 3; ++q) {
-        unsigned long long c = lane <= stop ? va[q] : 0ull;
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        excl[q] += c;
+        const unsigned long long t = s_wt[q2][q];
+        s_wt[q2][q] = run[q];
+        run[q] += t;
+        excl[q] += s_pre[q2][q];
       }
-      finished = im != 0;
-    }
-    if (lane == 0) {
-      me->incl[0] = excl[0] + run[0];
-      me->incl[1] = excl[1] + run[1];
-      me->incl[2] = excl[2] + run[2];
-      __threadfence();
-      *(volatile unsigned int*)&me->incl_flag = 1u;
-      for (int q = 0; q < 3; ++q) s_excl[q] = excl[q];
+    for (int q = 0; q < 3; ++q) {
+      s_tot[q] = run[q];
+      s_excl[q] = excl[q];
     }
   }
   __syncthreads();
@@ -525,11 +499,8 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_encode_assemble(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
-  __shared__ uint32_t s_gid;
   if (cta_failed(w.st)) return;
-  if (threadIdx.x == 0) s_gid = atomicAdd(&w.st->ticket, 1u);
-  __syncthreads();
-  assemble_group<T>(g, w, out, cap, s_gid);
+  assemble_group<T>(g, w, out, cap, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- batches
@@ -550,8 +521,6 @@ __global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
       NoOp());
 }
 
-// A job's groups are pulled in increasing order, so each look-back only waits for groups
-// already taken by running CTAs.
 template <typename T>
 __global__ void __launch_bounds__(256) k_encode_assemble_batch(BatchArgs a) {
   __shared__ Job s_job;

@@ -74,13 +74,15 @@ __device__ __forceinline__ uint64_t cta_pull(unsigned long long* q) {
   return s_item_q;
 }
 
-// Decoupled look-back record of one group (encode kernel).
-struct LookBack {
-  unsigned long long agg;      // flag << 62 | reg << 43 | unpred << 22 | bytes
-  unsigned long long incl[3];  // inclusive prefix: payload bytes, unpredictables, regression blocks
-  unsigned int incl_flag;
-  unsigned int pad[7];
-};
+// Totals the per-block encoder sums for the stream assembly (64-bit atomics per warp): one word
+// per group of kGroup blocks, regression blocks << 46 | unpredictables << 25 | payload bytes
+// (at most 256, 2^20 and 256 * 65535 < 2^25: no field carries into the next), then two words
+// per super-group of kSuper groups: payload bytes, and unpredictables << 17 | regression
+// blocks (at most 2^28 and 2^16).
+constexpr uint64_t kSuper = 256;
+__host__ __device__ inline uint64_t group_total_words(uint64_t ngroups) {
+  return ngroups + 2 * ((ngroups + kSuper - 1) / kSuper);
+}
 
 // Pointers into a compress workspace.
 struct Ws {
@@ -93,7 +95,7 @@ struct Ws {
   void* coefT;         // dtype coefficients used by regression blocks (4 per block)
   unsigned long long* hist;
   uint32_t* codebook;  // code << 5 | length per symbol
-  LookBack* lb;
+  unsigned long long* gt;  // group and super-group totals (group_total_words)
   unsigned long long* sort_keys;  // codebook construction scratch
   unsigned long long* node_w;
   uint32_t* node_parent;
