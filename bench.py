@@ -44,12 +44,12 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 555866068, "src": "2c49ff0da773"},
-    ("384cube", "prep"): {"bytes": 234505998, "src": "2c49ff0da773"},
-    ("512cube", "predict"): {"bytes": 941574529, "src": "30f4f57490d8"},
-    ("384cube", "predict"): {"bytes": 397226754, "src": "30f4f57490d8"},
-    ("512cube", "decode"): {"bytes": 482648448, "src": "7a174b65ea5e"},
-    ("384cube", "decode"): {"bytes": 203617314, "src": "7a174b65ea5e"},
+    ("512cube", "prep"): {"bytes": 555498343, "src": "cd979e1ad757"},
+    ("384cube", "prep"): {"bytes": 234350863, "src": "cd979e1ad757"},
+    ("512cube", "predict"): {"bytes": 941265186, "src": "68a3a739879d"},
+    ("384cube", "predict"): {"bytes": 397096250, "src": "68a3a739879d"},
+    ("512cube", "decode"): {"bytes": 484662356, "src": "4e805f4d2728"},
+    ("384cube", "decode"): {"bytes": 204466931, "src": "4e805f4d2728"},
 }
 
 
