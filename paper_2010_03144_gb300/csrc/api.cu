@@ -727,7 +727,7 @@ extern "C" int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p
   if (plan_ws(g).total > kStaticScratchBytes) return SDCSZ_ECAPACITY;  // field too large for the array
   void* ws = static_scratch_address();
   if (!ws) return SDCSZ_ECUDA;
-  // the regions that must start at zero (state, histogram, look-back records) are cleared on
+  // the regions that must start at zero (state, histogram, group totals) are cleared on
   // the stream by every call; everything else is written before it is read
   return compress_impl(d_field, p, d_out, out_cap, out_bytes, ws, kStaticScratchBytes, report, stream, nullptr, 0);
 }
