@@ -37,6 +37,7 @@ CASES = [
     ((31, 33, 37), np.float32, 6, 1e-3, "rel", {"predictor": "regression"}),
     ((31, 33, 37), np.float32, 6, 1e-3, "rel", {"predictor": "lorenzo"}),
     ((31, 33, 37), np.float32, 6, 1e-5, "rel", {"bins": 1024}),
+    ((31, 33, 37), np.float32, 6, 1e-3, "rel", {"bins": 2}),  # central code next to code 0
     ((9, 10, 11), np.float32, 4, 0.01, "abs", {}),
 ]
 

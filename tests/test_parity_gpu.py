@@ -39,6 +39,12 @@ CASES = [
     ((31, 33, 37), np.float32, 6, 1e-3, "rel", {"predictor": "regression"}),
     ((31, 33, 37), np.float32, 6, 1e-3, "rel", {"bins": 16}),
     ((31, 33, 37), np.float32, 6, 1e-6, "rel", {"bins": 1024}),
+    # the smallest bin counts (central code R = 1 or 2 next to the unpredictable code 0) and
+    # coarse bounds where nearly every code is central (the encoder's and decoder's runs)
+    ((31, 33, 37), np.float32, 6, 1e-3, "rel", {"bins": 2}),
+    ((27, 30, 33), np.float64, 8, 1e-3, "rel", {"bins": 4}),
+    ((48, 50, 52), np.float32, 6, 1e-2, "rel", {}),
+    ((200, 300), np.float32, 8, 1e-2, "rel", {}),
 ]
 
 
