@@ -136,6 +136,13 @@ __device__ __forceinline__ void load_row(const T* __restrict__ row, bool vec2, T
   }
 }
 
+// A row of n <= B2 values (scalar loads; the rest of x is zero).
+template <typename T, int B2>
+__device__ __forceinline__ void load_row_n(const T* __restrict__ row, uint32_t n, T (&x)[B2]) {
+#pragma unroll
+  for (int l = 0; l < B2; ++l) x[l] = (uint32_t)l < n ? __ldg(row + l) : T(0);
+}
+
 __device__ __forceinline__ bool full_block(const Geo& g, uint64_t b, uint64_t c[3]) {
   c[2] = b % g.nbd[2];
   const uint64_t t = b / g.nbd[2];
@@ -249,22 +256,38 @@ __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
                : "memory");
 }
 
-// Fast path: full blocks of a compile-time shape B0 x B1 x B2 (leading 1 for 2D).
-template <typename T, int NDIM, int B0, int B1, int B2>
+// Fast path: full blocks of a compile-time shape B0 x B1 x B2 (leading 1 for 2D). EDGE: the
+// edge blocks of such a field (e-th of `count`), walked with the same code at their actual
+// extents (at most B0 x B1 x B2; the unrolled row skips what lies outside, and nothing outside
+// enters a sum).
+template <typename T, int NDIM, int B0, int B1, int B2, bool EDGE = false>
 __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo& g, const Ws& w, int vec2,
-                                          uint64_t cta, unsigned char* stage) {
+                                          uint64_t cta, unsigned char* stage, uint64_t count = 0) {
   State* st = w.st;
   const uint32_t tid = threadIdx.x;
-  const uint64_t b = cta * blockDim.x + tid;
+  const uint64_t tix = cta * blockDim.x + tid;
   const bool rel = g.eb_mode == 1;
   const bool est = g.predictor == 0;
   T mn = T(1.0 / 0.0), mx = T(-1.0 / 0.0);
   uint64_t c[3];
-  if (b < g.nb && full_block(g, b, c)) {
-    constexpr uint32_t P = B0 * B1 * B2;
-    const T* blk = field + (c[0] * B0 * g.d[1] + c[1] * B1) * g.d[2] + c[2] * B2;
+  uint64_t b = tix;
+  bool on;
+  Box bx;
+  if (EDGE) {
+    on = tix < count;
+    if (on) {
+      b = edge_block(g, tix);
+      bx = block_box(g, b);
+    }
+  } else {
+    on = b < g.nb && full_block(g, b, c);
+  }
+  if (on) {
+    const uint32_t n0 = EDGE ? bx.e[0] : B0, n1 = EDGE ? bx.e[1] : B1, n2 = EDGE ? bx.e[2] : B2;
+    const uint32_t P = n0 * n1 * n2;
+    const T* blk = EDGE ? field + row_base(g, bx, 0, 0) : field + (c[0] * B0 * g.d[1] + c[1] * B1) * g.d[2] + c[2] * B2;
     const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
-    const float c0 = 0.5f * (float)(B0 - 1), c1 = 0.5f * (float)(B1 - 1), c2 = 0.5f * (float)(B2 - 1);
+    const float c0 = 0.5f * (float)(n0 - 1), c1 = 0.5f * (float)(n1 - 1), c2 = 0.5f * (float)(n2 - 1);
     float S0 = 0.0f, Si = 0.0f, Sj = 0.0f, Sl = 0.0f, Elor = 0.0f;
     unsigned long long sum = 0, isum = 0;
     // E_lor neighbours of the sample rows: the previous row of this plane (brow) and, in 3D,
@@ -273,7 +296,7 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
 #pragma unroll
     for (int l = 0; l < B2; ++l) pa[l] = pb[l] = na[l] = nb[l] = 0.0f;
     using ST = PrepStage<T, NDIM, B1, B2>;
-    const bool staged = ST::on && vec2;
+    const bool staged = !EDGE && ST::on && vec2;
     // unit u of row r of buffer f of this thread: 8 bytes at ((f*B1 + r)*U + u)*blockDim + tid
     auto unit = [&](int f, int r, int u) {
       return reinterpret_cast<unsigned long long*>(stage) + (((size_t)f * B1 + r) * ST::U + u) * blockDim.x + tid;
@@ -288,9 +311,9 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
     };
     if (ST::on && staged) issue_plane(0);
 #pragma unroll 1
-    for (int i = 0; i < B0; ++i) {
+    for (int i = 0; i < (int)n0; ++i) {
       const float ti = __fsub_rn((float)i, c0);
-      const int s_cur = i % B1, s_next = (i + 1) % B1;
+      const int s_cur = i % (int)n1, s_next = (i + 1) % (int)n1;
       if (ST::on && staged) {
         if (i + 1 < B0) {
           issue_plane(i + 1);
@@ -300,10 +323,12 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
         }
       }
 #pragma unroll 1
-      for (int j = 0; j < B1; ++j) {
+      for (int j = 0; j < (int)n1; ++j) {
         const float tj = __fsub_rn((float)j, c1);
         T x[B2];
-        if (ST::on && staged) {
+        if (EDGE) {
+          load_row_n<T, B2>(blk + (uint64_t)i * si + (uint64_t)j * sj, n2, x);
+        } else if (ST::on && staged) {
 #pragma unroll
           for (int u = 0; u < ST::U; ++u) {
             const unsigned long long v = *unit(i & 1, j, u);
@@ -312,10 +337,11 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
         } else {
           load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)j * sj, vec2, x);
         }
-        const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
+        const uint32_t k0 = (uint32_t)((i * (int)n1 + j) * (int)n2);
         float r0 = 0.0f, rl = 0.0f;
 #pragma unroll
         for (int l = 0; l < B2; ++l) {
+          if (EDGE && l >= (int)n2) break;
           const T v = x[l];
           if (rel) minmax<T>(v, mn, mx);
           if (g.abft) cks<T>(v, k0 + l, sum, isum);
@@ -330,6 +356,7 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
             float cp = 0.0f, ac = 0.0f, bc = 0.0f, abc = 0.0f;
 #pragma unroll
             for (int l = 0; l < B2; ++l) {
+              if (EDGE && l >= (int)n2) break;
               const float xr = FT<T>::tofloat(x[l]);
               const float bb = hj ? brow[l] : 0.0f;
               float L;
@@ -379,10 +406,13 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
         }
       }
     }
-    const uint32_t e[3] = {B0, B1, B2};
+    const uint32_t e[3] = {n0, n1, n2};
     float cf[4];
-    constexpr float D0 = denom_c(P, B0), D1 = denom_c(P, B1), D2 = denom_c(P, B2);
-    const float D[3] = {D0, D1, D2};
+    constexpr uint32_t Pc = B0 * B1 * B2;
+    constexpr float D0 = denom_c(Pc, B0), D1 = denom_c(Pc, B1), D2 = denom_c(Pc, B2);
+    float D[3] = {D0, D1, D2};
+    if (EDGE)
+      for (int a = 0; a < 3; ++a) D[a] = e[a] > 1 ? denom(P, e[a]) : 0.0f;
     const bool finite = coefficients<NDIM>(P, e, D, S0, Si, Sj, Sl, c0, c1, c2, cf);
     if (g.abft) {
       w.sum_in[b] = sum;
@@ -399,6 +429,13 @@ template <typename T, int NDIM, int B0, int B1, int B2>
 __global__ void __launch_bounds__(128) k_prep_fast(const T* __restrict__ field, Geo g, Ws w, int vec2) {
   extern __shared__ __align__(16) unsigned char stage[];
   prep_fast<T, NDIM, B0, B1, B2>(field, g, w, vec2, blockIdx.x, stage);
+}
+
+// Edge blocks of a field whose full blocks take k_prep_fast (compact enumeration, one thread
+// per edge block).
+template <typename T, int NDIM, int B0, int B1, int B2>
+__global__ void __launch_bounds__(128) k_prep_edge(const T* __restrict__ field, Geo g, Ws w, uint64_t count) {
+  prep_fast<T, NDIM, B0, B1, B2, true>(field, g, w, 0, blockIdx.x, nullptr, count);
 }
 
 template <typename T, int NDIM, int B0, int B1, int B2>
@@ -446,8 +483,17 @@ __global__ void k_bound_batch(const Job* jobs, uint32_t n) {
   else bound_of<double>(jb.g, jb.w.st);
 }
 
+// EDGE_ONLY: the edge blocks (on the side stream), else the full blocks.
 template <typename T, int NDIM, int B0, int B1, int B2>
-static void run_fast(const void* field, const Geo& g, const Ws& w, const Launch& L) {
+static void run_fast(const void* field, const Geo& g, const Ws& w, const Launch& L, bool edge_only) {
+  if (edge_only) {
+    const uint64_t count = edge_count(g);
+    if (!count) return;
+    k_prep_edge<T, NDIM, B0, B1, B2><<<(unsigned)((count + 127) / 128), 128, 0, L.stream>>>(
+        static_cast<const T*>(field), g, w, count);
+    note_launch();
+    return;
+  }
   const size_t smem = PrepStage<T, NDIM, B1, B2>::bytes(128);
   auto kern = k_prep_fast<T, NDIM, B0, B1, B2>;
   allow_smem(reinterpret_cast<const void*>(kern), smem);
@@ -465,23 +511,23 @@ static bool has_fast(const Geo& g) {
 }
 
 template <typename T>
-static bool try_fast(const void* field, const Geo& g, const Ws& w, const Launch& L) {
+static bool try_fast(const void* field, const Geo& g, const Ws& w, const Launch& L, bool edge_only) {
   if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2]) {
     switch (g.B[2]) {
-      case 4: run_fast<T, 3, 4, 4, 4>(field, g, w, L); return true;
-      case 6: run_fast<T, 3, 6, 6, 6>(field, g, w, L); return true;
-      case 8: run_fast<T, 3, 8, 8, 8>(field, g, w, L); return true;
-      case 10: run_fast<T, 3, 10, 10, 10>(field, g, w, L); return true;
-      case 12: run_fast<T, 3, 12, 12, 12>(field, g, w, L); return true;
-      case 16: run_fast<T, 3, 16, 16, 16>(field, g, w, L); return true;
+      case 4: run_fast<T, 3, 4, 4, 4>(field, g, w, L, edge_only); return true;
+      case 6: run_fast<T, 3, 6, 6, 6>(field, g, w, L, edge_only); return true;
+      case 8: run_fast<T, 3, 8, 8, 8>(field, g, w, L, edge_only); return true;
+      case 10: run_fast<T, 3, 10, 10, 10>(field, g, w, L, edge_only); return true;
+      case 12: run_fast<T, 3, 12, 12, 12>(field, g, w, L, edge_only); return true;
+      case 16: run_fast<T, 3, 16, 16, 16>(field, g, w, L, edge_only); return true;
       default: return false;
     }
   }
   if (g.ndim == 2 && g.B[1] == g.B[2]) {
     switch (g.B[2]) {
-      case 8: run_fast<T, 2, 1, 8, 8>(field, g, w, L); return true;
-      case 12: run_fast<T, 2, 1, 12, 12>(field, g, w, L); return true;
-      case 16: run_fast<T, 2, 1, 16, 16>(field, g, w, L); return true;
+      case 8: run_fast<T, 2, 1, 8, 8>(field, g, w, L, edge_only); return true;
+      case 12: run_fast<T, 2, 1, 12, 12>(field, g, w, L, edge_only); return true;
+      case 16: run_fast<T, 2, 1, 16, 16>(field, g, w, L, edge_only); return true;
       default: return false;
     }
   }
@@ -507,10 +553,16 @@ static void launch_prep_t(const void* field, const Geo& g, const Ws& w, const La
     Fork fk(L);
     const Launch Ls = fk.side_launch(L);
     const bool fast = has_fast(g);
-    if (g.ndim == 3) run_generic<T, 3>(field, g, w, !fast, fast ? Ls : L);
-    else if (g.ndim == 2) run_generic<T, 2>(field, g, w, !fast, fast ? Ls : L);
-    else run_generic<T, 1>(field, g, w, !fast, fast ? Ls : L);
-    if (fast) try_fast<T>(field, g, w, L);
+    if (fast) {
+      try_fast<T>(field, g, w, Ls, true);  // edge blocks: the same walk at their extents
+      try_fast<T>(field, g, w, L, false);
+    } else if (g.ndim == 3) {
+      run_generic<T, 3>(field, g, w, true, L);
+    } else if (g.ndim == 2) {
+      run_generic<T, 2>(field, g, w, true, L);
+    } else {
+      run_generic<T, 1>(field, g, w, true, L);
+    }
     fk.join();
   }
   k_bound<T><<<1, 1, 0, L.stream>>>(g, w.st);
