@@ -44,12 +44,12 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 555498343, "src": "cd979e1ad757"},
-    ("384cube", "prep"): {"bytes": 234350863, "src": "cd979e1ad757"},
-    ("512cube", "predict"): {"bytes": 941265186, "src": "68a3a739879d"},
-    ("384cube", "predict"): {"bytes": 397096250, "src": "68a3a739879d"},
-    ("512cube", "decode"): {"bytes": 484662356, "src": "4e805f4d2728"},
-    ("384cube", "decode"): {"bytes": 204466931, "src": "4e805f4d2728"},
+    ("512cube", "prep"): {"bytes": 555524353, "src": "20d20df4cc1a"},
+    ("384cube", "prep"): {"bytes": 234361837, "src": "20d20df4cc1a"},
+    ("512cube", "predict"): {"bytes": 941237301, "src": "68a3a739879d"},
+    ("384cube", "predict"): {"bytes": 397084487, "src": "68a3a739879d"},
+    ("512cube", "decode"): {"bytes": 484708565, "src": "4e805f4d2728"},
+    ("384cube", "decode"): {"bytes": 204486426, "src": "4e805f4d2728"},
 }
 
 
