@@ -315,6 +315,27 @@ def test_huffman_brute_force_small_alphabets(orc):
         assert int((hist * ln).sum()) == best
 
 
+def test_huffman_brute_force_seven_and_eight_symbols(orc):
+    """Optimal prefix-code cost on 7-8 symbols by exhaustion over sorted length vectors: an
+    optimal code gives shorter codewords to more frequent symbols (exchange argument), so the
+    minimum over all nondecreasing length vectors with Kraft sum <= 1, paired with the
+    frequencies in decreasing order, is the optimum over all prefix codes."""
+    rng = np.random.default_rng(13)
+    for trial in range(30):
+        n = int(rng.integers(7, 9))
+        f = rng.integers(1, 200, size=n) if trial % 3 else rng.geometric(0.3, size=n)
+        fd = sorted((int(a) for a in f), reverse=True)
+        best = None
+        for lens in itertools.combinations_with_replacement(range(1, n), n):
+            if sum(Fraction(1, 2**l) for l in lens) <= 1:
+                c = sum(a * l for a, l in zip(fd, lens))
+                best = c if best is None else min(best, c)
+        hist = np.zeros(16, dtype=np.uint64)
+        hist[rng.choice(16, n, replace=False)] = f
+        ln = orc.huffman_lengths(hist)
+        assert int((hist * ln).sum()) == best
+
+
 def test_huffman_single_symbol_and_length_limit(orc):
     hist = np.zeros(65536, dtype=np.uint64)
     hist[32768] = 1000
