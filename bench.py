@@ -366,45 +366,130 @@ def _oracle_sample(args):
     return x, slab
 
 
-def cpu_baseline(args):
-    """The oracle as it stands (single-threaded C++), one compress + decompress of a slab."""
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(conn, shape, seed, spikes, block, enc, ll):
+    """One host core's share of the all-cores oracle baseline: its own slab of the recipe,
+    compressed and decompressed by the (single-threaded) oracle each time the parent says go."""
     import oracle
-    x, slab = _oracle_sample(args)
+    import synth
+    x = synth.sinusoid_field(shape, seed, spikes=spikes)
     oracle.lib()
-    t0 = time.perf_counter()
-    s, rep = oracle.compress(x, REL_EB, block=WORKLOADS[args.workload]["block"], encoding=args.encoding,
-                             lossless=args.lossless)
-    rc, y, st, _ = oracle.decompress(s)
-    dt = time.perf_counter() - t0
-    return {"value": round(x.nbytes / 1e9 / dt, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"one compress+decompress of a {slab} slab of the same recipe ({x.nbytes / 1e6:.0f} MB), "
-                      f"{dt:.1f} s"}
+    conn.send(x.nbytes)
+    while True:
+        abft = conn.recv()
+        if abft is None:
+            break
+        t0 = time.perf_counter()
+        s, _ = oracle.compress(x, REL_EB, block=block, abft=abft, encoding=enc, lossless=ll)
+        oracle.decompress(s)
+        conn.send(time.perf_counter() - t0)
+    conn.close()
 
 
-def run_reference(args):
-    """The reference arm: the CPU oracle on a bounded slab per step, on rank 0."""
-    world, rank, local = _dist()
-    if rank != 0:
-        return None
+class OraclePool:
+    """The oracle on every host core at once: one spawned process per core, each with its own
+    block-aligned slab of the workload's recipe (independent blocks, so the slabs are
+    independent problems). Spawned, not forked, so no CUDA state is inherited."""
+
+    def __init__(self, args, cores=None, planes=96):
+        import multiprocessing as mp
+        wl = WORKLOADS[args.workload]
+        self.cores = cores or os.cpu_count() or 1
+        shape = (planes,) + tuple(wl["shape"][1:])
+        self.slab = shape
+        ctx = mp.get_context("spawn")
+        self.procs, self.conns = [], []
+        for r in range(self.cores):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, shape, wl["seed"] + 17 * r, wl["spikes"], wl["block"],
+                                                         args.encoding, args.lossless), daemon=True)
+            p.start()
+            self.procs.append(p)
+            self.conns.append(a)
+        self.bytes = sum(c.recv() for c in self.conns)
+
+    def round(self, abft=True):
+        """Wall seconds for every core to compress + decompress its slab once."""
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(abft)
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def cpu_baseline(args):
+    """The oracle as it stands (single-threaded C++): one core on a slab, and every host core at
+    once on a slab each, ABFT on and off."""
     import oracle
     x, slab = _oracle_sample(args)
     oracle.lib()
     block = WORKLOADS[args.workload]["block"]
-    for _ in range(args.warmup):
-        oracle.compress(x[:8], REL_EB, block=block, encoding=args.encoding, lossless=args.lossless)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s, rep = oracle.compress(x, REL_EB, block=block, encoding=args.encoding, lossless=args.lossless)
+
+    def one(abft):
+        t0 = time.perf_counter()
+        s, rep = oracle.compress(x, REL_EB, block=block, abft=abft, encoding=args.encoding, lossless=args.lossless)
         oracle.decompress(s)
-    dt = time.perf_counter() - t0
-    value = x.nbytes * args.steps / 1e9 / dt
+        return x.nbytes / 1e9 / (time.perf_counter() - t0)
+
+    single_on, single_off = one(True), one(False)
+    pool = OraclePool(args)
+    try:
+        pool.round(True)  # warm-up
+        all_on = pool.bytes / 1e9 / pool.round(True)
+        all_off = pool.bytes / 1e9 / pool.round(False)
+    finally:
+        pool.close()
+    return {"value": round(all_on, 4), "unit": "GB/s", "cores": pool.cores, "kind": "oracle",
+            "sample": f"every host core compresses + decompresses its own {pool.slab} slab of the recipe "
+                      f"({pool.bytes / pool.cores / 1e6:.0f} MB each) once; single core: one {slab} slab",
+            "cpu_model": _cpu_model(),
+            "single": {"value": round(single_on, 4), "cores": 1},
+            "all_cores": {"value": round(all_on, 4), "cores": pool.cores},
+            "abft_off": {"single": round(single_off, 4), "all_cores": round(all_off, 4)},
+            "abft_overhead_pct": {"single": round(100.0 * (single_off / single_on - 1.0), 2),
+                                  "all_cores": round(100.0 * (all_off / all_on - 1.0), 2)}}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on every host core, a slab per core per step, on rank 0."""
+    world, rank, local = _dist()
+    if rank != 0:
+        return None
+    pool = OraclePool(args)
+    try:
+        for _ in range(args.warmup):
+            pool.round(True)
+        dt = sum(pool.round(True) for _ in range(args.steps))
+    finally:
+        pool.close()
+    block = WORKLOADS[args.workload]["block"]
+    value = pool.bytes * args.steps / 1e9 / dt
     res = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"{args.workload} recipe, slab {slab} per step, rel eb {REL_EB}, block {block}^3, "
-                                  f"ABFT on, {args.encoding} encoding; one step = compress + decompress"},
-           "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                            "sample": f"{slab} slab per step"},
+           "config": {"workload": f"{args.workload} recipe, one {pool.slab} slab per host core per step, "
+                                  f"rel eb {REL_EB}, block {block}^3, ABFT on, {args.encoding} encoding; "
+                                  "one step = compress + decompress"},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": pool.cores, "kind": "oracle",
+                            "sample": f"{pool.slab} slab per core per step", "cpu_model": _cpu_model()},
            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
     return res

@@ -180,17 +180,24 @@ int sdcsz_decompress_traced(const void* d_stream, size_t nbytes, void* d_field, 
 
 /*
  * Allocation-free compression. The paper has no counterpart: this entry point exists for
- * callers that cannot allocate device memory when they compress (while capturing a stream
- * into a CUDA graph, inside callbacks or latency-critical serving loops, or when another
- * framework owns the device memory pool). It runs the same kernels as sdcsz_compress, with the
- * workspace in a fixed 64 MiB device array that every GPU loading this library holds until the
- * process exits; it calls no allocator. Arguments as for sdcsz_compress, without d_ws/ws_bytes.
- *  - Returns SDCSZ_ECAPACITY when sdcsz_workspace_size(p) exceeds 64 MiB (float32 fields up to
- *    about ten million points fit).
- *  - The first call on a device looks up the array's device address; make that first call
- *    before any stream capture.
- *  - All calls share the array: calls whose GPU work overlaps (different streams, or
- *    different host threads) race and corrupt each other's output. Serialize them.
+ * callers that cannot allocate device memory when they compress: callbacks and
+ * latency-critical serving loops that must not enter an allocator (a cudaMalloc can
+ * synchronize the device and take milliseconds), and hosts whose device memory belongs to
+ * another framework's pool, which the library must not grow or fragment. It runs the same
+ * kernels as sdcsz_compress, with the workspace in a fixed 64 MiB device array that every GPU
+ * loading this library holds until the process exits; it calls no allocator. Arguments as
+ * for sdcsz_compress, without d_ws/ws_bytes.
+ *  - Returns SDCSZ_ECAPACITY when sdcsz_workspace_size(p) exceeds 64 MiB: compare the two
+ *    before calling. At the default block sizes that allows about 6.4 million float32 points
+ *    (a 186^3 cube, a 2592^2 square) or about 4.7 million float64 points (168^3, 2172^2); the
+ *    limit moves a little with the block size, and the lossless stage lowers it.
+ *  - The first call on a device looks up the array's device address (with that device
+ *    current) and keeps it for the life of the process; make that first call before any
+ *    stream capture. Do not call this entry point after cudaDeviceReset in the same process:
+ *    the kept address belongs to the context that the reset destroyed.
+ *  - All calls share the array and it keeps the last call's contents (each call clears what
+ *    must start at zero): calls whose GPU work overlaps (different streams, or different host
+ *    threads) race and corrupt each other's output. Serialize them.
  */
 int sdcsz_compress_noalloc(const void* d_field, const sdcsz_params* p, void* d_out, size_t out_cap,
                            size_t* out_bytes, sdcsz_report* report, void* stream);

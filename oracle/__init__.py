@@ -119,6 +119,12 @@ def lib():
         L.orc_ll_decode.restype = None
         L.orc_error_bound.argtypes = [vp, P]
         L.orc_error_bound.restype = ctypes.c_double
+        L.orc_sample_mask.argtypes = [u32, vp, vp]
+        L.orc_sample_mask.restype = u64
+        L.orc_selection_estimates.argtypes = [vp, u32, u32, vp, vp, ctypes.POINTER(ctypes.c_float),
+                                              ctypes.POINTER(ctypes.c_float)]
+        L.orc_selection_estimates.restype = None
+        L.orc_select_regression.argtypes = [ctypes.c_float, ctypes.c_float, u64, u32, ctypes.c_float]
         _lib = L
     return _lib
 
@@ -323,6 +329,33 @@ def ll_decode(chunk, n, freqs) -> np.ndarray:
     out = np.zeros(n, dtype=np.uint8)
     lib().orc_ll_decode(_ptr(c), c.size, n, _ptr(f), _ptr(out))
     return out
+
+
+def sample_mask(ext) -> np.ndarray:
+    """Sample membership (1 = in the selection sample) of every point of a block of extents ext."""
+    ext = [int(e) for e in ext]
+    e = np.array(ext, dtype=np.uint32)
+    m = np.zeros(int(np.prod(ext)), dtype=np.uint8)
+    n = lib().orc_sample_mask(len(ext), _ptr(e), _ptr(m))
+    assert n == int(m.sum()), "sample count disagrees with the mask"
+    return m.reshape(ext)
+
+
+def selection_estimates(block_values: np.ndarray, coef):
+    """(E_reg, E_lor) of one block for the given fp32 coefficients (b_0..b_ndim)."""
+    v = np.ascontiguousarray(block_values)
+    e = np.array(v.shape, dtype=np.uint32)
+    c = np.zeros(4, dtype=np.float32)
+    c[: len(coef)] = coef
+    er, el = ctypes.c_float(), ctypes.c_float()
+    lib().orc_selection_estimates(_ptr(v), 0 if v.dtype == np.float32 else 1, v.ndim, _ptr(e), _ptr(c),
+                                  ctypes.byref(er), ctypes.byref(el))
+    return er.value, el.value
+
+
+def select_regression(Ereg, Elor, S, ndim, eb) -> bool:
+    """Algorithm 1's indicator for the given estimates: True = regression."""
+    return bool(lib().orc_select_regression(Ereg, Elor, S, ndim, eb))
 
 
 def error_bound(field: np.ndarray, eb, eb_mode="rel") -> float:

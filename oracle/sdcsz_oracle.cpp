@@ -28,7 +28,7 @@
 //     value is predicted, so a repaired block compresses as the error-free one;
 //   * regression: closed-form least squares on the block grid in fp32, sequential sums;
 //   * selection: the sample is a set of whole rows (one diagonal row per plane in 3D, every
-//     fourth row in 2D); E_lor adds kappa*eb per sample point;
+//     fourth row in 2D); E_lor adds kappa*eb per sample point (kappa exact, see below);
 //   * duplication recomputes once more on a mismatch and keeps the third result;
 //   * the histogram is taken as the codes are produced (before the bin-array window that
 //     the code checksums protect);
@@ -45,8 +45,9 @@
 //     asymmetric numeral system coder of our own over the bytes after the block tables
 //     (sum_dc, coefficients, unpredictable values, payload), in independent 16 KiB chunks
 //     of 32 interleaved states.
-// Parity unpinned: the predictor-selection estimate (kappa, sample set) only changes the
-// compression ratio (Sec. 4.1.1) and is pinned by determinism and GPU/oracle equality only.
+// The predictor-selection estimate (kappa, sample set) only changes the compression ratio
+// (Sec. 4.1.1); it is pinned by hand-listed sample rows, exact rational kappa values and
+// integer blocks whose estimates are exact (tests/test_oracle_selection.py).
 
 #include <algorithm>
 #include <cmath>
@@ -334,10 +335,10 @@ void selection_estimates(const T* v, const uint32_t e[3], int ndim, const float 
 
 // Algorithm 1's indicator: the predictor with the smaller estimated error. E_lor gets the expected
 // effect of predicting from reconstructed instead of original neighbours: kappa*eb per point,
-// kappa = E|sum of n uniform(-eb,eb)| / eb for the n = 1, 3, 7 Lorenzo terms of 1D/2D/3D
-// (normal approximation for 2D/3D).
+// kappa = E|sum of n uniform(-eb,eb)| / eb for the n = 1, 3, 7 Lorenzo terms of 1D/2D/3D, the
+// exact Irwin-Hall expectations 1/2, 13/16 and 113149/92160, rounded to fp32.
 bool select_regression(float Ereg, float Elor, uint64_t S, int ndim, float ebf) {
-  static const float kappa[4] = {0.0f, 0.5f, 0.80f, 1.22f};
+  static const float kappa[4] = {0.0f, (float)(1.0 / 2.0), (float)(13.0 / 16.0), (float)(113149.0 / 92160.0)};
   float noise = kappa[ndim] * ebf;
   float total = Elor + (float)S * noise;
   return Ereg < total;
@@ -1606,6 +1607,36 @@ void orc_ll_decode(const uint8_t* in, uint64_t len, uint32_t n, const uint16_t* 
   for (int b = 0; b < 256; ++b)
     for (uint32_t q = c[b]; q < c[b + 1] && q < kLLM; ++q) sym[q] = (uint8_t)b;
   ll_decode_chunk(in, len, n, f, c, sym.data(), out);
+}
+
+// Predictor selection, for pinning (Algorithm 1, "sample and estimate"): the sample
+// membership of every point of a block of extents ext[0..ndim-1] (row-major, 1 = sampled);
+// returns the number of sampled points.
+uint64_t orc_sample_mask(uint32_t ndim, const uint32_t* ext, uint8_t* mask) {
+  uint32_t e[3] = {1, 1, 1};
+  for (uint32_t a = 0; a < ndim; ++a) e[3 - ndim + a] = ext[a];
+  uint64_t k = 0, n = 0;
+  for (uint32_t i = 0; i < e[0]; ++i)
+    for (uint32_t j = 0; j < e[1]; ++j)
+      for (uint32_t l = 0; l < e[2]; ++l, ++k) {
+        mask[k] = sample_row((int)ndim, i, j, e) ? 1 : 0;
+        n += mask[k];
+      }
+  return n == sample_points((int)ndim, e) ? n : ~0ull;
+}
+
+// The two estimates of one block for given fp32 coefficients.
+void orc_selection_estimates(const void* v, uint32_t dtype, uint32_t ndim, const uint32_t* ext, const float* coef,
+                             float* Ereg, float* Elor) {
+  uint32_t e[3] = {1, 1, 1};
+  for (uint32_t a = 0; a < ndim; ++a) e[3 - ndim + a] = ext[a];
+  if (dtype == 0) selection_estimates<float>((const float*)v, e, (int)ndim, coef, Ereg, Elor);
+  else selection_estimates<double>((const double*)v, e, (int)ndim, coef, Ereg, Elor);
+}
+
+// The indicator: 1 = regression.
+int orc_select_regression(float Ereg, float Elor, uint64_t S, uint32_t ndim, float eb) {
+  return select_regression(Ereg, Elor, S, (int)ndim, eb) ? 1 : 0;
 }
 
 // The value-range relative bound of the field, as the compressor computes it.

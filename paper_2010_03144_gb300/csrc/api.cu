@@ -623,11 +623,11 @@ const char* sdcsz_strerror(int code) {
 }  // extern "C"
 
 // ---------------------------------------------------------------- allocation-free compression
-// Some callers cannot allocate device memory at the moment they compress: code running while
-// a stream is being captured into a CUDA graph (allocation is not a capturable operation),
-// callbacks and latency-critical serving loops that must not enter the allocator, and hosts
-// whose device memory is owned by another framework's pool. For them, sdcsz_compress_noalloc
-// runs the same kernels with the workspace placed in a fixed device array of this library.
+// Some callers cannot allocate device memory at the moment they compress: callbacks and
+// latency-critical serving loops that must not enter the allocator (cudaMalloc can
+// synchronize the device), and hosts whose device memory is owned by another framework's
+// pool. For them, sdcsz_compress_noalloc runs the same kernels with the workspace placed in a
+// fixed device array of this library.
 
 namespace sdcsz {
 namespace {
@@ -638,7 +638,8 @@ constexpr size_t kStaticScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 // In host code `g_static_scratch` only names the symbol; its device address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached for the life of the process (a
+// cudaDeviceReset invalidates it; the header tells callers not to use the entry point after one).
 void* static_scratch_address() {
   static std::mutex mu;
   static void* addr[64] = {nullptr};

@@ -596,7 +596,8 @@ struct Consts {
     if (sizeof(T) == 4) inv2 = (T)__double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, ebd)));
     else inv2 = (T)__ddiv_rn(1.0, __dmul_rn(2.0, ebd));
     Rh = FT<T>::sub(FT<T>::fromi((int)R), T(0.5));
-    const float kappa = ndim == 3 ? 1.22f : (ndim == 2 ? 0.80f : 0.5f);
+    // E|sum of n uniform(-1,1)| for the n = 7 / 3 / 1 Lorenzo terms (exact Irwin-Hall values)
+    const float kappa = ndim == 3 ? (float)(113149.0 / 92160.0) : (ndim == 2 ? (float)(13.0 / 16.0) : 0.5f);
     noise = __fmul_rn(kappa, FT<T>::tofloat(eb));
   }
 };

@@ -46,3 +46,16 @@ def assert_same_field(y_gpu, y_ref):
     if not np.array_equal(bits(g), bits(y_ref)):
         bad = np.nonzero(bits(g).ravel() != bits(y_ref).ravel())[0]
         raise AssertionError(f"{bad.size} values differ, first at {bad[:8].tolist()}")
+
+
+def block_points(block_mask: np.ndarray, shape, block=None) -> np.ndarray:
+    """Expand a per-block boolean array (blocks in row-major order) to a per-point mask of the
+    field: a point is set when its block is set. Default blocks: 6^3, 12^2, 128."""
+    shape = tuple(int(n) for n in shape)
+    if block is None:
+        block = {1: (128,), 2: (12, 12), 3: (6, 6, 6)}[len(shape)]
+    nbd = tuple(-(-n // b) for n, b in zip(shape, block))
+    m = np.asarray(block_mask).reshape(nbd)
+    for ax, b in enumerate(block):
+        m = np.repeat(m, b, axis=ax)
+    return m[tuple(slice(0, n) for n in shape)]

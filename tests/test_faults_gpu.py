@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity import assert_same_field, assert_same_stream, compress_both, gpu_sz
+from parity import assert_same_field, assert_same_stream, bits, block_points, compress_both, gpu_sz
 
 pytestmark = pytest.mark.gpu
 
@@ -150,9 +150,11 @@ def test_stream_corruption_reported_like_oracle(sz, orc):
         rc, y, st, rep = sz.decompress(torch.from_numpy(bad).cuda())
         assert rc == rc_ref
         assert np.array_equal(st.cpu().numpy() >= 2, st_ref >= 2)
-        ok = st_ref == 0
-        # every block that verified decodes to the same values
         assert rc_ref in (0, orc.ESDC)
+        # every block that verified on both sides decodes to the same values
+        ok = block_points((st_ref == 0) & (st.cpu().numpy() == 0), x.shape)
+        assert ok.any()
+        assert np.array_equal(bits(y.cpu().numpy())[ok], bits(y_ref)[ok])
 
 
 def test_random_corruption_never_faults(sz, orc):

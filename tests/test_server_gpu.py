@@ -2,15 +2,17 @@
 
 Requests submitted together run concurrently on the server's streams under a memory budget
 small enough to make later requests wait for earlier ones. Each result must be identical to
-the same request run alone through the single-call entry points: same stream bytes, same
-reconstructed values, same reports.
+the same request run alone through the single-call entry points (same stream bytes, same
+reconstructed values, same reports) and to the CPU oracle on the same input: every served
+compress stream equals oracle.compress, every served decompression equals
+oracle.decompress, value for value.
 """
 
 import numpy as np
 import pytest
 
 import synth
-from parity import REPORT_KEYS, gpu_sz
+from parity import REPORT_KEYS, assert_same_stream, bits, gpu_sz
 
 pytestmark = pytest.mark.gpu
 
@@ -18,15 +20,19 @@ POOL = [((40, 50, 60), np.float32), ((64, 64, 64), np.float32), ((33, 70, 41), n
         ((300, 257), np.float64), ((512, 384), np.float64), ((10000,), np.float32)]
 
 
-def _pool(sz, torch):
-    fields, streams = [], []
+def _pool(sz, torch, orc=None):
+    fields, streams, host = [], [], []
     for i, (shape, dt) in enumerate(POOL):
         x = synth.sinusoid_field(shape, 50 + i, dtype=dt, spikes=0.01)
         d = torch.from_numpy(x).cuda()
-        s, _ = sz.compress(d, 10.0 ** -(2 + i % 3))
+        s, rep = sz.compress(d, 10.0 ** -(2 + i % 3))
+        if orc is not None:
+            s_ref, rep_ref = orc.compress(x, 10.0 ** -(2 + i % 3))
+            assert_same_stream(s, rep, s_ref, rep_ref)
         fields.append(d)
         streams.append(s.clone())
-    return fields, streams
+        host.append(x)
+    return fields, streams, host
 
 
 def _requests(n, seed):
@@ -45,10 +51,10 @@ def _requests(n, seed):
     return reqs
 
 
-def test_server_results_match_single_calls():
+def test_server_results_match_single_calls_and_oracle(orc):
     import torch
     sz = gpu_sz()
-    fields, streams = _pool(sz, torch)
+    fields, streams, host = _pool(sz, torch, orc)
     reqs = _requests(40, 1)
     srv = sz.Server(hbm_budget=48 << 20, slots=3)
     outs = {}
@@ -77,17 +83,24 @@ def test_server_results_match_single_calls():
             assert got.numel() == s_1.numel() and torch.equal(got, s_1), rid
             for key in REPORT_KEYS:
                 assert c["report"][key] == rep_1[key], (rid, key)
+            s_ref, rep_ref = orc.compress(host[k], eb, flips=flips)
+            assert_same_stream(got, c["report"], s_ref, rep_ref)
             srv.release(rid)
         elif op == "decompress":
             rc, y1, _, rep_1 = sz.decompress(streams[k], flips=flips)
             assert c["status"] == rc
             assert torch.equal(outs[rid].view(-1).view(torch.uint8), y1.view(-1).view(torch.uint8)), rid
             assert c["report"]["decomp_reexec_corrected"] == rep_1["decomp_reexec_corrected"]
+            rc_ref, y_ref, _, rep_ref = orc.decompress(streams[k].cpu().numpy(), flips=flips)
+            assert c["status"] == rc_ref
+            assert np.array_equal(bits(outs[rid].cpu().numpy()), bits(y_ref)), rid
+            assert c["report"]["decomp_reexec_corrected"] == rep_ref["decomp_reexec_corrected"]
         else:
             rc, _, rep_1 = sz.verify(streams[k], original=fields[k])
-            assert c["status"] == rc
+            assert c["status"] == rc == 0
             for key in ("uncorrectable_blocks", "bound_violations", "decomp_reexec_corrected"):
                 assert c["report"][key] == rep_1[key], (rid, key)
+            assert c["report"]["uncorrectable_blocks"] == 0 and c["report"]["bound_violations"] == 0
     assert srv.stats()["bytes_in_use"] == 0
     srv.close()
 
