@@ -69,6 +69,9 @@ KERNEL_SOURCES = {
     "codebook": ("k_codebook.cu", "sdcsz_internal.cuh"),
     "encode": ("k_encode.cu", "sdcsz_internal.cuh"),
     "decode": ("decode.cuh", "k_decode_f32.cu", "sdcsz_internal.cuh"),
+    "prep64": ("k_prep.cu", "sdcsz_internal.cuh"),
+    "predict64": ("predict.cuh", "k_predict_f64.cu", "sdcsz_internal.cuh"),
+    "decode64": ("decode.cuh", "k_decode_f64.cu", "sdcsz_internal.cuh"),
 }
 
 
@@ -687,7 +690,7 @@ def run_faults(args):
     libbuild.build()
     sz.lib()
     dev = torch.device("cuda", 0)
-    rel, rates = 1e-4, (1e-9, 1e-7, 1e-5)
+    rel, rates = 1e-4, (1e-9, 1e-8, 1e-7, 1e-6, 1e-5)
     results = []
     for shape, tdt, B in (((1024, 1024, 1024), torch.float32, 8), ((512, 512, 512), torch.float64, 8)):
         W = 1 if tdt == torch.float32 else 2
@@ -836,13 +839,106 @@ def run_region(args):
         "boxes": rows, "full_decompress_p50_ms": round(float(np.percentile(full_ms, 50)), 3)}), flush=True)
 
 
+# FP64 instructions (DADD + DMUL + DFMA, thread level) per point of each stage of the float64
+# path, from an ncu capture (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum
+# over every launch of the stage / points), keyed by the hash of the stage's sources.
+NCU_FP64_PER_POINT = {}
+
+
+def fp64_rate(device, reps=5):
+    """Measured FP64 instruction rate of this GPU (separate DADD + DMUL, and DFMA), ops/s."""
+    import ctypes
+
+    import torch
+
+    from paper_2010_03144_gb300 import build as libbuild
+    L = ctypes.CDLL(libbuild.PEAK_LIB)
+    L.sdcsz_peak_fp64.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_ulonglong)]
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, iters = sms * 8, 4096
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=device)
+    h = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    res = {}
+    for fused in (0, 1):
+        best = None
+        for _ in range(reps):
+            ms, n = ctypes.c_float(), ctypes.c_ulonglong()
+            if L.sdcsz_peak_fp64(ctypes.c_void_p(out.data_ptr()), blocks, iters, fused, h, ctypes.byref(ms),
+                                 ctypes.byref(n)):
+                raise RuntimeError("FP64 rate kernel failed")
+            r = n.value / (ms.value * 1e-3)
+            best = r if best is None else max(best, r)
+        res["fma" if fused else "add_mul"] = best
+    return res
+
+
+def run_fp64(args):
+    """The float64 path against the FP64 instruction rate: 512^3 float64 (spikes), rel 1e-4,
+    8^3 blocks, ABFT on and off, with this GPU's measured DADD/DMUL rate beside it."""
+    import torch
+
+    import paper_2010_03144_gb300 as sz
+    from paper_2010_03144_gb300 import build as libbuild
+    import synth
+
+    libbuild.build()
+    sz.lib()
+    dev = torch.device("cuda", 0)
+    clk = ClockSampler()
+    clk.start()
+    rate = fp64_rate(dev)
+    shape, B, rel = (512, 512, 512), 8, 1e-4
+    x = synth.device_field(shape, 21, torch.float64, dev, spikes=0.01)
+    N = x.numel()
+    rows = {}
+    for abft in (True, False):
+        p = sz.make_params(shape, torch.float64, rel, block=B, abft=abft)
+        ws = sz.Workspace(p, dev)
+        out = torch.empty_like(x)
+        s_t, rep = sz.compress(x, rel, block=B, workspace=ws, abft=abft)
+        dws = torch.empty(sz.decompress_workspace_size(s_t), dtype=torch.uint8, device=dev)
+        acc = {}
+        for it in range(args.warmup + args.steps):
+            _, ms = sz.compress_traced(x, p, ws)
+            dms = sz.decompress_traced(ws.out, out, dws)
+            if it >= args.warmup:
+                for k, v in zip(("reset", "prep", "predict", "codebook", "encode"), ms):
+                    acc[k] = acc.get(k, 0.0) + v / args.steps
+                acc["decode"] = acc.get("decode", 0.0) + dms / args.steps
+        step = sum(acc.values())
+        rows["abft_on" if abft else "abft_off"] = {
+            "round_trip_gbs": round(N * 8 / (step * 1e-3) / 1e9, 1), "ms_per_step": round(step, 4),
+            "stages_ms": {k: round(v, 4) for k, v in acc.items()},
+            "compression_ratio": round(N * 8 / int(rep["compressed_bytes"]), 3)}
+    clocks = clk.stop()
+    fp = {}
+    for stage in ("prep", "predict", "decode"):
+        e = NCU_FP64_PER_POINT.get(stage)
+        if e and e.get("src") == _src_hash(stage + "64"):
+            t = rows["abft_on"]["stages_ms"][stage] * 1e-3
+            ach = e["per_point"] * N / t
+            fp[stage] = {"fp64_per_point": e["per_point"], "achieved_ops": round(ach / 1e9, 1),
+                         "frac_of_add_mul_rate": round(ach / rate["add_mul"], 3)}
+    print(json.dumps({
+        "metric": "float64 round trip GB/s and FP64 instruction-rate fraction", "unit": "GB/s",
+        "value": rows["abft_on"]["round_trip_gbs"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fp64: 512^3 float64 sinusoids+noise+1% spikes, rel eb 1e-4, block 8^3; one step = "
+                               "compress + decompress", "l2": "inputs larger than L2 (no flush)"},
+        "fp64_rate_gops": {k: round(v / 1e9, 1) for k, v in rate.items()},
+        "fp64_rate_what": "measured: independent DADD+DMUL chains (add_mul) and DFMA chains (fma), "
+                          "thread-level instructions per second",
+        "runs": rows, "fp64_roofline": fp or None, "clocks": clocks}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve", "faults", "region"),
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve", "faults", "region", "fp64"),
                     default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
@@ -862,6 +958,8 @@ def main():
         run_faults(args)
     elif args.workload == "region":
         run_region(args)
+    elif args.workload == "fp64":
+        run_fp64(args)
     else:
         run_ours(args)
 

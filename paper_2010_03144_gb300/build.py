@@ -20,6 +20,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsdcsz.so")
+# measurement helper (FP64 instruction rate), kept out of the compressor's library
+PEAK_SRC = "peak_fp64.cu"
+PEAK_LIB = os.path.join(HERE, "libsdcsz_peak.so")
 SOURCES = ["api.cu", "k_prep.cu", "k_predict_f32.cu", "k_predict_f64.cu", "k_predict_f32c.cu", "k_predict_f64c.cu",
            "k_flip.cu", "k_codebook.cu", "k_encode.cu", "k_decode_f32.cu", "k_decode_f64.cu", "k_lossless.cu",
            "server.cu"]
@@ -63,10 +66,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         if verbose and r.stderr:
             print(r.stderr, file=sys.stderr)
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    lib_jobs = len(jobs)
+    peak_src = os.path.join(CSRC, PEAK_SRC)
+    if force or _stale(PEAK_LIB, [peak_src]):
+        jobs.append([nvcc, *ARCH, *FLAGS, *extra_flags, "-shared", peak_src, "-o", PEAK_LIB])
+    with cf.ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if force or jobs or _stale(LIB, objs):
+    if force or lib_jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)

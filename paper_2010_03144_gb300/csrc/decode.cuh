@@ -398,6 +398,12 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
 #pragma unroll
     for (int q = 0; q < B1 * B2; ++q) plane[q * 256] = T(0);
   }
+  // regression along the row: the block's products c_l * l
+  T clp[B2];
+  if (REG) {
+#pragma unroll
+    for (int l = 0; l < B2; ++l) clp[l] = FT<T>::mul(cT[NDIM == 3 ? 2 : 1], (T)l);
+  }
   T brow[B2], arow[B2];
 #pragma unroll 1
   for (int i = 0; i < B0; ++i) {
@@ -417,55 +423,29 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       T out[B2];
       T c = T(0), ac = T(0), bc = T(0), abc = T(0);
       const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
-      int qp = 0;  // second symbol of the pair decoded at even l
-      // a row of central codes (the common case of a smooth field) in one comparison
-      bool crow = false;
-      if (tb.rbits && (br.peek() >> (32 - tb.rbits)) == tb.rpat) {
-        crow = true;
-        br.advance(tb.rbits);
-      }
-#pragma unroll
-      for (int l = 0; l < B2; ++l) {
-        int q;
-        if (crow) {
-          q = R;
-        } else if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
-          if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp, CMP);
-          else q = (CMP && qp == kDefer) ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : qp;
-        } else {
-          q = br.next(tb.lut, *tb.cn, tb.syms, tb.n_live);
-        }
-        T a = T(0), bb = T(0), ab = T(0);
-        if (!REG) {
-          if (NDIM == 3) {
-            a = prow[l * 256];
-            bb = brow[l];
-            ab = arow[l];
-          } else {
-            a = brow[l];
-          }
-        }
-        T pred;
+      // the neighbours of point l (Lorenzo) and its prediction
+      auto predict = [&](int l, T& a, T& bb, T& ab) {
+        a = bb = ab = T(0);
         if (REG) {
-          const int lc = NDIM == 3 ? 2 : 1;
-          pred = FT<T>::add(FT<T>::add(ra, FT<T>::mul(cT[lc], (T)l)), cT[lc + 1]);
-        } else if (NDIM == 3) {
+          if (NDIM == 3) return FT<T>::add(FT<T>::add(ra, clp[l]), cT[3]);
+          return FT<T>::add(FT<T>::add(ra, clp[l]), cT[2]);
+        }
+        if (NDIM == 3) {
+          a = prow[l * 256];
+          bb = brow[l];
+          ab = arow[l];
           T sacc = FT<T>::add(a, bb);
           sacc = FT<T>::sub(sacc, ab);
           sacc = FT<T>::sub(sacc, ac);
           sacc = FT<T>::sub(sacc, bc);
           sacc = FT<T>::add(sacc, abc);
-          pred = FT<T>::add(sacc, c);
-        } else {
-          pred = FT<T>::add(FT<T>::sub(a, ac), c);
+          return FT<T>::add(sacc, c);
         }
-        T xr = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
-        if (q <= 0) {  // unpredictable value (code 0) or an undecodable block (rare)
-          xr = T(0);
-          if (q == 0 && used_u < bi.ucnt) xr = CMP ? read_unpred<T>(br, h.texp) : un[used_u];
-          else ok = false;
-          ++used_u;
-        }
+        a = brow[l];
+        return FT<T>::add(FT<T>::sub(a, ac), c);
+      };
+      // point l reconstructed as xr: the Lorenzo state, the output row and sum_dc
+      auto commit = [&](int l, T xr, T a, T bb, T ab) {
         if (HOOK && k0 + l == kinj) xr = FT<T>::flip(xr, bitinj);
         if (!REG) {
           if (NDIM == 3) {
@@ -482,6 +462,39 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
         }
         out[l] = xr;
         sum_words<T>(xr, sum);
+      };
+      // a row of central codes (the common case of a smooth field) in one comparison: every
+      // point is pred + (T)(2 * 0) * eb = pred + 0
+      if (tb.rbits && (br.peek() >> (32 - tb.rbits)) == tb.rpat) {
+        br.advance(tb.rbits);
+#pragma unroll
+        for (int l = 0; l < B2; ++l) {
+          T a, bb, ab;
+          const T pred = predict(l, a, bb, ab);
+          commit(l, FT<T>::add(pred, T(0)), a, bb, ab);
+        }
+      } else {
+        int qp = 0;  // second symbol of the pair decoded at even l
+#pragma unroll
+        for (int l = 0; l < B2; ++l) {
+          int q;
+          if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
+            if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp, CMP);
+            else q = (CMP && qp == kDefer) ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : qp;
+          } else {
+            q = br.next(tb.lut, *tb.cn, tb.syms, tb.n_live);
+          }
+          T a, bb, ab;
+          const T pred = predict(l, a, bb, ab);
+          T xr = FT<T>::add(pred, FT<T>::mul(FT<T>::fromi(2 * (q - R)), eb));
+          if (q <= 0) {  // unpredictable value (code 0) or an undecodable block (rare)
+            xr = T(0);
+            if (q == 0 && used_u < bi.ucnt) xr = CMP ? read_unpred<T>(br, h.texp) : un[used_u];
+            else ok = false;
+            ++used_u;
+          }
+          commit(l, xr, a, bb, ab);
+        }
       }
       const uint64_t ro = (uint64_t)i * si + (uint64_t)j * sj;
       if (WRITE) {

@@ -227,6 +227,22 @@ __device__ __forceinline__ void load_row_n(const T* __restrict__ row, uint32_t n
   for (int l = 0; l < B2; ++l) x[l] = (uint32_t)l < n ? __ldg(row + l) : T(0);
 }
 
+// The 3D (2D) Lorenzo prediction from its seven (three) neighbours, in the reading's order:
+// the previous point of the row (c) last.
+template <typename T, int NDIM, class Op>
+__device__ __forceinline__ T lorenzo_of(T a, T bb, T ab, T ac, T bc, T abc, T c) {
+  if (NDIM == 3) {
+    T s = Op::add(a, bb);
+    s = Op::sub(s, ab);
+    s = Op::sub(s, ac);
+    s = Op::sub(s, bc);
+    s = Op::add(s, abc);
+    return Op::add(s, c);
+  }
+  if (NDIM == 2) return Op::add(Op::sub(a, ac), c);
+  return c;
+}
+
 // One full block with compile-time edges. `blk` points at the block origin in the field,
 // `plane` at this thread's shared-memory slot 0 (3D Lorenzo only; slot stride kCta).
 // HOOK: the voting walk that also applies the soft-error records in `hk` (VOTE of quantize);
@@ -234,13 +250,22 @@ __device__ __forceinline__ void load_row_n(const T* __restrict__ row, uint32_t n
 // EDGE: a block cut by the field boundary, extents e0 x e1 x e2 at most B0 x B1 x B2 (the
 // loops keep their compile-time bounds and skip what lies outside; codes are paired by the
 // block-local index, which need not start a row on a pair).
+//
+// Central rows (the unvoted walk of full blocks): a row is first walked on the assumption that
+// every point lands in the central bin, where quantize() gives code R and x' = pred + 0
+// exactly (see central_threshold). The assumption holds for a point when |x - pred| <= D*;
+// if it holds for every point of the row in every lane of the warp, the row's codes, x' and
+// checksums are the ones quantize() would give (the codes all R, sum_q and isum_q in closed
+// form) and the row is done; otherwise the row is walked again point by point with the full
+// quantizer. Both give the same values bit for bit; only the work differs.
 template <typename T, int NDIM, int B0, int B1, int B2, int kCta, bool REG, bool ABFT, bool HOOK, bool CMP,
           bool EDGE = false>
 __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t si, uint64_t sj, bool vec2,
-                                             const T* cT, T* plane, T eb, T inv2, T Rh, uint32_t R,
+                                             const T* cT, T* plane, T eb, T inv2, T Rh, T dstar, uint32_t R,
                                              uint32_t* __restrict__ pptr, T* __restrict__ uptr, const Hist& h,
                                              const Hooks hk, T xfix, uint32_t e0 = B0, uint32_t e1 = B1,
                                              uint32_t e2 = B2) {
+  constexpr bool SPEC = !HOOK && !EDGE;
   PassRes r = {0, 0, 0, 0, 0, 0, 0, 0};
   Run run(R);
   const int n0 = EDGE ? (int)e0 : B0, n1 = EDGE ? (int)e1 : B1;
@@ -249,6 +274,18 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
 #pragma unroll
     for (int s = 0; s < B1 * B2; ++s) plane[s * kCta] = T(0);
   }
+  // regression along the row: the block's products c_l * l, primary and duplicate (the voting
+  // walk recomputes them point by point, so a disagreement is settled by a fresh evaluation)
+  constexpr int LC = NDIM == 3 ? 2 : (NDIM == 2 ? 1 : 0);
+  T clp[B2], clv[B2];
+  if (REG && !HOOK) {
+#pragma unroll
+    for (int l = 0; l < B2; ++l) {
+      clp[l] = FT<T>::mul(cT[LC], (T)l);
+      clv[l] = FT<T>::mul_v(cT[LC], (T)l);
+    }
+  }
+  const uint32_t RR = R | (R << 16);
   T brow[B2], arow[B2];  // Lorenzo: d[i][j-1][l] and d[i-1][j-1][l] (3D); d[j-1][l] (2D)
 #pragma unroll 1
   for (int i = 0; i < n0; ++i) {
@@ -272,7 +309,13 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
       const uint32_t k0 = EDGE ? (uint32_t)((i * n1 + j) * (int)e2) : (uint32_t)((i * B1 + j) * B2);
       uint32_t* prow = pptr + (uint64_t)(k0 >> 1) * 32;  // B2 is even: rows start on a pair
       T* urow = uptr + (uint64_t)k0 * 32;
-      uint32_t lowc = 0;
+      // the input words' checksums (Algorithm 1's check of the input, verified at the block end)
+#pragma unroll
+      for (int l = 0; l < B2; ++l) {
+        if (EDGE && l >= (int)e2) break;
+        if (HOOK && k0 + l == hk.kfix) x[l] = xfix;
+        if (ABFT) cks_words<T>(x[l], k0 + l, r.sw, r.isw);
+      }
       // regression: (b0*i + b1*j) of this row, twice (primary and duplicate)
       T ra = T(0), rv = T(0);
       if (REG) {
@@ -285,92 +328,136 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
         }
       }
       T* plrow = plane + (uint64_t)j * B2 * kCta;
-      T c = T(0), ac = T(0), bc = T(0), abc = T(0);
+      bool done = false;
+      if (SPEC) {
+        T xs[B2], as[B2];
+        bool ok = true;
+        T c = T(0), ac = T(0), bc = T(0), abc = T(0);
 #pragma unroll
-      for (int l = 0; l < B2; ++l) {
-        if (EDGE && l >= (int)e2) break;
-        const uint32_t k = k0 + l;
-        T v = x[l];
-        if (HOOK && k == hk.kfix) v = xfix;
-        if (ABFT) cks_words<T>(v, k, r.sw, r.isw);
-        T a = T(0), bb = T(0), ab = T(0);
-        if (!REG) {
-          if (NDIM == 3) {
-            a = plrow[l * kCta];
-            bb = brow[l];
-            ab = arow[l];
-          } else if (NDIM == 2) {
-            a = brow[l];
+        for (int l = 0; l < B2; ++l) {
+          T a = T(0), bb = T(0), ab = T(0);
+          if (!REG) {
+            if (NDIM == 3) {
+              a = plrow[l * kCta];
+              bb = brow[l];
+              ab = arow[l];
+            } else if (NDIM == 2) {
+              a = brow[l];
+            }
           }
-        }
-        const T L = (T)l;
-        const T pred = dup_pred<T, ABFT, HOOK>(
-            [&] {
-              if (REG) {
-                const int lc = NDIM == 3 ? 2 : (NDIM == 2 ? 1 : 0);
-                if (NDIM == 1) return FT<T>::add(FT<T>::mul(cT[0], L), cT[1]);
-                return FT<T>::add(FT<T>::add(ra, FT<T>::mul(cT[lc], L)), cT[lc + 1]);
-              }
-              if (NDIM == 3) {
-                T s = FT<T>::add(a, bb);
-                s = FT<T>::sub(s, ab);
-                s = FT<T>::sub(s, ac);
-                s = FT<T>::sub(s, bc);
-                s = FT<T>::add(s, abc);
-                return FT<T>::add(s, c);
-              }
-              if (NDIM == 2) return FT<T>::add(FT<T>::sub(a, ac), c);
-              return c;
-            },
-            [&] {
-              if (REG) {
-                const int lc = NDIM == 3 ? 2 : (NDIM == 2 ? 1 : 0);
-                if (NDIM == 1) return FT<T>::add_v(FT<T>::mul_v(cT[0], L), cT[1]);
-                return FT<T>::add_v(FT<T>::add_v(rv, FT<T>::mul_v(cT[lc], L)), cT[lc + 1]);
-              }
-              if (NDIM == 3) {
-                T s = FT<T>::add_v(a, bb);
-                s = FT<T>::sub_v(s, ab);
-                s = FT<T>::sub_v(s, ac);
-                s = FT<T>::sub_v(s, bc);
-                s = FT<T>::add_v(s, abc);
-                return FT<T>::add_v(s, c);
-              }
-              if (NDIM == 2) return FT<T>::add_v(FT<T>::sub_v(a, ac), c);
-              return c;
-            },
-            HOOK && k == hk.kp, hk.bitp, r.dup, r.mm);
-        T xr;
-        const uint32_t code = quantize<T, ABFT, HOOK, CMP>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr,
-                                                           r.dup, r.mm, hk.texp);
-        if (EDGE) {
-          if (k & 1) pptr[(uint64_t)(k >> 1) * 32] = lowe | (code << 16);
-          else lowe = code;
-        } else {
-          if (l & 1) prow[(l >> 1) * 32] = lowc | (code << 16);
-          else lowc = code;
-        }
-        if (!code) urow[l * 32] = v;
-        r.nun += (code == 0u);
-        if (ABFT) {
-          r.sq += code;
-          mad_wide(r.isq, code, k + 1);
-          sum_words<T>(xr, r.sdc);
-        }
-        run.push(code, h);
-        if (!REG) {
-          if (NDIM == 3) {
-            plrow[l * kCta] = xr;
-            arow[l] = a;
+          T pred;
+          if (REG) pred = NDIM == 1 ? FT<T>::add(clp[l], cT[1]) : FT<T>::add(FT<T>::add(ra, clp[l]), cT[LC + 1]);
+          else pred = lorenzo_of<T, NDIM, OpRN<T>>(a, bb, ab, ac, bc, abc, c);
+          if (ABFT) {
+            T pv;
+            if (REG) pv = NDIM == 1 ? FT<T>::add_v(clv[l], cT[1]) : FT<T>::add_v(FT<T>::add_v(rv, clv[l]), cT[LC + 1]);
+            else pv = lorenzo_of<T, NDIM, OpV<T>>(a, bb, ab, ac, bc, abc, c);
+            r.mm |= FT<T>::diffbits(pred, pv);
+          }
+          ok = ok && (FT<T>::absv(FT<T>::sub(x[l], pred)) <= dstar);
+          const T xr = FT<T>::add(pred, T(0));
+          if (ABFT) r.mm |= FT<T>::diffbits(xr, FT<T>::add_v(pred, T(0)));
+          xs[l] = xr;
+          as[l] = a;
+          if (!REG) {
             ac = a;
             bc = bb;
             abc = ab;
-            brow[l] = xr;
-          } else if (NDIM == 2) {
-            ac = a;
-            brow[l] = xr;
+            c = xr;
           }
-          c = xr;
+        }
+        done = __all_sync(__activemask(), ok);
+        if (done) {
+#pragma unroll
+          for (int l = 0; l < B2; ++l) {
+            if (ABFT) sum_words<T>(xs[l], r.sdc);
+            if (l & 1) prow[(l >> 1) * 32] = RR;
+            if (!REG) {
+              if (NDIM == 3) {
+                plrow[l * kCta] = xs[l];
+                arow[l] = as[l];
+                brow[l] = xs[l];
+              } else if (NDIM == 2) {
+                brow[l] = xs[l];
+              }
+            }
+          }
+          if (ABFT) {
+            r.sq += (uint32_t)B2 * R;
+            r.isq += (unsigned long long)R * ((unsigned long long)B2 * (k0 + 1) + (uint32_t)(B2 * (B2 - 1) / 2));
+          }
+          run.n += B2;
+        }
+      }
+      if (!done) {
+        uint32_t lowc = 0;
+        T c = T(0), ac = T(0), bc = T(0), abc = T(0);
+#pragma unroll
+        for (int l = 0; l < B2; ++l) {
+          if (EDGE && l >= (int)e2) break;
+          const uint32_t k = k0 + l;
+          const T v = x[l];
+          T a = T(0), bb = T(0), ab = T(0);
+          if (!REG) {
+            if (NDIM == 3) {
+              a = plrow[l * kCta];
+              bb = brow[l];
+              ab = arow[l];
+            } else if (NDIM == 2) {
+              a = brow[l];
+            }
+          }
+          const T L = (T)l;
+          const T pred = dup_pred<T, ABFT, HOOK>(
+              [&] {
+                if (REG) {
+                  const T cl = HOOK ? FT<T>::mul(cT[LC], L) : clp[l];
+                  if (NDIM == 1) return FT<T>::add(cl, cT[1]);
+                  return FT<T>::add(FT<T>::add(ra, cl), cT[LC + 1]);
+                }
+                return lorenzo_of<T, NDIM, OpRN<T>>(a, bb, ab, ac, bc, abc, c);
+              },
+              [&] {
+                if (REG) {
+                  const T cl = HOOK ? FT<T>::mul_v(cT[LC], L) : clv[l];
+                  if (NDIM == 1) return FT<T>::add_v(cl, cT[1]);
+                  return FT<T>::add_v(FT<T>::add_v(rv, cl), cT[LC + 1]);
+                }
+                return lorenzo_of<T, NDIM, OpV<T>>(a, bb, ab, ac, bc, abc, c);
+              },
+              HOOK && k == hk.kp, hk.bitp, r.dup, r.mm);
+          T xr;
+          const uint32_t code = quantize<T, ABFT, HOOK, CMP>(v, pred, eb, inv2, Rh, R, HOOK && k == hk.kr, hk.bitr, xr,
+                                                             r.dup, r.mm, hk.texp);
+          if (EDGE) {
+            if (k & 1) pptr[(uint64_t)(k >> 1) * 32] = lowe | (code << 16);
+            else lowe = code;
+          } else {
+            if (l & 1) prow[(l >> 1) * 32] = lowc | (code << 16);
+            else lowc = code;
+          }
+          if (!code) urow[l * 32] = v;
+          r.nun += (code == 0u);
+          if (ABFT) {
+            r.sq += code;
+            mad_wide(r.isq, code, k + 1);
+            sum_words<T>(xr, r.sdc);
+          }
+          run.push(code, h);
+          if (!REG) {
+            if (NDIM == 3) {
+              plrow[l * kCta] = xr;
+              arow[l] = a;
+              ac = a;
+              bc = bb;
+              abc = ab;
+              brow[l] = xr;
+            } else if (NDIM == 2) {
+              ac = a;
+              brow[l] = xr;
+            }
+            c = xr;
+          }
         }
       }
     }
@@ -584,9 +671,26 @@ struct Counters {
   }
 };
 
+// The largest |x - pred| (of the dtype) whose point certainly quantizes into the central bin and
+// passes the bound check, i.e. for which quantize() returns code R and x' = pred + 0: the code
+// is R iff round(round(|d| * inv2) + 1/2) < 1, i.e. round(|d| * inv2) < 1/2 - u/2 (u the ulp
+// of [1/2, 1); the tie at 1 - u/2 rounds to the even 1), and the check |x - x'| <= eb then
+// compares |d| itself (x' = pred, or +0 for pred = -0, leaves |x - x'| = |d|). round(d * inv2)
+// never decreases with d, so one threshold D* <= eb with round(D* * inv2) below that limit
+// covers every smaller |d|. Stepping down from eb takes a few ulps; -1 (never) if it does not.
+template <typename T>
+__device__ __forceinline__ T central_threshold(T eb, T inv2) {
+  typedef typename Bitsof<T>::U U;
+  const T lim = sizeof(T) == 4 ? T(0.5f - 0x1p-25f) : T(0.5 - 0x1p-54);
+  T d = eb;
+  for (int it = 0; it < 64 && d > T(0) && !(FT<T>::mul(d, inv2) < lim); ++it) d = Bitsof<T>::val(Bitsof<T>::raw(d) - (U)1);
+  return (d > T(0) && d <= eb && FT<T>::mul(d, inv2) < lim) ? d : T(-1);
+}
+
 template <typename T>
 struct Consts {
   T eb, inv2, Rh;
+  T dstar;  // central_threshold(eb, inv2)
   float noise;
   int texp;  // compact encoding: truncation exponent of unpredictable values, else kNoTrunc
   __device__ __forceinline__ Consts(double ebd, const Geo& g, int ndim) {
@@ -595,6 +699,7 @@ struct Consts {
     texp = g.enc ? bound_exponent<T>(eb) : kNoTrunc;
     if (sizeof(T) == 4) inv2 = (T)__double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, ebd)));
     else inv2 = (T)__ddiv_rn(1.0, __dmul_rn(2.0, ebd));
+    dstar = central_threshold<T>(eb, inv2);
     Rh = FT<T>::sub(FT<T>::fromi((int)R), T(0.5));
     // E|sum of n uniform(-1,1)| for the n = 7 / 3 / 1 Lorenzo terms (exact Irwin-Hall values)
     const float kappa = ndim == 3 ? (float)(113149.0 / 92160.0) : (ndim == 2 ? (float)(13.0 / 16.0) : 0.5f);
@@ -763,10 +868,11 @@ __device__ __forceinline__ PassRes fast_dispatch(bool reg, const T* blk, uint64_
                                                  T* uptr, const Hist& h, const Hooks& hk, T xfix, const uint32_t* e) {
   if (reg)
     return fast_pass<T, NDIM, B0, B1, B2, 128, true, ABFT, HOOK, CMP, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2,
-                                                                       K.Rh, R, cptr, uptr, h, hk, xfix, e[0], e[1],
-                                                                       e[2]);
-  return fast_pass<T, NDIM, B0, B1, B2, 128, false, ABFT, HOOK, CMP, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2, K.Rh,
-                                                                      R, cptr, uptr, h, hk, xfix, e[0], e[1], e[2]);
+                                                                       K.Rh, K.dstar, R, cptr, uptr, h, hk, xfix,
+                                                                       e[0], e[1], e[2]);
+  return fast_pass<T, NDIM, B0, B1, B2, 128, false, ABFT, HOOK, CMP, EDGE>(blk, si, sj, vec2, cT, plane, K.eb, K.inv2,
+                                                                        K.Rh, K.dstar, R, cptr, uptr, h, hk, xfix,
+                                                                        e[0], e[1], e[2]);
 }
 
 // One full block of a compile-time shape (B0 x B1 x B2, leading 1s below 3D); edge blocks
