@@ -134,6 +134,7 @@ int make_geo(const sdcsz_params* p, Geo* g) {
   g->enc = (int)(p->encoding & 1);
   g->lossless = (int)((p->encoding >> 1) & 1);
   g->e = p->eb;
+  geo_rcp(g);
   return SDCSZ_OK;
 }
 

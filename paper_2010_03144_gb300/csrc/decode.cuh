@@ -662,6 +662,36 @@ __device__ bool group_scan(const uint8_t* s, const Hdr& h, uint64_t gid, uint64_
   return !sm.bad;
 }
 
+// Group gid's data on its way to L2, a group ahead of its decoding: its block-table, unpredictable-count
+// and sum_dc entries (fixed places; a line per thread) and, by warp 0 after reading the group
+// table, its payload and coefficient ranges. Every address is clamped to the stream.
+__device__ __forceinline__ void prefetch_group(const uint8_t* s, uint64_t nbytes, const Hdr& h, uint64_t gid,
+                                               uint64_t ngroups) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint64_t b0 = gid * kGroup;
+  {
+    uint64_t off;
+    if (tid < 4) off = h.L.sizes + 2 * b0 + 128 * tid;
+    else if (tid < 8) off = h.L.ucounts + 2 * b0 + 128 * (tid - 4);
+    else if (tid < 24 && h.g.abft) off = h.L.sumdc + 8 * b0 + 128 * (tid - 8);
+    else off = nbytes;
+    if (off < nbytes) prefetch_l2(s + off);
+  }
+  if (tid >= 32) return;
+  const uint8_t* gp = s + h.L.groups + 24 * gid;
+  const uint64_t p0 = ld_u64(gp), r0 = ld_u64(gp + 16);
+  const bool last = gid + 1 >= ngroups;
+  const uint64_t p1 = last ? h.payload_bytes : ld_u64(gp + 24), r1 = last ? h.n_reg : ld_u64(gp + 40);
+  auto range = [&](uint64_t lo, uint64_t hi, uint64_t floor_, uint64_t ceil_) {
+    lo = max(lo, floor_);
+    hi = min(min(hi, ceil_), lo + 65536);  // a group's payload rarely exceeds a few KB
+    for (uint64_t a = (lo & ~uint64_t(127)) + 128 * (uint64_t)lane; a < hi; a += 32 * 128) prefetch_l2(s + a);
+  };
+  if (p0 <= p1) range(h.L.payload + p0, h.L.payload + p1, h.L.payload, nbytes);
+  const uint64_t cs = (uint64_t)(h.g.ndim + 1) * (h.g.dtype ? 8 : 4);
+  if (!h.g.enc && r0 <= r1 && r1 <= h.n_reg) range(h.L.coef + cs * r0, h.L.coef + cs * r1, h.L.coef, nbytes);
+}
+
 struct Acc {
   unsigned long long fix = 0, bad = 0, viol = 0;
   double maxerr = 0.0;
@@ -680,8 +710,8 @@ struct Acc {
 };
 
 __device__ __forceinline__ bool is_full(const Geo& g, uint64_t b) {
-  const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
-  const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+  uint64_t c0, c1, c2;
+  block_coords(g, b, c0, c1, c2);
   return (c0 + 1) * g.B[0] <= g.d[0] && (c1 + 1) * g.B[1] <= g.d[1] && (c2 + 1) * g.B[2] <= g.d[2];
 }
 
@@ -764,6 +794,98 @@ __device__ __forceinline__ bool place_block(const uint8_t* __restrict__ s, const
   const bool reg = (*reinterpret_cast<const uint32_t*>(s + h.L.bitmap + 4 * (b / 32)) >> (b % 32)) & 1u;
   bi.reg_idx = reg ? (int64_t)rg : -1;
   return !(pay + bi.size > h.payload_bytes || un + bi.ucnt > h.n_unpred || (reg && rg >= h.n_reg));
+}
+
+// Warp items of the fast decoder: item i is the 32 blocks [32 i, 32 i + 32), one per lane, all in
+// group i / 8. The warp places them from the group's table entry and a warp scan of the group's
+// block table (lane L sums entries 8L .. 8L+7, one 16-byte load each of the payload sizes and
+// unpredictable counts; the regression flags by popcount of the group's 8 bitmap words), and
+// checks the group's entry against the next one (as the CTA scan of a whole group does).
+// Returns false, with a format error, when they disagree; then no block of the item is placed.
+__device__ __forceinline__ bool warp_place(const uint8_t* __restrict__ s, const Hdr& h, uint64_t item,
+                                           uint64_t ngroups, State* st, BlockIn* out) {
+  const Geo& g = h.g;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t G = item >> 3, q0 = G * kGroup;
+  const uint32_t m = (uint32_t)(item & 7);
+  const uint32_t nblk = (uint32_t)min((uint64_t)kGroup, g.nb - q0);
+  uint4 sz = make_uint4(0u, 0u, 0u, 0u), uc = sz;
+  if (8 * lane < nblk) {
+    sz = __ldg(reinterpret_cast<const uint4*>(s + h.L.sizes + 2 * q0) + lane);
+    uc = __ldg(reinterpret_cast<const uint4*>(s + h.L.ucounts + 2 * q0) + lane);
+  }
+  const uint32_t lim = nblk > 8 * lane ? min(8u, nblk - 8 * lane) : 0u;  // entries of this lane's chunk in the group
+  auto entry = [](const uint4& v, uint32_t e) {  // 16-bit entry e (< 8) of a chunk
+    const uint32_t w = e < 2 ? v.x : (e < 4 ? v.y : (e < 6 ? v.z : v.w));
+    return (w >> (16 * (e & 1))) & 0xffffu;
+  };
+  auto head = [&](const uint4& v, uint32_t n) {  // sum of the first n (<= 8) entries
+    uint32_t t = 0;
+#pragma unroll
+    for (uint32_t e = 0; e < 8; ++e)
+      if (e < n) t += entry(v, e);
+    return t;
+  };
+  const uint32_t ssum = head(sz, lim), usum = head(uc, lim);
+  uint32_t bw = 0;
+  if (lane < 8 && 32 * lane < nblk) {
+    bw = __ldg(reinterpret_cast<const uint32_t*>(s + h.L.bitmap) + q0 / 32 + lane);
+    const uint32_t nb_w = nblk - 32 * lane;
+    if (nb_w < 32) bw &= (1u << nb_w) - 1u;
+  }
+  uint32_t si = ssum, ui = usum, ri = __popc(bw);  // inclusive warp scans
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(0xffffffffu, si, o), b2 = __shfl_up_sync(0xffffffffu, ui, o),
+                   c = __shfl_up_sync(0xffffffffu, ri, o);
+    if (lane >= (uint32_t)o) {
+      si += a;
+      ui += b2;
+      ri += c;
+    }
+  }
+  const uint8_t* gp = s + h.L.groups + 24 * G;
+  const unsigned long long base[3] = {ld_u64(gp), ld_u64(gp + 8), ld_u64(gp + 16)};
+  const bool last = G + 1 >= ngroups;
+  const unsigned long long next[3] = {last ? h.payload_bytes : ld_u64(gp + 24), last ? h.n_unpred : ld_u64(gp + 32),
+                                      last ? h.n_reg : ld_u64(gp + 40)};
+  const uint32_t tot_s = __shfl_sync(0xffffffffu, si, 31), tot_u = __shfl_sync(0xffffffffu, ui, 31),
+                 tot_r = __shfl_sync(0xffffffffu, ri, 31);
+  bool bad = base[0] + tot_s != next[0] || base[1] + tot_u != next[1] || base[2] + tot_r != next[2] ||
+             (G == 0 && (base[0] | base[1] | base[2]) != 0);
+  if (bad) {
+    if (lane == 0) atomicOr(&st->error, ERR_FORMAT);
+    return false;
+  }
+  // this lane's block: entry e = 32 m + lane of the group, in the chunk of lane e / 8
+  const uint32_t e = 32 * m + lane, c = e >> 3, pos = e & 7;
+  uint4 csz, cuc;
+  csz.x = __shfl_sync(0xffffffffu, sz.x, c);
+  csz.y = __shfl_sync(0xffffffffu, sz.y, c);
+  csz.z = __shfl_sync(0xffffffffu, sz.z, c);
+  csz.w = __shfl_sync(0xffffffffu, sz.w, c);
+  cuc.x = __shfl_sync(0xffffffffu, uc.x, c);
+  cuc.y = __shfl_sync(0xffffffffu, uc.y, c);
+  cuc.z = __shfl_sync(0xffffffffu, uc.z, c);
+  cuc.w = __shfl_sync(0xffffffffu, uc.w, c);
+  const uint32_t sx = __shfl_sync(0xffffffffu, si - ssum, c), ux = __shfl_sync(0xffffffffu, ui - usum, c);
+  const uint32_t word = __shfl_sync(0xffffffffu, bw, m), rx = __shfl_sync(0xffffffffu, ri - __popc(bw), m);
+  BlockIn& bi = *out;
+  bi.b = 32 * item + lane;
+  bi.pay_off = base[0] + sx + head(csz, pos);
+  bi.un_off = base[1] + ux + head(cuc, pos);
+  bi.size = entry(csz, pos);
+  bi.ucnt = entry(cuc, pos);
+  const bool reg = (word >> lane) & 1u;
+  const unsigned long long rg = base[2] + rx + __popc(word & ((1u << lane) - 1u));
+  bi.reg_idx = reg ? (int64_t)rg : -1;
+  return true;
+}
+
+__device__ __forceinline__ uint64_t warp_pull(unsigned long long* q) {
+  unsigned long long v = 0;
+  if ((threadIdx.x & 31) == 0) v = atomicAdd(q, 1ull);
+  return __shfl_sync(0xffffffffu, v, 0);
 }
 
 // Generic kernel: edge blocks (or all blocks when `all`).
@@ -971,30 +1093,40 @@ __device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, u
   const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
   const uint64_t ngroups = (g.nb + kGroup - 1) / kGroup;
   Acc acc;
-  for (uint64_t gid = cta_pull(&st->queue[0]); gid < ngroups; gid = cta_pull(&st->queue[0])) {
-    const uint64_t b0 = gid * kGroup;
-    const uint32_t nblk = (uint32_t)min((uint64_t)kGroup, g.nb - b0);
-    if (!group_scan(s, h, gid, ngroups, sm, st)) {
-      if (status)
-        for (uint32_t t = threadIdx.x; t < nblk; t += blockDim.x) status[b0 + t] = SDCSZ_BLOCK_BAD;
+  // warp items (32 blocks) from the queue, one ahead: the next item's block-table lines are on
+  // their way to L2 while this one is decoded; no barrier between the CTA's warps
+  const uint64_t nitems = (g.nb + 31) / 32;
+  const uint32_t lane = threadIdx.x & 31;
+  uint64_t item = warp_pull(&st->queue[0]);
+  while (item < nitems) {
+    const uint64_t nxt = warp_pull(&st->queue[0]);
+    if (nxt < nitems && lane < 3) {
+      const uint64_t q0 = (nxt >> 3) * kGroup;
+      const uint64_t off = lane == 0 ? h.L.sizes + 2 * 32 * nxt : (lane == 1 ? h.L.ucounts + 2 * 32 * nxt
+                                                                            : h.L.groups + 24 * (nxt >> 3));
+      (void)q0;
+      if (off < nbytes) prefetch_l2(s + off);
+    }
+    BlockIn bi;
+    const bool placed = warp_place(s, h, item, ngroups, st, &bi);
+    const uint64_t b = 32 * item + lane;
+    if (!placed) {
+      if (status && b < g.nb) status[b] = SDCSZ_BLOCK_BAD;
+      item = nxt;
       continue;
     }
-    for (uint32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
-      const uint64_t b = b0 + t;
-      const uint64_t c2 = b % g.nbd[2], tq = b / g.nbd[2];
-      const uint64_t c1 = tq % g.nbd[1], c0 = tq / g.nbd[1];
-      if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) continue;
-      const uint64_t bo = (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
+    bool full = false;
+    uint64_t bo = 0;
+    if (b < g.nb) {
+      uint64_t c0, c1, c2;
+      block_coords(g, b, c0, c1, c2);
+      full = (c0 + 1) * B0 <= g.d[0] && (c1 + 1) * B1 <= g.d[1] && (c2 + 1) * B2 <= g.d[2];
+      bo = (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
+    }
+    if (full) {
       T* out = WRITE ? field + bo : nullptr;
       const T* org = (!WRITE && orig) ? orig + bo : nullptr;
-      BlockIn bi;
-      bi.b = b;
-      bi.pay_off = sm.off[t][0];
-      bi.un_off = sm.off[t][1];
-      const bool reg = sm.rg[t] != 0;
-      bi.reg_idx = reg ? (int64_t)sm.off[t][2] : -1;
-      bi.size = sm.sz[t];
-      bi.ucnt = sm.uc[t];
+      const bool reg = bi.reg_idx >= 0;
       uint32_t kinj, bitinj;
       find_inj(flips, nflips, b, &kinj, &bitinj);
       // The unchecked reader consumes at most 24 bits per point whatever the data (in the compact
@@ -1003,21 +1135,25 @@ __device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, u
       // worst case could reach the end of the stream take the bounds-checked reader.
       const uint64_t worst = CMP ? (3ull + sizeof(T)) * (B0 * B1 * B2) + 19 : 3ull * (B0 * B1 * B2);
       const bool safe = (uint64_t)(lim - (s + h.L.payload)) >= bi.pay_off + worst + 16;
-      const uint8_t stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv,
-                                                     double* me) {
-        if (!safe)
-          return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone, bitinj, sum, nv,
-                                         me);
-        if (first && kinj != kNone)
-          return fast_dispatch<T, NDIM, B0, B1, B2, true, WRITE, CMP>(reg, s, lim, h, bi, tb, plane, out, org, si, sj,
-                                                                      vec2,
-                                                                 kinj, bitinj, sum, nv, me);
-        return fast_dispatch<T, NDIM, B0, B1, B2, false, WRITE, CMP>(reg, s, lim, h, bi, tb, plane, out, org, si, sj,
-                                                                      vec2,
-                                                                kNone, 0, sum, nv, me);
-      }, acc);
+      const bool in_range = !(bi.pay_off + bi.size > h.payload_bytes || bi.un_off + bi.ucnt > h.n_unpred ||
+                              (reg && (uint64_t)bi.reg_idx >= h.n_reg));
+      uint8_t stv = SDCSZ_BLOCK_BAD;
+      if (in_range)
+        stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv, double* me) {
+          if (!safe)
+            return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone,
+                                           bitinj, sum, nv, me);
+          if (first && kinj != kNone)
+            return fast_dispatch<T, NDIM, B0, B1, B2, true, WRITE, CMP>(reg, s, lim, h, bi, tb, plane, out, org, si, sj,
+                                                                        vec2, kinj, bitinj, sum, nv, me);
+          return fast_dispatch<T, NDIM, B0, B1, B2, false, WRITE, CMP>(reg, s, lim, h, bi, tb, plane, out, org, si,
+                                                                       sj, vec2, kNone, 0, sum, nv, me);
+        }, acc);
+      else
+        ++acc.bad;
       if (status) status[b] = stv;
     }
+    item = nxt;
   }
   acc.commit(st);
 }

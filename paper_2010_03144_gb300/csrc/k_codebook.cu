@@ -207,14 +207,17 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
     const uint32_t sym = (uint32_t)(keys[r] & 0xffffu);
     const uint32_t code = first_code[len] + (r - first_index[len]);
     w.codebook[sym] = (code << 5) | len;
-    put_u16(out, L.table + 4 * (kMaxLen + 1) + 2 * (uint64_t)r, (uint16_t)sym);
+    if (out) put_u16(out, L.table + 4 * (kMaxLen + 1) + 2 * (uint64_t)r, (uint16_t)sym);
   }
-  if (tid <= (uint32_t)kMaxLen) put_u32(out, L.table + 4 * tid, tid == 0 ? 0u : cnt[tid]);
+  if (out && tid <= (uint32_t)kMaxLen) put_u32(out, L.table + 4 * tid, tid == 0 ? 0u : cnt[tid]);
   if (tid == 0) {
     st->n_live = n;
     st->L = L;
     st->payload_bytes = 0;
     st->total_bytes = L.payload;
+  }
+  // no output: the codebook and the layout only (a shard of a field whose header another writes)
+  if (tid == 0 && out) {
     // header (128 bytes, little-endian)
     for (int q = 0; q < kHeaderBytes; ++q) out[q] = 0;
     out[0] = 'S'; out[1] = 'D'; out[2] = 'S'; out[3] = 'Z';

@@ -86,14 +86,30 @@ struct Extra {
   int texp;
 };
 
+// Code pairs reach the encoder through a ring of kRing batches of 8 words per thread in shared
+// memory (word q of slot r of thread t at ((r * 8 + q) * blockDim + t)), filled by cp.async:
+// each thread copies exactly the words it later reads, so its own wait suffices, and
+// kRing - 1 batches are in flight while one is encoded.
+constexpr uint32_t kRing = 3;
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst_smem, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // One pass over a block's codes: the Huffman bits into `slot` (stream byte order, the last
 // word zero padded), the code checksums (ABFT), the unpredictable count and the first
 // kPosKept unpredictable positions. With FIX, code kfix reads as vfix. CMP: compact encoding.
-// R is the central code (prediction within half a bin).
+// R is the central code (prediction within half a bin). ring: this thread's staging ring
+// (nullptr: the pairs are loaded from memory directly).
 template <bool ABFT, bool FIX, bool CMP, typename T>
 __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, uint32_t P, uint32_t* __restrict__ slot,
                                                const Codebook& cb, uint32_t cw0, uint32_t R, uint32_t kfix,
-                                               uint32_t vfix, const Extra<T>& ex) {
+                                               uint32_t vfix, const Extra<T>& ex, uint32_t* ring = nullptr) {
   EncRes e;
   e.bits = 0;
   e.nun = 0;
@@ -202,9 +218,30 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) w[q] = (base + q < P2) ? pp[32 * (uint64_t)(base + q)] : 0u;
   };
-  load8(0, wq);
+  const uint32_t nthr = blockDim.x;
+  auto stage8 = [&](uint32_t base) {  // batch base / 8 into its ring slot (words past P2 are not read)
+    uint32_t* r = ring + (uint64_t)((base >> 3) % kRing) * 8 * nthr;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (base + q < P2) cp_async4(r + (uint64_t)q * nthr, pp + 32 * (uint64_t)(base + q));
+    cp_async_commit();
+  };
+  if (ring) {
+#pragma unroll
+    for (uint32_t t = 0; t < kRing - 1; ++t) stage8(8 * t);
+  } else {
+    load8(0, wq);
+  }
   for (uint32_t k8 = 0; k8 < P2; k8 += 8) {
-    if (k8 + 8 < P2) load8(k8 + 8, wn);
+    if (ring) {
+      stage8(k8 + 8 * (kRing - 1));  // an empty group past the end keeps the count uniform
+      cp_async_wait<kRing - 1>();
+      const uint32_t* r = ring + (uint64_t)((k8 >> 3) % kRing) * 8 * nthr;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) wq[q] = r[(uint64_t)q * nthr];
+    } else if (k8 + 8 < P2) {
+      load8(k8 + 8, wn);
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const uint32_t k2 = k8 + 4 * h;
@@ -227,9 +264,12 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
           if (k2 + q < P2) put2(wq[4 * h + q] & 0xffffu, wq[4 * h + q] >> 16, 2 * (k2 + q));
       }
     }
+    if (!ring) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) wq[q] = wn[q];
+      for (int q = 0; q < 8; ++q) wq[q] = wn[q];
+    }
   }
+  if (ring) cp_async_wait<0>();
   if (P & 1) put(pp[32 * (uint64_t)P2] & 0xffffu, P - 1);
   if (nacc) slot[wi] = __byte_perm((uint32_t)(acc << (32 - nacc)), 0, 0x0123);
   return e;
@@ -252,7 +292,7 @@ __host__ __device__ inline uint64_t slot_words_of(const Geo& g) {
 // ---------------------------------------------------------------- K4a
 template <typename T, bool ABFT, bool CMP>
 __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t* __restrict__ out,
-                                             const uint32_t* cb_s, uint64_t b) {
+                                             const uint32_t* cb_s, uint64_t b, uint32_t* ring) {
   State* st = w.st;
   const Layout L = st->L;
   const uint32_t lane = threadIdx.x & 31;
@@ -277,7 +317,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
       ex.up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
       ex.texp = bound_exponent<T>((T)st->eb);
     }
-    EncRes e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, g.R, 0u, 0u, ex);
+    EncRes e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, g.R, 0u, 0u, ex, ring);
     uint32_t kfix = 0xffffffffu, vfix = 0;
     bool bad = false;
     if (ABFT && (e.sq != w.sum_q[b] || e.isq != w.isum_q[b])) {
@@ -348,10 +388,11 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
 template <typename T, bool ABFT, bool CMP>
 __global__ void __launch_bounds__(128) k_encode_blocks(Geo g, Ws w, uint8_t* __restrict__ out) {
   __shared__ uint32_t cb_s[kCbWindow];
+  __shared__ uint32_t ring_s[kRing * 8 * 128];
   if (cta_failed(w.st)) return;
   cb_load(cb_s, g, w);
   __syncthreads();
-  encode_block<T, ABFT, CMP>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  encode_block<T, ABFT, CMP>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, ring_s + threadIdx.x);
 }
 
 // ---------------------------------------------------------------- K4b
@@ -376,6 +417,13 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   L.payload = align16(L.unpred + (g.enc ? 0 : s_dt * n_unpred));
   uint32_t bytes = 0, nun = 0;
   bool reg = false;
+  // the first 64 bytes of the block's payload slot, loaded with its sizes: the slot does not
+  // depend on the scan, only where it goes does
+  const uint32_t n4 = (uint32_t)(slot_words_of(g) / 4);  // 16-byte pieces in a slot
+  const uint4* src4 = reinterpret_cast<const uint4*>(w.etmp + b * slot_words_of(g));
+  uint4 head[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) head[q] = (active && (uint32_t)q < n4) ? src4[q] : make_uint4(0u, 0u, 0u, 0u);
   if (active) {
     bytes = *reinterpret_cast<const uint16_t*>(out + L.sizes + 2 * b);
     nun = *reinterpret_cast<const uint16_t*>(out + L.ucounts + 2 * b);
@@ -471,20 +519,23 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
     atomicOr(&st->error, ERR_CAPACITY);
     return;
   }
-  // The slot is read four words (16 bytes, aligned) at a time, and the previous word carried.
-  const uint4* src4 = reinterpret_cast<const uint4*>(w.etmp + b * slot_words_of(g));
+  // The slot is read 64 bytes (four aligned 16-byte loads, issued together) at a time, the first
+  // 64 already in `head`, and the previous word carried.
   const uint32_t r = (uint32_t)(lo & 3), nw = (bytes + 3) / 4;
   const uint64_t wa0 = lo - r;
   const uint32_t nout = (uint32_t)((hi - wa0 + 3) >> 2);  // stream words touched
   uint32_t prev = 0;
-  uint4 qn = nw ? src4[0] : make_uint4(0u, 0u, 0u, 0u);  // the next 16 bytes, loaded one step ahead
-  for (uint32_t i0 = 0; i0 < nout; i0 += 4) {
-    const uint4 q = qn;
-    if (i0 + 4 < nw) qn = src4[(i0 >> 2) + 1];
-    else qn = make_uint4(0u, 0u, 0u, 0u);
-    const uint32_t cur[4] = {q.x, q.y, q.z, q.w};
+  for (uint32_t i0 = 0; i0 < nout; i0 += 16) {
+    uint4 q4[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t pi = (i0 >> 2) + q;
+      q4[q] = i0 == 0 ? head[q] : ((pi < n4 && 4 * pi < nw) ? src4[pi] : make_uint4(0u, 0u, 0u, 0u));
+    }
+    const uint32_t cur[16] = {q4[0].x, q4[0].y, q4[0].z, q4[0].w, q4[1].x, q4[1].y, q4[1].z, q4[1].w,
+                              q4[2].x, q4[2].y, q4[2].z, q4[2].w, q4[3].x, q4[3].y, q4[3].z, q4[3].w};
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
       const uint32_t i = i0 + t;
       if (i >= nout) break;
       const uint32_t c = i < nw ? cur[t] : 0u;
@@ -498,7 +549,7 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_encode_assemble(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
+__global__ void __launch_bounds__(256, 3) k_encode_assemble(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap) {
   if (cta_failed(w.st)) return;
   assemble_group<T>(g, w, out, cap, blockIdx.x);
 }
@@ -507,6 +558,7 @@ __global__ void __launch_bounds__(256) k_encode_assemble(Geo g, Ws w, uint8_t* _
 template <typename T, bool ABFT>
 __global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
   __shared__ uint32_t cb_s[kCbWindow];
+  __shared__ uint32_t ring_s[kRing * 8 * 128];
   __shared__ Job s_job;
   batch_loop(
       a, s_job,
@@ -515,8 +567,12 @@ __global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
         __syncthreads();
       },
       [&](uint64_t it) {
-        if (s_job.g.enc) encode_block<T, ABFT, true>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x);
-        else encode_block<T, ABFT, false>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x);
+        if (s_job.g.enc)
+          encode_block<T, ABFT, true>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x,
+                                      ring_s + threadIdx.x);
+        else
+          encode_block<T, ABFT, false>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x,
+                                       ring_s + threadIdx.x);
       },
       NoOp());
 }

@@ -144,10 +144,7 @@ __device__ __forceinline__ void load_row_n(const T* __restrict__ row, uint32_t n
 }
 
 __device__ __forceinline__ bool full_block(const Geo& g, uint64_t b, uint64_t c[3]) {
-  c[2] = b % g.nbd[2];
-  const uint64_t t = b / g.nbd[2];
-  c[1] = t % g.nbd[1];
-  c[0] = t / g.nbd[1];
+  block_coords(g, b, c[0], c[1], c[2]);
   return (c[0] + 1) * g.B[0] <= g.d[0] && (c[1] + 1) * g.B[1] <= g.d[1] && (c[2] + 1) * g.B[2] <= g.d[2];
 }
 
@@ -338,12 +335,29 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
           load_row<T, B2>(blk + (uint64_t)i * si + (uint64_t)j * sj, vec2, x);
         }
         const uint32_t k0 = (uint32_t)((i * (int)n1 + j) * (int)n2);
+        if (rel && !EDGE) {
+          // the row's range with NaN-ignoring min/max (fmin/fmax return the other operand of a
+          // NaN); a row holding an infinity, or only NaNs, is filtered point by point instead
+          T rmn = x[0], rmx = x[0];
+#pragma unroll
+          for (int l = 1; l < B2; ++l) {
+            rmn = fmin(rmn, x[l]);
+            rmx = fmax(rmx, x[l]);
+          }
+          if (FT<T>::finite(rmn) && FT<T>::finite(rmx)) {
+            mn = rmn < mn ? rmn : mn;
+            mx = rmx > mx ? rmx : mx;
+          } else {
+#pragma unroll
+            for (int l = 0; l < B2; ++l) minmax<T>(x[l], mn, mx);
+          }
+        }
         float r0 = 0.0f, rl = 0.0f;
 #pragma unroll
         for (int l = 0; l < B2; ++l) {
           if (EDGE && l >= (int)n2) break;
           const T v = x[l];
-          if (rel) minmax<T>(v, mn, mx);
+          if (rel && EDGE) minmax<T>(v, mn, mx);
           if (g.abft) cks<T>(v, k0 + l, sum, isum);
           const float xr = FT<T>::tofloat(v);
           r0 = __fadd_rn(r0, xr);

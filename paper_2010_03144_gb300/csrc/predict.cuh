@@ -294,6 +294,10 @@ __device__ __forceinline__ PassRes fast_pass(const T* __restrict__ blk, uint64_t
       brow[l] = T(0);
       arow[l] = T(0);
     }
+    if (!EDGE && i + 1 < n0) {  // the next plane's rows on their way to L2 while this one is walked
+#pragma unroll
+      for (int r = 0; r < B1; ++r) prefetch_l2(blk + (uint64_t)(i + 1) * si + (uint64_t)r * sj);
+    }
     T xn[B2];
     if (EDGE) load_row_n<T, B2>(blk + (uint64_t)i * si, e2, xn);
     else load_row<T, B2>(blk + (uint64_t)i * si, vec2, xn);
@@ -517,7 +521,7 @@ __device__ __forceinline__ float ereg_fast(const T* __restrict__ blk, uint64_t s
   float E = 0.0f;
   // sample rows: (i, i mod B1) in 3D; rows 1, 5, 9, ... in 2D
   constexpr int NR = NDIM == 3 ? B0 : (B1 + 2) / 4;
-#pragma unroll 1
+#pragma unroll 2
   for (int r = 0; r < NR; ++r) {
     const int i = NDIM == 3 ? r : 0;
     const int j = NDIM == 3 ? r % B1 : 4 * r + 1;
@@ -708,8 +712,8 @@ struct Consts {
 };
 
 __device__ __forceinline__ bool block_is_full(const Geo& g, uint64_t b) {
-  const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
-  const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+  uint64_t c0, c1, c2;
+  block_coords(g, b, c0, c1, c2);
   return (c0 + 1) * g.B[0] <= g.d[0] && (c1 + 1) * g.B[1] <= g.d[1] && (c2 + 1) * g.B[2] <= g.d[2];
 }
 
@@ -905,12 +909,20 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
     blk = field + row_base(g, x, 0, 0);
     vec2 = 0;
   } else {
-    const uint64_t c2 = b % g.nbd[2], t = b / g.nbd[2];
-    const uint64_t c1 = t % g.nbd[1], c0 = t / g.nbd[1];
+    uint64_t c0, c1, c2;
+    block_coords(g, b, c0, c1, c2);
     if ((c0 + 1) * B0 > g.d[0] || (c1 + 1) * B1 > g.d[1] || (c2 + 1) * B2 > g.d[2]) return;
     blk = field + (c0 * B0 * g.d[1] + c1 * B1) * g.d[2] + c2 * B2;
   }
   const uint32_t S = EDGE ? sample_points(NDIM, x.e) : (NDIM == 3 ? B0 * B2 : ((B1 + 2) / 4) * B2);
+  if (!EDGE) {  // the first plane and the selection sample's rows on their way to L2
+#pragma unroll
+    for (int r = 0; r < B1; ++r) prefetch_l2(blk + (uint64_t)r * sj);
+    if (NDIM == 3) {
+#pragma unroll
+      for (int i = 1; i < B0; ++i) prefetch_l2(blk + (uint64_t)i * si + (uint64_t)(i % B1) * sj);
+    }
+  }
   CoefSel cq = coef_select<T, NDIM>(g, w, b);
   auto ereg = [&](float4 c4, uint32_t kf, T xf) {
     if (EDGE) return ereg_generic<T, NDIM>(field, g, x, c4, kf, xf);

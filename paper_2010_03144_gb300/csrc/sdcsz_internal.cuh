@@ -38,7 +38,38 @@ struct Geo {
   int enc;       // 1: compact encoding (coefficients and unpredictable values in the payload)
   int lossless;  // 1: the lossless stage codes the stream after its block tables
   double e;
+  // block-index decomposition without a division (fields of fewer than 2^32 blocks):
+  // floor(n / nbd[a]) = mulhi64(rcp[a], n) for every 32-bit n, rcp[a] = ceil(2^64 / nbd[a])
+  // (Lemire, Kaser, Kurz, "Faster remainder by direct computation", 2019); 0 for nbd[a] = 1
+  uint64_t rcp[3];
 };
+
+// The reciprocals of the block counts along each axis (host side, after nbd is set).
+inline void geo_rcp(Geo* g) {
+  for (int a = 0; a < 3; ++a) g->rcp[a] = (g->nbd[a] > 1 && g->nbd[a] <= 0xffffffffull) ? ~0ull / g->nbd[a] + 1 : 0ull;
+}
+
+// floor(n / d) for the 32-bit n of a field of fewer than 2^32 blocks (rcp from geo_rcp)
+__device__ __forceinline__ uint32_t div_rcp(uint32_t n, uint64_t rcp) {
+  return rcp ? (uint32_t)__umul64hi(rcp, (unsigned long long)n) : n;
+}
+
+// Block b's coordinates in the block grid (row-major, the fastest axis last).
+__device__ __forceinline__ void block_coords(const Geo& g, uint64_t b, uint64_t& c0, uint64_t& c1, uint64_t& c2) {
+  if (g.nb <= 0xffffffffull) {
+    const uint32_t bb = (uint32_t)b, n2 = (uint32_t)g.nbd[2], n1 = (uint32_t)g.nbd[1];
+    const uint32_t t = div_rcp(bb, g.rcp[2]);
+    const uint32_t q = div_rcp(t, g.rcp[1]);
+    c2 = bb - t * n2;
+    c1 = t - q * n1;
+    c0 = q;
+  } else {
+    c2 = b % g.nbd[2];
+    const uint64_t t = b / g.nbd[2];
+    c1 = t % g.nbd[1];
+    c0 = t / g.nbd[1];
+  }
+}
 
 // Byte offsets of the stream sections (16-byte aligned).
 struct Layout {
@@ -160,10 +191,8 @@ struct Box {
 
 __device__ __forceinline__ Box block_box(const Geo& g, uint64_t b) {
   Box x;
-  uint64_t c2 = b % g.nbd[2];
-  uint64_t t = b / g.nbd[2];
-  uint64_t c1 = t % g.nbd[1];
-  uint64_t c0 = t / g.nbd[1];
+  uint64_t c0, c1, c2;
+  block_coords(g, b, c0, c1, c2);
   x.org[0] = c0 * g.B[0];
   x.org[1] = c1 * g.B[1];
   x.org[2] = c2 * g.B[2];
@@ -543,6 +572,10 @@ __device__ __forceinline__ bool find_flip(const sdcsz_flip* f, uint32_t n, uint3
     }
   return false;
 }
+
+// Ask the memory system to bring the 128-byte line holding p into L2 ahead of its use (no
+// register is written and nothing waits on it). Callers pass addresses inside their buffers.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
