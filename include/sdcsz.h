@@ -404,6 +404,58 @@ int sdcsz_server_release(sdcsz_server* s, uint64_t id);
 int sdcsz_server_get_stats(sdcsz_server* s, sdcsz_server_stats* out);
 void sdcsz_server_destroy(sdcsz_server* s);
 
+/*
+ * Sharded compression: one field split over several GPUs (ranks) into slabs of whole block rows
+ * along its slowest axis (axis 0 of dims), written as the stream sdcsz_compress writes for the
+ * whole field, byte for byte. Sec. 5.1 of the paper makes the blocks independent, so a slab's
+ * blocks compress exactly as inside the field once the ranks agree on three field-wide values:
+ * the value range (value-range relative bound, Fig. 2), the code histogram (one Huffman code,
+ * Algorithm 1) and the running totals of payload bytes, unpredictable values and regression
+ * blocks (where each block's data goes, Sec. 5.1). The stages run in this order on every rank,
+ * with an exchange (a collective over the ranks, made by the caller) between them:
+ *
+ *  1. sdcsz_shard_prep: the slab's first pass (range, input checksums, regression,
+ *     estimates). range_keys[2] (host) receive the slab's range in an order-preserving form.
+ *       exchange: elementwise maximum of range_keys over the ranks.
+ *  2. sdcsz_shard_predict(the field's range_keys): the field's bound, then prediction,
+ *     quantization and the ABFT checks of the slab. counts[3] (host): the slab's regression
+ *     blocks, unpredictable points, uncorrectable blocks; *d_hist (device, 65536 u64 inside the
+ *     workspace): the slab's code histogram.
+ *       exchange: sum of counts, and of the histograms in place.
+ *  3. sdcsz_shard_encode(the field's counts): the Huffman code of the field's histogram (the
+ *     same on every rank) and the slab's blocks encoded at the field's layout into d_out
+ *     (header != 0 on exactly one rank: it also writes the header and the code table).
+ *     totals[4] (host): the slab's payload bytes, unpredictable values (as encoded),
+ *     regression blocks and uncorrectable blocks.
+ *       exchange: the sum of totals over the ranks of the earlier slabs (prefix[3], the first
+ *       three) and over all ranks (field_totals[4]).
+ *  4. sdcsz_shard_assemble(prefix, field_totals): the slab's payload, unpredictable values,
+ *     coefficients and random-access table entries at their places in d_out; the header rank
+ *     also the field's totals. *out_bytes: the field's stream size; report: the slab's counters.
+ *       exchange: the byte-wise sum of every rank's d_out over [0, out_bytes) is the stream (the
+ *       ranks write disjoint bytes, except bitmap words of two slabs whose bits are disjoint).
+ *
+ * p_field: the whole field's parameters (raw or compact encoding; the lossless stage is
+ * SDCSZ_EINVAL). The slab is block rows [slab_b0, slab_b1) of axis 0: planes
+ * [slab_b0 * B, min(slab_b1 * B, dims[0])), B the block edge along axis 0, contiguous in C
+ * order at d_slab. d_ws: sdcsz_shard_workspace_size bytes, 256-byte aligned, kept through the
+ * four stages. d_out: out_cap >= sdcsz_compress_bound(p_field) bytes, zero when stage 3 starts.
+ * Each stage synchronises the stream once to return its host values. Return codes as for
+ * sdcsz_compress.
+ */
+int sdcsz_shard_workspace_size(const sdcsz_params* p_field, uint64_t slab_b0, uint64_t slab_b1, size_t* bytes);
+int sdcsz_shard_prep(const void* d_slab, const sdcsz_params* p_field, uint64_t slab_b0, uint64_t slab_b1, void* d_ws,
+                     size_t ws_bytes, uint64_t* range_keys, void* stream);
+int sdcsz_shard_predict(const void* d_slab, const sdcsz_params* p_field, uint64_t slab_b0, uint64_t slab_b1,
+                        void* d_ws, size_t ws_bytes, const uint64_t* field_range_keys, uint64_t* counts,
+                        void** d_hist, void* stream);
+int sdcsz_shard_encode(const sdcsz_params* p_field, uint64_t slab_b0, uint64_t slab_b1, void* d_ws, size_t ws_bytes,
+                       const uint64_t* field_counts, int header, void* d_out, size_t out_cap, uint64_t* totals,
+                       void* stream);
+int sdcsz_shard_assemble(const sdcsz_params* p_field, uint64_t slab_b0, uint64_t slab_b1, void* d_ws,
+                         size_t ws_bytes, const uint64_t* prefix, const uint64_t* field_totals, int header,
+                         void* d_out, size_t out_cap, size_t* out_bytes, sdcsz_report* report, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

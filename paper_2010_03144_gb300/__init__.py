@@ -31,7 +31,8 @@ EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_wor
            "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy",
            "sdcsz_autotune_block", "sdcsz_server_create", "sdcsz_server_submit", "sdcsz_server_poll",
            "sdcsz_server_release", "sdcsz_server_get_stats", "sdcsz_server_destroy", "sdcsz_decompress_region",
-           "sdcsz_decompress_workspace_size_for")
+           "sdcsz_decompress_workspace_size_for", "sdcsz_shard_workspace_size", "sdcsz_shard_prep",
+           "sdcsz_shard_predict", "sdcsz_shard_encode", "sdcsz_shard_assemble")
 
 
 class SdcszError(RuntimeError):
@@ -179,6 +180,15 @@ def lib():
         L.sdcsz_decompress_workspace_size_for.restype = i32
         L.sdcsz_kernel_launches.argtypes = []
         L.sdcsz_kernel_launches.restype = ctypes.c_ulonglong
+        u64, u64a = ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)
+        L.sdcsz_shard_workspace_size.argtypes = [P, u64, u64, ctypes.POINTER(sz)]
+        L.sdcsz_shard_prep.argtypes = [vp, P, u64, u64, vp, sz, u64a, vp]
+        L.sdcsz_shard_predict.argtypes = [vp, P, u64, u64, vp, sz, u64a, u64a, ctypes.POINTER(ctypes.c_void_p), vp]
+        L.sdcsz_shard_encode.argtypes = [P, u64, u64, vp, sz, u64a, i32, vp, sz, u64a, vp]
+        L.sdcsz_shard_assemble.argtypes = [P, u64, u64, vp, sz, u64a, u64a, i32, vp, sz, ctypes.POINTER(sz), R, vp]
+        for f in ("sdcsz_shard_workspace_size", "sdcsz_shard_prep", "sdcsz_shard_predict", "sdcsz_shard_encode",
+                  "sdcsz_shard_assemble"):
+            getattr(L, f).restype = i32
         BI, BP = ctypes.POINTER(BatchItem), ctypes.c_void_p
         L.sdcsz_batch_create.argtypes = [BI, ctypes.c_uint32, ctypes.POINTER(BP)]
         L.sdcsz_batch_workspace_size.argtypes = [BP, ctypes.POINTER(sz)]
@@ -715,3 +725,69 @@ def _device_view(ptr, nbytes, device=None):
     a.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
                                   "version": 3, "strides": None}
     return torch.as_tensor(a, device=dev)
+
+
+# ---------------------------------------------------------------- sharded compression (C ABI stages)
+# Argument marshalling for the four stages of sdcsz_shard_*; the exchanges between them and
+# their order are in paper_2010_03144_gb300.shard.
+
+def _u64s(vals):
+    return (ctypes.c_uint64 * len(vals))(*[int(v) for v in vals])
+
+
+def shard_workspace_size(p: Params, b0: int, b1: int) -> int:
+    out = ctypes.c_size_t()
+    rc = lib().sdcsz_shard_workspace_size(ctypes.byref(p), b0, b1, ctypes.byref(out))
+    if rc:
+        raise SdcszError(rc, "shard_workspace_size")
+    return out.value
+
+
+def shard_prep(slab, p: Params, b0: int, b1: int, ws, stream=None):
+    keys = (ctypes.c_uint64 * 2)()
+    rc = lib().sdcsz_shard_prep(ctypes.c_void_p(slab.data_ptr()), ctypes.byref(p), b0, b1, ctypes.c_void_p(ws.data_ptr()),
+                                ws.numel(), keys, _stream_handle(stream))
+    if rc:
+        raise SdcszError(rc, "shard_prep")
+    return [int(keys[0]), int(keys[1])]
+
+
+def shard_predict(slab, p: Params, b0: int, b1: int, ws, field_keys, stream=None):
+    """Returns (counts [regression blocks, unpredictable points, uncorrectable blocks], the slab's
+    code histogram as an int64 CUDA tensor view of 65536 bins inside the workspace)."""
+    import torch
+    counts = (ctypes.c_uint64 * 3)()
+    hp = ctypes.c_void_p()
+    rc = lib().sdcsz_shard_predict(ctypes.c_void_p(slab.data_ptr()), ctypes.byref(p), b0, b1,
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _u64s(field_keys), counts,
+                                   ctypes.byref(hp), _stream_handle(stream))
+    if rc:
+        raise SdcszError(rc, "shard_predict")
+    hist = _device_view(hp.value, 8 * 65536, ws.device).view(torch.int64)
+    return [int(c) for c in counts], hist
+
+
+def shard_encode(p: Params, b0: int, b1: int, ws, field_counts, header: bool, out, stream=None):
+    """Returns the slab's totals [payload bytes, unpredictable values, regression blocks,
+    uncorrectable blocks]; `out` (the field's stream buffer, zero on entry) receives the slab's
+    per-block tables and, with header, the header and code table."""
+    totals = (ctypes.c_uint64 * 4)()
+    rc = lib().sdcsz_shard_encode(ctypes.byref(p), b0, b1, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                  _u64s(field_counts), 1 if header else 0, ctypes.c_void_p(out.data_ptr()),
+                                  out.numel(), totals, _stream_handle(stream))
+    if rc:
+        raise SdcszError(rc, "shard_encode")
+    return [int(t) for t in totals]
+
+
+def shard_assemble(p: Params, b0: int, b1: int, ws, prefix, field_totals, header: bool, out, stream=None):
+    """Places the slab's data in `out`; returns (the field's stream size, the slab's report)."""
+    nbytes = ctypes.c_size_t()
+    rep = Report()
+    rc = lib().sdcsz_shard_assemble(ctypes.byref(p), b0, b1, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                    _u64s(prefix), _u64s(field_totals), 1 if header else 0,
+                                    ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(nbytes),
+                                    ctypes.byref(rep), _stream_handle(stream))
+    if rc:
+        raise SdcszError(rc, "shard_assemble")
+    return nbytes.value, rep.as_dict()

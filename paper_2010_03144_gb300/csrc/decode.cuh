@@ -497,7 +497,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
         }
       }
       const uint64_t ro = (uint64_t)i * si + (uint64_t)j * sj;
-      if (WRITE) {
+      if (WRITE) {  // streaming stores: the field is not read again, the stream's bytes are
         if ((B2 % 2) == 0 && vec2) {
           typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type V2;
           V2* p = reinterpret_cast<V2*>(blk_out + ro);
@@ -506,11 +506,11 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
             V2 t;
             t.x = out[2 * l];
             t.y = out[2 * l + 1];
-            p[l] = t;
+            __stcs(p + l, t);
           }
         } else {
 #pragma unroll
-          for (int l = 0; l < B2; ++l) blk_out[ro + l] = out[l];
+          for (int l = 0; l < B2; ++l) __stcs(blk_out + ro + l, out[l]);
         }
       }
       if (!WRITE && blk_orig) {

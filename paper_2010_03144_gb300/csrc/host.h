@@ -35,6 +35,8 @@ int make_geo(const sdcsz_params* p, Geo* g);
 WsPlan plan_ws(const Geo& g);
 Ws bind_ws(void* base, const WsPlan& p);
 int map_error(unsigned int e);
+// The State of a call to the host (synchronises the stream).
+int read_state(const State* d_st, cudaStream_t s, State* h);
 void fill_report(const State& h, uint64_t nb, sdcsz_report* r);
 int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout);
 

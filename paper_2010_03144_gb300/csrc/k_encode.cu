@@ -86,14 +86,22 @@ struct Extra {
   int texp;
 };
 
-// Code pairs reach the encoder through a ring of kRing batches of 8 words per thread in shared
-// memory (word q of slot r of thread t at ((r * 8 + q) * blockDim + t)), filled by cp.async:
-// each thread copies exactly the words it later reads, so its own wait suffices, and
-// kRing - 1 batches are in flight while one is encoded.
+// Code pairs reach the encoder through a ring of kRing batches of 8 pair rows in shared memory
+// (word q of slot r of thread t at ((r * 8 + q) * kRingStride + t)), filled by cp.async while
+// kRing - 1 batches are in flight: a warp's 32 blocks keep each pair row in one 128-byte line
+// (the pairs are warp-interleaved), so the warp copies 8 rows with two 16-byte copies per lane
+// and shares them after a warp barrier. Every lane of the warp runs the ring over the pairs the
+// layout keeps per block, whatever its own block's size.
 constexpr uint32_t kRing = 3;
+constexpr uint32_t kRingStride = 128;  // threads of the encoding kernels' CTAs
 
 __device__ __forceinline__ void cp_async4(uint32_t* dst_smem, const uint32_t* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t* dst_smem, const uint32_t* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
                "l"(src)
                : "memory");
 }
@@ -104,12 +112,14 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // One pass over a block's codes: the Huffman bits into `slot` (stream byte order, the last
 // word zero padded), the code checksums (ABFT), the unpredictable count and the first
 // kPosKept unpredictable positions. With FIX, code kfix reads as vfix. CMP: compact encoding.
-// R is the central code (prediction within half a bin). ring: this thread's staging ring
-// (nullptr: the pairs are loaded from memory directly).
+// R is the central code (prediction within half a bin). pa: the pairs the staging layout keeps
+// per block (pairs_of of the full block). ring: this thread's staging ring (nullptr: the pairs
+// are loaded from memory directly).
 template <bool ABFT, bool FIX, bool CMP, typename T>
 __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, uint32_t P, uint32_t* __restrict__ slot,
                                                const Codebook& cb, uint32_t cw0, uint32_t R, uint32_t kfix,
-                                               uint32_t vfix, const Extra<T>& ex, uint32_t* ring = nullptr) {
+                                               uint32_t vfix, const Extra<T>& ex, uint32_t pa,
+                                               uint32_t* ring = nullptr) {
   EncRes e;
   e.bits = 0;
   e.nun = 0;
@@ -203,13 +213,16 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
   // Eight central codes in a row (the common case of a smooth field) go in with one append of
   // the central codeword repeated eight times, their checksums in closed form: sum_q gains 8 R
   // and isum_q gains R (8k + 36) for codes k .. k+7. The bits are those of eight single appends
-  // (one flush suffices: fewer than 32 bits were pending and the run adds at most 32).
+  // (one flush suffices: fewer than 32 bits were pending and the run adds at most 32). With a
+  // central codeword of at most 2 bits, sixteen at once the same way (R (16k + 136)).
   const uint32_t cwc = cb(R), lc = cwc & 31u, lrun = 8 * lc;
   const bool runs = !FIX && lc != 0 && lc <= 4;
+  const bool runs16 = runs && lc <= 2;
   uint32_t rep = 0;
   if (runs)
 #pragma unroll
     for (int t = 0; t < 8; ++t) rep = (rep << lc) | (cwc >> 5);
+  const uint32_t rep16 = runs16 ? ((rep << lrun) | rep) : 0u;
   const uint32_t pc = R | (R << 16);  // a pair word of two central codes
   // code pairs eight at a time, the next eight loaded while these are encoded
   const uint32_t P2 = P >> 1;
@@ -218,50 +231,77 @@ __device__ __forceinline__ EncRes encode_codes(const uint32_t* __restrict__ pp, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) w[q] = (base + q < P2) ? pp[32 * (uint64_t)(base + q)] : 0u;
   };
-  const uint32_t nthr = blockDim.x;
-  auto stage8 = [&](uint32_t base) {  // batch base / 8 into its ring slot (words past P2 are not read)
-    uint32_t* r = ring + (uint64_t)((base >> 3) % kRing) * 8 * nthr;
+  // batch `base` into ring slot `sl`: every pair below pa (the pairs the layout keeps per
+  // block) lies inside the staging array, so only a batch reaching past pa needs a test
+  const uint32_t lane = threadIdx.x & 31;
+  auto stage8 = [&](uint32_t base, uint32_t sl) {
+    // lane L: 16 bytes (lanes 4c .. 4c+3, c = L mod 8) of rows base + L/8 and base + 4 + L/8
+    const uint32_t c = 4 * (lane & 7), q0 = lane >> 3;
+    uint32_t* r = ring - lane + sl * 8 * kRingStride + c;
+    const uint32_t* src = pp - lane + 32 * (uint64_t)base + c;
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (base + q < P2) cp_async4(r + (uint64_t)q * nthr, pp + 32 * (uint64_t)(base + q));
+    for (uint32_t q = q0; q < 8; q += 4)
+      if (base + q < pa) cp_async16(r + q * kRingStride, src + 32 * q);
     cp_async_commit();
   };
+  uint32_t s_in = kRing - 1, s_out = 0;  // ring slots of the next batch staged and consumed
   if (ring) {
 #pragma unroll
-    for (uint32_t t = 0; t < kRing - 1; ++t) stage8(8 * t);
+    for (uint32_t t = 0; t < kRing - 1; ++t) stage8(8 * t, t);
   } else {
     load8(0, wq);
   }
-  for (uint32_t k8 = 0; k8 < P2; k8 += 8) {
+  const uint32_t nk = ring ? pa : P2;  // the ring's loop is the same for the whole warp
+  for (uint32_t k8 = 0; k8 < nk; k8 += 8) {
     if (ring) {
-      stage8(k8 + 8 * (kRing - 1));  // an empty group past the end keeps the count uniform
+      __syncwarp();  // every lane is done with the slot the next batch goes to
+      stage8(k8 + 8 * (kRing - 1), s_in);  // an empty group past the end keeps the count uniform
+      s_in = s_in + 1 == kRing ? 0 : s_in + 1;
       cp_async_wait<kRing - 1>();
-      const uint32_t* r = ring + (uint64_t)((k8 >> 3) % kRing) * 8 * nthr;
+      __syncwarp();  // the other lanes' copies of this batch are visible
+      const uint32_t* r = ring + s_out * 8 * kRingStride;
+      s_out = s_out + 1 == kRing ? 0 : s_out + 1;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) wq[q] = r[(uint64_t)q * nthr];
+      for (int q = 0; q < 8; ++q) wq[q] = r[q * kRingStride];
     } else if (k8 + 8 < P2) {
       load8(k8 + 8, wn);
     }
+    if (runs16 && k8 + 8 <= P2 &&
+        (((wq[0] ^ pc) | (wq[1] ^ pc) | (wq[2] ^ pc) | (wq[3] ^ pc)) |
+         ((wq[4] ^ pc) | (wq[5] ^ pc) | (wq[6] ^ pc) | (wq[7] ^ pc))) == 0u) {
+      acc = (acc << (2 * lrun)) | rep16;
+      nacc += 2 * lrun;
+      e.bits += 2 * lrun;
+      if (nacc >= 32) {
+        nacc -= 32;
+        slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+      }
+      if (ABFT) {
+        e.sq += 16 * R;
+        mad_wide(e.isq, R, 32 * k8 + 136);  // codes k = 2 k8 .. k + 15: 16 k + 136
+      }
+    } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t k2 = k8 + 4 * h;
-      if (runs && k2 + 3 < P2 &&
-          ((wq[4 * h] ^ pc) | (wq[4 * h + 1] ^ pc) | (wq[4 * h + 2] ^ pc) | (wq[4 * h + 3] ^ pc)) == 0u) {
-        acc = (acc << lrun) | rep;
-        nacc += lrun;
-        e.bits += lrun;
-        if (nacc >= 32) {
-          nacc -= 32;
-          slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
-        }
-        if (ABFT) {
-          e.sq += 8 * R;
-          mad_wide(e.isq, R, 16 * k2 + 36);  // codes k = 2 k2 .. k + 7: 8 k + 36
-        }
-      } else {
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k2 = k8 + 4 * h;
+        if (runs && k2 + 3 < P2 &&
+            ((wq[4 * h] ^ pc) | (wq[4 * h + 1] ^ pc) | (wq[4 * h + 2] ^ pc) | (wq[4 * h + 3] ^ pc)) == 0u) {
+          acc = (acc << lrun) | rep;
+          nacc += lrun;
+          e.bits += lrun;
+          if (nacc >= 32) {
+            nacc -= 32;
+            slot[wi++] = __byte_perm((uint32_t)(acc >> nacc), 0, 0x0123);
+          }
+          if (ABFT) {
+            e.sq += 8 * R;
+            mad_wide(e.isq, R, 16 * k2 + 36);  // codes k = 2 k2 .. k + 7: 8 k + 36
+          }
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (k2 + q < P2) put2(wq[4 * h + q] & 0xffffu, wq[4 * h + q] >> 16, 2 * (k2 + q));
+          for (int q = 0; q < 4; ++q)
+            if (k2 + q < P2) put2(wq[4 * h + q] & 0xffffu, wq[4 * h + q] >> 16, 2 * (k2 + q));
+        }
       }
     }
     if (!ring) {
@@ -292,7 +332,8 @@ __host__ __device__ inline uint64_t slot_words_of(const Geo& g) {
 // ---------------------------------------------------------------- K4a
 template <typename T, bool ABFT, bool CMP>
 __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t* __restrict__ out,
-                                             const uint32_t* cb_s, uint64_t b, uint32_t* ring) {
+                                             const uint32_t* cb_s, uint64_t b, uint32_t* ring,
+                                             const Shard& sh = Shard{}) {
   State* st = w.st;
   const Layout L = st->L;
   const uint32_t lane = threadIdx.x & 31;
@@ -300,24 +341,28 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
   bool reg = false;
   unsigned long long nun_enc = 0;
   uint32_t nbytes = 0;
+  // the first pass stages the warp's codes together (ring): every lane of the warp takes part,
+  // and a lane past the field's blocks encodes nothing (P = 0)
+  Codebook cb;
+  cb.lo = cb_lo(g);
+  cb.s = cb_s;
+  cb.g = w.codebook;
+  const uint32_t cw0 = __ldg(&w.codebook[0]);
+  const uint32_t P = active ? block_box(g, b).P : 0u;
+  reg = active && (w.flags[b] & 1);
+  const uint32_t* pp = reinterpret_cast<const uint32_t*>(w.codes) + pair_index(b, g.P, 0);
+  uint32_t* slot = w.etmp + (active ? b : 0) * slot_words_of(g);
+  Extra<T> ex = {nullptr, 0, nullptr, kNoTrunc};
+  if (CMP && active) {
+    ex.kq = static_cast<const int*>(w.coefT) + 4 * b;
+    ex.nco = reg ? g.ndim + 1 : 0;
+    ex.up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
+    ex.texp = bound_exponent<T>((T)st->eb);
+  }
+  EncRes e = {0u, 0u, 0u, 0ull, {0u, 0u, 0u, 0u}};
+  if ((b & ~uint64_t(31)) < g.nb)  // a warp with blocks in the field (its pair rows exist)
+    e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, g.R, 0u, 0u, ex, pairs_of(g.P), ring);
   if (active) {
-    Codebook cb;
-    cb.lo = cb_lo(g);
-    cb.s = cb_s;
-    cb.g = w.codebook;
-    const uint32_t cw0 = __ldg(&w.codebook[0]);
-    const uint32_t P = block_box(g, b).P;
-    reg = w.flags[b] & 1;
-    const uint32_t* pp = reinterpret_cast<const uint32_t*>(w.codes) + pair_index(b, g.P, 0);
-    uint32_t* slot = w.etmp + b * slot_words_of(g);
-    Extra<T> ex = {nullptr, 0, nullptr, kNoTrunc};
-    if (CMP) {
-      ex.kq = static_cast<const int*>(w.coefT) + 4 * b;
-      ex.nco = reg ? g.ndim + 1 : 0;
-      ex.up = static_cast<const T*>(w.ustage) + code_index(b, g.P, 0);
-      ex.texp = bound_exponent<T>((T)st->eb);
-    }
-    EncRes e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, g.R, 0u, 0u, ex, ring);
     uint32_t kfix = 0xffffffffu, vfix = 0;
     bool bad = false;
     if (ABFT && (e.sq != w.sum_q[b] || e.isq != w.isum_q[b])) {
@@ -330,7 +375,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
         if (nv >= 0 && nv < (long long)g.bins) {
           kfix = (uint32_t)m;
           vfix = (uint32_t)nv;
-          e = encode_codes<ABFT, true, CMP, T>(pp, P, slot, cb, cw0, g.R, kfix, vfix, ex);  // the repaired block
+          e = encode_codes<ABFT, true, CMP, T>(pp, P, slot, cb, cw0, g.R, kfix, vfix, ex, pairs_of(g.P));  // repaired
           fixed = true;
         }
       }
@@ -362,12 +407,14 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
       }
     }
     nbytes = (uint16_t)((e.bits + 7u) >> 3);
-    *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * b) = (uint16_t)nbytes;
-    *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * b) = (uint16_t)e.nun;
+    const uint64_t fb = sh.boff + b;  // the block's index in the field
+    *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * fb) = (uint16_t)nbytes;
+    *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * fb) = (uint16_t)e.nun;
     nun_enc = e.nun;
-    if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * b) = w.sum_dc[b];
-    // a block whose codes could not be repaired is reported in the header status word
-    if (bad) atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
+    if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * fb) = w.sum_dc[b];
+    // a block whose codes could not be repaired is reported in the header status word (by the
+    // header's writer, from every shard's count, in a sharded field)
+    if (bad && !sh.on) atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
   }
   // regression bitmap word of this warp's 32 blocks; the warp's unpredictable count; the
   // warp's share of its group's totals (the 32 blocks lie in one group of kGroup)
@@ -375,7 +422,15 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
   unsigned long long wun = warp_sum(nun_enc);
   const unsigned long long wtot = warp_sum(active ? pack_tot(nbytes, nun_enc, reg ? 1u : 0u) : 0ull);
   if (lane == 0 && b < g.nb) {
-    *reinterpret_cast<uint32_t*>(out + L.bitmap + 4 * (b >> 5)) = ballot;
+    if (!sh.on) {
+      *reinterpret_cast<uint32_t*>(out + L.bitmap + 4 * (b >> 5)) = ballot;
+    } else if (ballot) {  // a shard's 32 blocks may straddle two bitmap words of the field
+      const uint64_t fb = sh.boff + (b & ~uint64_t(31));
+      unsigned int* bw = reinterpret_cast<unsigned int*>(out + L.bitmap) + (fb >> 5);
+      const uint32_t r = (uint32_t)(fb & 31);
+      atomicOr(bw, ballot << r);
+      if (r && (ballot >> (32 - r))) atomicOr(bw + 1, ballot >> (32 - r));
+    }
     if (wun) atomicAdd(&st->n_unpred_enc, wun);
     const uint64_t gid = b / kGroup, ng = (g.nb + kGroup - 1) / kGroup;
     atomicAdd(&w.gt[gid], wtot);
@@ -388,7 +443,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
 template <typename T, bool ABFT, bool CMP>
 __global__ void __launch_bounds__(128) k_encode_blocks(Geo g, Ws w, uint8_t* __restrict__ out) {
   __shared__ uint32_t cb_s[kCbWindow];
-  __shared__ uint32_t ring_s[kRing * 8 * 128];
+  __shared__ __align__(16) uint32_t ring_s[kRing * 8 * kRingStride];
   if (cta_failed(w.st)) return;
   cb_load(cb_s, g, w);
   __syncthreads();
@@ -398,7 +453,7 @@ __global__ void __launch_bounds__(128) k_encode_blocks(Geo g, Ws w, uint8_t* __r
 // ---------------------------------------------------------------- K4b
 template <typename T>
 __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
-                                               uint64_t gid) {
+                                               uint64_t gid, const Shard& sh = Shard{}) {
   __shared__ unsigned long long s_wt[8][3];
   __shared__ unsigned long long s_pre[8][3];
   __shared__ unsigned long long s_excl[3];
@@ -411,7 +466,7 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   // The unpredictable section holds the points whose code, as encoded, is 0: the count K2 took
   // unless a block's codes could not be repaired. The payload follows that section (which the
   // compact encoding leaves empty).
-  const unsigned long long n_unpred = st->n_unpred_enc;
+  const unsigned long long n_unpred = sh.on ? sh.tot[1] : st->n_unpred_enc;
   const uint64_t s_dt = g.dtype ? 8 : 4;
   Layout L = st->L;
   L.payload = align16(L.unpred + (g.enc ? 0 : s_dt * n_unpred));
@@ -425,8 +480,8 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
 #pragma unroll
   for (int q = 0; q < 4; ++q) head[q] = (active && (uint32_t)q < n4) ? src4[q] : make_uint4(0u, 0u, 0u, 0u);
   if (active) {
-    bytes = *reinterpret_cast<const uint16_t*>(out + L.sizes + 2 * b);
-    nun = *reinterpret_cast<const uint16_t*>(out + L.ucounts + 2 * b);
+    bytes = *reinterpret_cast<const uint16_t*>(out + L.sizes + 2 * (sh.boff + b));
+    nun = *reinterpret_cast<const uint16_t*>(out + L.ucounts + 2 * (sh.boff + b));
     reg = w.flags[b] & 1;
   }
 
@@ -476,7 +531,7 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   }
   __syncthreads();
 
-  if (tid == 0) {
+  if (tid == 0 && !sh.on) {
     const uint64_t go = L.groups + 24 * gid;
     for (int q = 0; q < 3; ++q) *reinterpret_cast<unsigned long long*>(out + go + 8 * q) = s_excl[q];
     if (gid == ngroups - 1) {
@@ -492,11 +547,32 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
       if (L.payload + pay > cap) atomicOr(&st->error, ERR_CAPACITY);
     }
   }
+  if (sh.on && sh.header && gid == 0 && tid == 0) {  // the field's totals, from every shard's
+    const unsigned long long pay = sh.tot[0];
+    *reinterpret_cast<unsigned long long*>(out + 88) = n_unpred;
+    *reinterpret_cast<unsigned long long*>(out + 96) = pay;
+    *reinterpret_cast<unsigned long long*>(out + 104) = L.payload + pay;
+    *reinterpret_cast<unsigned int*>(out + 112) = sh.tot[3] ? 1u : 0u;
+  }
+  if (sh.on && tid == 0) {
+    st->n_unpred = n_unpred;
+    st->L = L;
+    st->payload_bytes = sh.tot[0];
+    st->total_bytes = L.payload + sh.tot[0];
+    if (L.payload + sh.tot[0] > cap) atomicOr(&st->error, ERR_CAPACITY);
+  }
   if (!active) return;
 
-  const unsigned long long pay_off = s_excl[0] + s_wt[wid][0] + inc[0] - v[0];
-  const unsigned long long un_off = s_excl[1] + s_wt[wid][1] + inc[1] - v[1];
-  const unsigned long long rg_off = s_excl[2] + s_wt[wid][2] + inc[2] - v[2];
+  // this block's offsets in the field's stream (the earlier shards' totals first)
+  const unsigned long long pay_off = sh.pre[0] + s_excl[0] + s_wt[wid][0] + inc[0] - v[0];
+  const unsigned long long un_off = sh.pre[1] + s_excl[1] + s_wt[wid][1] + inc[1] - v[1];
+  const unsigned long long rg_off = sh.pre[2] + s_excl[2] + s_wt[wid][2] + inc[2] - v[2];
+  if (sh.on && (sh.boff + b) % kGroup == 0) {  // the first block of a group of the field: its entry
+    unsigned long long* ge = reinterpret_cast<unsigned long long*>(out + L.groups + 24 * ((sh.boff + b) / kGroup));
+    ge[0] = pay_off;
+    ge[1] = un_off;
+    ge[2] = rg_off;
+  }
   if (reg && !g.enc) {
     const T* cT = static_cast<const T*>(w.coefT) + 4 * b;
     T* dst = reinterpret_cast<T*>(out + L.coef) + (uint64_t)(g.ndim + 1) * rg_off;
@@ -554,11 +630,30 @@ __global__ void __launch_bounds__(256, 3) k_encode_assemble(Geo g, Ws w, uint8_t
   assemble_group<T>(g, w, out, cap, blockIdx.x);
 }
 
+// A shard of a field (see Shard).
+template <typename T, bool ABFT, bool CMP>
+__global__ void __launch_bounds__(128) k_encode_blocks_shard(Geo g, Ws w, uint8_t* __restrict__ out, Shard sh) {
+  __shared__ uint32_t cb_s[kCbWindow];
+  __shared__ __align__(16) uint32_t ring_s[kRing * 8 * kRingStride];
+  if (cta_failed(w.st)) return;
+  cb_load(cb_s, g, w);
+  __syncthreads();
+  encode_block<T, ABFT, CMP>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, ring_s + threadIdx.x,
+                             sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 3) k_encode_assemble_shard(Geo g, Ws w, uint8_t* __restrict__ out, uint64_t cap,
+                                                                   Shard sh) {
+  if (cta_failed(w.st)) return;
+  assemble_group<T>(g, w, out, cap, blockIdx.x, sh);
+}
+
 // ---------------------------------------------------------------- batches
 template <typename T, bool ABFT>
 __global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
   __shared__ uint32_t cb_s[kCbWindow];
-  __shared__ uint32_t ring_s[kRing * 8 * 128];
+  __shared__ __align__(16) uint32_t ring_s[kRing * 8 * kRingStride];
   __shared__ Job s_job;
   batch_loop(
       a, s_job,
@@ -634,6 +729,40 @@ void batch_encode_blocks(int dtype, bool abft, const BatchArgs& a, const Launch&
 void batch_encode_assemble(int dtype, const BatchArgs& a, const Launch& L) {
   if (dtype == 0) batch_assemble_t<float>(a, L);
   else batch_assemble_t<double>(a, L);
+}
+
+void launch_encode_shard_blocks(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Shard& sh,
+                                const Launch& L) {
+  (void)cap;
+  const unsigned nchunks = (unsigned)((g.nb + 127) / 128);
+  if (!nchunks) return;
+  if (g.dtype == 0) {
+    if (g.enc) {
+      if (g.abft) k_encode_blocks_shard<float, true, true><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+      else k_encode_blocks_shard<float, false, true><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+    } else {
+      if (g.abft) k_encode_blocks_shard<float, true, false><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+      else k_encode_blocks_shard<float, false, false><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+    }
+  } else {
+    if (g.enc) {
+      if (g.abft) k_encode_blocks_shard<double, true, true><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+      else k_encode_blocks_shard<double, false, true><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+    } else {
+      if (g.abft) k_encode_blocks_shard<double, true, false><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+      else k_encode_blocks_shard<double, false, false><<<nchunks, 128, 0, L.stream>>>(g, w, out, sh);
+    }
+  }
+  note_launch();
+}
+
+void launch_encode_shard_assemble(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Shard& sh,
+                                  const Launch& L) {
+  const unsigned ngroups = (unsigned)((g.nb + kGroup - 1) / kGroup);
+  if (!ngroups) return;
+  if (g.dtype == 0) k_encode_assemble_shard<float><<<ngroups, 256, 0, L.stream>>>(g, w, out, cap, sh);
+  else k_encode_assemble_shard<double><<<ngroups, 256, 0, L.stream>>>(g, w, out, cap, sh);
+  note_launch();
 }
 
 void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {

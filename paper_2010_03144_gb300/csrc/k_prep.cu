@@ -253,6 +253,8 @@ __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
                : "memory");
 }
 
+constexpr int kPrepCta = 128;  // threads of the fast prep kernels' CTAs
+
 // Fast path: full blocks of a compile-time shape B0 x B1 x B2 (leading 1 for 2D). EDGE: the
 // edge blocks of such a field (e-th of `count`), walked with the same code at their actual
 // extents (at most B0 x B1 x B2; the unrolled row skips what lies outside, and nothing outside
@@ -262,7 +264,7 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
                                           uint64_t cta, unsigned char* stage, uint64_t count = 0) {
   State* st = w.st;
   const uint32_t tid = threadIdx.x;
-  const uint64_t tix = cta * blockDim.x + tid;
+  const uint64_t tix = cta * kPrepCta + tid;
   const bool rel = g.eb_mode == 1;
   const bool est = g.predictor == 0;
   T mn = T(1.0 / 0.0), mx = T(-1.0 / 0.0);
@@ -294,10 +296,9 @@ __device__ __forceinline__ void prep_fast(const T* __restrict__ field, const Geo
     for (int l = 0; l < B2; ++l) pa[l] = pb[l] = na[l] = nb[l] = 0.0f;
     using ST = PrepStage<T, NDIM, B1, B2>;
     const bool staged = !EDGE && ST::on && vec2;
-    // unit u of row r of buffer f of this thread: 8 bytes at ((f*B1 + r)*U + u)*blockDim + tid
-    auto unit = [&](int f, int r, int u) {
-      return reinterpret_cast<unsigned long long*>(stage) + (((size_t)f * B1 + r) * ST::U + u) * blockDim.x + tid;
-    };
+    // unit u of row r of buffer f of this thread: 8 bytes at ((f*B1 + r)*U + u)*kPrepCta + tid
+    unsigned long long* my = reinterpret_cast<unsigned long long*>(stage) + tid;
+    auto unit = [&](int f, int r, int u) { return my + ((f * B1 + r) * ST::U + u) * kPrepCta; };
     auto issue_plane = [&](int i) {
 #pragma unroll 1
       for (int r = 0; r < B1; ++r)
@@ -653,6 +654,12 @@ void batch_bound(const Job* jobs, uint32_t n, const Launch& L) {
 }
 
 bool prep_has_fast(const Geo& g) { return has_fast(g); }
+
+void launch_bound(const Geo& g, State* st, const Launch& L) {
+  if (g.dtype == 0) k_bound<float><<<1, 1, 0, L.stream>>>(g, st);
+  else k_bound<double><<<1, 1, 0, L.stream>>>(g, st);
+  note_launch();
+}
 
 void launch_prep(const void* field, const Geo& g, const Ws& w, const Launch& L) {
   if (g.dtype == 0) launch_prep_t<float>(field, g, w, L);

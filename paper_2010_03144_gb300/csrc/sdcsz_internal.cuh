@@ -635,6 +635,8 @@ struct Fork {
 };
 
 void launch_prep(const void* field, const Geo& g, const Ws& w, const Launch& L);
+// The absolute bound from the range keys in the State (the last kernel of launch_prep).
+void launch_bound(const Geo& g, State* st, const Launch& L);
 void launch_predict(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
                     const Launch& L);
 void launch_flip_input(void* field, const Geo& g, const sdcsz_flip* flips, uint32_t nflips, const Ws& w,
@@ -642,6 +644,25 @@ void launch_flip_input(void* field, const Geo& g, const sdcsz_flip* flips, uint3
 void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips, const Launch& L);
 void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
 void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
+
+// A slab of a field compressed as one shard of the field's stream (sharded compression over
+// several GPUs). The slab is a field of its own to every kernel up to the encoder; the encoder
+// places its blocks in the field's stream: block b of the slab is block boff + b of the field,
+// and its payload, unpredictable values and coefficients follow those of the earlier shards
+// (pre: their payload bytes, unpredictable values and regression blocks). tot: the field's
+// payload bytes, unpredictable values, regression blocks and uncorrectable blocks. Only the
+// shard with header = 1 writes the header and the code table. on = 0: a whole field.
+struct Shard {
+  int on, header;
+  uint64_t boff;
+  unsigned long long pre[3], tot[4];
+};
+// K4a of a shard into `out` at the field's layout (State::L, set by the codebook kernel from the
+// field's geometry), then K4b with the shard's offsets.
+void launch_encode_shard_blocks(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Shard& sh,
+                                const Launch& L);
+void launch_encode_shard_assemble(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Shard& sh,
+                                  const Launch& L);
 
 // ---------------------------------------------------------------- batches
 // A batch compresses many fields with one launch per stage and kernel shape: every field is
