@@ -720,10 +720,11 @@ template <class F>
 __device__ __forceinline__ uint8_t verify_block(const uint8_t* s, const Hdr& h, uint64_t b, F run, Acc& acc) {
   unsigned long long sum = 0, nv = 0;
   double me = 0.0;
+  // the stored sum_dc is loaded before the block is decoded, so the load is in flight meanwhile
+  const unsigned long long ref = h.g.abft ? ld_u64(s + h.L.sumdc + 8 * b) : 0ull;
   bool ok = run(true, &sum, &nv, &me);
   uint8_t stv = SDCSZ_BLOCK_OK;
   if (h.g.abft) {
-    const unsigned long long ref = ld_u64(s + h.L.sumdc + 8 * b);
     if (!ok || sum != ref) {
       ok = run(false, &sum, &nv, &me);  // decompress this block again from its bytes
       if (ok && sum == ref) {
@@ -1097,22 +1098,46 @@ __device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, u
   // their way to L2 while this one is decoded; no barrier between the CTA's warps
   const uint64_t nitems = (g.nb + 31) / 32;
   const uint32_t lane = threadIdx.x & 31;
+  // Items are placed one ahead: while item i is decoded, item i+1's blocks are already placed and
+  // the head of each one's payload, its coefficients and its sum_dc are on their way to L2.
+  auto prefetch_block = [&](const BlockIn& q, uint64_t it) {
+    if (32 * it + lane >= g.nb) return;
+    const uint64_t offs[3] = {h.L.payload + q.pay_off, h.L.coef + (q.reg_idx >= 0 ? (uint64_t)q.reg_idx : 0ull) *
+                                                                         (uint64_t)(NDIM + 1) * sizeof(T),
+                              h.L.sumdc + 8 * (32 * it + lane)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if ((k != 1 || (q.reg_idx >= 0 && !CMP)) && (k != 2 || g.abft) && offs[k] < nbytes) prefetch_l2(s + offs[k]);
+  };
+  // the block-table, unpredictable-count and group-table lines of an item, two items ahead
+  auto prefetch_tables = [&](uint64_t it) {  // what warp_place reads: the whole group's tables
+    if (it >= nitems || lane >= 11) return;
+    const uint64_t G = it >> 3;
+    uint64_t off;
+    if (lane < 4) off = h.L.sizes + 512 * G + 128 * lane;
+    else if (lane < 8) off = h.L.ucounts + 512 * G + 128 * (lane - 4);
+    else if (lane == 8) off = h.L.bitmap + 32 * G;
+    else off = h.L.groups + 24 * G + 24 * (lane - 9);  // this group's entry and the next one's
+    if (off < nbytes) prefetch_l2(s + off);
+  };
   uint64_t item = warp_pull(&st->queue[0]);
+  BlockIn bi;
+  bool placed = item < nitems && warp_place(s, h, item, ngroups, st, &bi);
+  uint64_t nxt = warp_pull(&st->queue[0]);
+  prefetch_tables(nxt);
   while (item < nitems) {
-    const uint64_t nxt = warp_pull(&st->queue[0]);
-    if (nxt < nitems && lane < 3) {
-      const uint64_t q0 = (nxt >> 3) * kGroup;
-      const uint64_t off = lane == 0 ? h.L.sizes + 2 * 32 * nxt : (lane == 1 ? h.L.ucounts + 2 * 32 * nxt
-                                                                            : h.L.groups + 24 * (nxt >> 3));
-      (void)q0;
-      if (off < nbytes) prefetch_l2(s + off);
-    }
-    BlockIn bi;
-    const bool placed = warp_place(s, h, item, ngroups, st, &bi);
+    const uint64_t nn = warp_pull(&st->queue[0]);
+    prefetch_tables(nn);
+    BlockIn bn;
+    const bool placed_n = nxt < nitems && warp_place(s, h, nxt, ngroups, st, &bn);
+    if (placed_n) prefetch_block(bn, nxt);
     const uint64_t b = 32 * item + lane;
     if (!placed) {
       if (status && b < g.nb) status[b] = SDCSZ_BLOCK_BAD;
       item = nxt;
+      nxt = nn;
+      bi = bn;
+      placed = placed_n;
       continue;
     }
     bool full = false;
@@ -1154,6 +1179,9 @@ __device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, u
       if (status) status[b] = stv;
     }
     item = nxt;
+    nxt = nn;
+    bi = bn;
+    placed = placed_n;
   }
   acc.commit(st);
 }
