@@ -215,8 +215,8 @@ __device__ __forceinline__ T read_unpred(Reader& br, int texp) {
   int m = Bitsof<T>::M;
   if (Ex != 0 && Ex != (1 << Bitsof<T>::E) - 1) m = min(max(Ex - Bitsof<T>::BIAS - texp, 0), Bitsof<T>::M);
   U mant = 0;
-  if (m > 32) {
-    mant = (U)br.bits((uint32_t)m - 32) << 32;
+  if (m > 32) {  // float64 only (a float keeps at most 23 bits)
+    mant = (U)((unsigned long long)br.bits((uint32_t)m - 32) << 32);
     mant |= br.bits(32);
   } else if (m > 0) {
     mant = br.bits((uint32_t)m);
@@ -374,13 +374,16 @@ __device__ __noinline__ bool decode_generic(const uint8_t* __restrict__ s, const
 
 // ---------------------------------------------------------------- fast path (full blocks)
 // WRITE: decompression (the block is stored to blk_out); otherwise verification (compared
-// with blk_orig when there is one).
-template <typename T, int NDIM, int B0, int B1, int B2, bool REG, bool HOOK, bool WRITE, bool CMP>
+// with blk_orig when there is one). EDGE: a block cut by the field boundary, extents
+// e0 x e1 x e2 within the compile-time shape: the loops stop at the extents, a central row is
+// e2 central codewords, symbols are decoded one at a time and stored one at a time.
+template <typename T, int NDIM, int B0, int B1, int B2, bool REG, bool HOOK, bool WRITE, bool CMP, bool EDGE = false>
 __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const uint8_t* lim, const Hdr& h,
                                             const BlockIn& bi, const Tables& tb, T* plane, T* __restrict__ blk_out,
                                             const T* __restrict__ blk_orig, uint64_t si, uint64_t sj, bool vec2,
                                             uint32_t kinj, uint32_t bitinj, unsigned long long* sum_out,
-                                            unsigned long long* viol, double* maxerr) {
+                                            unsigned long long* viol, double* maxerr, uint32_t e0 = B0,
+                                            uint32_t e1 = B1, uint32_t e2 = B2) {
   const Geo& g = h.g;
   const T eb = (T)h.eb;
   const int R = (int)g.R;
@@ -404,16 +407,24 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
 #pragma unroll
     for (int l = 0; l < B2; ++l) clp[l] = FT<T>::mul(cT[NDIM == 3 ? 2 : 1], (T)l);
   }
+  // a central row: the central codeword repeated over the row (e2 codes for an edge block)
+  uint32_t rbits = tb.rbits, rpat = tb.rpat;
+  if (EDGE && rbits) {
+    const uint32_t lc = rbits / B2;
+    rbits = lc * e2;
+    rpat >>= lc * (B2 - e2);
+  }
+  const int n0 = EDGE ? (int)e0 : B0, n1 = EDGE ? (int)e1 : B1;
   T brow[B2], arow[B2];
 #pragma unroll 1
-  for (int i = 0; i < B0; ++i) {
+  for (int i = 0; i < n0; ++i) {
 #pragma unroll
     for (int l = 0; l < B2; ++l) {
       brow[l] = T(0);
       arow[l] = T(0);
     }
 #pragma unroll 1
-    for (int j = 0; j < B1; ++j) {
+    for (int j = 0; j < n1; ++j) {
       T ra = T(0);
       if (REG) {
         if (NDIM == 3) ra = FT<T>::add(FT<T>::mul(cT[0], (T)i), FT<T>::mul(cT[1], (T)j));
@@ -422,7 +433,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       T* prow = plane + j * B2 * 256;
       T out[B2];
       T c = T(0), ac = T(0), bc = T(0), abc = T(0);
-      const uint32_t k0 = (uint32_t)((i * B1 + j) * B2);
+      const uint32_t k0 = EDGE ? (uint32_t)((i * n1 + j) * (int)e2) : (uint32_t)((i * B1 + j) * B2);
       // the neighbours of point l (Lorenzo) and its prediction
       auto predict = [&](int l, T& a, T& bb, T& ab) {
         a = bb = ab = T(0);
@@ -465,10 +476,11 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       };
       // a row of central codes (the common case of a smooth field) in one comparison: every
       // point is pred + (T)(2 * 0) * eb = pred + 0
-      if (tb.rbits && (br.peek() >> (32 - tb.rbits)) == tb.rpat) {
-        br.advance(tb.rbits);
+      if (rbits && (br.peek() >> (32 - rbits)) == rpat) {
+        br.advance(rbits);
 #pragma unroll
         for (int l = 0; l < B2; ++l) {
+          if (EDGE && l >= (int)e2) break;
           T a, bb, ab;
           const T pred = predict(l, a, bb, ab);
           commit(l, FT<T>::add(pred, T(0)), a, bb, ab);
@@ -477,8 +489,9 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
         int qp = 0;  // second symbol of the pair decoded at even l
 #pragma unroll
         for (int l = 0; l < B2; ++l) {
+          if (EDGE && l >= (int)e2) break;
           int q;
-          if ((B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
+          if (!EDGE && (B2 & 1) == 0) {  // the fast shapes have even rows: symbols come in pairs
             if (!(l & 1)) br.next2(tb.lut2, tb.lut, *tb.cn, tb.syms, tb.n_live, q, qp, CMP);
             else q = (CMP && qp == kDefer) ? br.next(tb.lut, *tb.cn, tb.syms, tb.n_live) : qp;
           } else {
@@ -498,7 +511,11 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       }
       const uint64_t ro = (uint64_t)i * si + (uint64_t)j * sj;
       if (WRITE) {  // streaming stores: the field is not read again, the stream's bytes are
-        if ((B2 % 2) == 0 && vec2) {
+        if (EDGE) {
+#pragma unroll
+          for (int l = 0; l < B2; ++l)
+            if (l < (int)e2) __stcs(blk_out + ro + l, out[l]);
+        } else if ((B2 % 2) == 0 && vec2) {
           typedef typename std::conditional<sizeof(T) == 4, float2, double2>::type V2;
           V2* p = reinterpret_cast<V2*>(blk_out + ro);
 #pragma unroll
@@ -516,6 +533,7 @@ __device__ __forceinline__ bool decode_fast(const uint8_t* __restrict__ s, const
       if (!WRITE && blk_orig) {
 #pragma unroll
         for (int l = 0; l < B2; ++l) {
+          if (EDGE && l >= (int)e2) break;
           const T xo = blk_orig[ro + l];
           bool bad;
           if (FT<T>::finite(xo)) {
@@ -944,50 +962,6 @@ __global__ void __launch_bounds__(256) k_decode(const uint8_t* __restrict__ s, u
   acc.commit(st);
 }
 
-// Edge blocks after the fast kernel: one thread per edge block, enumerated compactly; offsets
-// from the stored group base plus the block table of the group up to the block.
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_decode_edges(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h, T* field,
-                                                      uint8_t* status, const T* orig, State* st,
-                                                      const sdcsz_flip* __restrict__ flips, uint32_t nflips,
-                                                      uint64_t count) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Smem sm;
-  uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
-  const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
-  if (!cta_tables(s, h, sm, lut, syms, st)) return;
-  const Tables tb = {lut, &sm.cn, syms, h.n_live, nullptr};
-  const uint8_t* lim = s + nbytes;
-  Walker<T, NDIM> wk;
-  wk.base = reinterpret_cast<T*>(smem + (4u << kLutBits)) + threadIdx.x;
-  wk.stride = blockDim.x;
-  wk.B2 = h.g.B[2];
-  wk.sr = h.g.B[1] * h.g.B[2];
-  Acc acc;
-  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < count) {
-    const Geo& g = h.g;
-    const uint64_t b = edge_block(g, e);
-    BlockIn bi;
-    const bool placed = place_block(s, h, b, &bi);
-    uint8_t stv;
-    if (!placed) {
-      atomicOr(&st->error, ERR_FORMAT);
-      stv = SDCSZ_BLOCK_BAD;
-      ++acc.bad;
-    } else {
-      uint32_t kinj, bitinj;
-      find_inj(flips, nflips, b, &kinj, &bitinj);
-      stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv, double* me) {
-        return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone, bitinj,
-                                       sum, nv, me);
-      }, acc);
-    }
-    if (status) status[b] = stv;
-  }
-  acc.commit(st);
-}
-
 // Region decompression: the blocks that intersect a box, one thread each (enumerated over the
 // box's block range), decoded and verified on their own (Sec. 5.1 random access) and stored
 // into a dense array of the box's shape.
@@ -1054,17 +1028,17 @@ __device__ __forceinline__ bool fast_dispatch(bool reg, const uint8_t* s, const 
 
 // Fast kernel: full blocks of a compile-time shape (WRITE: decompression, else verification;
 // CMP: compact encoding).
-template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE, bool CMP>
-__device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, uint64_t nbytes, const Hdr& h, T* field,
-                                                uint8_t* status, const T* orig, State* st,
-                                                const sdcsz_flip* __restrict__ flips, uint32_t nflips, int vec2,
-                                                unsigned char* smem) {
-  __shared__ Smem sm;
+// The fast decoder's shared-memory tables (every thread of the CTA): the first-level table and
+// the pair table in `smem`, the canonical tables in `sm`, and the pattern of a row of B2 central
+// codes. False for a bad code table.
+template <int B2, bool CMP>
+__device__ __forceinline__ bool fast_tables(const uint8_t* s, const Hdr& h, Smem& sm, unsigned char* smem, State* st,
+                                            Tables* tb) {
   uint32_t* lut = reinterpret_cast<uint32_t*>(smem);
   const uint16_t* syms = reinterpret_cast<const uint16_t*>(s + h.L.table + 4 * (kMaxLen + 1));
   __shared__ uint32_t s_central;  // central codeword: bits << 8 | length (0: none in the window)
   if (threadIdx.x == 0) s_central = 0;
-  if (!cta_tables(s, h, sm, lut, syms, st)) return;
+  if (!cta_tables(s, h, sm, lut, syms, st)) return false;
   uint2* lut2 = reinterpret_cast<uint2*>(smem + (4u << kLutBits));
   __syncthreads();
   pair_table(lut2, lut, CMP);
@@ -1082,7 +1056,84 @@ __device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, u
       for (int l = 0; l < B2; ++l) rpat = (lc * (B2 - 1 - l) < 32u) ? (rpat | (cc << (lc * (B2 - 1 - l)))) : rpat;
     }
   }
-  const Tables tb = {lut, &sm.cn, syms, h.n_live, lut2, rbits, rpat};
+  *tb = Tables{lut, &sm.cn, syms, h.n_live, lut2, rbits, rpat};
+  return true;
+}
+
+// Edge blocks of a field whose full blocks take the fast kernel: one thread per edge block
+// (compact enumeration), walked by the fast decoder's compile-time code at the block's extents;
+// a block whose worst case could read past the stream takes the bounds-checked generic walk.
+// Offsets from the stored group base plus the group's block table up to the block.
+template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE, bool CMP>
+__global__ void __launch_bounds__(256, 2) k_decode_edges_fast(const uint8_t* __restrict__ s, uint64_t nbytes, Hdr h,
+                                                              T* field, uint8_t* status, const T* orig, State* st,
+                                                              const sdcsz_flip* __restrict__ flips, uint32_t nflips,
+                                                              uint64_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Smem sm;
+  Tables tb;
+  if (!fast_tables<B2, CMP>(s, h, sm, smem, st, &tb)) return;
+  const uint8_t* lim = s + nbytes;
+  T* plane = reinterpret_cast<T*>(smem + (12u << kLutBits)) + threadIdx.x;
+  Walker<T, NDIM> wk;
+  wk.base = plane;
+  wk.stride = blockDim.x;
+  wk.B2 = B2;
+  wk.sr = B1 * B2;
+  const Geo& g = h.g;
+  const uint64_t si = g.d[1] * g.d[2], sj = g.d[2];
+  Acc acc;
+  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) {
+    const uint64_t b = edge_block(g, e);
+    const Box x = block_box(g, b);
+    BlockIn bi;
+    uint8_t stv;
+    if (!place_block(s, h, b, &bi)) {
+      atomicOr(&st->error, ERR_FORMAT);
+      stv = SDCSZ_BLOCK_BAD;
+      ++acc.bad;
+    } else {
+      const uint64_t bo = row_base(g, x, 0, 0);
+      T* out = WRITE ? field + bo : nullptr;
+      const T* org = (!WRITE && orig) ? orig + bo : nullptr;
+      const bool reg = bi.reg_idx >= 0;
+      uint32_t kinj, bitinj;
+      find_inj(flips, nflips, b, &kinj, &bitinj);
+      const uint64_t worst = CMP ? (3ull + sizeof(T)) * (B0 * B1 * B2) + 19 : 3ull * (B0 * B1 * B2);
+      const bool safe = (uint64_t)(lim - (s + h.L.payload)) >= bi.pay_off + worst + 16;
+      stv = verify_block(s, h, b, [&](bool first, unsigned long long* sum, unsigned long long* nv, double* me) {
+        if (!safe)
+          return decode_generic<T, NDIM>(s, lim, h, bi, tb, wk, FieldSink<T>{field}, orig, first ? kinj : kNone,
+                                         bitinj, sum, nv, me);
+        const uint32_t ki = first ? kinj : kNone;
+        if (reg) {
+          if (ki != kNone)
+            return decode_fast<T, NDIM, B0, B1, B2, true, true, WRITE, CMP, true>(
+                s, lim, h, bi, tb, plane, out, org, si, sj, false, ki, bitinj, sum, nv, me, x.e[0], x.e[1], x.e[2]);
+          return decode_fast<T, NDIM, B0, B1, B2, true, false, WRITE, CMP, true>(
+              s, lim, h, bi, tb, plane, out, org, si, sj, false, kNone, 0, sum, nv, me, x.e[0], x.e[1], x.e[2]);
+        }
+        if (ki != kNone)
+          return decode_fast<T, NDIM, B0, B1, B2, false, true, WRITE, CMP, true>(
+              s, lim, h, bi, tb, plane, out, org, si, sj, false, ki, bitinj, sum, nv, me, x.e[0], x.e[1], x.e[2]);
+        return decode_fast<T, NDIM, B0, B1, B2, false, false, WRITE, CMP, true>(
+            s, lim, h, bi, tb, plane, out, org, si, sj, false, kNone, 0, sum, nv, me, x.e[0], x.e[1], x.e[2]);
+      }, acc);
+    }
+    if (status) status[b] = stv;
+  }
+  acc.commit(st);
+}
+
+template <typename T, int NDIM, int B0, int B1, int B2, bool WRITE, bool CMP>
+__device__ __forceinline__ void decode_fast_cta(const uint8_t* __restrict__ s, uint64_t nbytes, const Hdr& h, T* field,
+                                                uint8_t* status, const T* orig, State* st,
+                                                const sdcsz_flip* __restrict__ flips, uint32_t nflips, int vec2,
+                                                unsigned char* smem) {
+  __shared__ Smem sm;
+  Tables tb;
+  if (!fast_tables<B2, CMP>(s, h, sm, smem, st, &tb)) return;
   const uint8_t* lim = s + nbytes;
   T* plane = reinterpret_cast<T*>(smem + (12u << kLutBits)) + threadIdx.x;
   Walker<T, NDIM> wk;  // for the few blocks that take the generic decoder
@@ -1213,12 +1264,22 @@ inline unsigned persistent_grid(K kern, uint32_t threads, size_t smem, uint64_t 
   return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ngroups, (uint64_t)occ * L.sms));
 }
 
-template <typename T, int NDIM, int B0, int B1, int B2>
+// CMP: the compact encoding's kernels (instantiated in their own translation units).
+template <typename T, int NDIM, int B0, int B1, int B2, bool CMP>
 void run_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
-              const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
+              const sdcsz_flip* flips, uint32_t nflips, const Launch& L, const Launch& Le) {
   const size_t smem = (12u << kLutBits) + (size_t)walker_slots(NDIM, h.g.B) * 256 * sizeof(T);  // lut, pair lut, plane
-  auto kern = h.g.enc ? (field ? k_decode_fast_c<T, NDIM, B0, B1, B2, true> : k_decode_fast_c<T, NDIM, B0, B1, B2, false>)
-                      : (field ? k_decode_fast<T, NDIM, B0, B1, B2, true> : k_decode_fast<T, NDIM, B0, B1, B2, false>);
+  // the edge blocks, on Le (the side stream), with the same compile-time walk at their extents
+  if (const uint64_t count = edge_count(h.g)) {
+    auto ke = field ? k_decode_edges_fast<T, NDIM, B0, B1, B2, true, CMP>
+                    : k_decode_edges_fast<T, NDIM, B0, B1, B2, false, CMP>;
+    allow_smem(reinterpret_cast<const void*>(ke), smem);
+    ke<<<(unsigned)((count + 255) / 256), 256, smem, Le.stream>>>(s, nbytes, h, field, status, orig, st, flips, nflips,
+                                                                   count);
+    note_launch();
+  }
+  auto kern = CMP ? (field ? k_decode_fast_c<T, NDIM, B0, B1, B2, true> : k_decode_fast_c<T, NDIM, B0, B1, B2, false>)
+                  : (field ? k_decode_fast<T, NDIM, B0, B1, B2, true> : k_decode_fast<T, NDIM, B0, B1, B2, false>);
   const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
   const unsigned grid = persistent_grid(kern, 256, smem, ngroups, L);
   const uintptr_t al = 2 * sizeof(T);
@@ -1235,32 +1296,32 @@ bool has_fast(const Geo& g) {
   return false;
 }
 
-template <typename T>
+template <typename T, bool CMP>
 bool try_fast(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint8_t* status, const T* orig, State* st,
-              const sdcsz_flip* flips, uint32_t nflips, const Launch& L) {
+              const sdcsz_flip* flips, uint32_t nflips, const Launch& L, const Launch& Le) {
   const Geo& g = h.g;
   // a 3D 16^3 float64 plane would not fit 256 threads' shared memory: generic path
   if (g.ndim == 3 && g.B[0] == g.B[1] && g.B[1] == g.B[2]) {
     switch (g.B[2]) {
-      case 4: run_fast<T, 3, 4, 4, 4>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
-      case 6: run_fast<T, 3, 6, 6, 6>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
-      case 8: run_fast<T, 3, 8, 8, 8>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      case 4: run_fast<T, 3, 4, 4, 4, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le); return true;
+      case 6: run_fast<T, 3, 6, 6, 6, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le); return true;
+      case 8: run_fast<T, 3, 8, 8, 8, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le); return true;
       case 10:
         if (sizeof(T) == 8) return false;
-        run_fast<T, 3, 10, 10, 10>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
+        run_fast<T, 3, 10, 10, 10, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le);
         return true;
       case 12:
         if (sizeof(T) == 8) return false;
-        run_fast<T, 3, 12, 12, 12>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
+        run_fast<T, 3, 12, 12, 12, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le);
         return true;
       default: return false;
     }
   }
   if (g.ndim == 2 && g.B[1] == g.B[2]) {
     switch (g.B[2]) {
-      case 8: run_fast<T, 2, 1, 8, 8>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
-      case 12: run_fast<T, 2, 1, 12, 12>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
-      case 16: run_fast<T, 2, 1, 16, 16>(s, nbytes, h, field, status, orig, st, flips, nflips, L); return true;
+      case 8: run_fast<T, 2, 1, 8, 8, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le); return true;
+      case 12: run_fast<T, 2, 1, 12, 12, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le); return true;
+      case 16: run_fast<T, 2, 1, 16, 16, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, Le); return true;
       default: return false;
     }
   }
@@ -1274,16 +1335,6 @@ void run_generic(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint
   uint32_t threads = 256;
   while (threads > 64 && per * threads > 192 * 1024) threads >>= 1;
   const size_t smem = (4u << kLutBits) + per * threads;
-  if (!all) {
-    const uint64_t count = edge_count(h.g);
-    if (!count) return;
-    auto ke = k_decode_edges<T, NDIM>;
-    allow_smem(reinterpret_cast<const void*>(ke), smem);
-    ke<<<(unsigned)((count + threads - 1) / threads), threads, smem, L.stream>>>(s, nbytes, h, field, status, orig,
-                                                                                  st, flips, nflips, count);
-    note_launch();
-    return;
-  }
   auto kern = k_decode<T, NDIM>;
   const uint64_t ngroups = (h.g.nb + kGroup - 1) / kGroup;
   const unsigned grid = persistent_grid(kern, threads, smem, ngroups, L);
@@ -1291,21 +1342,31 @@ void run_generic(const uint8_t* s, uint64_t nbytes, const Hdr& h, T* field, uint
   note_launch();
 }
 
-template <typename T>
-void launch_decode_t(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field_v, uint8_t* status,
-                     const void* orig_v, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
-                     const Launch& L) {
+// Fields whose block shape has a fast path: full blocks on the caller's stream, edge blocks on the
+// side stream (the encoding fixed at compile time).
+template <typename T, bool CMP>
+void launch_decode_fast_t(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field_v, uint8_t* status,
+                          const void* orig_v, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                          const Launch& L) {
   if (h.g.nb == 0) return;
   T* field = write ? static_cast<T*>(field_v) : nullptr;
   const T* orig = static_cast<const T*>(orig_v);
   Fork fk(L);
-  const bool fast = has_fast<T>(h.g);
-  const Launch Lg = fast ? fk.side_launch(L) : L;
-  if (h.g.ndim == 3) run_generic<T, 3>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, Lg);
-  else if (h.g.ndim == 2) run_generic<T, 2>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, Lg);
-  else run_generic<T, 1>(s, nbytes, h, field, status, orig, st, flips, nflips, !fast, Lg);
-  if (fast) try_fast<T>(s, nbytes, h, field, status, orig, st, flips, nflips, L);
+  try_fast<T, CMP>(s, nbytes, h, field, status, orig, st, flips, nflips, L, fk.side_launch(L));
   fk.join();
+}
+
+// Other shapes: the generic kernel for every block (either encoding).
+template <typename T>
+void launch_decode_generic_t(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field_v, uint8_t* status,
+                             const void* orig_v, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
+                             const Launch& L) {
+  if (h.g.nb == 0) return;
+  T* field = write ? static_cast<T*>(field_v) : nullptr;
+  const T* orig = static_cast<const T*>(orig_v);
+  if (h.g.ndim == 3) run_generic<T, 3>(s, nbytes, h, field, status, orig, st, flips, nflips, true, L);
+  else if (h.g.ndim == 2) run_generic<T, 2>(s, nbytes, h, field, status, orig, st, flips, nflips, true, L);
+  else run_generic<T, 1>(s, nbytes, h, field, status, orig, st, flips, nflips, true, L);
 }
 
 template <typename T>
