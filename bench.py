@@ -882,7 +882,10 @@ def run_region(args):
 # FP64 instructions (DADD + DMUL + DFMA, thread level) per point of each stage of the float64
 # path, from an ncu capture (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum
 # over every launch of the stage / points), keyed by the hash of the stage's sources.
-NCU_FP64_PER_POINT = {}
+NCU_FP64_PER_POINT = {
+    "predict": {"per_point": 10.75, "src": "1a3f5d6f3cb9"},
+    "decode": {"per_point": 3.46, "src": "b14b0f440dd1"},
+}
 
 
 def fp64_rate(device, reps=5):
@@ -914,8 +917,8 @@ def fp64_rate(device, reps=5):
 
 
 def run_fp64(args):
-    """The float64 path against the FP64 instruction rate: 512^3 float64 (spikes), rel 1e-4,
-    8^3 blocks, ABFT on and off, with this GPU's measured DADD/DMUL rate beside it."""
+    """The float64 path against the FP64 instruction rate: 512^3 float64 (spikes; --fp64-size
+    sets the edge), rel 1e-4, 8^3 blocks, ABFT on and off, with this GPU's measured DADD/DMUL rate beside it."""
     import torch
 
     import paper_2010_03144_gb300 as sz
@@ -928,7 +931,8 @@ def run_fp64(args):
     clk = ClockSampler()
     clk.start()
     rate = fp64_rate(dev)
-    shape, B, rel = (512, 512, 512), 8, 1e-4
+    n = args.fp64_size
+    shape, B, rel = (n, n, n), 8, 1e-4
     x = synth.device_field(shape, 21, torch.float64, dev, spikes=0.01)
     N = x.numel()
     rows = {}
@@ -964,7 +968,7 @@ def run_fp64(args):
         "metric": "float64 round trip GB/s and FP64 instruction-rate fraction", "unit": "GB/s",
         "value": rows["abft_on"]["round_trip_gbs"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fp64: 512^3 float64 sinusoids+noise+1% spikes, rel eb 1e-4, block 8^3; one step = "
+        "config": {"workload": f"fp64: {n}^3 float64 sinusoids+noise+1% spikes, rel eb 1e-4, block 8^3; one step = "
                                "compress + decompress", "l2": "inputs larger than L2 (no flush)"},
         "fp64_rate_gops": {k: round(v / 1e9, 1) for k, v in rate.items()},
         "fp64_rate_what": "measured: independent DADD+DMUL chains (add_mul) and DFMA chains (fma), "
@@ -981,6 +985,7 @@ def main():
     ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batch13", "serve", "faults", "region", "fp64"),
                     default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--fp64-size", type=int, default=512, help="float64 workload: edge of the cube")
     ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
     ap.add_argument("--encoding", choices=("raw", "compact"), default="raw",
                     help="stream encoding: raw coefficient/unpredictable sections, or compact (in the payload)")
