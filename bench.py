@@ -986,6 +986,8 @@ def main():
                     default="512cube")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--fp64-size", type=int, default=512, help="float64 workload: edge of the cube")
+    ap.add_argument("--block", type=int, default=0,
+                    help="block edge for the 512cube/384cube/64cube workloads (default: the workload's)")
     ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
     ap.add_argument("--encoding", choices=("raw", "compact"), default="raw",
                     help="stream encoding: raw coefficient/unpredictable sections, or compact (in the payload)")
@@ -993,6 +995,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.block and args.workload in WORKLOADS and args.block != WORKLOADS[args.workload]["block"]:
+        # another block edge is another workload (its own name, no stored ncu figures)
+        name = f"{args.workload}_b{args.block}"
+        WORKLOADS[name] = dict(WORKLOADS[args.workload], block=args.block)
+        args.workload = name
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch13":

@@ -1012,7 +1012,7 @@ int sdcsz_batch_bind(sdcsz_batch* b, void* d_ws, size_t ws_bytes, void* stream) 
     Job& jb = b->h_table[j];
     jb.g = b->geo[j];
     jb.w = bind_ws(base + b->ws_off[j], b->plan[j]);
-    jb.fast = prep_has_fast(jb.g) ? 1 : 0;
+    jb.fast = batch_fast_ok(jb.g) ? 1 : 0;
     jb.gcount = jb.fast ? edge_count(jb.g) : jb.g.nb;
   }
   batch_fill_jobs(b);

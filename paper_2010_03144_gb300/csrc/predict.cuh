@@ -1052,7 +1052,20 @@ __global__ void __launch_bounds__(128, SDCSZ_PRED_MINB) k_predict_fast_batch(Bat
       });
 }
 
+}  // namespace
+}  // namespace kpred
+}  // namespace sdcsz
+
+#include "predict_wave.cuh"
+
+namespace sdcsz {
+namespace kpred {
+namespace {
+
 // ---------------------------------------------------------------- launch
+// Shared memory the one-thread-per-block kernels may ask for (128 threads' Lorenzo planes).
+constexpr size_t kLanePlaneSmemMax = 200 * 1024;
+
 template <class K>
 inline void launch_persistent(K kern, uint32_t threads, size_t smem, uint64_t nb, const Launch& L, dim3* grid_out) {
   const int occ = occupancy(reinterpret_cast<const void*>(kern), (int)threads, smem);
@@ -1089,12 +1102,43 @@ void run_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
   note_launch();
 }
 
+// Cube blocks of edge B (10, 12, 16) by the wavefront kernel, G blocks per CTA: the full
+// blocks (edge = false), or the blocks cut by the field boundary (edge = true, their compact
+// enumeration, on the second work queue).
+template <typename T, int B, int G, bool ABFT, bool CMP>
+void run_wave(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
+              const Launch& L, bool edge) {
+  typedef WaveCfg<T, B, G> C;
+  auto kern = k_predict_wave<T, B, G, ABFT, CMP>;
+  const uint64_t count = edge ? edge_count(g) : g.nb;
+  if (!count) return;
+  const uint64_t ngroups = (count + G - 1) / G;
+  dim3 grid;
+  launch_persistent(kern, C::NT, C::SMEM, ngroups * C::NT, L, &grid);
+  // the widest cp.async chunk every row start of every block allows
+  const uintptr_t fp = reinterpret_cast<uintptr_t>(field);
+  int cb = C::ES;
+  for (int c = 16; c > C::ES; c >>= 1)
+    if ((B * C::ES) % c == 0 && (g.d[2] * C::ES) % c == 0 && fp % c == 0) {
+      cb = c;
+      break;
+    }
+  const bool vec2 = (g.d[2] % 2 == 0) && (fp % (2 * sizeof(T)) == 0);
+  kern<<<grid, C::NT, C::SMEM, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, cb, vec2 ? 1 : 0,
+                                           edge ? 1 : 0, count);
+  note_launch();
+}
+
 template <typename T, int NDIM, int B0, int B1, int B2, bool ABFT, bool CMP>
 void run_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips,
               const Launch& L) {
   const uint64_t count = edge_count(g);
   if (!count) return;
   const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
+  if (smem > kLanePlaneSmemMax) {  // 16^3 float64: 128 threads' planes do not fit, the generic walk
+    run_generic<T, NDIM, ABFT>(field, g, w, flips, nflips, false, L);
+    return;
+  }
   auto kern = k_predict_edge<T, NDIM, B0, B1, B2, ABFT, CMP>;
   dim3 grid;
   launch_persistent(kern, 128, smem, count, L, &grid);
@@ -1110,9 +1154,9 @@ void try_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
       case 4: run_edge<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       case 6: run_edge<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       case 8: run_edge<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); break;
-      case 10: run_edge<T, 3, 10, 10, 10, ABFT, CMP>(field, g, w, flips, nflips, L); break;
-      case 12: run_edge<T, 3, 12, 12, 12, ABFT, CMP>(field, g, w, flips, nflips, L); break;
-      case 16: run_edge<T, 3, 16, 16, 16, ABFT, CMP>(field, g, w, flips, nflips, L); break;
+      case 10: run_wave<T, 10, 16, ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
+      case 12: run_wave<T, 12, 16, ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
+      case 16: run_wave<T, 16, 8, ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
       default: break;
     }
   } else if (g.ndim == 2) {
@@ -1141,9 +1185,9 @@ bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
       case 4: run_fast<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       case 6: run_fast<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       case 8: run_fast<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
-      case 10: run_fast<T, 3, 10, 10, 10, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
-      case 12: run_fast<T, 3, 12, 12, 12, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
-      case 16: run_fast<T, 3, 16, 16, 16, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
+      case 10: run_wave<T, 10, 16, ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
+      case 12: run_wave<T, 12, 16, ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
+      case 16: run_wave<T, 16, 8, ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
       default: return false;
     }
   }
@@ -1190,6 +1234,7 @@ void batch_fast(const BatchArgs& a, const Launch& L) {
 
 template <typename T, bool ABFT, bool CMP>
 bool batch_fast_shape(int ndim, uint32_t B, const BatchArgs& a, const Launch& L) {
+  if (ndim == 3 && (size_t)B * B * 128 * sizeof(T) > kLanePlaneSmemMax) return false;  // see batch_fast_ok
   if (ndim == 3) {
     switch (B) {
       case 4: batch_fast<T, 3, 4, 4, 4, ABFT, CMP>(a, L); return true;

@@ -749,6 +749,11 @@ struct NoOp {
 
 // Batched launches (one per stage and kernel shape; see BatchArgs).
 bool prep_has_fast(const Geo& g);
+// Batched jobs whose full blocks take the fast kernels of every stage: the fast shapes, except
+// 16^3 float64, whose one-thread-per-block Lorenzo planes (2 KB a thread) do not fit a CTA.
+inline bool batch_fast_ok(const Geo& g) {
+  return prep_has_fast(g) && !(g.ndim == 3 && g.dtype == 1 && g.B[2] == 16);
+}
 bool batch_prep_fast(int dtype, int ndim, uint32_t B, const BatchArgs& a, const Launch& L);
 void batch_prep_generic(int dtype, int ndim, const BatchArgs& a, size_t smem, const Launch& L);
 void batch_bound(const Job* jobs, uint32_t n, const Launch& L);
