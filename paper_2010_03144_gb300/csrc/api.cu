@@ -862,7 +862,10 @@ void batch_plan_launches(sdcsz_batch* b) {
     const uint32_t slots = walker_slots(g.ndim, g.B);
     if (jb.fast) {
       add(BK_PREP_FAST, g.dtype, g.ndim, g.B[2], false, 128, 0, j, ceil_div(g.nb, 128));
-      add(BK_PREDICT_FAST, g.dtype, g.ndim, g.B[2], g.abft != 0, 128, 0, j, ceil_div(g.nb, 128), g.enc != 0);
+      // wavefront shapes: items are groups of full blocks, then groups of edge blocks
+      const uint64_t wg = wave_groups(g);
+      add(BK_PREDICT_FAST, g.dtype, g.ndim, g.B[2], g.abft != 0, 128, 0, j, wg ? wg : ceil_div(g.nb, 128),
+          g.enc != 0);
     }
     add(BK_PREP_GENERIC, g.dtype, g.ndim, 0, false, 128, g.predictor == 0 ? (size_t)slots * 128 * 4 : 0, j,
         ceil_div(jb.gcount, 128));
@@ -880,7 +883,8 @@ void batch_plan_launches(sdcsz_batch* b) {
     std::vector<uint64_t> items;
     for (uint32_t j : L.jobs) {
       const Geo& g = b->geo[j];
-      const uint64_t n = ceil_div(b->h_table[j].gcount, L.threads);
+      // the wavefront kernel predicts the edge blocks of its shapes too
+      const uint64_t n = (b->h_table[j].fast && wave_groups(g)) ? 0 : ceil_div(b->h_table[j].gcount, L.threads);
       if (!n) continue;
       per = std::max(per, (size_t)walker_slots(g.ndim, g.B) * (g.dtype ? 8 : 4));
       jobs.push_back(j);
@@ -1012,7 +1016,7 @@ int sdcsz_batch_bind(sdcsz_batch* b, void* d_ws, size_t ws_bytes, void* stream) 
     Job& jb = b->h_table[j];
     jb.g = b->geo[j];
     jb.w = bind_ws(base + b->ws_off[j], b->plan[j]);
-    jb.fast = batch_fast_ok(jb.g) ? 1 : 0;
+    jb.fast = prep_has_fast(jb.g) ? 1 : 0;
     jb.gcount = jb.fast ? edge_count(jb.g) : jb.g.nb;
   }
   batch_fill_jobs(b);

@@ -1115,17 +1115,7 @@ void run_wave(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
   const uint64_t ngroups = (count + G - 1) / G;
   dim3 grid;
   launch_persistent(kern, C::NT, C::SMEM, ngroups * C::NT, L, &grid);
-  // the widest cp.async chunk every row start of every block allows
-  const uintptr_t fp = reinterpret_cast<uintptr_t>(field);
-  int cb = C::ES;
-  for (int c = 16; c > C::ES; c >>= 1)
-    if ((B * C::ES) % c == 0 && (g.d[2] * C::ES) % c == 0 && fp % c == 0) {
-      cb = c;
-      break;
-    }
-  const bool vec2 = (g.d[2] % 2 == 0) && (fp % (2 * sizeof(T)) == 0);
-  kern<<<grid, C::NT, C::SMEM, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, cb, vec2 ? 1 : 0,
-                                           edge ? 1 : 0, count);
+  kern<<<grid, C::NT, C::SMEM, L.stream>>>(static_cast<const T*>(field), g, w, flips, nflips, edge ? 1 : 0, count);
   note_launch();
 }
 
@@ -1135,7 +1125,7 @@ void run_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
   const uint64_t count = edge_count(g);
   if (!count) return;
   const size_t smem = (NDIM == 3) ? (size_t)B1 * B2 * 128 * sizeof(T) : 0;
-  if (smem > kLanePlaneSmemMax) {  // 16^3 float64: 128 threads' planes do not fit, the generic walk
+  if (smem > kLanePlaneSmemMax) {  // 128 threads' planes would not fit: the generic walk
     run_generic<T, NDIM, ABFT>(field, g, w, flips, nflips, false, L);
     return;
   }
@@ -1154,9 +1144,9 @@ void try_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
       case 4: run_edge<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       case 6: run_edge<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       case 8: run_edge<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); break;
-      case 10: run_wave<T, 10, 16, ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
-      case 12: run_wave<T, 12, 16, ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
-      case 16: run_wave<T, 16, 8, ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
+      case 10: run_wave<T, 10, wave_group_blocks(10), ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
+      case 12: run_wave<T, 12, wave_group_blocks(12), ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
+      case 16: run_wave<T, 16, wave_group_blocks(16), ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
       default: break;
     }
   } else if (g.ndim == 2) {
@@ -1185,9 +1175,9 @@ bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
       case 4: run_fast<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       case 6: run_fast<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       case 8: run_fast<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
-      case 10: run_wave<T, 10, 16, ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
-      case 12: run_wave<T, 12, 16, ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
-      case 16: run_wave<T, 16, 8, ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
+      case 10: run_wave<T, 10, wave_group_blocks(10), ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
+      case 12: run_wave<T, 12, wave_group_blocks(12), ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
+      case 16: run_wave<T, 16, wave_group_blocks(16), ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
       default: return false;
     }
   }
@@ -1232,17 +1222,28 @@ void batch_fast(const BatchArgs& a, const Launch& L) {
   note_launch();
 }
 
+// Batched wavefront kernel: items are groups of G blocks (wave_groups).
+template <typename T, int B, int G, bool ABFT, bool CMP>
+void batch_wave(const BatchArgs& a, const Launch& L) {
+  static_assert(G == wave_group_blocks(B), "the launch plan counts groups of this size");
+  typedef WaveCfg<T, B, G> C;
+  auto kern = k_predict_wave_batch<T, B, G, ABFT, CMP>;
+  dim3 grid;
+  launch_persistent(kern, C::NT, C::SMEM, a.start[a.n] * C::NT, L, &grid);
+  kern<<<grid, C::NT, C::SMEM, L.stream>>>(a);
+  note_launch();
+}
+
 template <typename T, bool ABFT, bool CMP>
 bool batch_fast_shape(int ndim, uint32_t B, const BatchArgs& a, const Launch& L) {
-  if (ndim == 3 && (size_t)B * B * 128 * sizeof(T) > kLanePlaneSmemMax) return false;  // see batch_fast_ok
   if (ndim == 3) {
     switch (B) {
       case 4: batch_fast<T, 3, 4, 4, 4, ABFT, CMP>(a, L); return true;
       case 6: batch_fast<T, 3, 6, 6, 6, ABFT, CMP>(a, L); return true;
       case 8: batch_fast<T, 3, 8, 8, 8, ABFT, CMP>(a, L); return true;
-      case 10: batch_fast<T, 3, 10, 10, 10, ABFT, CMP>(a, L); return true;
-      case 12: batch_fast<T, 3, 12, 12, 12, ABFT, CMP>(a, L); return true;
-      case 16: batch_fast<T, 3, 16, 16, 16, ABFT, CMP>(a, L); return true;
+      case 10: batch_wave<T, 10, wave_group_blocks(10), ABFT, CMP>(a, L); return true;
+      case 12: batch_wave<T, 12, wave_group_blocks(12), ABFT, CMP>(a, L); return true;
+      case 16: batch_wave<T, 16, wave_group_blocks(16), ABFT, CMP>(a, L); return true;
       default: return false;
     }
   }

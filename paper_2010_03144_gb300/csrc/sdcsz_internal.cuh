@@ -749,10 +749,13 @@ struct NoOp {
 
 // Batched launches (one per stage and kernel shape; see BatchArgs).
 bool prep_has_fast(const Geo& g);
-// Batched jobs whose full blocks take the fast kernels of every stage: the fast shapes, except
-// 16^3 float64, whose one-thread-per-block Lorenzo planes (2 KB a thread) do not fit a CTA.
-inline bool batch_fast_ok(const Geo& g) {
-  return prep_has_fast(g) && !(g.ndim == 3 && g.dtype == 1 && g.B[2] == 16);
+// Cube edges whose prediction takes the wavefront kernel, and its blocks per CTA group (0: the
+// one-thread-per-block kernels).
+__host__ __device__ constexpr uint32_t wave_group_blocks(uint32_t B) { return B == 16 ? 8 : (B == 10 || B == 12) ? 16 : 0; }
+inline uint64_t wave_groups(const Geo& g) {  // 0 unless g's blocks take the wavefront kernel
+  if (g.ndim != 3 || g.B[0] != g.B[1] || g.B[1] != g.B[2]) return 0;
+  const uint64_t G = wave_group_blocks(g.B[2]);
+  return G ? (g.nb + G - 1) / G + (edge_count(g) + G - 1) / G : 0;
 }
 bool batch_prep_fast(int dtype, int ndim, uint32_t B, const BatchArgs& a, const Launch& L);
 void batch_prep_generic(int dtype, int ndim, const BatchArgs& a, size_t smem, const Launch& L);

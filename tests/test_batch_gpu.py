@@ -25,6 +25,13 @@ CASES = [
     ((40, 40, 40), np.float32, dict(eb=1e-3, abft=False)),           # ABFT off
     ((50, 60), np.float64, dict(eb=0.01, eb_mode="abs")),            # absolute bound
     ((26, 100, 120), np.float32, dict(eb=1e-2, predictor="lorenzo")),
+    # the wavefront kernel's shapes: full and edge blocks of several jobs in one launch
+    ((50, 40, 64), np.float32, dict(eb=1e-3, block=16)),
+    ((48, 48, 48), np.float32, dict(eb=1e-3, block=16, abft=False)),
+    ((64, 35, 33), np.float32, dict(eb=1e-3, block=16)),
+    ((36, 30, 40), np.float32, dict(eb=1e-4, block=12)),
+    ((40, 45, 30), np.float64, dict(eb=1e-4, block=10)),
+    ((34, 32, 48), np.float64, dict(eb=1e-4, block=16)),
 ]
 
 
