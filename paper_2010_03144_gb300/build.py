@@ -25,7 +25,7 @@ PEAK_SRC = "peak_fp64.cu"
 PEAK_LIB = os.path.join(HERE, "libsdcsz_peak.so")
 SOURCES = ["api.cu", "k_prep.cu", "k_predict_f32.cu", "k_predict_f64.cu", "k_predict_f32c.cu", "k_predict_f64c.cu",
            "k_flip.cu", "k_codebook.cu", "k_encode.cu", "k_decode_f32.cu", "k_decode_f64.cu", "k_decode_f32c.cu",
-           "k_decode_f64c.cu", "k_lossless.cu", "server.cu", "shard.cu"]
+           "k_decode_f64c.cu", "k_decode_wave.cu", "k_lossless.cu", "server.cu", "shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false",
          "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

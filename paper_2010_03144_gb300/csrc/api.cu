@@ -435,7 +435,7 @@ int parse_header(const uint8_t* s, uint64_t nbytes, Hdr* h, sdcsz_params* pout) 
 
 int decode_enqueue(const void* d_stream, size_t nbytes, const Hdr& h, void* d_field, size_t field_bytes,
                    uint8_t* status, const void* d_orig, bool write, State* st, cudaStream_t s, const sdcsz_flip* flips,
-                   size_t n_flips, uint8_t* raw) {
+                   size_t n_flips, uint8_t* raw, uint8_t* wave) {
   const uint64_t need = h.g.N * (h.g.dtype ? 8 : 4);
   if (write && need && (!d_field || field_bytes < need)) return d_field ? SDCSZ_ECAPACITY : SDCSZ_EINVAL;
   if (n_flips > 0xffffffffu || (n_flips && !flips)) return SDCSZ_EINVAL;
@@ -453,14 +453,14 @@ int decode_enqueue(const void* d_stream, size_t nbytes, const Hdr& h, void* d_fi
     src = raw;
     n = h.raw_total;
   }
-  launch_decode(src, n, h, d_field, status, d_orig, st, write, flips, (uint32_t)n_flips, L);
+  launch_decode(src, n, h, d_field, status, d_orig, st, write, flips, (uint32_t)n_flips, L, wave);
   return SDCSZ_OK;
 }
 
-// Decompression workspace: the State, then (lossless stage) the stream without the stage.
-size_t decode_ws_bytes(const Hdr& h) {
-  return align256(sizeof(State)) + (h.g.lossless ? align256(h.raw_total) : 0);
-}
+// Decompression workspace: the State, then (lossless stage) the stream without the stage, then
+// (recommended size) the two-pass decoder's buffers.
+size_t decode_ws_min(const Hdr& h) { return align256(sizeof(State)) + (h.g.lossless ? align256(h.raw_total) : 0); }
+size_t decode_ws_bytes(const Hdr& h) { return decode_ws_min(h) + wave_decode_ws_bytes(h.g); }
 
 int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes, uint8_t* status,
                     const void* d_orig, bool write, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,
@@ -478,16 +478,21 @@ int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t f
   Hdr h;
   int rc = parse_header(hb, nbytes, &h, nullptr);
   if (rc) return rc;
-  if (ws_bytes < decode_ws_bytes(h)) return SDCSZ_ECAPACITY;
+  if (ws_bytes < decode_ws_min(h)) return SDCSZ_ECAPACITY;
   State* st = static_cast<State*>(d_ws);
   uint8_t* raw = static_cast<uint8_t*>(d_ws) + align256(sizeof(State));
+  // the two-pass decoder of large cube blocks when the workspace holds its buffers
+  uint8_t* wave = (wave_decode_ws_bytes(h.g) && ws_bytes >= decode_ws_bytes(h))
+                      ? static_cast<uint8_t*>(d_ws) + decode_ws_min(h)
+                      : nullptr;
   Trace tr;
   tr.ms = stage_ms;
   tr.n = 1;
   tr.start(s);
   {
     NvtxRange r(write ? "sdcsz decode" : "sdcsz verify");
-    rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips, raw);
+    rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips, raw,
+                        wave);
   }
   if (rc) return rc;
   tr.mark();
@@ -674,7 +679,7 @@ extern "C" int sdcsz_decompress_region(const void* d_stream, size_t nbytes, cons
   Hdr h;
   int rc = parse_header(hb, nbytes, &h, nullptr);
   if (rc) return rc;
-  if (ws_bytes < decode_ws_bytes(h)) return SDCSZ_ECAPACITY;
+  if (ws_bytes < decode_ws_min(h)) return SDCSZ_ECAPACITY;
   if (h.g.lossless && (reinterpret_cast<uintptr_t>(d_stream) & 15)) return SDCSZ_EINVAL;
   // the box in padded 3D coordinates
   uint64_t lo3[3] = {0, 0, 0}, hi3[3] = {1, 1, 1}, pts = 1, nblk = 1;

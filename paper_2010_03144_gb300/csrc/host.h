@@ -52,8 +52,11 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
 // aligned; unused otherwise).
 int decode_enqueue(const void* d_stream, size_t nbytes, const Hdr& h, void* d_field, size_t field_bytes,
                    uint8_t* status, const void* d_orig, bool write, State* st, cudaStream_t s, const sdcsz_flip* flips,
-                   size_t n_flips, uint8_t* raw = nullptr);
+                   size_t n_flips, uint8_t* raw = nullptr, uint8_t* wave = nullptr);
 
+// Decompression workspace: the least (the State and the lossless stage's scratch) and the
+// recommended (plus the two-pass decoder's buffers, for the shapes it serves).
+size_t decode_ws_min(const Hdr& h);
 size_t decode_ws_bytes(const Hdr& h);
 int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t field_bytes, uint8_t* status,
                     const void* d_orig, bool write, void* d_ws, size_t ws_bytes, sdcsz_report* report, void* stream,

@@ -93,7 +93,8 @@ void launch_region(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, c
 
 void launch_decode(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
                    const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
-                   const Launch& L) {
+                   const Launch& L, uint8_t* wave_ws) {
+  if (wave_ws && write && !nflips && launch_decode_wave(s, nbytes, h, field, status, st, wave_ws, L)) return;
   if (h.g.dtype == 0) launch_decode_f32(s, nbytes, h, field, status, original, st, write, flips, nflips, L);
   else launch_decode_f64(s, nbytes, h, field, status, original, st, write, flips, nflips, L);
 }

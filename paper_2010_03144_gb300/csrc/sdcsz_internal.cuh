@@ -752,6 +752,21 @@ bool prep_has_fast(const Geo& g);
 // Cube edges whose prediction takes the wavefront kernel, and its blocks per CTA group (0: the
 // one-thread-per-block kernels).
 __host__ __device__ constexpr uint32_t wave_group_blocks(uint32_t B) { return B == 16 ? 8 : (B == 10 || B == 12) ? 16 : 0; }
+// The two-pass decoder of those shapes keeps, per block: its code pairs and unpredictable values
+// at the compression's interleaved places (a full block's stride), four coefficients, a flag
+// byte and a re-execution list entry. wave_dws_part(g, i) is part i's size (i < 5).
+inline uint64_t wave_dws_part(const Geo& g, int i) {
+  const uint64_t P = g.P, nb32 = (g.nb + 31) / 32 * 32, es = g.dtype ? 8 : 4;
+  const uint64_t n[5] = {nb32 * pairs_of((uint32_t)P) * 4, nb32 * P * es, g.nb * 4 * es, g.nb, g.nb * 8};
+  return (n[i] + 255) & ~uint64_t(255);
+}
+inline uint64_t wave_decode_ws_bytes(const Geo& g) {  // 0 for shapes the two-pass decoder does not serve
+  if (g.ndim != 3 || g.B[0] != g.B[1] || g.B[1] != g.B[2] || !wave_group_blocks(g.B[2]) || !g.nb) return 0;
+  if (g.B[2] != 16 && g.dtype == 0) return 0;  // 10^3 and 12^3 float32 decode in one pass
+  uint64_t t = 0;
+  for (int i = 0; i < 5; ++i) t += wave_dws_part(g, i);
+  return t;
+}
 inline uint64_t wave_groups(const Geo& g) {  // 0 unless g's blocks take the wavefront kernel
   if (g.ndim != 3 || g.B[0] != g.B[1] || g.B[1] != g.B[2]) return 0;
   const uint64_t G = wave_group_blocks(g.B[2]);
@@ -796,8 +811,13 @@ __host__ __device__ inline uint64_t ll_data(uint64_t from, uint64_t nchunks) {
 // Blocks intersecting the box [lo, hi) (padded 3D coordinates) into a dense array of its shape.
 void launch_region(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* out, const uint64_t lo[3],
                    const uint64_t hi[3], uint8_t* status, State* st, const Launch& L);
+// wave_ws: the two-pass decoder's workspace (wave_decode_ws_bytes), or nullptr (then the one-pass
+// kernels decode every shape); the two-pass decoder serves decompression without soft-error
+// records only.
 void launch_decode(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status,
                    const void* original, State* st, bool write, const sdcsz_flip* flips, uint32_t nflips,
-                   const Launch& L);
+                   const Launch& L, uint8_t* wave_ws = nullptr);
+bool launch_decode_wave(const uint8_t* s, uint64_t nbytes, const Hdr& h, void* field, uint8_t* status, State* st,
+                        uint8_t* wave_ws, const Launch& L);
 
 }  // namespace sdcsz

@@ -163,8 +163,9 @@ int launch(sdcsz_server* S, Slot& sl) {
     uint8_t* base = static_cast<uint8_t*>(q.ws);
     uint8_t* raw = base + align256(sizeof(State));  // the lossless stage's scratch, when there is one
     uint8_t* status = write ? nullptr : base + decode_ws_bytes(q.h);
+    uint8_t* wave = wave_decode_ws_bytes(q.h.g) ? base + decode_ws_min(q.h) : nullptr;  // the two-pass decoder's
     rc = decode_enqueue(r.d_in, r.in_bytes, q.h, field, fb, status, write ? nullptr : r.d_original, write, st, s,
-                        r.d_flips, r.n_flips, raw);
+                        r.d_flips, r.n_flips, raw, wave);
   }
   if (rc) return rc;
   if (cudaMemcpyAsync(sl.h_state, st, sizeof(State), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SDCSZ_ECUDA;

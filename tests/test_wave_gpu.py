@@ -157,3 +157,62 @@ def test_wave_coefficient_flips_keep_the_bound(sz, orc):
     assert_same_stream(s_gpu, rep_gpu, s_ref, rep_ref)
     rc, y, st, rep = sz.decompress(s_gpu)
     assert rc == 0 and np.all(np.abs(y.cpu().numpy() - x) <= rep_gpu["eb_abs"])
+
+
+# ---- decompression of the shapes without a one-pass fast kernel (16^3; 10^3 and 12^3 in
+# float64): the two-pass decoder (codes, then the wavefront), which the binding's default
+# workspace enables, against the one-pass kernels (the least workspace) and the oracle
+
+
+@pytest.mark.parametrize("shape,dt,block,eb,kw", [
+    ((48, 50, 64), np.float32, 16, 1e-3, {}),
+    ((61, 37, 49), np.float64, 12, 1e-4, {}),
+    ((40, 40, 48), np.float64, 16, 1e-5, {}),
+    ((30, 40, 50), np.float64, 10, 1e-3, {"abft": False}),
+    ((32, 36, 48), np.float32, 16, 1e-3, {"encoding": "compact"}),
+    ((48, 50, 64), np.float32, 16, 1e-3, {"predictor": "regression"}),
+])
+def test_two_pass_decoder_matches_one_pass_and_oracle(sz, orc, shape, dt, block, eb, kw):
+    import torch
+    x = synth.sinusoid_field(shape, 41 + block, dtype=dt, spikes=0.01)
+    s, rep = sz.compress(torch.from_numpy(x).cuda(), eb, block=block, **kw)
+    s_ref, _ = orc.compress(x, eb, block=block, **kw)
+    assert np.array_equal(s.cpu().numpy(), s_ref)
+    assert sz.decompress_workspace_size(s) > sz.decompress_workspace_size()
+    rc2, y2, st2, rep2 = sz.decompress(s)                                    # two passes
+    ws1 = torch.empty(sz.decompress_workspace_size(), dtype=torch.uint8, device="cuda")
+    rc1, y1, st1, rep1 = sz.decompress(s, ws=ws1)                            # one pass
+    rc_ref, y_ref, st_ref, _ = orc.decompress(s_ref)
+    assert rc1 == rc2 == rc_ref == 0
+    assert_same_field(y2, y_ref)
+    assert_same_field(y1, y_ref)
+    assert np.array_equal(st2.cpu().numpy(), st_ref) and np.array_equal(st1.cpu().numpy(), st_ref)
+    for k in ("uncorrectable_blocks", "decomp_reexec_corrected"):
+        assert rep2[k] == rep1[k] == 0
+
+
+@pytest.mark.parametrize("dt,block", [(np.float32, 16), (np.float64, 12), (np.float64, 10)])
+def test_two_pass_decoder_reports_corruption_like_oracle(sz, orc, dt, block):
+    """Bit flips in the payload of a stored stream: the blocks the oracle flags are flagged, the
+    re-execution of the two-pass decoder's failed blocks reports what the oracle reports, and
+    every block that verified on both sides decodes to the oracle's values."""
+    import torch
+    from parity import bits, block_points
+    shape = (3 * block, 2 * block + 5, 3 * block)
+    x = synth.sinusoid_field(shape, 43, dtype=dt)
+    s_ref, _ = orc.compress(x, 1e-4, block=block)
+    total = s_ref.size
+    payload_bytes = int(s_ref[96:104].view(np.uint64)[0])
+    rng = np.random.default_rng(block)
+    for trial in range(8):
+        bad = s_ref.copy()
+        for _ in range(1 + trial % 3):
+            pos = int(total - payload_bytes + rng.integers(payload_bytes))
+            bad[pos] ^= np.uint8(1 << int(rng.integers(8)))
+        rc_ref, y_ref, st_ref, rep_ref = orc.decompress(bad)
+        rc, y, st, rep = sz.decompress(torch.from_numpy(bad).cuda())
+        assert rc == rc_ref
+        assert np.array_equal(st.cpu().numpy() >= 2, st_ref >= 2)
+        assert rep["uncorrectable_blocks"] == rep_ref["uncorrectable_blocks"]
+        ok = block_points(st_ref == 0, x.shape, (block,) * 3)
+        assert np.array_equal(bits(y.cpu().numpy())[ok], bits(y_ref)[ok])
