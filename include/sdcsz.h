@@ -123,12 +123,17 @@ int sdcsz_compress_bound(const sdcsz_params* p, size_t* max_bytes);
 int sdcsz_workspace_size(const sdcsz_params* p, size_t* bytes);
 
 /* Device workspace bytes needed by sdcsz_decompress, sdcsz_verify and
- * sdcsz_decompress_region for any stream without the lossless stage. */
+ * sdcsz_decompress_region for any stream without the lossless stage (the least they accept). */
 size_t sdcsz_decompress_workspace_size(void);
 
-/* Device workspace bytes needed to decompress, verify or take a region of the stream whose
+/* Device workspace bytes recommended to decompress, verify or take a region of the stream whose
  * first 128 bytes (the header) are at h_header in HOST memory; nbytes is the stream's size.
- * With the lossless stage this includes the stream without it. SDCSZ_EFORMAT for a bad header. */
+ * With the lossless stage this includes the stream without it. For 3D cube blocks of edge 16
+ * (float32) or 10, 12, 16 (float64), sdcsz_decompress uses a two-pass decoder when the workspace
+ * has this size: the blocks' codes (2 bytes a point), unpredictable values (one value a point)
+ * and a few bytes a block; a workspace of at least sdcsz_decompress_workspace_size() bytes (plus
+ * the lossless stage's part) but less than this decodes the same values with the one-pass
+ * kernels, more slowly. SDCSZ_EFORMAT for a bad header. */
 int sdcsz_decompress_workspace_size_for(const void* h_header, size_t nbytes, size_t* bytes);
 
 /*
