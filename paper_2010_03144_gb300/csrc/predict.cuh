@@ -1144,7 +1144,7 @@ void try_edge(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
       case 4: run_edge<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       case 6: run_edge<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       case 8: run_edge<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); break;
-      case 10: run_wave<T, 10, wave_group_blocks(10), ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
+      case 10: run_edge<T, 3, 10, 10, 10, ABFT, CMP>(field, g, w, flips, nflips, L); break;
       case 12: run_wave<T, 12, wave_group_blocks(12), ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
       case 16: run_wave<T, 16, wave_group_blocks(16), ABFT, CMP>(field, g, w, flips, nflips, L, true); break;
       default: break;
@@ -1175,7 +1175,7 @@ bool try_fast(const void* field, const Geo& g, const Ws& w, const sdcsz_flip* fl
       case 4: run_fast<T, 3, 4, 4, 4, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       case 6: run_fast<T, 3, 6, 6, 6, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       case 8: run_fast<T, 3, 8, 8, 8, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
-      case 10: run_wave<T, 10, wave_group_blocks(10), ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
+      case 10: run_fast<T, 3, 10, 10, 10, ABFT, CMP>(field, g, w, flips, nflips, L); return true;
       case 12: run_wave<T, 12, wave_group_blocks(12), ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
       case 16: run_wave<T, 16, wave_group_blocks(16), ABFT, CMP>(field, g, w, flips, nflips, L, false); return true;
       default: return false;
@@ -1241,7 +1241,7 @@ bool batch_fast_shape(int ndim, uint32_t B, const BatchArgs& a, const Launch& L)
       case 4: batch_fast<T, 3, 4, 4, 4, ABFT, CMP>(a, L); return true;
       case 6: batch_fast<T, 3, 6, 6, 6, ABFT, CMP>(a, L); return true;
       case 8: batch_fast<T, 3, 8, 8, 8, ABFT, CMP>(a, L); return true;
-      case 10: batch_wave<T, 10, wave_group_blocks(10), ABFT, CMP>(a, L); return true;
+      case 10: batch_fast<T, 3, 10, 10, 10, ABFT, CMP>(a, L); return true;
       case 12: batch_wave<T, 12, wave_group_blocks(12), ABFT, CMP>(a, L); return true;
       case 16: batch_wave<T, 16, wave_group_blocks(16), ABFT, CMP>(a, L); return true;
       default: return false;

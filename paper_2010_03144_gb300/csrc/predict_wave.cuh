@@ -1,4 +1,4 @@
-// K2 for large cube blocks (B = 10, 12, 16): the prediction loop of Algorithm 1 with the rows of
+// K2 for large cube blocks (B = 12, 16): the prediction loop of Algorithm 1 with the rows of
 // a block spread over the lanes of a warp and an anti-diagonal wavefront inside the block.
 //
 // Why: the one-thread-per-block walk keeps a B x B plane of reconstructed values per thread

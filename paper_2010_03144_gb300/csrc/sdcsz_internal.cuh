@@ -749,9 +749,11 @@ struct NoOp {
 
 // Batched launches (one per stage and kernel shape; see BatchArgs).
 bool prep_has_fast(const Geo& g);
-// Cube edges whose prediction takes the wavefront kernel, and its blocks per CTA group (0: the
-// one-thread-per-block kernels).
+// Blocks per CTA group of the wavefront kernels for cube edge B (0: none). Prediction takes
+// them for 12^3 and 16^3 (wave_predicts); 10^3 predicts faster one thread per block on smooth
+// fields, where nearly every row is a central row (0.44 against 0.87 ms at 512^3).
 __host__ __device__ constexpr uint32_t wave_group_blocks(uint32_t B) { return B == 16 ? 8 : (B == 10 || B == 12) ? 16 : 0; }
+__host__ __device__ constexpr bool wave_predicts(uint32_t B) { return B == 12 || B == 16; }
 // The two-pass decoder of those shapes keeps, per block: its code pairs and unpredictable values
 // at the compression's interleaved places (a full block's stride), four coefficients, a flag
 // byte and a re-execution list entry. wave_dws_part(g, i) is part i's size (i < 5).
@@ -768,7 +770,7 @@ inline uint64_t wave_decode_ws_bytes(const Geo& g) {  // 0 for shapes the two-pa
   return t;
 }
 inline uint64_t wave_groups(const Geo& g) {  // 0 unless g's blocks take the wavefront kernel
-  if (g.ndim != 3 || g.B[0] != g.B[1] || g.B[1] != g.B[2]) return 0;
+  if (g.ndim != 3 || g.B[0] != g.B[1] || g.B[1] != g.B[2] || !wave_predicts(g.B[2])) return 0;
   const uint64_t G = wave_group_blocks(g.B[2]);
   return G ? (g.nb + G - 1) / G + (edge_count(g) + G - 1) / G : 0;
 }

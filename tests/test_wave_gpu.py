@@ -1,5 +1,6 @@
-"""The wavefront prediction kernel (cube blocks of edge 10, 12 and 16, full ones and those cut by
-the field boundary: rows on lanes, an anti-diagonal schedule inside each block) against the
+"""The wavefront prediction kernel (cube blocks of edge 12 and 16, full ones and those cut by the
+field boundary: rows on lanes, an anti-diagonal schedule inside each block; 10^3 cases check its
+neighbour, the one-thread walk, whose float64 streams take the two-pass decoder) against the
 oracle: the stream and the decompressed
 field are bit-identical, with and without ABFT, for both predictors, both encodings, both
 precisions, several groups of blocks per CTA, edge blocks beside the full ones, and rows whose
