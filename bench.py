@@ -45,14 +45,14 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 556886699, "src": "f09118403609"},
-    ("384cube", "prep"): {"bytes": 234936576, "src": "f09118403609"},
-    ("512cube", "predict"): {"bytes": 954670194, "src": "316bc81d0641"},
-    ("384cube", "predict"): {"bytes": 402751488, "src": "316bc81d0641"},
-    ("512cube", "encode"): {"bytes": 480232031, "src": "3057987cd606"},
-    ("384cube", "encode"): {"bytes": 202597888, "src": "3057987cd606"},
-    ("512cube", "decode"): {"bytes": 454998850, "src": "2775ec127b58"},
-    ("384cube", "decode"): {"bytes": 191952640, "src": "2775ec127b58"},
+    ("512cube", "prep"): {"bytes": 556481346, "src": "8d24e918a655"},
+    ("384cube", "prep"): {"bytes": 234765568, "src": "8d24e918a655"},
+    ("512cube", "predict"): {"bytes": 953910462, "src": "2e19572e7bf6"},
+    ("384cube", "predict"): {"bytes": 402430976, "src": "2e19572e7bf6"},
+    ("512cube", "encode"): {"bytes": 479629464, "src": "91c2596f6924"},
+    ("384cube", "encode"): {"bytes": 202343680, "src": "91c2596f6924"},
+    ("512cube", "decode"): {"bytes": 454495194, "src": "9ab384c1a550"},
+    ("384cube", "decode"): {"bytes": 191740160, "src": "9ab384c1a550"},
 }
 
 
@@ -68,13 +68,13 @@ def _peaks():
 # sources that define each stage's kernels (the hash keys the stored ncu traffic)
 KERNEL_SOURCES = {
     "prep": ("k_prep.cu", "sdcsz_internal.cuh"),
-    "predict": ("predict.cuh", "k_predict_f32.cu", "sdcsz_internal.cuh"),
+    "predict": ("predict.cuh", "predict_wave.cuh", "k_predict_f32.cu", "sdcsz_internal.cuh"),
     "codebook": ("k_codebook.cu", "sdcsz_internal.cuh"),
     "encode": ("k_encode.cu", "sdcsz_internal.cuh"),
-    "decode": ("decode.cuh", "k_decode_f32.cu", "sdcsz_internal.cuh"),
+    "decode": ("decode.cuh", "decode_wave.cuh", "k_decode_f32.cu", "k_decode_wave.cu", "sdcsz_internal.cuh"),
     "prep64": ("k_prep.cu", "sdcsz_internal.cuh"),
-    "predict64": ("predict.cuh", "k_predict_f64.cu", "sdcsz_internal.cuh"),
-    "decode64": ("decode.cuh", "k_decode_f64.cu", "sdcsz_internal.cuh"),
+    "predict64": ("predict.cuh", "predict_wave.cuh", "k_predict_f64.cu", "sdcsz_internal.cuh"),
+    "decode64": ("decode.cuh", "decode_wave.cuh", "k_decode_f64.cu", "k_decode_wave.cu", "sdcsz_internal.cuh"),
 }
 
 
@@ -883,8 +883,8 @@ def run_region(args):
 # path, from an ncu capture (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum
 # over every launch of the stage / points), keyed by the hash of the stage's sources.
 NCU_FP64_PER_POINT = {
-    "predict": {"per_point": 10.75, "src": "1a3f5d6f3cb9"},
-    "decode": {"per_point": 3.46, "src": "b14b0f440dd1"},
+    "predict": {"per_point": 10.751, "src": "71e0c011fcda"},
+    "decode": {"per_point": 3.46, "src": "a3f40169af02"},
 }
 
 
