@@ -37,6 +37,8 @@ WORKLOADS = {
     "64cube": dict(shape=(64, 64, 64), block=6, spikes=0.0, seed=1),
     # profiling size for ncu captures: the same recipe, 226 MB (above L2), a few hundred MB held
     "384cube": dict(shape=(384, 384, 384), block=6, spikes=0.01, seed=2010),
+    # the 2D single-field config: 1800 x 3600 float32 (Hurricane-sized slices), 12^2 blocks
+    "1800x3600": dict(shape=(1800, 3600), block=12, spikes=0.01, seed=2010),
 }
 REL_EB = 1e-3
 
@@ -365,7 +367,7 @@ def run_ours(args):
             "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload} float32 {shape} sinusoids+noise+{wl['spikes']:.0%} spikes, "
-                                   f"rel eb {REL_EB}, block {block}^3, ABFT on, {enc} encoding"
+                                   f"rel eb {REL_EB}, block {block}^{len(shape)}, ABFT on, {enc} encoding"
                                    f"{' + lossless stage' if ll else ''}; "
                                    "one step = compress + decompress",
                        "field_bytes": N * s_dt, "compressed_bytes": stream_bytes,
@@ -421,7 +423,7 @@ def _cpu_model():
     return platform.processor() or platform.machine()
 
 
-def _oracle_worker(conn, shape, seed, spikes, block, enc, ll):
+def _oracle_worker(conn, shape, seed, spikes, block, enc, ll, rel):
     """One host core's share of the all-cores oracle baseline: its own slab of the recipe,
     compressed and decompressed by the (single-threaded) oracle each time the parent says go."""
     import oracle
@@ -434,7 +436,7 @@ def _oracle_worker(conn, shape, seed, spikes, block, enc, ll):
         if abft is None:
             break
         t0 = time.perf_counter()
-        s, _ = oracle.compress(x, REL_EB, block=block, abft=abft, encoding=enc, lossless=ll)
+        s, _ = oracle.compress(x, rel, block=block, abft=abft, encoding=enc, lossless=ll)
         oracle.decompress(s)
         conn.send(time.perf_counter() - t0)
     conn.close()
@@ -456,7 +458,7 @@ class OraclePool:
         for r in range(self.cores):
             a, b = ctx.Pipe()
             p = ctx.Process(target=_oracle_worker, args=(b, shape, wl["seed"] + 17 * r, wl["spikes"], wl["block"],
-                                                         args.encoding, args.lossless), daemon=True)
+                                                         args.encoding, args.lossless, REL_EB), daemon=True)
             p.start()
             self.procs.append(p)
             self.conns.append(a)
@@ -529,7 +531,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"{args.workload} recipe, one {pool.slab} slab per host core per step, "
-                                  f"rel eb {REL_EB}, block {block}^3, ABFT on, {args.encoding} encoding; "
+                                  f"rel eb {REL_EB}, block {block}^{len(pool.slab)}, ABFT on, {args.encoding} encoding; "
                                   "one step = compress + decompress"},
            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": pool.cores, "kind": "oracle",
                             "sample": f"{pool.slab} slab per core per step", "cpu_model": _cpu_model()},
@@ -987,7 +989,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--fp64-size", type=int, default=512, help="float64 workload: edge of the cube")
     ap.add_argument("--block", type=int, default=0,
-                    help="block edge for the 512cube/384cube/64cube workloads (default: the workload's)")
+                    help="block edge for the single-field workloads (default: the workload's)")
+    ap.add_argument("--rel", type=float, default=REL_EB,
+                    help="value-range-relative error bound of the single-field workloads (default 1e-3)")
     ap.add_argument("--slots", type=int, default=16, help="serving: requests on the device at once")
     ap.add_argument("--encoding", choices=("raw", "compact"), default="raw",
                     help="stream encoding: raw coefficient/unpredictable sections, or compact (in the payload)")
@@ -999,6 +1003,11 @@ def main():
         # another block edge is another workload (its own name, no stored ncu figures)
         name = f"{args.workload}_b{args.block}"
         WORKLOADS[name] = dict(WORKLOADS[args.workload], block=args.block)
+        args.workload = name
+    if args.rel != REL_EB and args.workload in WORKLOADS:  # likewise another bound
+        globals()["REL_EB"] = args.rel
+        name = f"{args.workload}_rel{args.rel:g}"
+        WORKLOADS[name] = dict(WORKLOADS[args.workload])
         args.workload = name
     if args.impl == "reference":
         run_reference(args)
