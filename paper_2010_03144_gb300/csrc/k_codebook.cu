@@ -69,6 +69,42 @@ __device__ __forceinline__ void put_u64(uint8_t* o, uint64_t off, unsigned long 
 
 constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this many
 
+// Huffman's algorithm on n >= 2 leaves sorted by (count, symbol), with two queues: the next node
+// is the lighter of the next leaf and the oldest unmerged internal node, a leaf winning ties
+// (ties broken by creation order, leaves first in sorted order). Writes every node's parent
+// (leaves 0..n-1, internal nodes n..2n-2). W holds any weight (a sum of counts).
+// One thread; the next two leaf weights and the next two internal weights are kept in
+// registers, so a pick compares registers, and the loads that refill them are issued a pick
+// or more before their values are needed; a node just created is forwarded.
+template <typename W>
+__device__ __forceinline__ void huffman_merge(const unsigned long long* __restrict__ keys, uint32_t n,
+                                              W* __restrict__ iw, uint32_t* __restrict__ parent) {
+  uint32_t lp = 0, ip = 0;
+  W l0 = (W)(keys[0] >> 16), l1 = (W)(keys[1] >> 16), h0 = 0, h1 = 0;
+  for (uint32_t ni = 0; ni + 1 < n; ++ni) {
+    W wsum = 0;
+#pragma unroll
+    for (int pick = 0; pick < 2; ++pick) {
+      // internal nodes waiting: ni - ip (h0 is the oldest, h1 the next when there are two);
+      // both refills are loaded (from clamped addresses) and the pick selects, without a branch
+      const bool leaf = lp < n && (ip >= ni || l0 <= h0);
+      const W nl = (W)(keys[min(lp + 2, n - 1)] >> 16);
+      const W nh = iw[ip + 2 < ni ? ip + 2 : 0];
+      wsum += leaf ? l0 : h0;
+      parent[leaf ? lp : n + ip] = n + ni;
+      l0 = leaf ? l1 : l0;
+      l1 = leaf ? nl : l1;
+      h0 = leaf ? h0 : h1;
+      h1 = leaf ? h1 : nh;
+      lp += leaf ? 1u : 0u;
+      ip += leaf ? 0u : 1u;
+    }
+    iw[ni] = wsum;
+    if (ip == ni) h0 = wsum;            // the only waiting node is the one just made
+    else if (ip + 1 == ni) h1 = wsum;   // it is the second in line
+  }
+}
+
 }  // namespace
 
 __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __restrict__ out, uint64_t cap,
@@ -95,35 +131,21 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
 
   // 2-3. Huffman merge and leaf depths (one thread), length counts
   if (n >= 2) {
-    // node arrays: internal weights [n-1], parents [2n-1]
-    const bool small = n <= 4096;
-    unsigned long long* iw = small ? reinterpret_cast<unsigned long long*>(smem + kSmemSort * 8) : w.node_w;
-    uint32_t* parent = small ? reinterpret_cast<uint32_t*>(smem + kSmemSort * 8 + 4096 * 8) : w.node_parent;
+    // node arrays: internal weights [n-1], parents [2n-1]; in shared memory when they fit
+    // (32-bit weights, used when the field has fewer than 2^32 points, fit twice as many)
+    const bool w32 = g.N < (1ull << 32);
+    const bool small = n <= (w32 ? 8192u : 4096u);  // then the keys are in shared memory too
+    uint32_t* parent = small ? reinterpret_cast<uint32_t*>(smem + kSmemSort * 8 + 8192 * 4) : w.node_parent;
     if (tid == 0) {
-      // The next leaf weights (two ahead) and the oldest unmerged internal weight stay in
-      // registers, so each pick is a compare of registers; the node just created is forwarded.
-      uint32_t lp = 0, ip = 0;
-      unsigned long long lw = keys[0] >> 16, lw1 = keys[1] >> 16, hw = 0;
-      for (uint32_t ni = 0; ni + 1 < n; ++ni) {
-        unsigned long long wsum = 0;
-#pragma unroll
-        for (int pick = 0; pick < 2; ++pick) {
-          const bool leaf = lp < n && (ip >= ni || lw <= hw);
-          if (leaf) {
-            wsum += lw;
-            parent[lp] = n + ni;
-            ++lp;
-            lw = lw1;
-            lw1 = lp + 1 < n ? keys[lp + 1] >> 16 : 0ull;
-          } else {
-            wsum += hw;
-            parent[n + ip] = n + ni;
-            ++ip;
-            if (ip < ni) hw = iw[ip];
-          }
-        }
-        iw[ni] = wsum;
-        if (ip == ni) hw = wsum;
+      if (small) {  // every array in shared memory (addresses the compiler sees as shared)
+        const unsigned long long* ks = reinterpret_cast<const unsigned long long*>(smem);
+        uint32_t* ps = reinterpret_cast<uint32_t*>(smem + kSmemSort * 8 + 8192 * 4);
+        if (w32) huffman_merge<uint32_t>(ks, n, reinterpret_cast<uint32_t*>(smem + kSmemSort * 8), ps);
+        else huffman_merge<unsigned long long>(ks, n, reinterpret_cast<unsigned long long*>(smem + kSmemSort * 8), ps);
+      } else if (w32) {
+        huffman_merge<uint32_t>(keys, n, reinterpret_cast<uint32_t*>(w.node_w), w.node_parent);
+      } else {
+        huffman_merge<unsigned long long>(keys, n, w.node_w, w.node_parent);
       }
     }
     __syncthreads();
@@ -301,7 +323,8 @@ __global__ void __launch_bounds__(1024) k_codebook_batch(const Job* __restrict__
   codebook(s_job.g, s_job.w, s_job.out, s_job.cap, smem);
 }
 
-constexpr size_t kCodebookSmem = kSmemSort * 8 + 4096 * 8 + 8192 * 4 + 8192;
+// keys (kSmemSort x 8), internal weights (8192 x 4, or 4096 x 8), parents (16384 x 4), lengths
+constexpr size_t kCodebookSmem = kSmemSort * 8 + 8192 * 4 + 16384 * 4 + 8192;
 
 void batch_codebook(const Job* jobs, uint32_t n, const Launch& L) {
   k_codebook_gather_batch<<<dim3(64, n), 1024, 0, L.stream>>>(jobs);
