@@ -15,6 +15,10 @@ namespace sdcsz {
 
 namespace {
 
+constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this many
+constexpr size_t kCodebookMerge = 224 * 1024;  // the kernels' dynamic shared memory
+static_assert(kCodebookMerge >= kSmemSort * 8 + 8192 * 4 + 16384 * 4, "the small case's arrays fit");
+
 // Ascending bitonic sort of n_pad (power of two) 64-bit keys, shared or global memory.
 __device__ void bitonic_sort(unsigned long long* a, uint32_t n_pad) {
   for (uint32_t size = 2; size <= n_pad; size <<= 1) {
@@ -37,8 +41,16 @@ __device__ void bitonic_sort(unsigned long long* a, uint32_t n_pad) {
 // Ascending sort of n distinct keys (padded to n_pad with ~0). Up to one key per thread: each
 // thread counts the keys below its own (all threads read the same key at a time, a broadcast)
 // and stores it at that rank; three barriers instead of the bitonic network's many.
-__device__ void sort_keys(unsigned long long* a, uint32_t n, uint32_t n_pad) {
+__device__ void sort_global(unsigned long long* a, unsigned long long* tmp, uint32_t n_pad, unsigned long long* s);
+
+// (tmp, s: scratch of sort_global for n_pad above kSmemSort)
+__device__ void sort_keys(unsigned long long* a, uint32_t n, uint32_t n_pad, unsigned long long* tmp = nullptr,
+                          unsigned long long* s = nullptr) {
   if (n <= 1) return;
+  if (n_pad > kSmemSort) {
+    sort_global(a, tmp, n_pad, s);
+    return;
+  }
   if (n > blockDim.x) {
     bitonic_sort(a, n_pad);
     return;
@@ -67,7 +79,59 @@ __device__ __forceinline__ void put_u64(uint8_t* o, uint64_t off, unsigned long 
   for (int q = 0; q < 8; ++q) o[off + q] = (uint8_t)(v >> (8 * q));
 }
 
-constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this many
+// Leaf weights for the merge: the counts of sorted keys (count << 16 | symbol), or a copy of
+// them as 32-bit values.
+struct KeyLeaf {
+  const unsigned long long* __restrict__ k;
+  __device__ __forceinline__ unsigned long long operator()(uint32_t i) const { return k[i] >> 16; }
+};
+struct U32Leaf {
+  const uint32_t* __restrict__ v;
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return v[i]; }
+};
+
+// Ascending sort of n_pad (a power of two above kSmemSort) distinct keys in global memory:
+// runs of kSmemSort keys sorted in shared memory (s), then merge rounds between a and tmp,
+// each thread producing n_pad / blockDim.x consecutive outputs from where a binary search on
+// its diagonal (the merge path) puts them. The result ends in a.
+__device__ void sort_global(unsigned long long* a, unsigned long long* tmp, uint32_t n_pad, unsigned long long* s) {
+  for (uint32_t base = 0; base < n_pad; base += kSmemSort) {
+    for (uint32_t t = threadIdx.x; t < kSmemSort; t += blockDim.x) s[t] = a[base + t];
+    __syncthreads();
+    bitonic_sort(s, kSmemSort);
+    for (uint32_t t = threadIdx.x; t < kSmemSort; t += blockDim.x) a[base + t] = s[t];
+    __syncthreads();
+  }
+  unsigned long long *src = a, *dst = tmp;
+  const uint32_t per = n_pad / blockDim.x;
+  for (uint32_t wdt = kSmemSort; wdt < n_pad; wdt <<= 1) {
+    const uint32_t o0 = threadIdx.x * per;
+    const uint32_t base = o0 / (2 * wdt) * (2 * wdt), d = o0 - base;
+    const unsigned long long* A = src + base;
+    const unsigned long long* Bk = src + base + wdt;
+    uint32_t lo = d > wdt ? d - wdt : 0, hi = d < wdt ? d : wdt;
+    while (lo < hi) {  // the number of A's keys among the pair's d smallest
+      const uint32_t mid = (lo + hi) >> 1;
+      if (A[mid] < Bk[d - 1 - mid]) lo = mid + 1;
+      else hi = mid;
+    }
+    uint32_t i = lo, j = d - lo;
+    for (uint32_t q = 0; q < per; ++q) {
+      const bool takeA = i < wdt && (j >= wdt || A[i] < Bk[j]);
+      dst[base + d + q] = takeA ? A[i] : Bk[j];
+      i += takeA ? 1u : 0u;
+      j += takeA ? 0u : 1u;
+    }
+    __syncthreads();
+    unsigned long long* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != a) {
+    for (uint32_t t = threadIdx.x; t < n_pad; t += blockDim.x) a[t] = src[t];
+    __syncthreads();
+  }
+}
 
 // Huffman's algorithm on n >= 2 leaves sorted by (count, symbol), with two queues: the next node
 // is the lighter of the next leaf and the oldest unmerged internal node, a leaf winning ties
@@ -76,11 +140,10 @@ constexpr uint32_t kSmemSort = 8192;  // keys sorted in shared memory up to this
 // One thread; the next two leaf weights and the next two internal weights are kept in
 // registers, so a pick compares registers, and the loads that refill them are issued a pick
 // or more before their values are needed; a node just created is forwarded.
-template <typename W>
-__device__ __forceinline__ void huffman_merge(const unsigned long long* __restrict__ keys, uint32_t n,
-                                              W* __restrict__ iw, uint32_t* __restrict__ parent) {
+template <typename W, class Leaf>
+__device__ __forceinline__ void huffman_merge(Leaf leafw, uint32_t n, W* __restrict__ iw, uint32_t* __restrict__ parent) {
   uint32_t lp = 0, ip = 0;
-  W l0 = (W)(keys[0] >> 16), l1 = (W)(keys[1] >> 16), h0 = 0, h1 = 0;
+  W l0 = (W)leafw(0), l1 = (W)leafw(1), h0 = 0, h1 = 0;
   for (uint32_t ni = 0; ni + 1 < n; ++ni) {
     W wsum = 0;
 #pragma unroll
@@ -88,7 +151,7 @@ __device__ __forceinline__ void huffman_merge(const unsigned long long* __restri
       // internal nodes waiting: ni - ip (h0 is the oldest, h1 the next when there are two);
       // both refills are loaded (from clamped addresses) and the pick selects, without a branch
       const bool leaf = lp < n && (ip >= ni || l0 <= h0);
-      const W nl = (W)(keys[min(lp + 2, n - 1)] >> 16);
+      const W nl = (W)leafw(min(lp + 2, n - 1));
       const W nh = iw[ip + 2 < ni ? ip + 2 : 0];
       wsum += leaf ? l0 : h0;
       parent[leaf ? lp : n + ip] = n + ni;
@@ -124,7 +187,7 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
   __syncthreads();
   for (uint32_t t = tid; t < n_pad; t += blockDim.x) keys[t] = (t < n) ? w.sort_keys[t] : ~0ull;
   __syncthreads();
-  sort_keys(keys, n, n_pad);
+  sort_keys(keys, n, n_pad, w.node_w, reinterpret_cast<unsigned long long*>(smem));
   for (uint32_t t = tid; t < 64; t += blockDim.x) cnt[t] = 0;
   if (tid == 0) s_maxlen = 0;
   __syncthreads();
@@ -135,17 +198,28 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
     // (32-bit weights, used when the field has fewer than 2^32 points, fit twice as many)
     const bool w32 = g.N < (1ull << 32);
     const bool small = n <= (w32 ? 8192u : 4096u);  // then the keys are in shared memory too
+    // more leaves (keys in global memory): 32-bit copies of the leaf weights and the internal
+    // weights in the shared memory the keys did not need, the parents in global memory
+    const bool mid = !small && w32 && 8ull * n <= kCodebookMerge;
     uint32_t* parent = small ? reinterpret_cast<uint32_t*>(smem + kSmemSort * 8 + 8192 * 4) : w.node_parent;
+    if (mid) {
+      uint32_t* lws = reinterpret_cast<uint32_t*>(smem);
+      for (uint32_t t = tid; t < n; t += blockDim.x) lws[t] = (uint32_t)(keys[t] >> 16);
+      __syncthreads();
+    }
     if (tid == 0) {
       if (small) {  // every array in shared memory (addresses the compiler sees as shared)
-        const unsigned long long* ks = reinterpret_cast<const unsigned long long*>(smem);
+        const KeyLeaf ks{reinterpret_cast<const unsigned long long*>(smem)};
         uint32_t* ps = reinterpret_cast<uint32_t*>(smem + kSmemSort * 8 + 8192 * 4);
         if (w32) huffman_merge<uint32_t>(ks, n, reinterpret_cast<uint32_t*>(smem + kSmemSort * 8), ps);
         else huffman_merge<unsigned long long>(ks, n, reinterpret_cast<unsigned long long*>(smem + kSmemSort * 8), ps);
+      } else if (mid) {
+        const U32Leaf ls{reinterpret_cast<const uint32_t*>(smem)};
+        huffman_merge<uint32_t>(ls, n, reinterpret_cast<uint32_t*>(smem) + n, w.node_parent);
       } else if (w32) {
-        huffman_merge<uint32_t>(keys, n, reinterpret_cast<uint32_t*>(w.node_w), w.node_parent);
+        huffman_merge<uint32_t>(KeyLeaf{keys}, n, reinterpret_cast<uint32_t*>(w.node_w), w.node_parent);
       } else {
-        huffman_merge<unsigned long long>(keys, n, w.node_w, w.node_parent);
+        huffman_merge<unsigned long long>(KeyLeaf{keys}, n, w.node_w, w.node_parent);
       }
     }
     __syncthreads();
@@ -206,7 +280,7 @@ __device__ __forceinline__ void codebook(const Geo& g, const Ws& w, uint8_t* __r
   __syncthreads();
   for (uint32_t t = tid; t < n_pad; t += blockDim.x) keys[t] = (t < n) ? w.sort_keys[t] : ~0ull;
   __syncthreads();
-  sort_keys(keys, n, n_pad);
+  sort_keys(keys, n, n_pad, w.node_w, reinterpret_cast<unsigned long long*>(smem));
   if (tid == 0) {
     uint32_t code = 0, idx = 0;
     for (uint32_t l = 1; l <= (uint32_t)kMaxLen; ++l) {
@@ -323,8 +397,9 @@ __global__ void __launch_bounds__(1024) k_codebook_batch(const Job* __restrict__
   codebook(s_job.g, s_job.w, s_job.out, s_job.cap, smem);
 }
 
-// keys (kSmemSort x 8), internal weights (8192 x 4, or 4096 x 8), parents (16384 x 4), lengths
-constexpr size_t kCodebookSmem = kSmemSort * 8 + 8192 * 4 + 16384 * 4 + 8192;
+// keys (kSmemSort x 8), internal weights (8192 x 4, or 4096 x 8), parents (16384 x 4); for more
+// leaves, their 32-bit weights and the internal weights (kCodebookMerge bytes: 28672 leaves)
+constexpr size_t kCodebookSmem = kCodebookMerge;
 
 void batch_codebook(const Job* jobs, uint32_t n, const Launch& L) {
   k_codebook_gather_batch<<<dim3(64, n), 1024, 0, L.stream>>>(jobs);

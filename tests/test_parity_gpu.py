@@ -126,3 +126,17 @@ def test_repeated_calls_reuse_workspace(sz, orc):
     s2, _ = sz.compress(d, 1e-3, workspace=ws)
     assert np.array_equal(a, s2.cpu().numpy())
     assert np.array_equal(a, orc.compress(x, 1e-3)[0])
+
+
+@pytest.mark.parametrize("shape,rel", [((64, 64, 64), 1.5e-4), ((64, 64, 64), 4e-5), ((64, 64, 64), 2e-5),
+                                       ((64, 64, 64), 1e-5), ((128, 128, 128), 4e-6)])
+def test_many_live_bins(sz, orc, shape, rel):
+    """White noise at tight bounds: 2.5 k to over 32 k live bins, i.e. every way the codebook
+    kernel sorts its keys (shared memory, runs merged in global memory) and keeps its Huffman
+    nodes (shared memory, 32-bit copies in shared memory, global memory)."""
+    x = np.random.default_rng(5).standard_normal(shape).astype(np.float32)
+    s_gpu, rep_gpu, s_ref, rep_ref, _ = compress_both(sz, orc, x, rel)
+    assert_same_stream(s_gpu, rep_gpu, s_ref, rep_ref)
+    rc, y, st, rep = sz.decompress(s_gpu)
+    assert rc == 0
+    assert_same_field(y, orc.decompress(s_ref)[1])
