@@ -470,6 +470,20 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
   const uint64_t s_dt = g.dtype ? 8 : 4;
   Layout L = st->L;
   L.payload = align16(L.unpred + (g.enc ? 0 : s_dt * n_unpred));
+  // the group's exclusive prefix: the totals of the earlier super-groups and of the earlier
+  // groups of its own super-group (summed by K4a, complete when this kernel starts), read
+  // straight from memory without waiting on other CTAs; loaded first, so that these loads and
+  // the slot's are in flight together
+  // (each thread's first super-group and group entries are only loaded here and added after
+  // the slot loads below have been issued; a field of up to 2^24 blocks has no more)
+  unsigned long long pre[3] = {0, 0, 0};
+  const uint64_t s0 = gid / kSuper;
+  unsigned long long sga = 0, sgb = 0, gtv = 0;
+  if (tid < s0) {
+    sga = w.gt[ngroups + 2 * tid];
+    sgb = w.gt[ngroups + 2 * tid + 1];
+  }
+  if (s0 * kSuper + tid < gid) gtv = w.gt[s0 * kSuper + tid];
   uint32_t bytes = 0, nun = 0;
   bool reg = false;
   // the first 64 bytes of the block's payload slot, loaded with its sizes: the slot does not
@@ -484,6 +498,21 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
     nun = *reinterpret_cast<const uint16_t*>(out + L.ucounts + 2 * (sh.boff + b));
     reg = w.flags[b] & 1;
   }
+  pre[0] = sga + (gtv & kMaskBytes);
+  pre[1] = (sgb >> 17) + ((gtv >> 25) & kMaskUn);
+  pre[2] = (sgb & 0x1ffffull) + (gtv >> 46);
+  for (uint64_t p = tid + blockDim.x; p < s0; p += blockDim.x) {  // larger fields: the rest
+    const unsigned long long* sg = w.gt + ngroups + 2 * p;
+    pre[0] += sg[0];
+    pre[1] += sg[1] >> 17;
+    pre[2] += sg[1] & 0x1ffffull;
+  }
+  for (uint64_t p = s0 * kSuper + tid + blockDim.x; p < gid; p += blockDim.x) {
+    const unsigned long long t = w.gt[p];
+    pre[0] += t & kMaskBytes;
+    pre[1] += (t >> 25) & kMaskUn;
+    pre[2] += t >> 46;
+  }
 
   // CTA exclusive scan of (bytes, unpredictables, regression flag)
   unsigned long long v[3] = {bytes, nun, reg ? 1ull : 0ull}, inc[3] = {v[0], v[1], v[2]};
@@ -494,23 +523,6 @@ __device__ __forceinline__ void assemble_group(const Geo& g, const Ws& w, uint8_
     }
   if (lane == 31)
     for (int q = 0; q < 3; ++q) s_wt[wid][q] = inc[q];
-  // the group's exclusive prefix: the totals of the earlier super-groups and of the earlier
-  // groups of its own super-group (summed by K4a, complete when this kernel starts), read
-  // straight from memory without waiting on other CTAs
-  unsigned long long pre[3] = {0, 0, 0};
-  const uint64_t s0 = gid / kSuper;
-  for (uint64_t p = tid; p < s0; p += blockDim.x) {
-    const unsigned long long* sg = w.gt + ngroups + 2 * p;
-    pre[0] += sg[0];
-    pre[1] += sg[1] >> 17;
-    pre[2] += sg[1] & 0x1ffffull;
-  }
-  for (uint64_t p = s0 * kSuper + tid; p < gid; p += blockDim.x) {
-    const unsigned long long t = w.gt[p];
-    pre[0] += t & kMaskBytes;
-    pre[1] += (t >> 25) & kMaskUn;
-    pre[2] += t >> 46;
-  }
   for (int q = 0; q < 3; ++q) pre[q] = warp_sum(pre[q]);
   if (lane == 0)
     for (int q = 0; q < 3; ++q) s_pre[wid][q] = pre[q];
