@@ -350,6 +350,10 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
   const uint32_t cw0 = __ldg(&w.codebook[0]);
   const uint32_t P = active ? block_box(g, b).P : 0u;
   reg = active && (w.flags[b] & 1);
+  // what the checks after the encoding compare and copy, loaded now (in flight meanwhile)
+  const unsigned long long sq_ref = (ABFT && active) ? w.sum_q[b] : 0ull;
+  const unsigned long long isq_ref = (ABFT && active) ? w.isum_q[b] : 0ull;
+  const unsigned long long sdc_ref = (ABFT && active) ? w.sum_dc[b] : 0ull;
   const uint32_t* pp = reinterpret_cast<const uint32_t*>(w.codes) + pair_index(b, g.P, 0);
   uint32_t* slot = w.etmp + (active ? b : 0) * slot_words_of(g);
   Extra<T> ex = {nullptr, 0, nullptr, kNoTrunc};
@@ -365,9 +369,9 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
   if (active) {
     uint32_t kfix = 0xffffffffu, vfix = 0;
     bool bad = false;
-    if (ABFT && (e.sq != w.sum_q[b] || e.isq != w.isum_q[b])) {
+    if (ABFT && (e.sq != sq_ref || e.isq != isq_ref)) {
       long long delta = 0;
-      const long long m = locate_word(w.sum_q[b], w.isum_q[b], e.sq, e.isq, P, 0, &delta);
+      const long long m = locate_word(sq_ref, isq_ref, e.sq, e.isq, P, 0, &delta);
       bool fixed = false;
       if (m >= 0) {
         const uint32_t old = (pp[32 * (uint64_t)(m >> 1)] >> (16 * (m & 1))) & 0xffffu;
@@ -411,7 +415,7 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
     *reinterpret_cast<uint16_t*>(out + L.sizes + 2 * fb) = (uint16_t)nbytes;
     *reinterpret_cast<uint16_t*>(out + L.ucounts + 2 * fb) = (uint16_t)e.nun;
     nun_enc = e.nun;
-    if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * fb) = w.sum_dc[b];
+    if (ABFT) *reinterpret_cast<unsigned long long*>(out + L.sumdc + 8 * fb) = sdc_ref;
     // a block whose codes could not be repaired is reported in the header status word (by the
     // header's writer, from every shard's count, in a sharded field)
     if (bad && !sh.on) atomicOr(reinterpret_cast<unsigned int*>(out + 112), 1u);
