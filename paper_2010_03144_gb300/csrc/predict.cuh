@@ -923,6 +923,8 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
       for (int i = 1; i < B0; ++i) prefetch_l2(blk + (uint64_t)i * si + (uint64_t)(i % B1) * sj);
     }
   }
+  // the input checksums the walk is checked against at the end, loaded now (in flight meanwhile)
+  const unsigned long long sin_ref = ABFT ? w.sum_in[b] : 0ull, isin_ref = ABFT ? w.isum_in[b] : 0ull;
   CoefSel cq = coef_select<T, NDIM>(g, w, b);
   auto ereg = [&](float4 c4, uint32_t kf, T xf) {
     if (EDGE) return ereg_generic<T, NDIM>(field, g, x, c4, kf, xf);
@@ -950,11 +952,11 @@ __device__ __forceinline__ void predict_fast_block(const T* __restrict__ field, 
     r.dup = r.dup ? r.dup : 1u;
   }
   uint8_t flag = 0;
-  if (ABFT && (r.sw != w.sum_in[b] || r.isw != w.isum_in[b])) {
+  if (ABFT && (r.sw != sin_ref || r.isw != isin_ref)) {
     if (!EDGE) x = block_box(g, b);
     uint32_t kf;
     T xf;
-    if (locate_input<T>(field, g, x, w.sum_in[b], w.isum_in[b], r, &kf, &xf)) {
+    if (locate_input<T>(field, g, x, sin_ref, isin_ref, r, &kf, &xf)) {
       withdraw(w, g, b, Pb, h);
       hk.kfix = kf;
       const CoefSel cq2 = coef_select<T, NDIM>(g, w, b);
