@@ -47,14 +47,14 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 556481346, "src": "8d24e918a655"},
-    ("384cube", "prep"): {"bytes": 234765568, "src": "8d24e918a655"},
-    ("512cube", "predict"): {"bytes": 953910462, "src": "2e19572e7bf6"},
-    ("384cube", "predict"): {"bytes": 402430976, "src": "2e19572e7bf6"},
-    ("512cube", "encode"): {"bytes": 479629464, "src": "91c2596f6924"},
-    ("384cube", "encode"): {"bytes": 202343680, "src": "91c2596f6924"},
-    ("512cube", "decode"): {"bytes": 454495194, "src": "9ab384c1a550"},
-    ("384cube", "decode"): {"bytes": 191740160, "src": "9ab384c1a550"},
+    ("512cube", "prep"): {"bytes": 556590573, "src": "8d24e918a655"},
+    ("384cube", "prep"): {"bytes": 234811648, "src": "8d24e918a655"},
+    ("512cube", "predict"): {"bytes": 977377204, "src": "176528aa19d7"},
+    ("384cube", "predict"): {"bytes": 412331008, "src": "176528aa19d7"},
+    ("512cube", "encode"): {"bytes": 473634740, "src": "23623feef194"},
+    ("384cube", "encode"): {"bytes": 199814656, "src": "23623feef194"},
+    ("512cube", "decode"): {"bytes": 454629907, "src": "9ab384c1a550"},
+    ("384cube", "decode"): {"bytes": 191796992, "src": "9ab384c1a550"},
 }
 
 
