@@ -184,6 +184,29 @@ int sdcsz_decompress_traced(const void* d_stream, size_t nbytes, void* d_field, 
                             float* stage_ms);
 
 /*
+ * Deferred stage timing, for timing many calls without a host wait in each. Between
+ * sdcsz_trace_begin and sdcsz_trace_end, every sdcsz_compress, sdcsz_decompress and
+ * sdcsz_verify call (from any host thread) records CUDA events between its stages on its own
+ * stream (the stages of the profiling variants above) and returns as it would untimed; the
+ * events are created by sdcsz_trace_begin, so the calls create none.
+ *  - sdcsz_trace_begin(max_calls): opens the recorder for up to max_calls calls (1 to 2^20;
+ *    6 CUDA events each, on the current device). SDCSZ_EINVAL when max_calls is out of range
+ *    or a recorder is already open; SDCSZ_ECUDA when the events cannot be created.
+ *  - sdcsz_trace_end(kinds, stage_ms, cap_calls, n_calls): waits for the recorded events,
+ *    writes per call, in call order, its kind to kinds[c] (host; 0 compress, 1 decompress,
+ *    2 verify) and its stage milliseconds to stage_ms[5c .. 5c+4] (host; compression: reset,
+ *    K1, K2, K3, K4; decompression and verification: K5 in the first, zeros after), and the
+ *    number of calls to *n_calls (nullable); then closes the recorder and frees its events.
+ *    Calls that returned an error before their last stage are left out. SDCSZ_EINVAL when no
+ *    recorder is open; SDCSZ_ECAPACITY when calls were made beyond max_calls (those are not
+ *    timed) or more calls were timed than cap_calls (the first cap_calls are written);
+ *    SDCSZ_ECUDA when an event cannot be read. Call it after every call made while the
+ *    recorder was open has returned.
+ */
+int sdcsz_trace_begin(size_t max_calls);
+int sdcsz_trace_end(int32_t* kinds, float* stage_ms, size_t cap_calls, size_t* n_calls);
+
+/*
  * Allocation-free compression. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory when they compress: callbacks and
  * latency-critical serving loops that must not enter an allocator (a cudaMalloc can

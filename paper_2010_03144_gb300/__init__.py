@@ -26,7 +26,7 @@ BLOCK_OK, BLOCK_CORRECTED, BLOCK_SDC, BLOCK_BAD = 0, 1, 2, 3
 EXPORTS = ("sdcsz_compress_bound", "sdcsz_workspace_size", "sdcsz_decompress_workspace_size", "sdcsz_compress",
            "sdcsz_decompress", "sdcsz_verify", "sdcsz_read_header", "sdcsz_strerror",
            "sdcsz_debug_compress_flips", "sdcsz_debug_decompress_flips", "sdcsz_compress_traced",
-           "sdcsz_decompress_traced", "sdcsz_compress_noalloc", "sdcsz_kernel_launches", "sdcsz_batch_create",
+           "sdcsz_decompress_traced", "sdcsz_trace_begin", "sdcsz_trace_end", "sdcsz_compress_noalloc", "sdcsz_kernel_launches", "sdcsz_batch_create",
            "sdcsz_batch_workspace_size", "sdcsz_batch_bind", "sdcsz_batch_set_fields", "sdcsz_batch_compress",
            "sdcsz_batch_capture", "sdcsz_batch_launch", "sdcsz_batch_results", "sdcsz_batch_destroy",
            "sdcsz_autotune_block", "sdcsz_server_create", "sdcsz_server_submit", "sdcsz_server_poll",
@@ -178,6 +178,10 @@ def lib():
         L.sdcsz_decompress_region.restype = i32
         L.sdcsz_decompress_workspace_size_for.argtypes = [vp, sz, ctypes.POINTER(sz)]
         L.sdcsz_decompress_workspace_size_for.restype = i32
+        L.sdcsz_trace_begin.argtypes = [sz]
+        L.sdcsz_trace_begin.restype = i32
+        L.sdcsz_trace_end.argtypes = [ctypes.POINTER(ctypes.c_int32), fp, sz, ctypes.POINTER(sz)]
+        L.sdcsz_trace_end.restype = i32
         L.sdcsz_kernel_launches.argtypes = []
         L.sdcsz_kernel_launches.restype = ctypes.c_ulonglong
         u64, u64a = ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)
@@ -409,9 +413,14 @@ def read_header_partial(header_bytes: np.ndarray, nbytes: int):
 
 def decompress(stream, out=None, status=None, flips=None, ws=None, cuda_stream=None, report=True):
     """Decompress a uint8 CUDA tensor holding a stream. Returns (rc, field, block status, report dict).
-    rc is 0 or ESDC (blocks that failed twice are named in the status); other errors raise."""
+    rc is 0 or ESDC (blocks that failed twice are named in the status); other errors raise.
+    When out, status and ws are all given (status holding a byte per block), the binding reads
+    nothing from the device itself and returns status whole."""
     import torch
-    h, nb, dt = _geometry(stream)
+    if out is not None and status is not None and ws is not None:
+        nb, dt = status.numel(), out.dtype
+    else:
+        h, nb, dt = _geometry(stream)
     field = out if out is not None else torch.empty(h["shape"], dtype=dt, device=stream.device)
     st = status if status is not None else torch.empty(max(nb, 1), dtype=torch.uint8, device=stream.device)
     w = ws if ws is not None else torch.empty(decompress_workspace_size(stream), dtype=torch.uint8, device=stream.device)
@@ -501,6 +510,28 @@ def decompress_traced(stream_t, out, ws, stream=None):
     if rc not in (OK,):
         raise SdcszError(rc, "decompress_traced")
     return ms[0]
+
+
+def trace_begin(max_calls: int):
+    """Open the deferred stage recorder: the next compress/decompress/verify calls (up to
+    max_calls) record stage events without a host wait."""
+    rc = lib().sdcsz_trace_begin(int(max_calls))
+    if rc:
+        raise SdcszError(rc, "trace_begin")
+
+
+def trace_end(max_calls: int):
+    """Wait for the recorded events and close the recorder. Returns a list of
+    (kind, stage milliseconds) per call, kind "compress" (reset, K1, K2, K3, K4),
+    "decompress" or "verify" (K5)."""
+    kinds = (ctypes.c_int32 * max(1, max_calls))()
+    ms = (ctypes.c_float * (5 * max(1, max_calls)))()
+    n = ctypes.c_size_t()
+    rc = lib().sdcsz_trace_end(kinds, ms, int(max_calls), ctypes.byref(n))
+    if rc:
+        raise SdcszError(rc, "trace_end")
+    names = ("compress", "decompress", "verify")
+    return [(names[kinds[c]], [ms[5 * c + q] for q in range(5)]) for c in range(n.value)]
 
 
 def compress_noalloc(field, out, eb, eb_mode="rel", block=None, bins=65536, abft=True, predictor="auto",

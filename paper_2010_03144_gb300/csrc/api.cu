@@ -259,33 +259,76 @@ void fill_report(const State& h, uint64_t nb, sdcsz_report* r) {
   r->max_abs_err = me;
 }
 
-// Optional stage timing: CUDA events recorded on the caller's stream between the kernels.
+// Deferred stage timing: while a recorder is open, every compression, decompression and
+// verification records CUDA events between its stages on its own stream, in events created
+// when the recorder opened, and returns without waiting for them; sdcsz_trace_end waits once
+// and converts them to milliseconds.
+constexpr int kTraceEvents = 6;  // one before the first stage and one after each of up to 5
+struct Recorder {
+  std::mutex mu;
+  bool open = false;
+  std::vector<cudaEvent_t> ev;  // cap * kTraceEvents
+  std::vector<int32_t> kind;    // per call: 0 compress, 1 decompress, 2 verify
+  std::vector<int32_t> marks;   // per call: events recorded when the call finished (0: unfinished)
+  size_t cap = 0, used = 0, dropped = 0;
+};
+Recorder& recorder() {
+  static Recorder r;
+  return r;
+}
+
+// Stage timing of one call: synchronous (stage_ms given) or into the open recorder.
 struct Trace {
   float* ms;
   int n;
   cudaEvent_t ev[8];
+  cudaEvent_t* e = nullptr;
   int used = 0;
+  long slot = -1;
   cudaStream_t s = nullptr;
-  bool on() const { return ms != nullptr; }
-  void start(cudaStream_t st) {
-    if (!on()) return;
+  bool on() const { return e != nullptr; }
+  void start(cudaStream_t st, int kind) {
     s = st;
-    for (int q = 0; q <= n && q < 8; ++q) cudaEventCreate(&ev[q]);
-    cudaEventRecord(ev[0], s);
+    used = 0;
+    if (ms) {
+      for (int q = 0; q <= n && q < 8; ++q) cudaEventCreate(&ev[q]);
+      e = ev;
+    } else {
+      Recorder& r = recorder();
+      std::lock_guard<std::mutex> lk(r.mu);
+      if (!r.open) return;
+      if (r.used == r.cap) {
+        ++r.dropped;
+        return;
+      }
+      slot = (long)r.used++;
+      r.kind[slot] = kind;
+      r.marks[slot] = 0;
+      e = &r.ev[(size_t)slot * kTraceEvents];
+    }
+    cudaEventRecord(e[0], s);
     used = 1;
   }
   void mark() {
     if (!on() || used > n) return;
-    cudaEventRecord(ev[used], s);
+    cudaEventRecord(e[used], s);
     ++used;
   }
   void finish() {
     if (!on()) return;
+    if (!ms) {
+      Recorder& r = recorder();
+      std::lock_guard<std::mutex> lk(r.mu);
+      r.marks[slot] = used;
+      e = nullptr;
+      return;
+    }
     cudaEventSynchronize(ev[used - 1]);
     for (int q = 0; q < n; ++q) ms[q] = 0.0f;
     for (int q = 1; q < used; ++q) cudaEventElapsedTime(&ms[q - 1], ev[q - 1], ev[q]);
-    for (int q = 0; q < used; ++q) cudaEventDestroy(ev[q]);
+    for (int q = 0; q <= n && q < 8; ++q) cudaEventDestroy(ev[q]);
     used = 0;
+    e = nullptr;
   }
 };
 
@@ -314,7 +357,7 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
   tr.ms = stage_ms;
   tr.n = 5;
   cudaGetLastError();
-  tr.start(L.stream);
+  tr.start(L.stream, 0);
   if (cudaMemsetAsync(w.st, 0, sizeof(State), L.stream) != cudaSuccess) return SDCSZ_ECUDA;
   if (cudaMemsetAsync(w.hist, 0, 8 * (size_t)g.bins, L.stream) != cudaSuccess) return SDCSZ_ECUDA;
   const size_t ngroups = (g.nb + kGroup - 1) / kGroup;
@@ -488,7 +531,7 @@ int decompress_impl(const void* d_stream, size_t nbytes, void* d_field, size_t f
   Trace tr;
   tr.ms = stage_ms;
   tr.n = 1;
-  tr.start(s);
+  tr.start(s, write ? 1 : 2);
   {
     NvtxRange r(write ? "sdcsz decode" : "sdcsz verify");
     rc = decode_enqueue(d_stream, nbytes, h, d_field, field_bytes, status, d_orig, write, st, s, flips, n_flips, raw,
@@ -599,6 +642,55 @@ int sdcsz_decompress_traced(const void* d_stream, size_t nbytes, void* d_field, 
   if (!stage_ms) return SDCSZ_EINVAL;
   return decompress_impl(d_stream, nbytes, d_field, field_bytes, d_block_status, nullptr, true, d_ws, ws_bytes,
                          report, stream, nullptr, 0, stage_ms);
+}
+
+int sdcsz_trace_begin(size_t max_calls) {
+  if (max_calls == 0 || max_calls > (1u << 20)) return SDCSZ_EINVAL;
+  Recorder& r = recorder();
+  std::lock_guard<std::mutex> lk(r.mu);
+  if (r.open) return SDCSZ_EINVAL;
+  r.ev.assign(max_calls * kTraceEvents, nullptr);
+  for (size_t q = 0; q < r.ev.size(); ++q)
+    if (cudaEventCreate(&r.ev[q]) != cudaSuccess) {
+      for (size_t k = 0; k < q; ++k) cudaEventDestroy(r.ev[k]);
+      r.ev.clear();
+      return SDCSZ_ECUDA;
+    }
+  r.kind.assign(max_calls, 0);
+  r.marks.assign(max_calls, 0);
+  r.cap = max_calls;
+  r.used = 0;
+  r.dropped = 0;
+  r.open = true;
+  return SDCSZ_OK;
+}
+
+int sdcsz_trace_end(int32_t* kinds, float* stage_ms, size_t cap_calls, size_t* n_calls) {
+  Recorder& r = recorder();
+  std::lock_guard<std::mutex> lk(r.mu);
+  if (!r.open) return SDCSZ_EINVAL;
+  int rc = SDCSZ_OK;
+  size_t n = 0;
+  for (size_t c = 0; c < r.used; ++c) {
+    const int m = r.marks[c];
+    if (m < 2) continue;  // a call that returned an error before its last stage
+    if (n < cap_calls && kinds && stage_ms) {
+      cudaEvent_t* e = &r.ev[c * kTraceEvents];
+      if (cudaEventSynchronize(e[m - 1]) != cudaSuccess) rc = SDCSZ_ECUDA;
+      float* o = stage_ms + n * (kTraceEvents - 1);
+      for (int q = 0; q < kTraceEvents - 1; ++q) o[q] = 0.0f;
+      for (int q = 1; q < m && rc == SDCSZ_OK; ++q)
+        if (cudaEventElapsedTime(&o[q - 1], e[q - 1], e[q]) != cudaSuccess) rc = SDCSZ_ECUDA;
+      kinds[n] = r.kind[c];
+    }
+    ++n;
+  }
+  for (cudaEvent_t ev : r.ev) cudaEventDestroy(ev);
+  r.ev.clear();
+  r.open = false;
+  if (n_calls) *n_calls = n;
+  if (rc == SDCSZ_OK && (r.dropped || n > cap_calls || ((!kinds || !stage_ms) && n))) rc = SDCSZ_ECAPACITY;
+  return rc;
 }
 
 int sdcsz_read_header(const void* h_stream, size_t nbytes, sdcsz_params* out, uint64_t* total_bytes) {

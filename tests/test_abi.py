@@ -78,3 +78,14 @@ def test_library_parses_oracle_headers(sz, orc):
 def test_strerror(sz):
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert sz.strerror(code) and sz.strerror(code) != "unknown error"
+
+
+def test_trace_recorder_argument_checks(sz):
+    """The deferred stage recorder rejects a zero or oversized capacity and an end without a
+    begin before it touches the device."""
+    L = sz.lib()
+    assert L.sdcsz_trace_begin(0) == sz.EINVAL
+    assert L.sdcsz_trace_begin((1 << 20) + 1) == sz.EINVAL
+    n = ctypes.c_size_t(7)
+    assert L.sdcsz_trace_end(None, None, 0, ctypes.byref(n)) == sz.EINVAL
+    assert n.value == 7
