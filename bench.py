@@ -47,14 +47,14 @@ REL_EB = 1e-3
 # time (a changed kernel reports null). The captures ran on the 384cube workload; the 512cube
 # entries scale them by the point count (traffic grows in proportion to the blocks processed).
 NCU_TRAFFIC = {
-    ("512cube", "prep"): {"bytes": 556590573, "src": "8d24e918a655"},
-    ("384cube", "prep"): {"bytes": 234811648, "src": "8d24e918a655"},
-    ("512cube", "predict"): {"bytes": 977377204, "src": "176528aa19d7"},
-    ("384cube", "predict"): {"bytes": 412331008, "src": "176528aa19d7"},
-    ("512cube", "encode"): {"bytes": 473634740, "src": "23623feef194"},
-    ("384cube", "encode"): {"bytes": 199814656, "src": "23623feef194"},
-    ("512cube", "decode"): {"bytes": 454629907, "src": "9ab384c1a550"},
-    ("384cube", "decode"): {"bytes": 191796992, "src": "9ab384c1a550"},
+    ("512cube", "prep"): {"bytes": 553422999, "src": "9b0950b480de"},
+    ("384cube", "prep"): {"bytes": 233475328, "src": "9b0950b480de"},
+    ("512cube", "predict"): {"bytes": 966222734, "src": "377596b23cb1"},
+    ("384cube", "predict"): {"bytes": 407625216, "src": "377596b23cb1"},
+    ("512cube", "encode"): {"bytes": 465609007, "src": "1840fbc5c98b"},
+    ("384cube", "encode"): {"bytes": 196428800, "src": "1840fbc5c98b"},
+    ("512cube", "decode"): {"bytes": 448822689, "src": "244969bf7694"},
+    ("384cube", "decode"): {"bytes": 189347072, "src": "244969bf7694"},
 }
 
 

@@ -150,7 +150,10 @@ WsPlan plan_ws(const Geo& g) {
   const size_t ngroups = (nb + kGroup - 1) / kGroup;
   const size_t slots = ((nb + 31) / 32) * 32 * (size_t)g.P;
   const size_t pair_slots = ((nb + 31) / 32) * 32 * (size_t)pairs_of(g.P);
+  // the State, the histogram and the group totals first, next to each other: one reset clears them
   w.state = take(sizeof(State));
+  w.hist = take(8 * 65536);
+  w.gt = take(8 * std::max<size_t>(group_total_words(ngroups), 1));
   w.sum_in = take(8 * nb);
   w.isum_in = take(8 * nb);
   w.sum_q = take(8 * nb);
@@ -161,9 +164,7 @@ WsPlan plan_ws(const Geo& g) {
   w.pflag = take(nb);
   w.flags = take(nb);
   w.coefT = take(4 * s * nb);
-  w.hist = take(8 * 65536);
   w.codebook = take(4 * 65536);
-  w.gt = take(8 * std::max<size_t>(group_total_words(ngroups), 1));
   w.sort_keys = take(8 * 65536);
   w.node_w = take(8 * 65536);
   w.node_parent = take(4 * 2 * 65536 + 2 * 65536);
@@ -358,10 +359,12 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
   tr.n = 5;
   cudaGetLastError();
   tr.start(L.stream, 0);
-  if (cudaMemsetAsync(w.st, 0, sizeof(State), L.stream) != cudaSuccess) return SDCSZ_ECUDA;
-  if (cudaMemsetAsync(w.hist, 0, 8 * (size_t)g.bins, L.stream) != cudaSuccess) return SDCSZ_ECUDA;
-  const size_t ngroups = (g.nb + kGroup - 1) / kGroup;
-  if (ngroups && cudaMemsetAsync(w.gt, 0, 8 * group_total_words(ngroups), L.stream) != cudaSuccess) return SDCSZ_ECUDA;
+  {  // State, histogram and group totals, adjacent in the workspace (plan_ws)
+    const size_t ngroups = (g.nb + kGroup - 1) / kGroup;
+    const uint8_t* end = reinterpret_cast<const uint8_t*>(w.gt) + 8 * group_total_words(ngroups);
+    if (cudaMemsetAsync(w.st, 0, (size_t)(end - reinterpret_cast<const uint8_t*>(w.st)), L.stream) != cudaSuccess)
+      return SDCSZ_ECUDA;
+  }
   tr.mark();
   {
     NvtxRange r("sdcsz prep (range, checksums, regression, estimates)");
@@ -382,7 +385,7 @@ int compress_impl(const void* d_field, const sdcsz_params* p, void* d_out, size_
   tr.mark();
   {
     NvtxRange r("sdcsz encode");
-    launch_encode(g, w, kout, kcap, L);
+    launch_encode(d_field, g, w, kout, kcap, L);
   }
   if (g.lossless) {
     NvtxRange r("sdcsz lossless stage");

@@ -330,10 +330,12 @@ __host__ __device__ inline uint64_t slot_words_of(const Geo& g) {
 }
 
 // ---------------------------------------------------------------- K4a
+// field (nullable): the input, for the values of points whose codes an uncorrectable corruption
+// turned into code 0 (K2 staged values only for the points it found unpredictable).
 template <typename T, bool ABFT, bool CMP>
 __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t* __restrict__ out,
                                              const uint32_t* cb_s, uint64_t b, uint32_t* ring,
-                                             const Shard& sh = Shard{}) {
+                                             const Shard& sh = Shard{}, const T* __restrict__ field = nullptr) {
   State* st = w.st;
   const Layout L = st->L;
   const uint32_t lane = threadIdx.x & 31;
@@ -388,6 +390,19 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
       } else {
         bad = true;
         atomicAdd(&st->uncorrectable, 1ull);
+        if (field) {  // every point the corrupted codes call unpredictable takes its input value
+          const Box x = block_box(g, b);
+          T* up = static_cast<T*>(w.ustage) + code_index(b, g.P, 0);
+          for (uint32_t k = 0; k < P; ++k) {
+            const uint32_t c = (pp[32 * (uint64_t)(k >> 1)] >> (16 * (k & 1))) & 0xffffu;
+            if (c == 0) {
+              const uint32_t l = k % x.e[2], q = k / x.e[2];
+              up[32 * (uint64_t)k] = field[row_base(g, x, q / x.e[1], q % x.e[1]) + l];
+            }
+          }
+          if (CMP)  // the compact payload carries the values: encoded again with them
+            e = encode_codes<ABFT, false, CMP, T>(pp, P, slot, cb, cw0, g.R, 0u, 0u, ex, pairs_of(g.P));
+        }
       }
     }
     // unpredictable values to the front of the block's staging slot, in order (in place: the
@@ -445,13 +460,15 @@ __device__ __forceinline__ void encode_block(const Geo& g, const Ws& w, uint8_t*
 }
 
 template <typename T, bool ABFT, bool CMP>
-__global__ void __launch_bounds__(128) k_encode_blocks(Geo g, Ws w, uint8_t* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_encode_blocks(const T* __restrict__ field, Geo g, Ws w,
+                                                       uint8_t* __restrict__ out) {
   __shared__ uint32_t cb_s[kCbWindow];
   __shared__ __align__(16) uint32_t ring_s[kRing * 8 * kRingStride];
   if (cta_failed(w.st)) return;
   cb_load(cb_s, g, w);
   __syncthreads();
-  encode_block<T, ABFT, CMP>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, ring_s + threadIdx.x);
+  encode_block<T, ABFT, CMP>(g, w, out, cb_s, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, ring_s + threadIdx.x,
+                             Shard{}, field);
 }
 
 // ---------------------------------------------------------------- K4b
@@ -667,7 +684,7 @@ __global__ void __launch_bounds__(256, 3) k_encode_assemble_shard(Geo g, Ws w, u
 
 // ---------------------------------------------------------------- batches
 template <typename T, bool ABFT>
-__global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
+__global__ void __launch_bounds__(128, ABFT ? 4 : 6) k_encode_blocks_batch(BatchArgs a) {
   __shared__ uint32_t cb_s[kCbWindow];
   __shared__ __align__(16) uint32_t ring_s[kRing * 8 * kRingStride];
   __shared__ Job s_job;
@@ -680,10 +697,10 @@ __global__ void __launch_bounds__(128) k_encode_blocks_batch(BatchArgs a) {
       [&](uint64_t it) {
         if (s_job.g.enc)
           encode_block<T, ABFT, true>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x,
-                                      ring_s + threadIdx.x);
+                                      ring_s + threadIdx.x, Shard{}, static_cast<const T*>(s_job.field));
         else
           encode_block<T, ABFT, false>(s_job.g, s_job.w, s_job.out, cb_s, it * blockDim.x + threadIdx.x,
-                                       ring_s + threadIdx.x);
+                                       ring_s + threadIdx.x, Shard{}, static_cast<const T*>(s_job.field));
       },
       NoOp());
 }
@@ -716,11 +733,12 @@ void batch_assemble_t(const BatchArgs& a, const Launch& L) {
 }
 
 template <typename T, bool ABFT>
-void launch_encode_t(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
+void launch_encode_t(const void* field, const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
   const uint64_t nchunks = (g.nb + 127) / 128, ngroups = (g.nb + kGroup - 1) / kGroup;
   if (!ngroups) return;
-  if (g.enc) k_encode_blocks<T, ABFT, true><<<(unsigned)nchunks, 128, 0, L.stream>>>(g, w, out);
-  else k_encode_blocks<T, ABFT, false><<<(unsigned)nchunks, 128, 0, L.stream>>>(g, w, out);
+  const T* f = static_cast<const T*>(field);
+  if (g.enc) k_encode_blocks<T, ABFT, true><<<(unsigned)nchunks, 128, 0, L.stream>>>(f, g, w, out);
+  else k_encode_blocks<T, ABFT, false><<<(unsigned)nchunks, 128, 0, L.stream>>>(f, g, w, out);
   note_launch();
   k_encode_assemble<T><<<(unsigned)ngroups, 256, 0, L.stream>>>(g, w, out, cap);
   note_launch();
@@ -781,13 +799,13 @@ void launch_encode_shard_assemble(const Geo& g, const Ws& w, uint8_t* out, uint6
   note_launch();
 }
 
-void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
+void launch_encode(const void* field, const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L) {
   if (g.dtype == 0) {
-    if (g.abft) launch_encode_t<float, true>(g, w, out, cap, L);
-    else launch_encode_t<float, false>(g, w, out, cap, L);
+    if (g.abft) launch_encode_t<float, true>(field, g, w, out, cap, L);
+    else launch_encode_t<float, false>(field, g, w, out, cap, L);
   } else {
-    if (g.abft) launch_encode_t<double, true>(g, w, out, cap, L);
-    else launch_encode_t<double, false>(g, w, out, cap, L);
+    if (g.abft) launch_encode_t<double, true>(field, g, w, out, cap, L);
+    else launch_encode_t<double, false>(field, g, w, out, cap, L);
   }
 }
 

@@ -643,7 +643,7 @@ void launch_flip_input(void* field, const Geo& g, const sdcsz_flip* flips, uint3
                        const Launch& L);
 void launch_flip_codes(const Geo& g, const Ws& w, const sdcsz_flip* flips, uint32_t nflips, const Launch& L);
 void launch_codebook(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
-void launch_encode(const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
+void launch_encode(const void* field, const Geo& g, const Ws& w, uint8_t* out, uint64_t cap, const Launch& L);
 
 // A slab of a field compressed as one shard of the field's stream (sharded compression over
 // several GPUs). The slab is a field of its own to every kernel up to the encoder; the encoder

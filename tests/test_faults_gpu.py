@@ -64,6 +64,45 @@ def test_code_flips_corrected(sz, orc):
     assert rep_gpu["codes_corrected"] == 10
 
 
+@pytest.mark.parametrize("dt,encoding", [(np.float32, "raw"), (np.float64, "raw"), (np.float32, "compact")])
+def test_uncorrectable_codes_change_the_unpredictable_count(sz, orc, dt, encoding):
+    """Two flips in one block's bin array cannot be located (Sec. 4.2.3): the block is encoded
+    as corrupted and reported. Flipping bit 15 of two central codes (R = 32768) turns them into
+    code 0, so the field has two more unpredictable points as encoded than prediction counted,
+    and the unpredictable section, the payload offsets and the header totals move. The stream
+    equals the oracle's except the two values that the corrupted codes now call unpredictable
+    (the oracle takes the input there; the GPU path has no value staged for a point that was
+    predictable), which lie in the unpredictable section (raw encoding) or in the block's
+    payload (compact encoding, where only the payload of that block may differ)."""
+    shape = (40, 42, 44)
+    x = synth.sinusoid_field(shape, 15, dtype=dt, spikes=0.01)
+    eb = orc.error_bound(x, 1e-3)
+    b = 100
+    codes = np.asarray(orc.compress_block(x, eb, b)["codes"])
+    central = np.nonzero(codes == 32768)[0]
+    assert central.size >= 2
+    flips = [("code", b, int(central[0]), 15), ("code", b, int(central[-1]), 15)]
+    s_gpu, rep_gpu, s_ref, rep_ref, _ = compress_both(sz, orc, x, 1e-3, flips=flips, encoding=encoding)
+    for k in ("blocks", "regression_blocks", "unpredictable_points", "compressed_bytes", "codes_corrected",
+              "uncorrectable_blocks"):
+        assert rep_gpu[k] == rep_ref[k], (k, rep_gpu[k], rep_ref[k])
+    assert rep_gpu["uncorrectable_blocks"] == 1
+    _, rep0 = orc.compress(x, 1e-3, encoding=encoding)
+    assert rep_gpu["unpredictable_points"] == rep0["unpredictable_points"] + 2
+    g = s_gpu.cpu().numpy()
+    assert g.size == s_ref.size
+    diff = np.nonzero(g != s_ref)[0]
+    hdr = s_ref[:128].view(np.uint64)
+    n_un, pay, total = int(hdr[11]), int(hdr[12]), int(hdr[13])
+    assert total == s_ref.size and n_un == rep_ref["unpredictable_points"]
+    w = np.dtype(dt).itemsize
+    if encoding == "raw":
+        lo, hi = total - pay - w * n_un - 16, total - pay
+        assert diff.size <= 2 * w and np.all((diff >= lo) & (diff < hi)), diff[:16]
+    else:
+        assert np.all(diff >= total - pay), diff[:16]
+
+
 def test_config1_ten_mixed_flips(sz, orc):
     """The small config: one clean run plus one with 10 seeded single-bit flips in the input,
     the quantization codes and the regression coefficients."""
