@@ -911,7 +911,7 @@ def run_region(args):
 # path, from an ncu capture (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum
 # over every launch of the stage / points), keyed by the hash of the stage's sources.
 NCU_FP64_PER_POINT = {
-    "predict": {"per_point": 10.751, "src": "71e0c011fcda"},
+    "predict": {"per_point": 10.751, "src": "0d23c2e2396a"},
     "decode": {"per_point": 3.46, "src": "a3f40169af02"},
 }
 
