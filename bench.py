@@ -912,7 +912,7 @@ def run_region(args):
 # over every launch of the stage / points), keyed by the hash of the stage's sources.
 NCU_FP64_PER_POINT = {
     "predict": {"per_point": 10.751, "src": "0d23c2e2396a"},
-    "decode": {"per_point": 3.46, "src": "a3f40169af02"},
+    "decode": {"per_point": 3.46, "src": "9a4285c83e39"},
 }
 
 
