@@ -441,6 +441,33 @@ def test_transient_prediction_and_reconstruction_errors(orc):
     assert np.array_equal(s, clean) and rep["dup_mismatch_corrected"] == 4
 
 
+def test_uncorrectable_codes_carry_input_values(orc):
+    """Two flipped codes in one block cannot be located (Sec. 4.2.3), so the block is encoded as
+    it is and reported. Flipping bit 15 of two central codes (R = 32768) makes them code 0: those
+    points become unpredictable as encoded and carry their input values (the value an
+    unpredictable point always carries). The header reports the block, the count of
+    unpredictable points grows by two, and decompression gives those two points back exactly.
+    (A NaN elsewhere puts code 0 in the code table; without it code 0 would have no codeword
+    and the block would not decode at all.)"""
+    x = synth.sinusoid_field((20, 22, 24), 7)
+    x[19, 21, 23] = np.nan
+    eb = orc.error_bound(x, 1e-2)
+    codes = np.asarray(orc.compress_block(x, eb, 0)["codes"])
+    central = np.nonzero(codes == 32768)[0]
+    assert central.size >= 2
+    k1, k2 = int(central[0]), int(central[-1])
+    _, rep0 = orc.compress(x, 1e-2)
+    s, rep = orc.compress(x, 1e-2, flips=[("code", 0, k1, 15), ("code", 0, k2, 15)])
+    assert rep["uncorrectable_blocks"] == 1 and rep["codes_corrected"] == 0
+    assert rep["unpredictable_points"] == rep0["unpredictable_points"] + 2
+    assert int(s[112:116].view(np.uint32)[0]) == 1
+    rc, y, st, _ = orc.decompress(s)
+    assert st[0] == 2  # decoded, but its sum_dc differs: reported, not corrected
+    for k in (k1, k2):  # block 0 is a full 6^3 block at the origin
+        i, j, l = k // 36, (k // 6) % 6, k % 6
+        assert y[i, j, l].view(np.uint32) == x[i, j, l].view(np.uint32)
+
+
 def test_coefficient_flip_keeps_bound_and_is_local(orc):
     """Sec. 4.1.1 / 4.2.2: a corrupted regression coefficient is used consistently by
     compression and decompression, so the bound holds; only the compression ratio may drop,
