@@ -89,3 +89,16 @@ def test_trace_recorder_argument_checks(sz):
     n = ctypes.c_size_t(7)
     assert L.sdcsz_trace_end(None, None, 0, ctypes.byref(n)) == sz.EINVAL
     assert n.value == 7
+
+
+def test_header_prefix_gives_the_stream_size(sz, orc):
+    """The end-to-end loop learns a compressed stream's size from its first 128 bytes alone
+    (read_header_partial): the total equals the stream's length, for every encoding."""
+    import synth
+    x = synth.sinusoid_field((30, 31, 32), 5, spikes=0.01)
+    for kw in (dict(), dict(encoding="compact"), dict(lossless=True)):
+        s, _ = orc.compress(x, 1e-3, **kw)
+        h = sz.read_header_partial(s[:128], 1 << 30)
+        assert h["total"] == s.size and h["shape"] == x.shape
+        with pytest.raises(sz.SdcszError):
+            sz.read_header_partial(s[:128], s.size - 1)  # a buffer shorter than the stream
