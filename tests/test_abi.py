@@ -102,3 +102,20 @@ def test_header_prefix_gives_the_stream_size(sz, orc):
         assert h["total"] == s.size and h["shape"] == x.shape
         with pytest.raises(sz.SdcszError):
             sz.read_header_partial(s[:128], s.size - 1)  # a buffer shorter than the stream
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/sdcsz.h is a C header: it compiles as C99 and as C++17 on its own, warnings on."""
+    import shutil
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text('#include "sdcsz.h"\nint main(void) { return sdcsz_decompress_workspace_size() == 0; }\n')
+    for comp, std, name in (("gcc", "-std=c99", "use.c"), ("g++", "-std=c++17", "use.cpp")):
+        exe = shutil.which(comp)
+        if exe is None:
+            pytest.skip(f"{comp} not found")
+        f = tmp_path / name
+        f.write_text(src.read_text())
+        r = subprocess.run([exe, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                            os.path.join(ROOT, "include"), str(f)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
